@@ -1,0 +1,223 @@
+"""Plain CPU FP64 oracle for the superfast Tikhonov solver (arXiv 1302.6945, l2 penalty).
+
+TEST INFRASTRUCTURE ONLY.  The test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package; the product path (``paper_1302_6945_gb300``) never does.
+It shares no code with the CUDA library.
+
+Two oracles live here:
+  * ``dense_solve`` -- the closed form of Eq. (tiksol): least squares of [T; sqrt(lam) I] x ~ [b; 0]
+    by Householder QR (numpy/LAPACK).  Ground truth for small n.
+  * the C oracle (``tikh_oracle.c``) -- the paper's algorithm step by step in FP64 (extension,
+    transformation, Algorithm 1 with paired interleaving, serial leaves with pivoting, difficult
+    points, extraction), with its own textbook DFT.
+"""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "tikh_oracle.c")
+_SO = os.path.join(_HERE, "_build", "libtikh_oracle.so")
+
+AUTO, DIRECT, FFT = 0, 1, 2
+
+
+def build(force=False):
+    """Compile the C oracle with gcc (plain -O2; no FMA contraction so x86 and Arm agree)."""
+    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= max(
+            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "tikh_oracle.h"))):
+        return _SO
+    os.makedirs(os.path.dirname(_SO), exist_ok=True)
+    tmp = _SO + ".%d.tmp" % os.getpid()
+    subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off",
+                           "-fcx-limited-range", "-o", tmp, _SRC, "-lm"])
+    os.replace(tmp, _SO)
+    return _SO
+
+
+_lib_handle = None
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("nlim", ctypes.c_int), ("m_min", ctypes.c_int), ("eps_diff", ctypes.c_double),
+                ("mode", ctypes.c_int), ("fill", ctypes.c_int), ("is_complex", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int64), ("M", ctypes.c_int64), ("k", ctypes.c_int64), ("p", ctypes.c_int),
+                ("n_difficult", ctypes.c_int64), ("n_dropped", ctypes.c_int64), ("delta", ctypes.c_int * 5),
+                ("jstar", ctypes.c_int), ("dual", ctypes.c_int)]
+
+    def as_dict(self):
+        return dict(N=self.N, M=self.M, k=self.k, p=self.p, n_difficult=self.n_difficult,
+                    n_dropped=self.n_dropped, delta=list(self.delta), jstar=self.jstar, dual=self.dual)
+
+
+def _lib():
+    global _lib_handle
+    if _lib_handle is None:
+        _lib_handle = ctypes.CDLL(build())
+    return _lib_handle
+
+
+def _c128(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.complex128))
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def opts(nlim=32, eps_diff=1e-8, mode=AUTO, m_min=0, fill=0, is_complex=1):
+    return Opts(nlim, m_min, eps_diff, mode, fill, is_complex)
+
+
+def _is_complex(*arrays):
+    return int(any(np.iscomplexobj(a) and np.any(np.imag(a) != 0) for a in arrays))
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise RuntimeError("oracle %s failed with status %d" % (what, rc))
+
+
+def plan(m, n, nlim=32, m_min=0):
+    """Algorithm 2 for the l2 case: returns (N, M, k, p)."""
+    N, M, k, p = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int()
+    o = opts(nlim=nlim, m_min=m_min)
+    _check(_lib().tikh_oracle_plan(ctypes.c_int64(m), ctypes.c_int64(n), ctypes.byref(o), ctypes.byref(N),
+                                   ctypes.byref(M), ctypes.byref(k), ctypes.byref(p)), "plan")
+    return N.value, M.value, k.value, p.value
+
+
+def fft(x, sign=+1):
+    """Unnormalised DFT X_k = sum_j x_j exp(sign 2 pi i jk/n)."""
+    a = _c128(x).copy()
+    _check(_lib().tikh_oracle_fft(ctypes.c_int64(a.size), _ptr(a), ctypes.c_int(sign)), "fft")
+    return a
+
+
+def conditions(col, row, y, lam, nlim=32, m_min=0, fill=0, is_complex=None):
+    """(F, G, tau, (N, M, k, p)) for (T^H T + lam I) x = y."""
+    if is_complex is None:
+        is_complex = _is_complex(col, row)
+    col, row, y = _c128(col), _c128(row), _c128(y)
+    m, n = col.size, row.size
+    pl = plan(m, n, nlim, m_min)
+    N = pl[0]
+    F = np.zeros((N, 5), np.complex128)
+    G = np.zeros((N, 5), np.complex128)
+    tau = (ctypes.c_int * 5)()
+    o = opts(nlim=nlim, m_min=m_min, fill=fill, is_complex=is_complex)
+    _check(_lib().tikh_oracle_conditions(ctypes.c_int64(m), ctypes.c_int64(n), _ptr(col), _ptr(row), _ptr(y),
+                                         ctypes.c_double(lam), ctypes.byref(o), _ptr(F), _ptr(G), tau),
+           "conditions")
+    return F, G, np.array(list(tau)), pl
+
+
+def leaf(sigma, r, delta, eps=1e-8, cap=None):
+    """Serial leaf construction.  Returns dict(B (25, cap), len, order, pivot, deferred, delta, r)."""
+    sigma = _c128(sigma)
+    r = _c128(r).reshape(-1, 5).copy()
+    K = sigma.size
+    cap = K + 1 if cap is None else cap
+    d = (ctypes.c_int * 5)(*[int(v) for v in delta])
+    B = np.zeros((25, cap), np.complex128)
+    ln = np.zeros(25, np.int64)
+    order = np.zeros(max(K, 1), np.int32)
+    piv = np.zeros(max(K, 1), np.int32)
+    dq = np.zeros(max(K, 1), np.int32)
+    nd = ctypes.c_int()
+    _check(_lib().tikh_oracle_leaf(ctypes.c_int(K), _ptr(sigma), _ptr(r), d, ctypes.c_double(eps),
+                                   ctypes.c_int64(cap), _ptr(B), _ptr(ln), _ptr(order), _ptr(piv), _ptr(dq),
+                                   ctypes.byref(nd)), "leaf")
+    return dict(B=B, len=ln, order=order[:K], pivot=piv[:K], deferred=dq[:nd.value], delta=np.array(list(d)), r=r)
+
+
+def solve_normal(col, row, y, lam, nlim=32, eps_diff=1e-8, mode=AUTO, m_min=0, want_basis=False, fill=0,
+                 is_complex=None):
+    """x = (T^H T + lam I)^{-1} y by the superfast algorithm.  Returns (x, stats[, B, len])."""
+    if is_complex is None:
+        is_complex = _is_complex(col, row)
+    col, row, y = _c128(col), _c128(row), _c128(y)
+    m, n = col.size, row.size
+    x = np.zeros(n, np.complex128)
+    st = Stats()
+    o = opts(nlim=nlim, eps_diff=eps_diff, mode=mode, m_min=m_min, fill=fill, is_complex=is_complex)
+    if want_basis:
+        cap = plan(m, n, nlim, m_min)[0] + 2
+        B = np.zeros((25, cap), np.complex128)
+        ln = np.zeros(25, np.int64)
+        bp, lp = _ptr(B), _ptr(ln)
+    else:
+        cap, B, ln, bp, lp = 0, None, None, None, None
+    rc = _lib().tikh_oracle_solve_normal(ctypes.c_int64(m), ctypes.c_int64(n), _ptr(col), _ptr(row), _ptr(y),
+                                         ctypes.c_double(lam), ctypes.byref(o), _ptr(x), ctypes.byref(st), bp,
+                                         ctypes.c_int64(cap), lp)
+    _check(rc, "solve_normal")
+    if want_basis:
+        return x, st.as_dict(), B, ln
+    return x, st.as_dict()
+
+
+def solve(col, row, b, lam, nlim=32, eps_diff=1e-8, mode=AUTO, m_min=0, fill=0, is_complex=None):
+    """Tikhonov solution argmin ||Tx-b||^2 + lam||x||^2.  Returns (x, stats)."""
+    if is_complex is None:
+        is_complex = _is_complex(col, row)
+    col, row, b = _c128(col), _c128(row), _c128(b)
+    m, n = col.size, row.size
+    x = np.zeros(n, np.complex128)
+    st = Stats()
+    o = opts(nlim=nlim, eps_diff=eps_diff, mode=mode, m_min=m_min, fill=fill, is_complex=is_complex)
+    _check(_lib().tikh_oracle_solve(ctypes.c_int64(m), ctypes.c_int64(n), _ptr(col), _ptr(row), _ptr(b),
+                                    ctypes.c_double(lam), ctypes.byref(o), _ptr(x), ctypes.byref(st)), "solve")
+    return x, st.as_dict()
+
+
+def apply_t(col, row, x):
+    col, row, x = _c128(col), _c128(row), _c128(x)
+    u = np.zeros(col.size, np.complex128)
+    _check(_lib().tikh_oracle_apply_t(ctypes.c_int64(col.size), ctypes.c_int64(row.size), _ptr(col), _ptr(row),
+                                      _ptr(x), _ptr(u)), "apply_t")
+    return u
+
+
+def apply_th(col, row, v):
+    col, row, v = _c128(col), _c128(row), _c128(v)
+    y = np.zeros(row.size, np.complex128)
+    _check(_lib().tikh_oracle_apply_th(ctypes.c_int64(col.size), ctypes.c_int64(row.size), _ptr(col), _ptr(row),
+                                       _ptr(v), _ptr(y)), "apply_th")
+    return y
+
+
+# ---------------------------------------------------------------------------------------------
+# The closed form (Eq. (tiksol)) written out densely.
+# ---------------------------------------------------------------------------------------------
+
+def toeplitz_dense(col, row):
+    """T[i, j] = a_{i-j}: col[d] = a_d, row[d] = a_{-d} (row[0] ignored)."""
+    col, row = _c128(col), _c128(row)
+    m, n = col.size, row.size
+    i = np.arange(m)[:, None]
+    j = np.arange(n)[None, :]
+    d = i - j
+    return np.where(d >= 0, col[np.clip(d, 0, m - 1)], row[np.clip(-d, 0, n - 1)])
+
+
+def dense_solve(col, row, b, lam):
+    """argmin ||Tx - b||^2 + lam ||x||^2 by Householder QR of [T; sqrt(lam) I]."""
+    T = toeplitz_dense(col, row)
+    m, n = T.shape
+    A = np.vstack([T, np.sqrt(lam) * np.eye(n)])
+    rhs = np.concatenate([_c128(b), np.zeros(n, np.complex128)])
+    Q, Rm = np.linalg.qr(A)
+    return np.linalg.solve(Rm, Q.conj().T @ rhs)
+
+
+def dense_solve_normal(col, row, y, lam):
+    """(T^H T + lam I)^{-1} y by a dense LAPACK solve."""
+    T = toeplitz_dense(col, row)
+    n = T.shape[1]
+    return np.linalg.solve(T.conj().T @ T + lam * np.eye(n), _c128(y))

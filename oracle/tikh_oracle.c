@@ -1,0 +1,809 @@
+/*
+ * tikh_oracle.c -- plain CPU FP64 oracle for the l2-penalised superfast Tikhonov solver of
+ * Turnes, Balcan & Romberg (arXiv 1302.6945).
+ *
+ * TEST INFRASTRUCTURE ONLY: used by the tests, the smoke check and the benchmark's CPU baseline,
+ * never by the product path.  It shares nothing with the CUDA library.
+ *
+ * Each function cites the passage it follows.  Where the paper is silent or garbled, the reading
+ * taken is stated at the point of use:
+ *  R1 pivot column = the column of minimum current tau-degree among the non-zero residual entries
+ *     (Sec. 4.3: "the column with lowest tau-degree has its degree increased"); ties: larger
+ *     |r|^2, then lower index.
+ *  R2 the extension's top-left entry is a_{-(n+k-1)} (Sec. 3.1 prints a_{-n-k}): the circulant
+ *     generator is c_T[j] = a_{j-(n+k-1)} over a periodic sequence of length N.
+ *  R3 tau for k != 1: gamma_1 has m+k-1 and gamma_2 has n+k-1 coefficients, so
+ *     tau = [n-1, m-1, m+k-2, n+k-2, 0] (Eq. (taudef) is printed for k = 1, p = 7).
+ *  R4 Algorithm 1 carries the absolute tau-degrees delta: the left child starts from delta_in,
+ *     the right child from the left child's output (Theorem 1 with tau_{kappa->K} = -delta).
+ *  R5 the k arbitrary entries (Sec. 5.2, "similar in value") are pseudo-random with the size of
+ *     the known coefficients: a = peak * u, peak = max over known d of max(|Re a_d|, |Im a_d|),
+ *     u uniform in [-1, 1) from the SplitMix64 generator (Steele, Lea, Flood 2014) used as a
+ *     counter-based hash of the entry index (real u for real data, u + i u' for complex).  Zero-like
+ *     fills (including a linear ramp between two near-zero PSF tails) lose accuracy for large k.
+ *     The T^H extension uses the same periodic sequence.  fill = 1 selects the linear ramp.
+ *  R6 Algorithm 2 for two condition sets with paired interleaving: halve M while 2M > N_lim,
+ *     then round M up to even (Sec. 5.2) and further to a 5-smooth number (FFT lengths with
+ *     factors 2, 3, 5 only; the solution does not depend on k).
+ *  R7 difficult point: the best remaining condition of a leaf has |r_pi| < eps ||r||_2; it and
+ *     the rest of the leaf are deferred and processed serially against the final basis.
+ *  R8 condition pivoting: the next condition of a leaf is the one with the largest
+ *     |r_pi|^2 / ||r||_2^2 (ties: lowest position).
+ *  R9 every basis returned by a recursion node has each column scaled by a power of two so that
+ *     its largest |Re|, |Im| coefficient lies in [0.5, 1); the solution is unchanged.
+ *  R10 entry (i,j) of a node's basis has degree <= delta_out_j - delta_in_i; a column that was
+ *     never a pivot only accumulates multiples of pivot columns, so its entries are also bounded
+ *     by (largest delta_out of a pivoted column) - delta_in_i (diagonal: >= 0).  Products are
+ *     trimmed to these bounds (what is cut is round-off).
+ *  R11 m < n is solved as x = T^H (T T^H + lam I)^{-1} b with the same algorithm on T^H, whose
+ *     right-hand-side term is b itself (Sec. 6.1 solves (G_T + G_L) x = y with y given).
+ */
+#include "tikh_oracle.h"
+
+#include <complex.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef double complex cx;
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+/* ------------------------------------------------------------------------------------------ */
+/* DFT by textbook mixed-radix decimation in time; any length (direct DFT for a large prime).  */
+/* ------------------------------------------------------------------------------------------ */
+
+static int64_t smallest_factor(int64_t n) {
+  for (int64_t f = 2; f * f <= n; ++f)
+    if (n % f == 0) return f;
+  return n;
+}
+
+/* a[0..n): in-place DFT with twiddles tw[t] = exp(sign 2 pi i t / ntop), n | ntop */
+static int fft_rec(cx* a, int64_t n, const cx* tw, int64_t ntop) {
+  if (n == 1) return 0;
+  int64_t r = smallest_factor(n), m = n / r, step = ntop / n;
+  cx* tmp = (cx*)malloc(sizeof(cx) * (size_t)n);
+  if (!tmp) return TIKH_ORACLE_ENOMEM;
+  for (int64_t t = 0; t < r; ++t)
+    for (int64_t j = 0; j < m; ++j) tmp[t * m + j] = a[j * r + t];
+  for (int64_t t = 0; t < r; ++t) {
+    int rc = fft_rec(tmp + t * m, m, tw, ntop);
+    if (rc) { free(tmp); return rc; }
+  }
+  /* a[k1 + m k2] = sum_t w_n^{t (k1 + m k2)} sub_t[k1] */
+  for (int64_t k1 = 0; k1 < m; ++k1)
+    for (int64_t k2 = 0; k2 < r; ++k2) {
+      int64_t kk = k1 + m * k2;
+      cx s = 0;
+      for (int64_t t = 0; t < r; ++t) s += tw[((t * kk) % n) * step] * tmp[t * m + k1];
+      a[kk] = s;
+    }
+  free(tmp);
+  return 0;
+}
+
+static int dft(cx* a, int64_t n, int sign) {
+  if (n <= 0) return TIKH_ORACLE_EINVAL;
+  cx* tw = (cx*)malloc(sizeof(cx) * (size_t)n);
+  if (!tw) return TIKH_ORACLE_ENOMEM;
+  for (int64_t t = 0; t < n; ++t) {
+    double ang = 2.0 * M_PI * (double)t / (double)n;
+    tw[t] = cos(ang) + (sign > 0 ? 1.0 : -1.0) * sin(ang) * I;
+  }
+  int rc = fft_rec(a, n, tw, n);
+  free(tw);
+  return rc;
+}
+
+int tikh_oracle_fft(int64_t n, double* data, int sign) { return dft((cx*)data, n, sign); }
+
+/* ------------------------------------------------------------------------------------------ */
+/* Plan: Algorithm 2 (OptExtend), reading R6.                                                  */
+/* ------------------------------------------------------------------------------------------ */
+
+static int is_5smooth(int64_t v) {
+  while (v % 2 == 0) v /= 2;
+  while (v % 3 == 0) v /= 3;
+  while (v % 5 == 0) v /= 5;
+  return v == 1;
+}
+
+int tikh_oracle_plan(int64_t m, int64_t n, const tikh_oracle_opts* opts, int64_t* N, int64_t* M, int64_t* k,
+                     int* p) {
+  if (m < 1 || n < 1 || !opts || opts->nlim < 2) return TIKH_ORACLE_EINVAL;
+  int64_t Nt = m + n - 1, Mv = Nt;
+  int pv = 0;
+  while (2 * Mv > opts->nlim) { /* two condition sets per node: s*M with s = 2 */
+    ++pv;
+    Mv = (Mv + 1) / 2;
+  }
+  if (Mv % 2) ++Mv;
+  if (Mv < opts->m_min) Mv = opts->m_min + (opts->m_min % 2);
+  while (!is_5smooth(Mv)) Mv += 2;
+  *N = Mv << pv;
+  *M = Mv;
+  *k = *N - Nt;
+  *p = pv;
+  return 0;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Toeplitz generator and the l2 interpolation conditions (Sec. 3.1, 3.3, 4.1).                */
+/* ------------------------------------------------------------------------------------------ */
+
+/* SplitMix64 output for counter value c (Steele, Lea, Flood 2014), mapped to [-1, 1) */
+static double splitmix_uniform(uint64_t c) {
+  uint64_t z = 0x5eedULL + (c + 1) * 0x9e3779b97f4a7c15ULL;
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+  z = z ^ (z >> 31);
+  return (double)(z >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+}
+
+/* periodic sequence at[d mod N] = a_d on d in [-(n-1), m-1]; k arbitrary entries filled by R5 */
+static void periodic_generator(int64_t m, int64_t n, int64_t N, int64_t k, const cx* col, const cx* row,
+                               int fill, int is_complex, cx* at) {
+  for (int64_t d = 0; d < N; ++d) at[d] = 0;
+  for (int64_t d = 0; d < m; ++d) at[d % N] = col[d];
+  for (int64_t d = 1; d < n; ++d) at[(N - d) % N] = row[d];
+  if (fill == 1) {
+    cx lo = (n > 1) ? row[n - 1] : col[0]; /* a_{-(n-1)} */
+    cx hi = col[m - 1];                    /* a_{m-1} */
+    for (int64_t i = 1; i <= k; ++i) at[(m - 1 + i) % N] = hi + (lo - hi) * ((double)i / (double)(k + 1));
+    return;
+  }
+  double peak = 0.0;
+  for (int64_t d = 0; d < m; ++d) {
+    if (fabs(creal(col[d])) > peak) peak = fabs(creal(col[d]));
+    if (fabs(cimag(col[d])) > peak) peak = fabs(cimag(col[d]));
+  }
+  for (int64_t d = 1; d < n; ++d) {
+    if (fabs(creal(row[d])) > peak) peak = fabs(creal(row[d]));
+    if (fabs(cimag(row[d])) > peak) peak = fabs(cimag(row[d]));
+  }
+  for (int64_t i = 1; i <= k; ++i) {
+    double re = peak * splitmix_uniform((uint64_t)(2 * i));
+    double im = is_complex ? peak * splitmix_uniform((uint64_t)(2 * i + 1)) : 0.0;
+    at[(m - 1 + i) % N] = re + im * I;
+  }
+}
+
+/* unit-modulus node omega^e for e taken mod N */
+static cx node(int64_t e, int64_t N) {
+  e %= N;
+  if (e < 0) e += N;
+  double ang = 2.0 * M_PI * (double)e / (double)N;
+  return cos(ang) + sin(ang) * I;
+}
+
+/* F, G per Sec. 4.1 specialised to the reduced l2 system (Eq. (ex6)), right-hand side y:
+ *   block row 1 (m+k-1 extension rows, then n rows):  lam*x + T^H sigma_1 + gamma_1 - y = 0
+ *   block row 2 (n+k-1 extension rows, then m rows): -T x + sigma_1 + gamma_2 = 0
+ * unknowns p = [x (n), sigma_1 (m), gamma_1 (m+k-1), gamma_2 (n+k-1), 1]; left-multiplying each
+ * block row by the DFT turns each partial circulant into the DFT of its generator (Eq. (circdiag)).
+ */
+static int build_conditions(int64_t m, int64_t n, int64_t N, int64_t k, const cx* col, const cx* row, const cx* y,
+                            double lam, int fill, int is_complex, cx* F, cx* G) {
+  cx* at = (cx*)malloc(sizeof(cx) * (size_t)N);
+  cx* cT = (cx*)malloc(sizeof(cx) * (size_t)N);
+  cx* cH = (cx*)malloc(sizeof(cx) * (size_t)N);
+  cx* cy = (cx*)malloc(sizeof(cx) * (size_t)N);
+  int rc = TIKH_ORACLE_ENOMEM;
+  if (!at || !cT || !cH || !cy) goto done;
+  periodic_generator(m, n, N, k, col, row, fill, is_complex, at);
+  for (int64_t j = 0; j < N; ++j) {
+    int64_t dT = ((j - (n + k - 1)) % N + N) % N; /* c_T[j]  = a_{j-(n+k-1)}         (R2) */
+    int64_t dH = ((m + k - 1 - j) % N + N) % N;   /* c_H[j]  = conj(a_{(m+k-1)-j})   (T^H) */
+    cT[j] = at[dT];
+    cH[j] = conj(at[dH]);
+    cy[j] = 0;
+  }
+  /* generator of the column of the constant unknown: -y placed after the m+k-1 extension rows */
+  for (int64_t i = 0; i < n; ++i) cy[m + k - 1 + i] = -y[i];
+  if ((rc = dft(cT, N, +1)) || (rc = dft(cH, N, +1)) || (rc = dft(cy, N, +1))) goto done;
+  for (int64_t e = 0; e < N; ++e) {
+    cx* f = F + 5 * e;
+    cx* g = G + 5 * e;
+    f[0] = lam * node(e * (m + k - 1), N); /* lam I_n below m+k-1 zero rows: generator lam e_{m+k-1} */
+    f[1] = cH[e];                          /* circulant extension of T^H */
+    f[2] = 1.0;                            /* [I_{m+k-1}; 0]: generator e_0 */
+    f[3] = 0.0;
+    f[4] = cy[e];
+    g[0] = -cT[e];                   /* -C_k(T) */
+    g[1] = node(e * (n + k - 1), N); /* [0; I_m] below n+k-1 rows: generator e_{n+k-1} */
+    g[2] = 0.0;
+    g[3] = 1.0; /* [I_{n+k-1}; 0] */
+    g[4] = 0.0;
+  }
+  rc = 0;
+done:
+  free(at); free(cT); free(cH); free(cy);
+  return rc;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Polynomial 5x5 matrices.                                                                   */
+/* ------------------------------------------------------------------------------------------ */
+
+typedef struct {
+  cx* c[25];
+  int64_t len[25]; /* number of stored coefficients; 0 = the zero polynomial */
+} pmat;
+
+static void pm_free(pmat* B) {
+  for (int e = 0; e < 25; ++e) { free(B->c[e]); B->c[e] = NULL; B->len[e] = 0; }
+}
+
+static int pm_identity(pmat* B) {
+  memset(B, 0, sizeof(*B));
+  for (int i = 0; i < 5; ++i) {
+    B->c[6 * i] = (cx*)malloc(sizeof(cx));
+    if (!B->c[6 * i]) return TIKH_ORACLE_ENOMEM;
+    B->c[6 * i][0] = 1.0;
+    B->len[6 * i] = 1;
+  }
+  return 0;
+}
+
+/* ensure entry e can hold len coefficients (new ones zero) */
+static int pm_reserve(pmat* B, int e, int64_t len) {
+  if (B->len[e] >= len) return 0;
+  cx* nc = (cx*)realloc(B->c[e], sizeof(cx) * (size_t)len);
+  if (!nc) return TIKH_ORACLE_ENOMEM;
+  for (int64_t t = B->len[e]; t < len; ++t) nc[t] = 0;
+  B->c[e] = nc;
+  B->len[e] = len;
+  return 0;
+}
+
+static cx horner(const cx* c, int64_t len, cx z) {
+  cx v = 0;
+  for (int64_t t = len - 1; t >= 0; --t) v = v * z + c[t];
+  return v;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Serial single-point construction (Eq. (spbasis), Sec. 4.3) with pivoting (R1, R7, R8).       */
+/* ------------------------------------------------------------------------------------------ */
+
+/* Processes the conditions (sigma[q], r[q]) q < K against basis B (updated in place, B <- B E_q).
+ * active[q] != 0 marks the conditions still to process.  eps < 0 disables deferral.
+ * order/pivot (may be null) record the processing; deferred (may be null) collects deferred
+ * positions; n_drop counts conditions whose residual is exactly zero. */
+static int serial_construct(int K, const cx* sigma, cx* r, char* active, int* delta, double eps, pmat* B,
+                            int* order, int* pivot, int* deferred, int* n_def, int64_t* n_drop) {
+  int step = 0;
+  if (n_def) *n_def = 0;
+  for (;;) {
+    int best = -1, bpi = -1;
+    double bscore = -1.0;
+    int remaining = 0;
+    for (int q = 0; q < K; ++q) {
+      if (!active[q]) continue;
+      const cx* rq = r + 5 * q;
+      double mag[5], tot = 0.0;
+      int pi = -1;
+      for (int i = 0; i < 5; ++i) {
+        mag[i] = creal(rq[i]) * creal(rq[i]) + cimag(rq[i]) * cimag(rq[i]);
+        tot += mag[i];
+      }
+      for (int i = 0; i < 5; ++i) {
+        if (creal(rq[i]) == 0.0 && cimag(rq[i]) == 0.0) continue; /* R1: non-zero entries only */
+        if (pi < 0 || delta[i] < delta[pi] || (delta[i] == delta[pi] && mag[i] > mag[pi])) pi = i;
+      }
+      if (pi < 0) { /* exactly zero residual: the condition is already satisfied */
+        active[q] = 0;
+        if (n_drop) ++*n_drop;
+        continue;
+      }
+      ++remaining;
+      double score = mag[pi] / tot; /* R8 */
+      if (score > bscore) { bscore = score; best = q; bpi = pi; }
+    }
+    if (best < 0) break;
+    if (eps >= 0.0 && bscore < eps * eps) { /* R7: defer this and every remaining condition */
+      for (int q = 0; q < K; ++q)
+        if (active[q]) {
+          active[q] = 0;
+          if (deferred) deferred[(*n_def)++] = q;
+        }
+      break;
+    }
+    (void)remaining;
+    const int pi = bpi;
+    const cx sg = sigma[best];
+    const cx* rs = r + 5 * best;
+    /* mu_i = -r_i / r_pi, division as r_i * conj(r_pi) / |r_pi|^2 */
+    double den = creal(rs[pi]) * creal(rs[pi]) + cimag(rs[pi]) * cimag(rs[pi]);
+    cx inv = creal(rs[pi]) / den - (cimag(rs[pi]) / den) * I;
+    cx mu[5];
+    for (int i = 0; i < 5; ++i) mu[i] = (i == pi) ? 0.0 : -(rs[i] * inv);
+    active[best] = 0;
+    if (order) order[step] = best;
+    if (pivot) pivot[step] = pi;
+    ++step;
+    /* residual update r_q <- r_q E(sigma_q): E = I except column pi = (z - sg) e_pi + sum mu_i e_i */
+    for (int q = 0; q < K; ++q) {
+      if (!active[q]) continue;
+      cx* rq = r + 5 * q;
+      cx rp = rq[pi];
+      for (int i = 0; i < 5; ++i)
+        if (i != pi) rq[i] = rq[i] + mu[i] * rp;
+      rq[pi] = rp * (sigma[q] - sg);
+    }
+    /* basis update B <- B E: column pi <- (z - sg) column pi; column i += mu_i * old column pi */
+    for (int row = 0; row < 5; ++row) {
+      int ep = 5 * row + pi;
+      int64_t L = B->len[ep];
+      if (L == 0) continue;
+      cx* old = (cx*)malloc(sizeof(cx) * (size_t)L);
+      if (!old) return TIKH_ORACLE_ENOMEM;
+      memcpy(old, B->c[ep], sizeof(cx) * (size_t)L);
+      for (int i = 0; i < 5; ++i) {
+        if (i == pi) continue;
+        int ei = 5 * row + i;
+        if (pm_reserve(B, ei, L)) { free(old); return TIKH_ORACLE_ENOMEM; }
+        for (int64_t t = 0; t < L; ++t) B->c[ei][t] = B->c[ei][t] + mu[i] * old[t];
+      }
+      if (pm_reserve(B, ep, L + 1)) { free(old); return TIKH_ORACLE_ENOMEM; }
+      B->c[ep][0] = -(sg * old[0]);
+      for (int64_t t = 1; t < L; ++t) B->c[ep][t] = old[t - 1] - sg * old[t];
+      B->c[ep][L] = old[L - 1];
+      free(old);
+    }
+    delta[pi] += 1;
+  }
+  if (order)
+    for (int s = step; s < K; ++s) order[s] = -1;
+  if (pivot)
+    for (int s = step; s < K; ++s) pivot[s] = -1;
+  return 0;
+}
+
+int tikh_oracle_leaf(int K, const double* sigma, double* r, int* delta, double eps, int64_t cap, double* B,
+                     int64_t* len, int* order, int* pivot, int* deferred, int* n_def) {
+  if (K < 0 || !sigma || !r || !delta || !B || !len) return TIKH_ORACLE_EINVAL;
+  pmat P;
+  int rc = pm_identity(&P);
+  char* active = (char*)malloc((size_t)K + 1);
+  if (rc || !active) { pm_free(&P); free(active); return TIKH_ORACLE_ENOMEM; }
+  memset(active, 1, (size_t)K);
+  int64_t ndrop = 0;
+  int nd = 0;
+  rc = serial_construct(K, (const cx*)sigma, (cx*)r, active, delta, eps, &P, order, pivot, deferred, &nd, &ndrop);
+  if (!rc) {
+    for (int e = 0; e < 25; ++e) {
+      /* drop trailing exact zeros so len reports the true storage */
+      int64_t L = P.len[e];
+      if (L > cap) { rc = TIKH_ORACLE_EINVAL; break; }
+      len[e] = L;
+      cx* dst = (cx*)B + (size_t)e * (size_t)cap;
+      for (int64_t t = 0; t < cap; ++t) dst[t] = (t < L) ? P.c[e][t] : 0.0;
+    }
+  }
+  if (n_def) *n_def = nd;
+  pm_free(&P);
+  free(active);
+  return rc;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Degree bounds (R10) and column scaling (R9).                                               */
+/* ------------------------------------------------------------------------------------------ */
+
+static void degree_bounds(const int* din, const int* dout, int64_t* bound /* 25 */) {
+  int have_active = 0, amax = 0;
+  for (int j = 0; j < 5; ++j)
+    if (dout[j] > din[j]) {
+      if (!have_active || dout[j] > amax) amax = dout[j];
+      have_active = 1;
+    }
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j < 5; ++j) {
+      int64_t b;
+      if (dout[j] > din[j]) {
+        b = (int64_t)dout[j] - din[i];
+      } else {
+        int64_t acc = have_active ? (int64_t)amax - din[i] : -1;
+        if (i == j && acc < 0) acc = 0;
+        int64_t tau_b = (int64_t)dout[j] - din[i];
+        b = acc < tau_b ? acc : tau_b;
+      }
+      bound[5 * i + j] = b;
+    }
+}
+
+static int trim_to_bounds(pmat* B, const int64_t* bound) {
+  for (int e = 0; e < 25; ++e) {
+    int64_t want = bound[e] < 0 ? 0 : bound[e] + 1;
+    if (B->len[e] > want) {
+      B->len[e] = want;
+      if (want == 0) { free(B->c[e]); B->c[e] = NULL; }
+    }
+  }
+  return 0;
+}
+
+static void scale_columns(pmat* B) {
+  for (int j = 0; j < 5; ++j) {
+    double mx = 0.0;
+    for (int i = 0; i < 5; ++i) {
+      int e = 5 * i + j;
+      for (int64_t t = 0; t < B->len[e]; ++t) {
+        double a = fabs(creal(B->c[e][t])), b = fabs(cimag(B->c[e][t]));
+        if (a > mx) mx = a;
+        if (b > mx) mx = b;
+      }
+    }
+    if (mx == 0.0) continue;
+    int ex;
+    frexp(mx, &ex); /* mx = f 2^ex, f in [0.5, 1) */
+    for (int i = 0; i < 5; ++i) {
+      int e = 5 * i + j;
+      for (int64_t t = 0; t < B->len[e]; ++t)
+        B->c[e][t] = ldexp(creal(B->c[e][t]), -ex) + ldexp(cimag(B->c[e][t]), -ex) * I;
+    }
+  }
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* The recursion (Algorithm 1 with paired interleaving, Sec. 5.1).                             */
+/* A node is (a, s, L): its nodes are omega^{a + c + s j}, c in {0,1}, j < L; s L = N.         */
+/* Its conditions, in list order, are position 4j + 2c + f (f = 0: F, f = 1: G).              */
+/* ------------------------------------------------------------------------------------------ */
+
+typedef struct {
+  int64_t N, M;
+  double eps;
+  int mode;
+  cx* R; /* residual rows [N][2][5] */
+  int64_t* deferred; /* deferred condition ids 2e + f */
+  int64_t n_def, n_drop;
+} rstate;
+
+static int leaf_node(rstate* st, int64_t a, int64_t s, int64_t L, int* delta, pmat* out) {
+  int K = (int)(4 * L);
+  cx* sig = (cx*)malloc(sizeof(cx) * (size_t)K);
+  cx* r = (cx*)malloc(sizeof(cx) * 5 * (size_t)K);
+  char* act = (char*)malloc((size_t)K);
+  int* dq = (int*)malloc(sizeof(int) * (size_t)K);
+  int rc = TIKH_ORACLE_ENOMEM, nd = 0;
+  if (!sig || !r || !act || !dq) goto done;
+  for (int64_t j = 0; j < L; ++j)
+    for (int c = 0; c < 2; ++c)
+      for (int f = 0; f < 2; ++f) {
+        int q = (int)(4 * j + 2 * c + f);
+        int64_t e = a + c + s * j;
+        sig[q] = node(e, st->N);
+        memcpy(r + 5 * q, st->R + 10 * e + 5 * f, sizeof(cx) * 5);
+        act[q] = 1;
+      }
+  int din[5];
+  memcpy(din, delta, sizeof(din));
+  if ((rc = pm_identity(out))) goto done;
+  rc = serial_construct(K, sig, r, act, delta, st->eps, out, NULL, NULL, dq, &nd, &st->n_drop);
+  if (rc) goto done;
+  for (int i = 0; i < nd; ++i) {
+    int q = dq[i];
+    int64_t j = q / 4, c = (q / 2) % 2, f = q % 2;
+    st->deferred[st->n_def++] = 2 * (a + c + s * j) + f;
+  }
+  int64_t bound[25];
+  degree_bounds(din, delta, bound);
+  trim_to_bounds(out, bound);
+  scale_columns(out);
+done:
+  free(sig); free(r); free(act); free(dq);
+  return rc;
+}
+
+static int64_t smooth_at_least(int64_t v) {
+  if (v < 1) v = 1;
+  while (!is_5smooth(v)) ++v;
+  return v;
+}
+
+/* step 2 of Algorithm 1: phi <- phi B_L(sigma) for every condition of the right child (aR, 2s, L/2) */
+static int update_right(rstate* st, const pmat* BL, int64_t aR, int64_t sR, int64_t Lr) {
+  int64_t N = st->N;
+  int use_fft = st->mode == TIKH_ORACLE_FFT || (st->mode == TIKH_ORACLE_AUTO && Lr > 64);
+  cx* val = (cx*)malloc(sizeof(cx) * 25 * 2 * (size_t)Lr); /* [entry][c][j] */
+  if (!val) return TIKH_ORACLE_ENOMEM;
+  for (int e = 0; e < 25; ++e)
+    for (int c = 0; c < 2; ++c) {
+      cx* v = val + ((size_t)e * 2 + c) * (size_t)Lr;
+      int64_t beta = aR + c;
+      if (!use_fft) {
+        for (int64_t j = 0; j < Lr; ++j) v[j] = horner(BL->c[e], BL->len[e], node(beta + sR * j, N));
+      } else {
+        /* P(omega^{beta + sR j}) = sum_u g_u exp(2 pi i u j / Lr), g_u = sum_{t = u mod Lr} P_t omega^{beta t} */
+        for (int64_t u = 0; u < Lr; ++u) v[u] = 0;
+        for (int64_t t = 0; t < BL->len[e]; ++t) v[t % Lr] += BL->c[e][t] * node(beta * t, N);
+        int rc = dft(v, Lr, +1);
+        if (rc) { free(val); return rc; }
+      }
+    }
+  for (int64_t j = 0; j < Lr; ++j)
+    for (int c = 0; c < 2; ++c) {
+      int64_t e = aR + c + sR * j;
+      for (int f = 0; f < 2; ++f) {
+        cx* rq = st->R + 10 * e + 5 * f;
+        cx nr[5];
+        for (int col = 0; col < 5; ++col) {
+          cx acc = 0;
+          for (int i = 0; i < 5; ++i) acc += rq[i] * val[((size_t)(5 * i + col) * 2 + c) * (size_t)Lr + j];
+          nr[col] = acc;
+        }
+        memcpy(rq, nr, sizeof(nr));
+      }
+    }
+  free(val);
+  return 0;
+}
+
+/* step 4 of Algorithm 1: B = B_L B_R, trimmed to the node's degree bounds */
+static int multiply(const rstate* st, const pmat* BL, const pmat* BR, const int64_t* bound, pmat* out) {
+  memset(out, 0, sizeof(*out));
+  int64_t D = -1;
+  for (int e = 0; e < 25; ++e)
+    if (bound[e] > D) D = bound[e];
+  int64_t maxlen = 0;
+  for (int e = 0; e < 25; ++e) {
+    if (BL->len[e] > maxlen) maxlen = BL->len[e];
+    if (BR->len[e] > maxlen) maxlen = BR->len[e];
+  }
+  int use_fft = st->mode == TIKH_ORACLE_FFT || (st->mode == TIKH_ORACLE_AUTO && maxlen > 64);
+  if (!use_fft) {
+    for (int i = 0; i < 5; ++i)
+      for (int j = 0; j < 5; ++j) {
+        int eo = 5 * i + j;
+        int64_t want = bound[eo] < 0 ? 0 : bound[eo] + 1;
+        if (want == 0) continue;
+        if (pm_reserve(out, eo, want)) return TIKH_ORACLE_ENOMEM;
+        for (int t = 0; t < 5; ++t) {
+          const cx* x = BL->c[5 * i + t];
+          const cx* y = BR->c[5 * t + j];
+          int64_t lx = BL->len[5 * i + t], ly = BR->len[5 * t + j];
+          for (int64_t u = 0; u < lx; ++u)
+            for (int64_t v = 0; v < ly; ++v)
+              if (u + v < want) out->c[eo][u + v] += x[u] * y[v];
+        }
+      }
+    return 0;
+  }
+  /* FFT products of length P > D: a linear convolution of polynomials whose product has degree
+   * <= D equals the cyclic one */
+  int64_t P = smooth_at_least(D + 1);
+  cx* fl = (cx*)calloc(25 * (size_t)P, sizeof(cx));
+  cx* fr = (cx*)calloc(25 * (size_t)P, sizeof(cx));
+  cx* acc = (cx*)malloc(sizeof(cx) * (size_t)P);
+  int rc = TIKH_ORACLE_ENOMEM;
+  if (!fl || !fr || !acc) goto done;
+  for (int e = 0; e < 25; ++e) {
+    /* entries longer than P would wrap; their high coefficients multiply into terms above D
+     * only if the bound is violated, which trim_to_bounds would have removed anyway */
+    int64_t lx = BL->len[e] < P ? BL->len[e] : P, ly = BR->len[e] < P ? BR->len[e] : P;
+    for (int64_t t = 0; t < lx; ++t) fl[(size_t)e * P + t] = BL->c[e][t];
+    for (int64_t t = 0; t < ly; ++t) fr[(size_t)e * P + t] = BR->c[e][t];
+    if (lx && (rc = dft(fl + (size_t)e * P, P, +1))) goto done;
+    if (ly && (rc = dft(fr + (size_t)e * P, P, +1))) goto done;
+  }
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j < 5; ++j) {
+      int eo = 5 * i + j;
+      int64_t want = bound[eo] < 0 ? 0 : bound[eo] + 1;
+      if (want == 0) continue;
+      for (int64_t u = 0; u < P; ++u) {
+        cx s = 0;
+        for (int t = 0; t < 5; ++t) s += fl[(size_t)(5 * i + t) * P + u] * fr[(size_t)(5 * t + j) * P + u];
+        acc[u] = s;
+      }
+      if ((rc = dft(acc, P, -1))) goto done;
+      if (pm_reserve(out, eo, want)) { rc = TIKH_ORACLE_ENOMEM; goto done; }
+      for (int64_t u = 0; u < want; ++u) out->c[eo][u] = acc[u] / (double)P;
+    }
+  rc = 0;
+done:
+  free(fl); free(fr); free(acc);
+  return rc;
+}
+
+static int rec_tanint(rstate* st, int64_t a, int64_t s, int64_t L, int* delta, pmat* out) {
+  if (2 * L == st->M) return leaf_node(st, a, s, L, delta, out);
+  int din[5];
+  memcpy(din, delta, sizeof(din));
+  pmat BL, BR;
+  memset(&BR, 0, sizeof(BR));
+  int rc = rec_tanint(st, a, 2 * s, L / 2, delta, &BL); /* step 1: {t mod 4 in {0,1}} */
+  if (rc) return rc;
+  rc = update_right(st, &BL, a + s, 2 * s, L / 2); /* step 2 */
+  if (!rc) rc = rec_tanint(st, a + s, 2 * s, L / 2, delta, &BR); /* step 3: {t mod 4 in {2,3}} */
+  if (!rc) {
+    int64_t bound[25];
+    degree_bounds(din, delta, bound);
+    rc = multiply(st, &BL, &BR, bound, out); /* step 4 */
+    if (!rc) scale_columns(out);
+  }
+  pm_free(&BL);
+  pm_free(&BR);
+  return rc;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Drivers.                                                                                   */
+/* ------------------------------------------------------------------------------------------ */
+
+int tikh_oracle_conditions(int64_t m, int64_t n, const double* col, const double* row, const double* y,
+                           double lam, const tikh_oracle_opts* opts, double* F, double* G, int* tau) {
+  int64_t N, M, k;
+  int p;
+  int rc = tikh_oracle_plan(m, n, opts, &N, &M, &k, &p);
+  if (rc) return rc;
+  rc = build_conditions(m, n, N, k, (const cx*)col, (const cx*)row, (const cx*)y, lam, opts->fill, opts->is_complex,
+                        (cx*)F, (cx*)G);
+  if (rc) return rc;
+  tau[0] = (int)(n - 1); tau[1] = (int)(m - 1); tau[2] = (int)(m + k - 2); tau[3] = (int)(n + k - 2); tau[4] = 0;
+  return 0;
+}
+
+int tikh_oracle_solve_normal(int64_t m, int64_t n, const double* col, const double* row, const double* y,
+                             double lam, const tikh_oracle_opts* opts, double* x, tikh_oracle_stats* stats,
+                             double* Bout, int64_t cap, int64_t* lenout) {
+  int64_t N, M, k;
+  int p;
+  int rc = tikh_oracle_plan(m, n, opts, &N, &M, &k, &p);
+  if (rc) return rc;
+  rstate st;
+  memset(&st, 0, sizeof(st));
+  st.N = N; st.M = M; st.eps = opts->eps_diff; st.mode = opts->mode;
+  cx* F = (cx*)malloc(sizeof(cx) * 5 * (size_t)N);
+  cx* G = (cx*)malloc(sizeof(cx) * 5 * (size_t)N);
+  cx* Phi = (cx*)malloc(sizeof(cx) * 10 * (size_t)N);
+  st.R = (cx*)malloc(sizeof(cx) * 10 * (size_t)N);
+  st.deferred = (int64_t*)malloc(sizeof(int64_t) * 2 * (size_t)N);
+  pmat B;
+  memset(&B, 0, sizeof(B));
+  rc = TIKH_ORACLE_ENOMEM;
+  if (!F || !G || !Phi || !st.R || !st.deferred) goto done;
+  if ((rc = build_conditions(m, n, N, k, (const cx*)col, (const cx*)row, (const cx*)y, lam, opts->fill,
+                             opts->is_complex, F, G)))
+    goto done;
+  for (int64_t e = 0; e < N; ++e) {
+    memcpy(st.R + 10 * e, F + 5 * e, sizeof(cx) * 5);
+    memcpy(st.R + 10 * e + 5, G + 5 * e, sizeof(cx) * 5);
+  }
+  memcpy(Phi, st.R, sizeof(cx) * 10 * (size_t)N);
+  /* Eq. (taudef) with reading R3; the starting basis I has tau-degrees -tau (Sec. 4.3) */
+  int delta[5] = {-(int)(n - 1), -(int)(m - 1), -(int)(m + k - 2), -(int)(n + k - 2), 0};
+  /* root node: all N nodes = omega^{0 + c + 2 j}, j < N/2 */
+  if ((rc = rec_tanint(&st, 0, 2, N / 2, delta, &B))) goto done;
+  if (st.n_def > 0) {
+    /* difficult points (Sec. 4 end): residual against the final basis, then serial processing */
+    int K = (int)st.n_def;
+    cx* sig = (cx*)malloc(sizeof(cx) * (size_t)K);
+    cx* r = (cx*)malloc(sizeof(cx) * 5 * (size_t)K);
+    char* act = (char*)malloc((size_t)K);
+    if (!sig || !r || !act) { free(sig); free(r); free(act); rc = TIKH_ORACLE_ENOMEM; goto done; }
+    for (int q = 0; q < K; ++q) {
+      int64_t id = st.deferred[q], e = id / 2;
+      const cx* ph = Phi + 10 * e + 5 * (id % 2);
+      sig[q] = node(e, N);
+      for (int j = 0; j < 5; ++j) {
+        cx acc = 0;
+        for (int i = 0; i < 5; ++i) acc += ph[i] * horner(B.c[5 * i + j], B.len[5 * i + j], sig[q]);
+        r[5 * q + j] = acc;
+      }
+      act[q] = 1;
+    }
+    rc = serial_construct(K, sig, r, act, delta, -1.0, &B, NULL, NULL, NULL, NULL, &st.n_drop);
+    free(sig); free(r); free(act);
+    if (rc) goto done;
+  }
+  /* Sec. 4.3 end: one column has tau-degree 0, the other four 1 */
+  int jstar = -1, nzero = 0, none = 0;
+  for (int j = 0; j < 5; ++j) {
+    if (delta[j] == 0) { jstar = j; ++nzero; }
+    else if (delta[j] == 1) ++none;
+  }
+  if (stats) {
+    stats->N = N; stats->M = M; stats->k = k; stats->p = p;
+    stats->n_difficult = st.n_def; stats->n_dropped = st.n_drop;
+    memcpy(stats->delta, delta, sizeof(delta));
+    stats->jstar = jstar; stats->dual = 0;
+  }
+  if (nzero != 1 || none != 4 || B.len[5 * 4 + jstar] < 1) { rc = TIKH_ORACLE_ENUMERIC; goto done; }
+  /* Sec. 4.4: x(z) = B*_1^{(j)}(z) / B*_5^{(j)} (the constant last component) */
+  {
+    cx c5 = B.c[5 * 4 + jstar][0];
+    const cx* b1 = B.c[jstar];
+    int64_t l1 = B.len[jstar];
+    for (int64_t i = 0; i < n; ++i) ((cx*)x)[i] = (i < l1 ? b1[i] : 0.0) / c5;
+  }
+  if (Bout && lenout) {
+    for (int e = 0; e < 25; ++e) {
+      int64_t L = B.len[e] < cap ? B.len[e] : cap;
+      lenout[e] = B.len[e];
+      cx* dst = (cx*)Bout + (size_t)e * (size_t)cap;
+      for (int64_t t = 0; t < cap; ++t) dst[t] = (t < L) ? B.c[e][t] : 0.0;
+    }
+  }
+  rc = 0;
+done:
+  pm_free(&B);
+  free(F); free(G); free(Phi); free(st.R); free(st.deferred);
+  return rc;
+}
+
+/* y = T^H v and u = T x through the circulant embedding of length >= m+n-1 (a plain DFT identity) */
+static int toeplitz_apply(int64_t m, int64_t n, const cx* col, const cx* row, const cx* in, cx* out, int herm) {
+  int64_t L = smooth_at_least(m + n - 1);
+  cx* g = (cx*)calloc((size_t)L, sizeof(cx));
+  cx* v = (cx*)calloc((size_t)L, sizeof(cx));
+  int rc = TIKH_ORACLE_ENOMEM;
+  if (!g || !v) goto done;
+  if (!herm) {
+    /* (T x)_i = sum_j a_{i-j} x_j: cyclic convolution of g[d mod L] = a_d with x */
+    for (int64_t d = 0; d < m; ++d) g[d] = col[d];
+    for (int64_t d = 1; d < n; ++d) g[L - d] = row[d];
+    for (int64_t j = 0; j < n; ++j) v[j] = in[j];
+  } else {
+    /* (T^H v)_i = sum_j conj(a_{j-i}) v_j: g[d mod L] = conj(a_{-d}) for d in [-(m-1), n-1] */
+    for (int64_t d = 0; d < n; ++d) g[d] = conj(d == 0 ? col[0] : row[d]);
+    for (int64_t d = 1; d < m; ++d) g[L - d] = conj(col[d]);
+    for (int64_t j = 0; j < m; ++j) v[j] = in[j];
+  }
+  if ((rc = dft(g, L, +1)) || (rc = dft(v, L, +1))) goto done;
+  for (int64_t t = 0; t < L; ++t) v[t] *= g[t];
+  if ((rc = dft(v, L, -1))) goto done;
+  for (int64_t i = 0; i < (herm ? n : m); ++i) out[i] = v[i] / (double)L;
+  rc = 0;
+done:
+  free(g); free(v);
+  return rc;
+}
+
+int tikh_oracle_apply_th(int64_t m, int64_t n, const double* col, const double* row, const double* v, double* y) {
+  if (m < 1 || n < 1) return TIKH_ORACLE_EINVAL;
+  return toeplitz_apply(m, n, (const cx*)col, (const cx*)row, (const cx*)v, (cx*)y, 1);
+}
+
+int tikh_oracle_apply_t(int64_t m, int64_t n, const double* col, const double* row, const double* x, double* u) {
+  if (m < 1 || n < 1) return TIKH_ORACLE_EINVAL;
+  return toeplitz_apply(m, n, (const cx*)col, (const cx*)row, (const cx*)x, (cx*)u, 0);
+}
+
+int tikh_oracle_solve(int64_t m, int64_t n, const double* col, const double* row, const double* b, double lam,
+                      const tikh_oracle_opts* opts, double* x, tikh_oracle_stats* stats) {
+  if (m < 1 || n < 1 || !(lam > 0.0) || !opts) return TIKH_ORACLE_EINVAL;
+  int rc;
+  if (m >= n) {
+    cx* y = (cx*)malloc(sizeof(cx) * (size_t)n);
+    if (!y) return TIKH_ORACLE_ENOMEM;
+    rc = tikh_oracle_apply_th(m, n, col, row, b, (double*)y);
+    if (!rc) rc = tikh_oracle_solve_normal(m, n, col, row, (const double*)y, lam, opts, x, stats, NULL, 0, NULL);
+    free(y);
+    return rc;
+  }
+  /* R11: T' = T^H is n x m with a'_d = conj(a_{-d}): col'[d] = conj(row[d]) (d >= 1),
+   * col'[0] = conj(a_0), row'[d] = conj(col[d]) */
+  cx* cp = (cx*)malloc(sizeof(cx) * (size_t)n);
+  cx* rp = (cx*)malloc(sizeof(cx) * (size_t)m);
+  cx* v = (cx*)malloc(sizeof(cx) * (size_t)m);
+  rc = TIKH_ORACLE_ENOMEM;
+  if (cp && rp && v) {
+    const cx* c = (const cx*)col;
+    const cx* r = (const cx*)row;
+    cp[0] = conj(c[0]);
+    for (int64_t d = 1; d < n; ++d) cp[d] = conj(r[d]);
+    for (int64_t d = 0; d < m; ++d) rp[d] = conj(c[d]);
+    rc = tikh_oracle_solve_normal(n, m, (const double*)cp, (const double*)rp, b, lam, opts, (double*)v, stats, NULL,
+                                  0, NULL);
+    if (!rc) rc = tikh_oracle_apply_th(m, n, col, row, (const double*)v, x);
+    if (stats) stats->dual = 1;
+  }
+  free(cp); free(rp); free(v);
+  return rc;
+}

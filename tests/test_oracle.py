@@ -1,0 +1,312 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix (no GPU needed).
+
+Every check here is independent of the oracle's own arithmetic: dense LAPACK solves, closed forms,
+numpy's FFT, the defining properties of the interpolation basis (Def. 1, Sec. 4.2-4.3) and the
+values the paper prints (Table 1).
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1302_6945_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def relerr(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300)
+
+
+# ----------------------------------------------------------------------------------------------
+# DFT
+# ----------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 7, 12, 60, 97, 128, 240, 1000])
+def test_fft_matches_numpy_and_brute_force(n):
+    rng = np.random.default_rng(n)
+    x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    # positive sign: evaluation at omega_k = exp(+2 pi i k/n) (Eq. (vandprod))
+    np.testing.assert_allclose(oracle.fft(x, +1), np.fft.ifft(x) * n, rtol=0, atol=1e-12 * n)
+    np.testing.assert_allclose(oracle.fft(x, -1), np.fft.fft(x), rtol=0, atol=1e-12 * n)
+    if n <= 128:
+        k = np.arange(n)
+        V = np.exp(2j * np.pi * np.outer(k, k) / n)
+        np.testing.assert_allclose(oracle.fft(x, +1), V @ x, rtol=0, atol=1e-11 * n)
+
+
+# ----------------------------------------------------------------------------------------------
+# Algorithm 2 (OptExtend), l2 reading: two condition sets, paired interleaving
+# ----------------------------------------------------------------------------------------------
+
+def _smooth5(v):
+    for f in (2, 3, 5):
+        while v % f == 0:
+            v //= f
+    return v == 1
+
+
+@pytest.mark.parametrize("m,n,nlim", [(1, 1, 32), (1024, 1024, 32), (98304, 65536, 32), (98304, 65536, 64),
+                                      (1572864, 1048576, 32), (327680, 262144, 64), (333, 222, 16),
+                                      (5, 700, 8), (257, 1, 32)])
+def test_plan_alg2_properties(m, n, nlim):
+    N, M, k, p = oracle.plan(m, n, nlim)
+    Nt = m + n - 1
+    assert N == (M << p) and k == N - Nt and k >= 0          # criteria 1 and 3 (Sec. 5.2)
+    assert M % 2 == 0 and _smooth5(M)                        # M even (Sec. 5.2) and 5-smooth (R6)
+    # criterion 2 with s = 2 sets: the halving loop stops at the first M with 2M <= N_lim
+    Mraw, praw = Nt, 0
+    while 2 * Mraw > nlim:
+        praw += 1
+        Mraw = -(-Mraw // 2)
+    assert p == praw and M >= Mraw and M - Mraw < max(8, Mraw // 4)
+
+
+def test_plan_worked_values():
+    # Nt = 2047: 2047 -> 1024 -> 512 -> ... -> 16 after 7 halvings (2*16 <= 32)
+    assert oracle.plan(1024, 1024, 32) == (2048, 16, 1, 7)
+    # Nt = 163839 -> ceil-halved 14 times to 10 (2*10 <= 32 < 2*20)
+    assert oracle.plan(98304, 65536, 32) == (163840, 10, 1, 14)
+    # odd M is made even: Nt = 7 with N_lim 100 -> M = 8, k = 1
+    assert oracle.plan(4, 4, 100) == (8, 8, 1, 0)
+
+
+# ----------------------------------------------------------------------------------------------
+# Interpolation conditions (Sec. 3.3 + 4.1): the stacked homogeneous system has the Tikhonov
+# solution in its null space
+# ----------------------------------------------------------------------------------------------
+
+def _stacked_system(F, G, tau, N):
+    w = np.exp(2j * np.pi * np.arange(N) / N)
+    cols = []
+    for i in range(5):
+        for t in range(tau[i] + 1):
+            cols.append(np.concatenate([F[:, i] * w ** t, G[:, i] * w ** t]))
+    return np.stack(cols, axis=1)
+
+
+@pytest.mark.parametrize("m,n,lam,cplx,nlim", [(6, 4, 0.3, True, 8), (9, 9, 1e-2, False, 8), (12, 7, 1e-3, True, 4),
+                                               (16, 16, 2.0, True, 16), (21, 13, 1e-4, False, 8)])
+def test_conditions_null_space_is_tikhonov_solution(m, n, lam, cplx, nlim):
+    P = W.random_problem(m, n, lam, seed=m * 31 + n, complex_data=cplx)
+    y = oracle.toeplitz_dense(P["col"], P["row"]).conj().T @ P["b"]
+    F, G, tau, (N, M, k, p) = oracle.conditions(P["col"], P["row"], y, lam, nlim=nlim)
+    assert list(tau) == [n - 1, m - 1, m + k - 2, n + k - 2, 0]
+    A = _stacked_system(F, G, tau, N)
+    assert A.shape == (2 * N, 2 * N + 1)
+    _, s, vh = np.linalg.svd(A)
+    assert s.size == 2 * N and s[-1] > 1e-9 * s[0]   # full row rank: a one-dimensional null space
+    v = vh[-1].conj()                                # the right singular vector beyond the 2N values
+    assert np.abs(A @ v).max() < 1e-10 * s[0]
+    v = v / v[-1]                                    # constant component = 1
+    np.testing.assert_allclose(v[:n], oracle.dense_solve(P["col"], P["row"], P["b"], lam), rtol=1e-8, atol=1e-10)
+    # sigma_1 = T x (Sec. 3.3): next m coefficients
+    T = oracle.toeplitz_dense(P["col"], P["row"])
+    np.testing.assert_allclose(v[n:n + m], T @ v[:n], rtol=1e-8, atol=1e-10)
+
+
+def test_conditions_adjoint_generator_identity():
+    # Sec. 6.3: the DFT of the T^H generator follows in O(n) from that of T: lam_H = w^{e(k-1)} conj(t_hat)
+    P = W.random_problem(37, 23, 1e-2, seed=3)
+    F, G, tau, (N, M, k, p) = oracle.conditions(P["col"], P["row"], np.zeros(23), 1e-2, nlim=8, m_min=12)
+    assert k > 1
+    e = np.arange(N)
+    w = np.exp(2j * np.pi * ((e * (k - 1)) % N) / N)
+    np.testing.assert_allclose(F[:, 1], w * np.conj(-G[:, 0]), rtol=1e-12, atol=1e-12)
+
+
+# ----------------------------------------------------------------------------------------------
+# Leaf: serial single-point construction (Eq. (spbasis))
+# ----------------------------------------------------------------------------------------------
+
+def _polyval(c, z):
+    return np.polyval(c[::-1], z) if len(c) else 0.0
+
+
+def _Bval(B, ln, z):
+    V = np.zeros((5, 5), complex)
+    for e in range(25):
+        V[e // 5, e % 5] = _polyval(B[e, :ln[e]], z)
+    return V
+
+
+def test_leaf_single_point_is_spbasis():
+    rng = np.random.default_rng(0)
+    phi = rng.standard_normal(5) + 1j * rng.standard_normal(5)
+    sigma = np.exp(2j * np.pi * 0.3)
+    delta = [-3, -5, -5, -2, 0]          # min delta on columns 1, 2: the larger |phi| of them pivots
+    out = oracle.leaf([sigma], phi, delta, eps=0.0)
+    pi = 1 if abs(phi[1]) > abs(phi[2]) else 2
+    assert out["pivot"][0] == pi and list(out["delta"]) == [d + (i == pi) for i, d in enumerate(delta)]
+    B = np.zeros((25, 2), complex)
+    for i in range(5):
+        B[6 * i, 0] = 1.0
+    B[6 * pi] = [-sigma, 1.0]                               # (z - sigma) on the pivot
+    for i in range(5):
+        if i != pi:
+            B[5 * pi + i, 0] = -phi[i] / phi[pi]            # mu_i = -phi_i / phi_pi
+    np.testing.assert_allclose(out["B"][:, :2], B, rtol=1e-14, atol=1e-15)
+    assert np.allclose(phi @ _Bval(out["B"], out["len"], sigma), 0, atol=1e-14)
+
+
+@pytest.mark.parametrize("K,seed", [(2, 1), (8, 2), (20, 3), (32, 4), (64, 5)])
+def test_leaf_basis_properties(K, seed):
+    rng = np.random.default_rng(seed)
+    sigma = np.exp(2j * np.pi * rng.permutation(4 * K)[:K] / (4 * K))
+    phi = rng.standard_normal((K, 5)) + 1j * rng.standard_normal((K, 5))
+    phi[::3, 3] = 0.0                                   # structural zeros like F_k, G_k
+    delta_in = np.array([-9, -11, -11, -9, 0])
+    out = oracle.leaf(sigma, phi.copy(), delta_in, eps=1e-12)
+    B, ln, dout = out["B"], out["len"], out["delta"]
+    done = [q for q in out["order"] if q >= 0]
+    assert len(done) + len(out["deferred"]) == K
+    assert (dout - delta_in).sum() == len(done)         # each processed condition raises one degree
+    # Def. 1: the basis annihilates every processed condition
+    for q in done:
+        r = phi[q] @ _Bval(B, ln, sigma[q])
+        assert np.abs(r).max() < 1e-9 * np.abs(phi[q]).max() * max(1.0, np.abs(_Bval(B, ln, sigma[q])).max())
+    # degree structure: deg B_ij <= delta_out_j - delta_in_i (tau-degree of column j)
+    for i in range(5):
+        for j in range(5):
+            c = B[5 * i + j, :ln[5 * i + j]]
+            nz = np.nonzero(np.abs(c) > 0)[0]
+            if len(nz):
+                assert nz[-1] <= dout[j] - delta_in[i]
+    # each elementary factor has determinant (z - sigma): det B(z) = prod over processed (z - sigma_q)
+    for z in (0.3 + 0.7j, -1.1 + 0.2j, 2.0):
+        ref = np.prod([z - sigma[q] for q in done])
+        np.testing.assert_allclose(np.linalg.det(_Bval(B, ln, z)), ref, rtol=1e-9)
+
+
+def test_leaf_pivot_and_condition_order():
+    # two conditions: q0 with a tiny entry in its minimum-degree column, q1 balanced.
+    sigma = np.array([1.0, -1.0], complex)
+    r = np.array([[1e-3, 1.0, 1.0, 1.0, 1.0], [1.0, 1.0, 0.0, 0.0, 0.0]], complex)
+    out = oracle.leaf(sigma, r.copy(), [-2, -1, -1, -1, 0], eps=0.0)
+    # column 0 has the minimum degree for both; q1 scores 1/2, q0 scores ~1e-6/4: q1 first (R8)
+    assert out["order"][0] == 1 and out["pivot"][0] == 0
+    # deferral (R7): with eps above q0's score after the update, q0 is deferred
+    out2 = oracle.leaf(sigma, r.copy(), [-2, -1, -1, -1, 0], eps=0.9)
+    assert list(out2["deferred"]) == [0, 1]
+
+
+# ----------------------------------------------------------------------------------------------
+# Full solve against the closed form and special cases
+# ----------------------------------------------------------------------------------------------
+
+SHAPES = [(1, 1), (2, 1), (1, 2), (5, 3), (3, 5), (17, 17), (64, 40), (40, 64), (100, 100), (131, 77)]
+
+
+@pytest.mark.parametrize("m,n", SHAPES)
+@pytest.mark.parametrize("lam", [1e-6, 1e-2, 3.0])
+@pytest.mark.parametrize("cplx", [True, False])
+def test_solve_matches_dense_qr(m, n, lam, cplx):
+    P = W.random_problem(m, n, lam, seed=7 * m + n, complex_data=cplx)
+    xd = oracle.dense_solve(P["col"], P["row"], P["b"], lam)
+    x, st = oracle.solve(P["col"], P["row"], P["b"], lam, nlim=16)
+    T = oracle.toeplitz_dense(P["col"], P["row"])
+    cond = np.linalg.cond(T.conj().T @ T + lam * np.eye(n))
+    assert relerr(x, xd) <= 1e-13 * cond + 1e-12, (relerr(x, xd), cond)
+    assert sorted(st["delta"]) == [0, 1, 1, 1, 1]
+
+
+def test_scalar_closed_form():
+    for a, b, lam in [(2.0 + 1j, 0.5 - 3j, 0.7), (-1e-3, 4.0, 1e-6), (0.0, 1.0, 2.0)]:
+        x, _ = oracle.solve([a], [a], [b], lam)
+        np.testing.assert_allclose(x[0], np.conj(a) * b / (abs(a) ** 2 + lam), rtol=1e-14)
+
+
+def test_diagonal_closed_form():
+    m, n = 12, 9
+    col = np.zeros(m, complex)
+    col[0] = 1.5 - 0.5j
+    row = np.zeros(n, complex)
+    row[0] = col[0]
+    b = np.arange(m) + 1j
+    x, _ = oracle.solve(col, row, b, 0.25, nlim=8)
+    np.testing.assert_allclose(x, np.conj(col[0]) * b[:n] / (abs(col[0]) ** 2 + 0.25), rtol=1e-13)
+
+
+@pytest.mark.parametrize("n,lam", [(16, 1e-3), (60, 0.1), (250, 1e-5)])
+def test_circulant_closed_form(n, lam):
+    # T circulant with first column c: x = F^{-1}(conj(c_hat) F b / (|c_hat|^2 + lam)) (numpy FFT)
+    rng = np.random.default_rng(n)
+    c = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    row = np.concatenate([[c[0]], c[1:][::-1]])      # a_{-d} = c_{n-d}
+    b = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    ch = np.fft.fft(c)
+    xref = np.fft.ifft(np.conj(ch) * np.fft.fft(b) / (np.abs(ch) ** 2 + lam))
+    x, _ = oracle.solve(c, row, b, lam, nlim=16)
+    assert relerr(x, xref) < 1e-10
+
+
+@pytest.mark.parametrize("mode", [oracle.DIRECT, oracle.FFT])
+def test_solution_independent_of_leaf_size_extension_and_mode(mode):
+    P = W.deconvolution_problem(300, 220, 4.0, 16, 1e-6, 1e-6, 1e-3, seed=11)
+    xd = oracle.dense_solve(P["col"], P["row"], P["b"], P["lam"])
+    for nlim, m_min in [(8, 0), (16, 0), (32, 0), (64, 0), (16, 12), (32, 20)]:
+        x, st = oracle.solve(P["col"], P["row"], P["b"], P["lam"], nlim=nlim, m_min=m_min, mode=mode)
+        assert relerr(x, xd) < 1e-9, (nlim, m_min, st)
+
+
+def test_basis_satisfies_all_conditions():
+    # Def. 1 at every node, final degree pattern (Sec. 4.3 end), per-entry degree bound
+    P = W.random_problem(45, 31, 1e-2, seed=21)
+    T = oracle.toeplitz_dense(P["col"], P["row"])
+    y = T.conj().T @ P["b"]
+    x, st, B, ln = oracle.solve_normal(P["col"], P["row"], y, 1e-2, nlim=16, want_basis=True)
+    F, G, tau, (N, M, k, p) = oracle.conditions(P["col"], P["row"], y, 1e-2, nlim=16)
+    assert sorted(st["delta"]) == [0, 1, 1, 1, 1]
+    w = np.exp(2j * np.pi * np.arange(N) / N)
+    for e in range(N):
+        V = _Bval(B, ln, w[e])
+        for phi in (F[e], G[e]):
+            r = phi @ V
+            assert np.abs(r).max() <= 1e-9 * np.abs(phi).max() * np.abs(V).max()
+    for i in range(5):
+        for j in range(5):
+            assert ln[5 * i + j] - 1 <= st["delta"][j] + tau[i]
+
+
+def test_normal_equation_identity_large():
+    P = W.deconvolution_problem(6000, 4096, 4.0, 16, 1e-6, 1e-6, 1e-4, seed=5)
+    x, st = oracle.solve(P["col"], P["row"], P["b"], P["lam"], nlim=32)
+    r = oracle.apply_th(P["col"], P["row"], P["b"] - oracle.apply_t(P["col"], P["row"], x)) - P["lam"] * x
+    assert np.linalg.norm(r) / np.linalg.norm(oracle.apply_th(P["col"], P["row"], P["b"])) < 1e-10
+    assert st["n_difficult"] == 0
+
+
+def test_toeplitz_apply_matches_dense():
+    P = W.random_problem(37, 58, 1.0, seed=9)
+    T = oracle.toeplitz_dense(P["col"], P["row"])
+    x = np.arange(58) * (1 - 0.5j)
+    np.testing.assert_allclose(oracle.apply_t(P["col"], P["row"], x), T @ x, rtol=1e-12, atol=1e-10)
+    np.testing.assert_allclose(oracle.apply_th(P["col"], P["row"], P["b"]), T.conj().T @ P["b"], rtol=1e-12,
+                               atol=1e-10)
+
+
+def test_paper_known_x_within_table1_band():
+    # Sec. 6.1-6.2: y = (T^H T + |beta|^2 I) x for known x; Table 1 bounds the max error
+    band = {}
+    with open(os.path.join(GOLDEN, "table1_l2.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                n, v = line.split()
+                band[int(n)] = float(v)
+    for n in (512, 1024):
+        P = W.paper_problem(n, seed=n)
+        T = oracle.toeplitz_dense(P["col"], P["row"])
+        y = T.conj().T @ (T @ P["x_true"]) + P["lam"] * P["x_true"]
+        x, st = oracle.solve_normal(P["col"], P["row"], y, P["lam"], nlim=32)
+        assert np.abs(x - P["x_true"]).max() <= 10 * band[n], (n, np.abs(x - P["x_true"]).max())
+
+
+def test_solution_independent_of_fill():
+    # Sec. 5.2: the arbitrary extension entries change only the conditioning, not the solution
+    P = W.deconvolution_problem(210, 150, 3.0, 12, 1e-6, 1e-6, 1e-2, seed=4)
+    xd = oracle.dense_solve(P["col"], P["row"], P["b"], P["lam"])
+    for fill in (0, 1):
+        for m_min in (0, 12):
+            x, st = oracle.solve(P["col"], P["row"], P["b"], P["lam"], nlim=16, m_min=m_min, fill=fill)
+            assert st["k"] > 1 and relerr(x, xd) < 1e-10, (fill, m_min, st["k"], relerr(x, xd))
