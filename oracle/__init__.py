@@ -176,6 +176,22 @@ def solve(col, row, b, lam, nlim=32, eps_diff=1e-8, mode=AUTO, m_min=0, fill=0, 
     return x, st.as_dict()
 
 
+def solve_refined(col, row, b, lam, steps=1, nlim=32, eps_diff=1e-8, mode=AUTO, m_min=0, fill=0, is_complex=None):
+    """solve() followed by `steps` refinement corrections.  Returns (x, stats, rel_residual)."""
+    if is_complex is None:
+        is_complex = _is_complex(col, row)
+    col, row, b = _c128(col), _c128(row), _c128(b)
+    m, n = col.size, row.size
+    x = np.zeros(n, np.complex128)
+    st = Stats()
+    rr = ctypes.c_double()
+    o = opts(nlim=nlim, eps_diff=eps_diff, mode=mode, m_min=m_min, fill=fill, is_complex=is_complex)
+    _check(_lib().tikh_oracle_solve_refined(ctypes.c_int64(m), ctypes.c_int64(n), _ptr(col), _ptr(row), _ptr(b),
+                                            ctypes.c_double(lam), ctypes.byref(o), ctypes.c_int(steps), _ptr(x),
+                                            ctypes.byref(st), ctypes.byref(rr)), "solve_refined")
+    return x, st.as_dict(), rr.value
+
+
 def apply_t(col, row, x):
     col, row, x = _c128(col), _c128(row), _c128(x)
     u = np.zeros(col.size, np.complex128)

@@ -23,8 +23,8 @@
  *     fills (including a linear ramp between two near-zero PSF tails) lose accuracy for large k.
  *     The T^H extension uses the same periodic sequence.  fill = 1 selects the linear ramp.
  *  R6 Algorithm 2 for two condition sets with paired interleaving: halve M while 2M > N_lim,
- *     then round M up to even (Sec. 5.2) and further to a 5-smooth number (FFT lengths with
- *     factors 2, 3, 5 only; the solution does not depend on k).
+ *     then round M up to even (Sec. 5.2) and further to a 7-smooth number (FFT lengths with
+ *     factors 2, 3, 5, 7 only; the solution does not depend on k).
  *  R7 difficult point: the best remaining condition of a leaf has |r_pi| < eps ||r||_2; it and
  *     the rest of the leaf are deferred and processed serially against the final basis.
  *  R8 condition pivoting: the next condition of a leaf is the one with the largest
@@ -111,6 +111,11 @@ static int is_5smooth(int64_t v) {
   return v == 1;
 }
 
+static int is_7smooth(int64_t v) {
+  while (v % 7 == 0) v /= 7;
+  return is_5smooth(v);
+}
+
 int tikh_oracle_plan(int64_t m, int64_t n, const tikh_oracle_opts* opts, int64_t* N, int64_t* M, int64_t* k,
                      int* p) {
   if (m < 1 || n < 1 || !opts || opts->nlim < 2) return TIKH_ORACLE_EINVAL;
@@ -122,7 +127,7 @@ int tikh_oracle_plan(int64_t m, int64_t n, const tikh_oracle_opts* opts, int64_t
   }
   if (Mv % 2) ++Mv;
   if (Mv < opts->m_min) Mv = opts->m_min + (opts->m_min % 2);
-  while (!is_5smooth(Mv)) Mv += 2;
+  while (!is_7smooth(Mv)) Mv += 2;
   *N = Mv << pv;
   *M = Mv;
   *k = *N - Nt;
@@ -805,5 +810,68 @@ int tikh_oracle_solve(int64_t m, int64_t n, const double* col, const double* row
     if (stats) stats->dual = 1;
   }
   free(cp); free(rp); free(v);
+  return rc;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Iterative refinement (Sec. 6.2 notes that the direct solution "can be further improved with  */
+/* iterative refinement"): on the core system A v = y, A = T_c^H T_c + lam I (T_c the tall core */
+/* matrix, y its right-hand side), v <- v + A^{-1}(y - A v), each correction by the same        */
+/* superfast solve with the residual as right-hand side.                                       */
+/* ------------------------------------------------------------------------------------------ */
+
+int tikh_oracle_solve_refined(int64_t m, int64_t n, const double* col, const double* row, const double* b,
+                              double lam, const tikh_oracle_opts* opts, int steps, double* x, tikh_oracle_stats* stats,
+                              double* rel_residual) {
+  if (m < 1 || n < 1 || !(lam > 0.0) || !opts || steps < 0) return TIKH_ORACLE_EINVAL;
+  int dual = m < n;
+  int64_t cm = dual ? n : m, cn = dual ? m : n;
+  cx* cc = (cx*)malloc(sizeof(cx) * (size_t)cm);
+  cx* cr = (cx*)malloc(sizeof(cx) * (size_t)cn);
+  cx* y = (cx*)malloc(sizeof(cx) * (size_t)cn);
+  cx* v = (cx*)malloc(sizeof(cx) * (size_t)cn);
+  cx* dv = (cx*)malloc(sizeof(cx) * (size_t)cn);
+  cx* r = (cx*)malloc(sizeof(cx) * (size_t)cn);
+  cx* u = (cx*)malloc(sizeof(cx) * (size_t)cm);
+  int rc = TIKH_ORACLE_ENOMEM;
+  if (!cc || !cr || !y || !v || !dv || !r || !u) goto done;
+  if (!dual) {
+    memcpy(cc, col, sizeof(cx) * (size_t)m);
+    memcpy(cr, row, sizeof(cx) * (size_t)n);
+    if ((rc = tikh_oracle_apply_th(m, n, col, row, b, (double*)y))) goto done;
+  } else { /* core matrix T^H: a'_d = conj(a_{-d}) */
+    const cx* c = (const cx*)col;
+    const cx* rw = (const cx*)row;
+    cc[0] = conj(c[0]);
+    for (int64_t d = 1; d < cm; ++d) cc[d] = conj(rw[d]);
+    for (int64_t d = 0; d < cn; ++d) cr[d] = conj(c[d]);
+    memcpy(y, b, sizeof(cx) * (size_t)cn);
+  }
+  if ((rc = tikh_oracle_solve_normal(cm, cn, (double*)cc, (double*)cr, (double*)y, lam, opts, (double*)v, stats, NULL,
+                                     0, NULL)))
+    goto done;
+  double ny = 0.0, nr = 0.0;
+  for (int64_t i = 0; i < cn; ++i) ny += creal(y[i]) * creal(y[i]) + cimag(y[i]) * cimag(y[i]);
+  for (int it = 0; it <= steps; ++it) {
+    /* r = y - (T_c^H (T_c v) + lam v) */
+    if ((rc = tikh_oracle_apply_t(cm, cn, (double*)cc, (double*)cr, (double*)v, (double*)u))) goto done;
+    if ((rc = tikh_oracle_apply_th(cm, cn, (double*)cc, (double*)cr, (double*)u, (double*)r))) goto done;
+    nr = 0.0;
+    for (int64_t i = 0; i < cn; ++i) {
+      r[i] = y[i] - (r[i] + lam * v[i]);
+      nr += creal(r[i]) * creal(r[i]) + cimag(r[i]) * cimag(r[i]);
+    }
+    if (it == steps) break;
+    if ((rc = tikh_oracle_solve_normal(cm, cn, (double*)cc, (double*)cr, (double*)r, lam, opts, (double*)dv, NULL,
+                                       NULL, 0, NULL)))
+      goto done;
+    for (int64_t i = 0; i < cn; ++i) v[i] += dv[i];
+  }
+  if (rel_residual) *rel_residual = ny > 0.0 ? sqrt(nr / ny) : sqrt(nr);
+  if (!dual) memcpy(x, v, sizeof(cx) * (size_t)n);
+  else rc = tikh_oracle_apply_th(m, n, col, row, (double*)v, x);
+  if (stats) stats->dual = dual;
+done:
+  free(cc); free(cr); free(y); free(v); free(dv); free(r); free(u);
   return rc;
 }

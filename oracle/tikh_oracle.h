@@ -53,7 +53,7 @@ typedef struct {
 } tikh_oracle_stats;
 
 /* Algorithm 2 (OptExtend) for the l2 case: two condition sets, paired interleaving, M even and
- * 5-smooth (so every FFT length has factors 2, 3, 5 only).  Outputs N = 2^p M, k = N - (m+n-1). */
+ * 7-smooth (so every FFT length has factors 2, 3, 5, 7 only).  Outputs N = 2^p M, k = N - (m+n-1). */
 int tikh_oracle_plan(int64_t m, int64_t n, const tikh_oracle_opts* opts, int64_t* N, int64_t* M,
                      int64_t* k, int* p);
 
@@ -87,6 +87,13 @@ int tikh_oracle_solve_normal(int64_t m, int64_t n, const double* col, const doub
  * same algorithm on the tall matrix T^H.  b: m complex; x: n complex. */
 int tikh_oracle_solve(int64_t m, int64_t n, const double* col, const double* row, const double* b,
                       double lam, const tikh_oracle_opts* opts, double* x, tikh_oracle_stats* stats);
+
+/* tikh_oracle_solve followed by `steps` iterative-refinement corrections on the core (tall) system
+ * A v = y, A = T_c^H T_c + lam I: v <- v + A^{-1} (y - A v), each correction by the same superfast
+ * solve.  rel_residual (may be null) receives ||y - A v|| / ||y|| after the last correction. */
+int tikh_oracle_solve_refined(int64_t m, int64_t n, const double* col, const double* row, const double* b,
+                              double lam, const tikh_oracle_opts* opts, int steps, double* x, tikh_oracle_stats* stats,
+                              double* rel_residual);
 
 /* y = T^H v (v: m complex, y: n complex) and u = T x (x: n, u: m), by a zero-padded circulant
  * embedding (the DFT diagonalises circulants, Eq. (circdiag)). */

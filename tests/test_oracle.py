@@ -40,8 +40,8 @@ def test_fft_matches_numpy_and_brute_force(n):
 # Algorithm 2 (OptExtend), l2 reading: two condition sets, paired interleaving
 # ----------------------------------------------------------------------------------------------
 
-def _smooth5(v):
-    for f in (2, 3, 5):
+def _smooth7(v):
+    for f in (2, 3, 5, 7):
         while v % f == 0:
             v //= f
     return v == 1
@@ -54,7 +54,7 @@ def test_plan_alg2_properties(m, n, nlim):
     N, M, k, p = oracle.plan(m, n, nlim)
     Nt = m + n - 1
     assert N == (M << p) and k == N - Nt and k >= 0          # criteria 1 and 3 (Sec. 5.2)
-    assert M % 2 == 0 and _smooth5(M)                        # M even (Sec. 5.2) and 5-smooth (R6)
+    assert M % 2 == 0 and _smooth7(M)                        # M even (Sec. 5.2) and 7-smooth (R6)
     # criterion 2 with s = 2 sets: the halving loop stops at the first M with 2M <= N_lim
     Mraw, praw = Nt, 0
     while 2 * Mraw > nlim:
