@@ -1,0 +1,258 @@
+"""Benchmark: superfast Tikhonov solves of the deconvolution workload on GB300.
+
+Workload (one step = one full solve: extension, transformation, recursive basis construction,
+difficult points, extraction, optional refinement): complex128, m = 98304, n = 65536, Gaussian PSF
+(sigma 8) with random phases, lambda = 1e-4.  value = solves/s over all ranks (weak scaling: every
+rank solves its own problem).  Inputs are resident in HBM when the timed region starts; the working
+set (~1 GB) exceeds L2 and L2 is also flushed between steps.  e2e repeats the measurement through
+tikh_solve_host with host buffers (copies inside the timed region).
+
+--impl reference times the CPU oracle (the paper's algorithm in plain C, FP64) on the host cores.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "solves/s and n*solves/s at n=2^16..2^20 vs plain FP64 GPU at rel err<=1e-8; HBM %"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def workload(seed_offset=0):
+    from paper_1302_6945_gb300 import workloads as W
+    return W.config_c2(seed=1 + seed_offset)
+
+
+def run_reference(args, world, rank):
+    """The CPU oracle on the host cores, on this arm's workload and metric."""
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+    oracle.build()
+    P = workload()
+    times = []
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.solve(P["col"], P["row"], P["b"], P["lam"], nlim=args.n_lim)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt)
+    t = sum(times) / len(times)
+    v = 1.0 / t
+    out = {"metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "c128", "data": "synthetic", "impl": "reference",
+           "config": {"workload": "c2 deconvolution m=98304 n=65536 complex128 lambda=1e-4", "m": P["m"],
+                      "n": P["n"], "n_lim": args.n_lim, "l2": "working set > L2"},
+           "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                            "sample": "full c2 solve per step, single thread"},
+           "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n-lim", type=int, default=32)
+    ap.add_argument("--refine", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1302_6945_gb300 import tikh
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    P = workload(seed_offset=rank)
+    m, n = P["m"], P["n"]
+    col = torch.tensor(P["col"], dtype=torch.complex128, device=dev)
+    row = torch.tensor(P["row"], dtype=torch.complex128, device=dev)
+    b = torch.tensor(P["b"], dtype=torch.complex128, device=dev)
+    x = torch.empty(n, dtype=torch.complex128, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    plan = tikh.Plan(m, n, "c128", n_lim=args.n_lim, refine_steps=args.refine, stream=stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # 256 MB > 129 MB L2
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            plan.solve(col, row, b, P["lam"], x)
+    st = plan.stats()
+
+    # accuracy of the benchmarked solution: relative residual of the normal equations (FFT matvec in
+    # torch, outside the timed region)
+    def normal_residual(xv):
+        L = 1 << int(math.ceil(math.log2(m + 2 * n)))
+        a = torch.cat([row[1:].flip(0), col])  # a_{-(n-1)} .. a_{m-1}
+        A = torch.fft.fft(a, L)
+        Tx = torch.fft.ifft(A * torch.fft.fft(xv, L))[n - 1:n - 1 + m]
+        r = b - Tx
+        # T^H r: correlate with conj(a)
+        Ah = torch.fft.fft(a.conj().flip(0), L)
+        Thr = torch.fft.ifft(Ah * torch.fft.fft(r, L))[m - 1:m - 1 + n]
+        Thb = torch.fft.ifft(Ah * torch.fft.fft(b, L))[m - 1:m - 1 + n]
+        return float(torch.linalg.norm(Thr - P["lam"] * xv) / torch.linalg.norm(Thb))
+
+    res = normal_residual(x)
+
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with torch.cuda.stream(stream):
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            plan.solve(col, row, b, P["lam"], x, sync=False)
+            ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    plan.sync()
+    clocks = clk.stop()
+    step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
+    t_step = sum(step_ms) / len(step_ms)
+    t_max = t_step
+    if world > 1:
+        tt = torch.tensor([t_step], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+        dist.barrier()
+    value = world / (t_max / 1e3)
+
+    # e2e through the host-buffer entry point (pinned host arrays, copies inside the region)
+    hcol = torch.tensor(P["col"], dtype=torch.complex128).pin_memory().numpy()
+    hrow = torch.tensor(P["row"], dtype=torch.complex128).pin_memory().numpy()
+    hb = torch.tensor(P["b"], dtype=torch.complex128).pin_memory().numpy()
+    hx = torch.empty(n, dtype=torch.complex128).pin_memory().numpy()
+    plan.solve_host(hcol, hrow, hb, P["lam"], hx)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        plan.solve_host(hcol, hrow, hb, P["lam"], hx)
+    e2e_t = (time.perf_counter() - t0) / args.steps
+    e2e_v = 1.0 / e2e_t
+    if world > 1:
+        tt = torch.tensor([e2e_t], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_v = world / float(tt.item())
+
+    pk, pk_kind = peaks()
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        t0 = time.perf_counter()
+        xo, _ = oracle.solve(P["col"], P["row"], P["b"], P["lam"], nlim=args.n_lim)
+        tc = time.perf_counter() - t0
+        err = float(np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo))
+        cpu = {"value": 1.0 / tc, "unit": "solves/s", "cores": 1, "kind": "oracle",
+               "sample": "one full c2 solve (m=98304, n=65536), single thread", "gpu_vs_oracle_rel_err": err}
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": t_max, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+               "config": {"workload": "c2 deconvolution m=98304 n=65536 complex128 lambda=1e-4", "m": m, "n": n,
+                          "N": st["N"], "p": st["p"], "M": st["M"], "n_lim": args.n_lim,
+                          "refine_steps": args.refine, "precision": "fp64",
+                          "l2": "256 MB flush between steps; working set > L2"},
+               "n_solves_per_s": value * n,
+               "normal_eq_rel_residual": res,
+               "e2e": {"value": e2e_v, "unit": "solves/s", "h2d_bytes_per_step": 16 * (2 * m + n),
+                       "d2h_bytes_per_step": 16 * n},
+               "gpu_launches": int(st["kernel_launches"]) * args.steps,
+               "clocks": clocks,
+               "peaks": {"hbm_gbs": pk.get("hbm_gbs"), "kind": pk_kind},
+               "cpu_baseline": cpu}
+        print(json.dumps(out))
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,147 @@
+/*
+ * tikh.h -- C-ABI of the GB300 superfast Tikhonov solver.
+ *
+ * Solves the l2-penalised Tikhonov problem of Turnes, Balcan & Romberg, "Superfast Tikhonov
+ * Regularization of Toeplitz Systems" (arXiv 1302.6945):
+ *
+ *     x = argmin_x ||T x - b||^2 + lambda ||x||^2 = (T^H T + lambda I)^{-1} T^H b      (Eq. (tik), (tiksol))
+ *
+ * for an m x n Toeplitz T = [a_{i-j}] (Sec. 2, l2-norm penalisation with L = beta I, lambda = |beta|^2),
+ * by the extension-and-transformation of Sec. 3-4.1 and the divide-and-conquer tangential
+ * interpolation of Sec. 4.3-5 (Algorithm 1 with paired interleaving, Algorithm 2 sizing).
+ * Every arithmetic step runs in CUDA kernels on the plan's stream.
+ *
+ * Conventions
+ *  - col[d] = a_d (d = 0..m-1, first column of T); row[d] = a_{-d} (d = 1..n-1, first row of T;
+ *    row[0] is ignored).
+ *  - TIKH_R64: col, row, b, x are real float64 arrays; TIKH_C128: interleaved complex128 (re, im).
+ *  - Pointers passed to tikh_solve / tikh_solve_normal are DEVICE pointers, caller-owned, contiguous,
+ *    16-byte aligned, valid until the stream reaches the end of the call's work.  tikh_solve_host
+ *    takes HOST pointers and copies through the plan's staging buffers.
+ *  - The plan owns all device workspace; nothing else is allocated per call.
+ *  - lambda must be finite and > 0.  m, n >= 1; m < n is solved through the identity
+ *    (T^H T + lambda I)^{-1} T^H b = T^H (T T^H + lambda I)^{-1} b on the tall matrix T^H.
+ *
+ * Errors: every int-returning call returns TIKH_OK (0) or a negative TIKH_E* code; nothing aborts,
+ * traps or exits.  Device-side failures are recorded in the plan's status word and returned by the
+ * next synchronising call (tikh_solve, tikh_solve_host, tikh_sync).
+ */
+#ifndef TIKH_H
+#define TIKH_H
+#include <stdint.h>
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TIKH_OK 0
+#define TIKH_EINVAL (-1)        /* bad argument (sizes, lambda, dtype, null pointer) */
+#define TIKH_ENOMEM (-2)        /* device or host allocation failed */
+#define TIKH_ECUDA (-3)         /* a CUDA runtime call failed */
+#define TIKH_ENUMERIC (-4)      /* final tau-degree pattern is not one 0 and four 1s, or a non-finite value */
+#define TIKH_EDIFFICULT (-5)    /* more deferred (difficult) conditions than the plan can hold */
+#define TIKH_ENOTCONVERGED (-6) /* iterative refinement did not reach its tolerance */
+#define TIKH_ETIMEOUT (-7)      /* a bounded device wait gave up */
+#define TIKH_EDEGREE (-8)       /* a basis degree exceeded its planned transform length (retried internally) */
+
+typedef enum { TIKH_R64 = 0, TIKH_C128 = 1 } tikh_dtype;
+typedef enum { TIKH_PREC_FP64 = 0 } tikh_prec;
+
+typedef struct tikh_plan_s* tikh_plan;
+
+/* Planner options (NULL -> defaults).
+ *  n_lim     leaf cutoff N_lim (Sec. 5.2): leaves hold at most 2M <= n_lim (+ rounding) conditions.
+ *            Default 32; valid 4..64.  Large serial leaves lose accuracy.
+ *  m_min     lower bound on M in Algorithm 2 (forces a larger extension k); 0 = none.
+ *  fill      extension entries "similar in value" (Sec. 5.2): 0 = seeded pseudo-random of the
+ *            coefficients' size (default), 1 = linear ramp between a_{m-1} and a_{-(n-1)}.
+ *  eps_diff  difficult-point threshold (Sec. 4.4): a leaf defers its remaining conditions when the
+ *            best one has |r_pivot| < eps_diff ||r||_2.  Default 1e-8.
+ *  max_difficult  capacity of the deferred-condition list (default 4096).
+ *  refine_steps   iterative-refinement corrections after the direct solve (default 0 = the plain
+ *            method; 0..8).  Each correction recomputes r = y - (T^H T + lambda I) x by FFT matrix-
+ *            vector products (Sec. 6.3) and solves for the correction with the same algorithm
+ *            (Sec. 6.2: the result "can be further improved with iterative refinement").
+ */
+typedef struct {
+  int n_lim;
+  int m_min;
+  int fill;
+  double eps_diff;
+  int max_difficult;
+  int refine_steps;
+} tikh_opts;
+
+typedef struct {
+  int64_t N, M, k; /* nodes N = 2^p M, extension k = N - (m+n-1) of the core (tall) problem */
+  int p;           /* paired-interleaving splits; 2^p leaves */
+  int dual;        /* 1: m < n solved through T^H */
+  int64_t n_difficult; /* conditions deferred to the end in the last solve */
+  int delta[5];        /* final tau-degrees of the basis columns in the last solve */
+  int jstar;           /* column holding the solution */
+  int retries;         /* internal re-runs after TIKH_EDEGREE */
+  int64_t kernel_launches; /* kernels enqueued by the last solve */
+  int64_t workspace_bytes; /* device bytes owned by the plan */
+  int refine_steps;        /* corrections applied in the last solve */
+  double rel_residual;     /* ||y - (T^H T + lambda I) x|| / ||y|| after refinement (-1 if none) */
+} tikh_stats;
+
+/* Build a plan for an m x n problem: sizing by Algorithm 2 (Sec. 5.2), the recursion schedule of
+ * Algorithm 1 (Sec. 4.3, 5.1), transform lengths and all device workspace.  stream is a
+ * cudaStream_t (NULL = legacy default stream); every later call enqueues on it.
+ * Returns TIKH_EINVAL for m < 1, n < 1, unknown dtype/prec or invalid opts; TIKH_ENOMEM / TIKH_ECUDA
+ * when the workspace cannot be allocated.  On failure *out is NULL. */
+int tikh_plan_create(tikh_plan* out, int64_t m, int64_t n, int dtype, int prec, const tikh_opts* opts,
+                     void* stream);
+
+/* Tikhonov solution x (n entries) from device arrays col (m), row (n), b (m).  Enqueues the whole
+ * path (Sec. 3-5: extension, DFT transformation, recursive basis construction, difficult points,
+ * extraction x(z) = B*_1^{(j)}(z) / B*_5^{(j)}) and then synchronises the stream to report the
+ * device status.  Returns TIKH_ENUMERIC / TIKH_EDIFFICULT when the device reported a failure. */
+int tikh_solve(tikh_plan plan, const void* col, const void* row, const void* b, double lambda, void* x);
+
+/* As tikh_solve, without the final synchronisation: the status of this solve is returned by the
+ * next tikh_sync.  A TIKH_EDEGREE status cannot be retried here; use tikh_solve for that. */
+int tikh_solve_async(tikh_plan plan, const void* col, const void* row, const void* b, double lambda, void* x);
+
+/* x = (T^H T + lambda I)^{-1} y for a given right-hand side y (n entries, device), the form the
+ * paper's experiments solve (Sec. 6.1).  Requires m >= n (the tall, stable formulation). */
+int tikh_solve_normal(tikh_plan plan, const void* col, const void* row, const void* y, double lambda, void* x);
+
+/* tikh_solve with HOST arrays: copies col, row, b to the plan's device staging buffers, solves and
+ * copies x back, all on the plan's stream; returns after x is in host memory. */
+int tikh_solve_host(tikh_plan plan, const void* col, const void* row, const void* b, double lambda, void* x);
+
+/* Wait for the plan's stream and return (then clear) the device status of the solves since the last
+ * synchronising call. */
+int tikh_sync(tikh_plan plan);
+
+/* Statistics of the plan and of the last synchronised solve. */
+int tikh_get_stats(tikh_plan plan, tikh_stats* out);
+
+/* Release all device and host memory of the plan.  NULL is ignored. */
+void tikh_plan_destroy(tikh_plan plan);
+
+/* Static description of a status code. */
+const char* tikh_strerror(int status);
+
+/* ---- test hooks: one building block on caller data (device pointers), for stage-wise parity ---- */
+
+/* In-place DFT of n complex128 values (device): X_k = sum_j x_j exp(sign 2 pi i jk / n), sign = +1
+ * evaluates the coefficient vector at the n-th roots of unity (Sec. 4.1, Eq. (vandprod)); unnormalised.
+ * n must factor into 2, 3, 5, 7 and be at most 4096^2.  Synchronises the stream; TIKH_EINVAL otherwise. */
+int tikh_test_fft(int64_t n, void* data, int sign, void* stream);
+
+/* One leaf of Algorithm 1: the serial single-point construction of Eq. (spbasis) (Sec. 4.3) with
+ * condition pivoting and difficult-point deferral (Sec. 4.4) over K <= 64 conditions.
+ * Inputs (device): sigma (K complex128 nodes), r (K x 5 complex128 residual rows), delta_in (5 ints,
+ * starting tau-degrees), eps (deferral threshold).  Outputs (device): B (25 entries x (K+1) complex128,
+ * entry (i,j) at (5i+j)(K+1), unscaled), len (25 ints, trimmed to the degree bounds), delta_out (5 ints),
+ * order / pivot (K ints: position and pivot column processed at each step, -1 after the last),
+ * deferred (K int64 positions, unordered) and n_def (1 int).  Synchronises the stream. */
+int tikh_test_leaf(int K, const void* sigma, const void* r, const int* delta_in, double eps, void* B, int* len,
+                   int* delta_out, int* order, int* pivot, int64_t* deferred, int* n_def, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,424 @@
+// api.cu -- planning, workspace and the C-ABI entry points of include/tikh.h.
+//
+// Planning follows Algorithm 2 (OptExtend, Sec. 5.2) for two condition sets with paired
+// interleaving: halve M while 2M > N_lim, make M even, and round it up to a 7-smooth value so every
+// transform length factors into radices 2, 3, 4, 5, 7, 8; N = 2^p M, k = N - (m+n-1).  The DFS of
+// Algorithm 1 is laid out once on the host as a list of steps; product transform lengths come from
+// a water-filling model of the tau-degrees (every condition raises the lowest column) plus slack,
+// and the device checks the real degrees against them (TIKH_EDEGREE triggers a re-plan and re-run).
+#include <cstdio>
+#include <cstdlib>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "internal.h"
+
+using namespace tikh;
+
+struct tikh_plan_s {
+  Plan P;
+};
+
+namespace {
+
+bool is_5smooth(int64_t v) {
+  if (v < 1) return false;
+  for (int q : {2, 3, 5})
+    while (v % q == 0) v /= q;
+  return v == 1;
+}
+bool is_7smooth(int64_t v) {
+  if (v < 1) return false;
+  for (int q : {2, 3, 5, 7})
+    while (v % q == 0) v /= q;
+  return v == 1;
+}
+int64_t smooth_at_least(int64_t v) {
+  if (v < 2) v = 2;
+  while (!is_5smooth(v)) ++v;
+  return v;
+}
+
+void* dalloc(Plan& P, size_t bytes, int& err) {
+  if (err) return nullptr;
+  void* p = nullptr;
+  if (bytes == 0) bytes = 16;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    err = TIKH_ENOMEM;
+    return nullptr;
+  }
+  P.allocs.push_back(p);
+  P.bytes += (int64_t)bytes;
+  return p;
+}
+
+cd* twiddle(Plan& P, int64_t L, int& err) {
+  auto it = P.twiddle_of_len.find(L);
+  if (it != P.twiddle_of_len.end()) return it->second;
+  cd* t = (cd*)dalloc(P, sizeof(cd) * (size_t)L, err);
+  if (err) return nullptr;
+  if (launch_twiddle(t, L, P.stream) < 0) { err = TIKH_ECUDA; return nullptr; }
+  P.twiddle_of_len[L] = t;
+  return t;
+}
+
+int fft_index(Plan& P, int64_t L, int& err) {
+  auto it = P.fft_of_len.find(L);
+  if (it != P.fft_of_len.end()) return it->second;
+  FftPlan f;
+  f.L = L;
+  if (L <= FFT_TILE_MAX) {
+    if (!fft_factor((int)L, f.d1)) { err = TIKH_EINVAL; return -1; }
+    f.d1.tw = twiddle(P, L, err);
+  } else {
+    int64_t L1, L2;
+    if (!fft_split(L, L1, L2)) { err = TIKH_EINVAL; return -1; }
+    f.four = true;
+    f.L1 = L1;
+    f.L2 = L2;
+    fft_factor((int)L1, f.d1);
+    fft_factor((int)L2, f.d2);
+    f.d1.tw = twiddle(P, L1, err);
+    f.d2.tw = twiddle(P, L2, err);
+    f.twL = twiddle(P, L, err);
+  }
+  if (err) return -1;
+  P.ffts.push_back(f);
+  P.fft_of_len[L] = (int)P.ffts.size() - 1;
+  return (int)P.ffts.size() - 1;
+}
+
+// same bound as the device: tau-degree bound for pivoted columns, accumulation bound otherwise
+int entry_bound_host(const int* din, const int* dout, int i, int j) {
+  int amax = 0;
+  bool have = false;
+  for (int c = 0; c < 5; ++c)
+    if (dout[c] > din[c]) { amax = have ? std::max(amax, dout[c]) : dout[c]; have = true; }
+  if (dout[j] > din[j]) return dout[j] - din[i];
+  int acc = have ? amax - din[i] : -1;
+  if (i == j && acc < 0) acc = 0;
+  return std::min(acc, dout[j] - din[i]);
+}
+
+void waterfill(int* d, int64_t C) {
+  for (int64_t c = 0; c < C; ++c) {
+    int j = 0;
+    for (int i = 1; i < 5; ++i)
+      if (d[i] < d[j]) j = i;
+    d[j] += 1;
+  }
+}
+
+void build_steps(Plan& P, int depth, int64_t a, int64_t s, int64_t L, int side, int* sd, uint64_t& pending,
+                 int64_t slack, int& err) {
+  if (err) return;
+  if (depth == P.p) {
+    Step st{STEP_LEAF, depth, side, a, s, L, -1, 0, pending};
+    pending = 0;
+    waterfill(sd, 4 * L);
+    P.sched.push_back(st);
+    return;
+  }
+  int din[5];
+  memcpy(din, sd, sizeof(din));
+  pending |= (1ULL << depth);
+  build_steps(P, depth + 1, a, 2 * s, L / 2, 0, sd, pending, slack, err);
+  Step ev{STEP_EVAL, depth, side, a, s, L, fft_index(P, L / 2, err), 0, 0};
+  P.sched.push_back(ev);
+  P.Lrmax = std::max(P.Lrmax, L / 2);
+  build_steps(P, depth + 1, a + s, 2 * s, L / 2, 1, sd, pending, slack, err);
+  int D = -1;
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j < 5; ++j) D = std::max(D, entry_bound_host(din, sd, i, j));
+  int64_t Pn = smooth_at_least((int64_t)D + 1 + slack);
+  Step pr{STEP_PROD, depth, side, a, s, L, fft_index(P, Pn, err), Pn, 0};
+  P.sched.push_back(pr);
+  P.Pmax = std::max(P.Pmax, Pn);
+}
+
+// (re)build the schedule and the product scratch for the current slack
+int make_schedule(Plan& P) {
+  int err = 0;
+  P.sched.clear();
+  int sd[5] = {-(int)(P.cn - 1), -(int)(P.cm - 1), -(int)(P.cm + P.k - 2), -(int)(P.cn + P.k - 2), 0};
+  uint64_t pending = 0;
+  int64_t oldP = P.Pmax;
+  int64_t slack = (int64_t)P.slack_mult * (P.k + 2 * P.M + 4);
+  build_steps(P, 0, 0, 2, P.N / 2, 0, sd, pending, slack, err);
+  if (err) return err;
+  if (P.Pmax > oldP || !P.FA) {
+    size_t n25 = 25 * (size_t)std::max<int64_t>(P.Pmax, 1);
+    P.FA = (cd*)dalloc(P, sizeof(cd) * n25, err);
+    P.FB = (cd*)dalloc(P, sizeof(cd) * n25, err);
+    P.FC = (cd*)dalloc(P, sizeof(cd) * n25, err);
+    P.ptmp = (cd*)dalloc(P, sizeof(cd) * 2 * n25, err);
+  }
+  // basis capacity per depth: a product's entries are at most P long (P exceeds every entry degree
+  // bound of the node, which can exceed the node's condition count by the spread of delta_in);
+  // leaves hold at most K + 1 coefficients; the root also absorbs the difficult points
+  int64_t need[MAX_DEPTH] = {0};
+  need[P.p] = 2 * P.M + 1;
+  for (const Step& st : P.sched)
+    if (st.kind == STEP_PROD) need[st.depth] = std::max(need[st.depth], st.P);
+  need[0] += std::min(P.opts.max_difficult, 4096) + 2;
+  for (int d = 0; d <= P.p && !err; ++d)
+    for (int side = 0; side < (d == 0 ? 1 : 2); ++side) {
+      BasisBuf& B = P.buf[d][side];
+      if (B.cap >= need[d]) continue;
+      B.cap = need[d];
+      B.c = (cd*)dalloc(P, sizeof(cd) * 25 * (size_t)B.cap, err);
+      if (!B.len) B.len = (int*)dalloc(P, sizeof(int) * 32, err);
+      if (!B.colmax) B.colmax = (unsigned long long*)dalloc(P, sizeof(unsigned long long) * 8, err);
+      if (d == 0) P.dscr = (cd*)dalloc(P, sizeof(cd) * (5 * (size_t)B.cap + (size_t)P.opts.max_difficult), err);
+    }
+  return err;
+}
+
+int status_to_code(int st) {
+  if (st & ST_DEGREE) return TIKH_EDEGREE;
+  if (st & ST_DIFFICULT) return TIKH_EDIFFICULT;
+  if (st & ST_NUMERIC) return TIKH_ENUMERIC;
+  return TIKH_OK;
+}
+
+// one superfast solve of the core system with right-hand side y, solution into out
+int enqueue_core(Plan& P, const cd* y, double lam, cd* out, int64_t& nl) {
+  int r;
+  if ((r = launch_conditions(P, y, lam)) < 0) return r;
+  nl += r;
+  for (const Step& st : P.sched) {
+    if (st.kind == STEP_LEAF) r = launch_leaf(P, st, 0);
+    else if (st.kind == STEP_EVAL) r = launch_eval(P, st);
+    else r = launch_prod(P, st);
+    if (r < 0) return r;
+    nl += r;
+  }
+  if ((r = launch_difficult(P)) < 0) return r;
+  nl += r;
+  if ((r = launch_extract(P, out)) < 0) return r;
+  nl += r;
+  return TIKH_OK;
+}
+
+int enqueue_solve(Plan& P, const void* col, const void* row, const void* rhs, int rhs_is_y, double lam, void* x) {
+  int64_t nl = 0;
+  int r;
+  if (cudaMemsetAsync(P.status, 0, sizeof(int), P.stream) != cudaSuccess) return TIKH_ECUDA;
+  if ((r = launch_spectrum(P, col, row)) < 0) return r;
+  nl += r;
+  // for m < n the core problem (T T^H + lam I) v = b takes b itself as its right-hand side
+  if ((r = launch_rhs(P, rhs, P.dual ? 1 : rhs_is_y)) < 0) return r;
+  nl += r;
+  if ((r = enqueue_core(P, P.ybuf, lam, P.xcore, nl)) < 0) return r;
+  // iterative refinement on the core system: v <- v + A^{-1}(y - A v)
+  for (int it = 0; it < P.opts.refine_steps; ++it) {
+    if ((r = launch_residual(P, P.ybuf, P.xcore, P.rbuf, lam)) < 0) return r;
+    nl += r;
+    if ((r = enqueue_core(P, P.rbuf, lam, P.dx, nl)) < 0) return r;
+    if ((r = launch_axpy(P, P.xcore, P.dx)) < 0) return r;
+    nl += r;
+  }
+  if (P.opts.refine_steps > 0) {  // residual of the refined solution, reported in the stats
+    if ((r = launch_residual(P, P.ybuf, P.xcore, P.rbuf, lam)) < 0) return r;
+    nl += r;
+  }
+  if ((r = launch_output(P, P.xcore, x)) < 0) return r;
+  nl += r;
+  P.launches = nl;
+  return TIKH_OK;
+}
+
+int sync_status(Plan& P) {
+  if (cudaStreamSynchronize(P.stream) != cudaSuccess) { cudaGetLastError(); return TIKH_ECUDA; }
+  int st = 0, nd = 0, dl[5];
+  if (cudaMemcpy(&st, P.status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return TIKH_ECUDA;
+  cudaMemcpy(&nd, P.ndiff, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaMemcpy(dl, P.delta, sizeof(dl), cudaMemcpyDeviceToHost);
+  P.last.n_difficult = nd;
+  memcpy(P.last.delta, dl, sizeof(dl));
+  P.last.jstar = -1;
+  for (int j = 0; j < 5; ++j)
+    if (dl[j] == 0) P.last.jstar = j;
+  P.last.kernel_launches = P.launches;
+  P.last.refine_steps = P.opts.refine_steps;
+  P.last.rel_residual = -1.0;
+  if (P.opts.refine_steps > 0) {
+    double nr[2] = {0.0, 0.0};
+    cudaMemcpy(nr, P.norms, sizeof(nr), cudaMemcpyDeviceToHost);
+    P.last.rel_residual = nr[1] > 0.0 ? sqrt(nr[0] / nr[1]) : sqrt(nr[0]);
+  }
+  int zero = 0;
+  cudaMemcpy(P.status, &zero, sizeof(int), cudaMemcpyHostToDevice);
+  return status_to_code(st);
+}
+
+int solve_with_retry(Plan& P, const void* col, const void* row, const void* rhs, int rhs_is_y, double lam, void* x,
+                     bool host_copy_back, void* x_host, size_t xbytes) {
+  P.last.retries = 0;
+  for (int attempt = 0;; ++attempt) {
+    int rc = enqueue_solve(P, col, row, rhs, rhs_is_y, lam, x);
+    if (rc) return rc;
+    if (host_copy_back && cudaMemcpyAsync(x_host, x, xbytes, cudaMemcpyDeviceToHost, P.stream) != cudaSuccess)
+      return TIKH_ECUDA;
+    rc = sync_status(P);
+    if (rc != TIKH_EDEGREE || attempt >= 3) return rc;
+    P.slack_mult *= 16;
+    P.last.retries = attempt + 1;
+    if ((rc = make_schedule(P))) return rc;
+  }
+}
+
+bool valid_lambda(double lam) { return lam > 0.0 && lam < 1e300; }
+
+}  // namespace
+
+extern "C" {
+
+int tikh_plan_create(tikh_plan* out, int64_t m, int64_t n, int dtype, int prec, const tikh_opts* opts, void* stream) {
+  if (!out) return TIKH_EINVAL;
+  *out = nullptr;
+  if (m < 1 || n < 1 || (dtype != TIKH_R64 && dtype != TIKH_C128) || prec != TIKH_PREC_FP64) return TIKH_EINVAL;
+  tikh_opts o{32, 0, 0, 1e-8, 4096, 0};
+  if (opts) o = *opts;
+  if (o.n_lim < 4 || o.n_lim > 64 || o.m_min < 0 || o.m_min > 32 || (o.fill != 0 && o.fill != 1) ||
+      !(o.eps_diff >= 0.0) || o.max_difficult < 1 || o.max_difficult > (1 << 20) || o.refine_steps < 0 ||
+      o.refine_steps > 8)
+    return TIKH_EINVAL;
+  tikh_plan h = new (std::nothrow) tikh_plan_s;
+  if (!h) return TIKH_ENOMEM;
+  Plan& P = h->P;
+  P.m = m;
+  P.n = n;
+  P.dtype = dtype;
+  P.opts = o;
+  P.stream = (cudaStream_t)stream;
+  P.dual = m < n ? 1 : 0;
+  P.cm = P.dual ? n : m;
+  P.cn = P.dual ? m : n;
+  // Algorithm 2 (reading: two condition sets, paired interleaving; M even, 7-smooth)
+  int64_t Nt = P.cm + P.cn - 1, Mv = Nt;
+  int pv = 0;
+  while (2 * Mv > o.n_lim) { ++pv; Mv = (Mv + 1) / 2; }
+  if (Mv % 2) ++Mv;
+  if (Mv < o.m_min) Mv = o.m_min + (o.m_min % 2);
+  while (!is_7smooth(Mv)) Mv += 2;
+  P.M = Mv;
+  P.p = pv;
+  P.N = Mv << pv;
+  P.k = P.N - Nt;
+  if (pv >= MAX_DEPTH - 1 || 4 * (Mv / 2) > 64 || P.N > (int64_t)1 << 31) { delete h; return TIKH_EINVAL; }
+
+  int err = 0;
+  size_t N = (size_t)P.N;
+  if (fft_index(P, P.N, err) < 0 && !err) err = TIKH_EINVAL;
+  P.wN = P.twiddle_of_len[P.N];
+  P.specT = (cd*)dalloc(P, sizeof(cd) * N, err);
+  P.work = (cd*)dalloc(P, sizeof(cd) * N, err);
+  P.work2 = (cd*)dalloc(P, sizeof(cd) * N, err);
+  P.ftmpN = (cd*)dalloc(P, sizeof(cd) * N, err);
+  P.R = (cd*)dalloc(P, sizeof(cd) * 10 * N, err);
+  P.Phi = (cd*)dalloc(P, sizeof(cd) * 10 * N, err);
+  P.delta = (int*)dalloc(P, sizeof(int) * 8, err);
+  P.dstack = (int*)dalloc(P, sizeof(int) * 5 * MAX_DEPTH, err);
+  P.status = (int*)dalloc(P, sizeof(int) * 4, err);
+  P.ndiff = (int*)dalloc(P, sizeof(int) * 4, err);
+  P.diff = (int64_t*)dalloc(P, sizeof(int64_t) * (size_t)o.max_difficult, err);
+  P.diffr = (cd*)dalloc(P, sizeof(cd) * 5 * (size_t)o.max_difficult, err);
+  P.peak = (unsigned long long*)dalloc(P, 16, err);
+  if (!err) err = make_schedule(P);
+  if (!err) {
+    size_t nl = 50 * (size_t)std::max<int64_t>(P.Lrmax, 1);
+    P.evalv = (cd*)dalloc(P, sizeof(cd) * nl, err);
+    P.etmp = (cd*)dalloc(P, sizeof(cd) * nl, err);
+    P.ybuf = (cd*)dalloc(P, sizeof(cd) * (size_t)P.cn, err);
+    P.rbuf = (cd*)dalloc(P, sizeof(cd) * (size_t)P.cn, err);
+    P.xcore = (cd*)dalloc(P, sizeof(cd) * (size_t)P.cn, err);
+    P.dx = (cd*)dalloc(P, sizeof(cd) * (size_t)P.cn, err);
+    P.norms = (double*)dalloc(P, sizeof(double) * 4, err);
+    size_t es = dtype == TIKH_C128 ? 16 : 8;
+    P.d_in = dalloc(P, es * (size_t)(2 * m + 2 * n) + 64, err);
+  }
+  if (!err && cudaStreamSynchronize(P.stream) != cudaSuccess) err = TIKH_ECUDA;
+  if (err) {
+    cudaGetLastError();
+    for (void* p : P.allocs) cudaFree(p);
+    delete h;
+    return err;
+  }
+  P.last.N = P.N;
+  P.last.M = P.M;
+  P.last.k = P.k;
+  P.last.p = P.p;
+  P.last.dual = P.dual;
+  *out = h;
+  return TIKH_OK;
+}
+
+int tikh_solve(tikh_plan h, const void* col, const void* row, const void* b, double lambda, void* x) {
+  if (!h || !col || !row || !b || !x || !valid_lambda(lambda)) return TIKH_EINVAL;
+  return solve_with_retry(h->P, col, row, b, 0, lambda, x, false, nullptr, 0);
+}
+
+int tikh_solve_async(tikh_plan h, const void* col, const void* row, const void* b, double lambda, void* x) {
+  if (!h || !col || !row || !b || !x || !valid_lambda(lambda)) return TIKH_EINVAL;
+  return enqueue_solve(h->P, col, row, b, 0, lambda, x);
+}
+
+int tikh_solve_normal(tikh_plan h, const void* col, const void* row, const void* y, double lambda, void* x) {
+  if (!h || !col || !row || !y || !x || !valid_lambda(lambda) || h->P.dual) return TIKH_EINVAL;
+  return solve_with_retry(h->P, col, row, y, 1, lambda, x, false, nullptr, 0);
+}
+
+int tikh_solve_host(tikh_plan h, const void* col, const void* row, const void* b, double lambda, void* x) {
+  if (!h || !col || !row || !b || !x || !valid_lambda(lambda)) return TIKH_EINVAL;
+  Plan& P = h->P;
+  size_t es = P.dtype == TIKH_C128 ? 16 : 8;
+  char* base = (char*)P.d_in;
+  char* dcol = base;
+  char* drow = dcol + es * P.m;
+  char* db = drow + es * P.n;
+  char* dx = db + es * P.m;
+  if (cudaMemcpyAsync(dcol, col, es * P.m, cudaMemcpyHostToDevice, P.stream) != cudaSuccess ||
+      cudaMemcpyAsync(drow, row, es * P.n, cudaMemcpyHostToDevice, P.stream) != cudaSuccess ||
+      cudaMemcpyAsync(db, b, es * P.m, cudaMemcpyHostToDevice, P.stream) != cudaSuccess)
+    return TIKH_ECUDA;
+  return solve_with_retry(P, dcol, drow, db, 0, lambda, dx, true, x, es * P.n);
+}
+
+int tikh_sync(tikh_plan h) {
+  if (!h) return TIKH_EINVAL;
+  return sync_status(h->P);
+}
+
+int tikh_get_stats(tikh_plan h, tikh_stats* out) {
+  if (!h || !out) return TIKH_EINVAL;
+  *out = h->P.last;
+  out->workspace_bytes = h->P.bytes;
+  return TIKH_OK;
+}
+
+void tikh_plan_destroy(tikh_plan h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->P.stream);
+  for (void* p : h->P.allocs) cudaFree(p);
+  delete h;
+}
+
+const char* tikh_strerror(int s) {
+  switch (s) {
+    case TIKH_OK: return "ok";
+    case TIKH_EINVAL: return "invalid argument";
+    case TIKH_ENOMEM: return "out of device memory";
+    case TIKH_ECUDA: return "CUDA runtime error";
+    case TIKH_ENUMERIC: return "numerical failure (degree pattern or non-finite value)";
+    case TIKH_EDIFFICULT: return "too many difficult points";
+    case TIKH_ENOTCONVERGED: return "refinement did not converge";
+    case TIKH_ETIMEOUT: return "device wait timed out";
+    case TIKH_EDEGREE: return "basis degree exceeded the planned transform length";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

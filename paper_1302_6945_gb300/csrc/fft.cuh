@@ -1,0 +1,333 @@
+// fft.cuh -- batched mixed-radix Stockham FFT (radices 2, 3, 4, 5, 7, 8) in shared memory, FP64.
+//
+// Transform:  X_k = sum_j x_j exp(sign 2 pi i j k / L).  sign = +1 evaluates a polynomial with
+// coefficients x at the L-th roots of unity omega_k = exp(+2 pi i k / L) (Sec. 4.1, Eq. (vandprod));
+// sign = -1 is the unnormalised inverse.
+//
+// Each CTA holds `tb` transforms of length L <= FFT_TILE_MAX in shared memory (element j of transform
+// t at sm[j * tb + t]) and runs all Stockham stages there; loads and stores go through functors so
+// that packing, twisting, folding, pointwise products and trimming fuse into the transform.  Longer
+// transforms use the four-step split L = L1 * L2: a column pass (L2 * batch transforms of length L1,
+// inter-pass twiddles applied on store) and a row pass (L1 * batch transforms of length L2), both with
+// the transform index as the contiguous dimension so global accesses coalesce.
+#pragma once
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+
+namespace tikh {
+
+constexpr int FFT_TILE_MAX = 4096;
+constexpr int FFT_MAX_STAGES = 24;
+
+struct FftDesc {
+  int L;
+  int nst;
+  unsigned char rad[FFT_MAX_STAGES];
+  const cd* tw;  // tw[t] = exp(+2 pi i t / L), t < L
+};
+
+struct FftPlan {
+  int64_t L = 0;
+  bool four = false;
+  int64_t L1 = 0, L2 = 0;
+  FftDesc d1{}, d2{};
+  const cd* twL = nullptr;  // table of length L (four-step inter-pass twiddles)
+};
+
+// ---------------------------------------------------------------------------------------------
+// in-register DFTs of size R
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ cd mul_i(cd a, int sign) { return sign > 0 ? mkc(-a.y, a.x) : mkc(a.y, -a.x); }
+
+template <int R>
+__device__ __forceinline__ void dft_r(cd* v, int sign);
+
+template <>
+__device__ __forceinline__ void dft_r<2>(cd* v, int) {
+  cd a = v[0], b = v[1];
+  v[0] = cadd(a, b);
+  v[1] = csub(a, b);
+}
+
+template <>
+__device__ __forceinline__ void dft_r<3>(cd* v, int sign) {
+  const double h = 0.86602540378443864676;  // sin(2 pi / 3)
+  cd a = v[0], t1 = cadd(v[1], v[2]), d = csub(v[1], v[2]);
+  cd t2 = mkc(a.x - 0.5 * t1.x, a.y - 0.5 * t1.y);
+  cd t3 = mul_i(cscale(d, h), sign);
+  v[0] = cadd(a, t1);
+  v[1] = cadd(t2, t3);
+  v[2] = csub(t2, t3);
+}
+
+template <>
+__device__ __forceinline__ void dft_r<4>(cd* v, int sign) {
+  cd t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+  cd t2 = cadd(v[1], v[3]), t3 = mul_i(csub(v[1], v[3]), sign);
+  v[0] = cadd(t0, t2);
+  v[1] = cadd(t1, t3);
+  v[2] = csub(t0, t2);
+  v[3] = csub(t1, t3);
+}
+
+template <>
+__device__ __forceinline__ void dft_r<5>(cd* v, int sign) {
+  const double c1 = 0.30901699437494742410;   // cos(2 pi / 5)
+  const double c2 = -0.80901699437494742410;  // cos(4 pi / 5)
+  const double s1 = 0.95105651629515357212;   // sin(2 pi / 5)
+  const double s2 = 0.58778525229247312917;   // sin(4 pi / 5)
+  cd a = v[0];
+  cd t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]), t3 = csub(v[1], v[4]), t4 = csub(v[2], v[3]);
+  cd p1 = mkc(a.x + c1 * t1.x + c2 * t2.x, a.y + c1 * t1.y + c2 * t2.y);
+  cd p2 = mkc(a.x + c2 * t1.x + c1 * t2.x, a.y + c2 * t1.y + c1 * t2.y);
+  cd q1 = mul_i(mkc(s1 * t3.x + s2 * t4.x, s1 * t3.y + s2 * t4.y), sign);
+  cd q2 = mul_i(mkc(s2 * t3.x - s1 * t4.x, s2 * t3.y - s1 * t4.y), sign);
+  v[0] = cadd(a, cadd(t1, t2));
+  v[1] = cadd(p1, q1);
+  v[4] = csub(p1, q1);
+  v[2] = cadd(p2, q2);
+  v[3] = csub(p2, q2);
+}
+
+template <>
+__device__ __forceinline__ void dft_r<7>(cd* v, int sign) {
+  // pairs (v_j, v_{7-j}): X_k = a + sum_j [cos(2 pi jk/7) (v_j + v_{7-j}) + i sign sin(2 pi jk/7) (v_j - v_{7-j})]
+  const double c1 = 0.62348980185873353053, c2 = -0.22252093395631440429, c3 = -0.90096886790241912624;
+  const double s1 = 0.78183148246802980871, s2 = 0.97492791218182360702, s3 = 0.43388373911755812048;
+  cd a = v[0];
+  cd t1 = cadd(v[1], v[6]), t2 = cadd(v[2], v[5]), t3 = cadd(v[3], v[4]);
+  cd d1 = csub(v[1], v[6]), d2 = csub(v[2], v[5]), d3 = csub(v[3], v[4]);
+  cd p1 = mkc(a.x + c1 * t1.x + c2 * t2.x + c3 * t3.x, a.y + c1 * t1.y + c2 * t2.y + c3 * t3.y);
+  cd p2 = mkc(a.x + c2 * t1.x + c3 * t2.x + c1 * t3.x, a.y + c2 * t1.y + c3 * t2.y + c1 * t3.y);
+  cd p3 = mkc(a.x + c3 * t1.x + c1 * t2.x + c2 * t3.x, a.y + c3 * t1.y + c1 * t2.y + c2 * t3.y);
+  // sin(2 pi jk / 7) for k = 1: (s1, s2, s3); k = 2: (s2, -s3, -s1); k = 3: (s3, -s1, s2)
+  cd q1 = mul_i(mkc(s1 * d1.x + s2 * d2.x + s3 * d3.x, s1 * d1.y + s2 * d2.y + s3 * d3.y), sign);
+  cd q2 = mul_i(mkc(s2 * d1.x - s3 * d2.x - s1 * d3.x, s2 * d1.y - s3 * d2.y - s1 * d3.y), sign);
+  cd q3 = mul_i(mkc(s3 * d1.x - s1 * d2.x + s2 * d3.x, s3 * d1.y - s1 * d2.y + s2 * d3.y), sign);
+  v[0] = cadd(a, cadd(t1, cadd(t2, t3)));
+  v[1] = cadd(p1, q1);
+  v[6] = csub(p1, q1);
+  v[2] = cadd(p2, q2);
+  v[5] = csub(p2, q2);
+  v[3] = cadd(p3, q3);
+  v[4] = csub(p3, q3);
+}
+
+template <>
+__device__ __forceinline__ void dft_r<8>(cd* v, int sign) {
+  const double r = 0.70710678118654752440;  // 1 / sqrt(2)
+  cd e[4] = {v[0], v[2], v[4], v[6]};
+  cd o[4] = {v[1], v[3], v[5], v[7]};
+  dft_r<4>(e, sign);
+  dft_r<4>(o, sign);
+  // w8^k = exp(sign 2 pi i k / 8)
+  cd w1 = mkc(r, sign * r), w3 = mkc(-r, sign * r);
+  cd o1 = cmul(o[1], w1), o2 = mul_i(o[2], sign), o3 = cmul(o[3], w3);
+  v[0] = cadd(e[0], o[0]);
+  v[4] = csub(e[0], o[0]);
+  v[1] = cadd(e[1], o1);
+  v[5] = csub(e[1], o1);
+  v[2] = cadd(e[2], o2);
+  v[6] = csub(e[2], o2);
+  v[3] = cadd(e[3], o3);
+  v[7] = csub(e[3], o3);
+}
+
+// ---------------------------------------------------------------------------------------------
+// one Stockham stage of radix R on tb interleaved transforms of length L; Ns = product of the
+// radices already applied.  Requires blockDim.x * ceil(8 / R) * R >= tb * L.
+// ---------------------------------------------------------------------------------------------
+template <int R>
+__device__ __forceinline__ void stockham_stage(cd* sm, int L, int tb, int Ns, const cd* __restrict__ tw, int sign) {
+  constexpr int MAXB = (8 + R - 1) / R;
+  const int nb = L / R;
+  const int total = nb * tb;
+  const int tstride = L / (Ns * R);
+  cd v[MAXB][R];
+#pragma unroll
+  for (int c = 0; c < MAXB; ++c) {
+    int g = threadIdx.x + c * blockDim.x;
+    if (g < total) {
+      int t = g % tb, j = g / tb, k = j % Ns;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        cd x = sm[(j + r * nb) * tb + t];
+        if (r > 0 && k > 0) {
+          cd w = tw_at(tw, (int64_t)(r * k) * tstride);
+          if (sign < 0) w.y = -w.y;
+          x = cmul(x, w);
+        }
+        v[c][r] = x;
+      }
+      dft_r<R>(v[c], sign);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int c = 0; c < MAXB; ++c) {
+    int g = threadIdx.x + c * blockDim.x;
+    if (g < total) {
+      int t = g % tb, j = g / tb, k = j % Ns;
+      int base = (j / Ns) * Ns * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) sm[(base + r * Ns) * tb + t] = v[c][r];
+    }
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ void fft_smem(cd* sm, const FftDesc& d, int tb, int sign) {
+  int Ns = 1;
+  for (int s = 0; s < d.nst; ++s) {
+    switch (d.rad[s]) {
+      case 2: stockham_stage<2>(sm, d.L, tb, Ns, d.tw, sign); break;
+      case 3: stockham_stage<3>(sm, d.L, tb, Ns, d.tw, sign); break;
+      case 4: stockham_stage<4>(sm, d.L, tb, Ns, d.tw, sign); break;
+      case 5: stockham_stage<5>(sm, d.L, tb, Ns, d.tw, sign); break;
+      case 7: stockham_stage<7>(sm, d.L, tb, Ns, d.tw, sign); break;
+      default: stockham_stage<8>(sm, d.L, tb, Ns, d.tw, sign); break;
+    }
+    Ns *= d.rad[s];
+  }
+}
+
+// generic tile kernel: transforms b0 .. b0 + tb - 1 of `batch`, loader ld(b, j), storer st(b, k, v)
+template <class LD, class ST>
+__global__ void __launch_bounds__(1024) fft_tile_kernel(FftDesc d, int tb, int batch, int sign, int load_jfast,
+                                                        int store_jfast, LD ld, ST st) {
+  extern __shared__ cd sm[];
+  const int b0 = blockIdx.x * tb;
+  const int ntr = min(tb, batch - b0);
+  const int L = d.L, n = tb * L;
+  for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
+    int t, j;
+    if (load_jfast) { j = idx % L; t = idx / L; } else { t = idx % tb; j = idx / tb; }
+    sm[j * tb + t] = (t < ntr) ? ld(b0 + t, j) : mkc(0.0, 0.0);
+  }
+  __syncthreads();
+  fft_smem(sm, d, tb, sign);
+  for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
+    int t, j;
+    if (store_jfast) { j = idx % L; t = idx / L; } else { t = idx % tb; j = idx / tb; }
+    if (t < ntr) st(b0 + t, j, sm[j * tb + t]);
+  }
+}
+
+// four-step adapters ---------------------------------------------------------------------------
+template <class LD>
+struct ColLoad {  // transform bb = b * L2 + j2, element j1 -> user element j1 * L2 + j2 of transform b
+  LD ld;
+  int64_t L2;
+  __device__ cd operator()(int bb, int j1) const {
+    int64_t b = bb / L2, j2 = bb % L2;
+    return ld((int)b, j1 * L2 + j2);
+  }
+};
+struct ColStore {  // tmp[b * L + k1 * L2 + j2] = v * w_L^{sign j2 k1}
+  cd* tmp;
+  const cd* twL;
+  int64_t L, L2;
+  int sign;
+  __device__ void operator()(int bb, int k1, cd v) const {
+    int64_t b = bb / L2, j2 = bb % L2;
+    int64_t e = (j2 * (int64_t)k1) % L;
+    cd w = tw_at(twL, e);
+    if (sign < 0) w.y = -w.y;
+    tmp[b * L + (int64_t)k1 * L2 + j2] = cmul(v, w);
+  }
+};
+struct RowLoad {  // transform bb = b * L1 + k1, element j2 -> tmp[b * L + k1 * L2 + j2]
+  const cd* tmp;
+  int64_t L, L1, L2;
+  __device__ cd operator()(int bb, int j2) const {
+    int64_t b = bb / L1, k1 = bb % L1;
+    return tmp[b * L + k1 * L2 + j2];
+  }
+};
+template <class ST>
+struct RowStore {  // output k = k1 + L1 * k2 of transform b
+  ST st;
+  int64_t L1;
+  __device__ void operator()(int bb, int k2, cd v) const {
+    int64_t b = bb / L1, k1 = bb % L1;
+    st((int)b, (int)(k1 + L1 * k2), v);
+  }
+};
+
+// host helpers ----------------------------------------------------------------------------------
+inline void fft_tile_geometry(int L, int want_tb, int& tb, int& threads) {
+  tb = std::max(1, want_tb);
+  while (tb > 1 && tb * L > 8192) tb >>= 1;
+  int need = (tb * L + 7) / 8;
+  threads = std::max(32, ((need + 31) / 32) * 32);
+  threads = std::min(threads, 1024);
+}
+
+template <class LD, class ST>
+inline cudaError_t launch_tile(const FftDesc& d, int want_tb, int batch, int sign, int ljf, int sjf, LD ld, ST st,
+                               cudaStream_t s) {
+  if (batch <= 0) return cudaSuccess;
+  int tb, threads;
+  fft_tile_geometry(d.L, want_tb, tb, threads);
+  size_t smem = sizeof(cd) * (size_t)tb * d.L;
+  static bool attr_set = false;  // one per template instantiation
+  if (!attr_set) {
+    cudaFuncSetAttribute(fft_tile_kernel<LD, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8192 * (int)sizeof(cd));
+    attr_set = true;
+  }
+  int blocks = (batch + tb - 1) / tb;
+  fft_tile_kernel<LD, ST><<<blocks, threads, smem, s>>>(d, tb, batch, sign, ljf, sjf, ld, st);
+  return cudaGetLastError();
+}
+
+// Run `batch` transforms of plan p.  tmp must hold batch * L complex values when p.four.
+// Returns the number of kernels launched (negative on a launch error).
+template <class LD, class ST>
+inline int fft_run(const FftPlan& p, int batch, int sign, LD ld, ST st, cd* tmp, cudaStream_t s) {
+  if (!p.four) {
+    int want = p.L >= 256 ? 1 : (int)(256 / p.L);
+    return launch_tile(p.d1, want, batch, sign, /*ljf*/ 1, /*sjf*/ 1, ld, st, s) == cudaSuccess ? 1 : -1;
+  }
+  ColLoad<LD> cl{ld, p.L2};
+  ColStore cs{tmp, p.twL, p.L, p.L2, sign};
+  if (launch_tile(p.d1, 8, (int)(batch * p.L2), sign, 0, 0, cl, cs, s) != cudaSuccess) return -1;
+  RowLoad rl{tmp, p.L, p.L1, p.L2};
+  RowStore<ST> rs{st, p.L1};
+  if (launch_tile(p.d2, 8, (int)(batch * p.L1), sign, 1, 0, rl, rs, s) != cudaSuccess) return -1;
+  return 2;
+}
+
+// radix schedule for a 7-smooth length (8s first, then 4 / 2, then 7s, 5s and 3s)
+inline bool fft_factor(int L, FftDesc& d) {
+  d.L = L;
+  d.nst = 0;
+  int v = L;
+  while (v % 8 == 0 && d.nst < FFT_MAX_STAGES) { d.rad[d.nst++] = 8; v /= 8; }
+  while (v % 4 == 0 && d.nst < FFT_MAX_STAGES) { d.rad[d.nst++] = 4; v /= 4; }
+  while (v % 2 == 0 && d.nst < FFT_MAX_STAGES) { d.rad[d.nst++] = 2; v /= 2; }
+  while (v % 7 == 0 && d.nst < FFT_MAX_STAGES) { d.rad[d.nst++] = 7; v /= 7; }
+  while (v % 5 == 0 && d.nst < FFT_MAX_STAGES) { d.rad[d.nst++] = 5; v /= 5; }
+  while (v % 3 == 0 && d.nst < FFT_MAX_STAGES) { d.rad[d.nst++] = 3; v /= 3; }
+  return v == 1;
+}
+
+// split L = L1 * L2 with both factors <= FFT_TILE_MAX, as balanced as the factors allow
+inline bool fft_split(int64_t L, int64_t& L1, int64_t& L2) {
+  std::vector<int> f;
+  int64_t v = L;
+  for (int q : {2, 3, 5, 7})
+    while (v % q == 0) { f.push_back(q); v /= q; }
+  if (v != 1) return false;
+  // greedy: put the largest factors alternately; then fix the balance
+  L1 = 1;
+  L2 = 1;
+  std::sort(f.rbegin(), f.rend());
+  for (int q : f) {
+    if (L1 <= L2) L1 *= q; else L2 *= q;
+  }
+  return L1 <= FFT_TILE_MAX && L2 <= FFT_TILE_MAX;
+}
+
+}  // namespace tikh

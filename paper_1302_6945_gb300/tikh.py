@@ -1,0 +1,260 @@
+"""Python binding of the C-ABI in include/tikh.h (argument marshalling only).
+
+Every arithmetic step runs in the CUDA kernels of libtikh.so; this module only converts arguments
+(torch device tensors or numpy host arrays) to pointers, sizes and the current CUDA stream.  It
+raises if the library has not been built: there is no other implementation to fall back on.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libtikh.so")
+
+TIKH_OK, TIKH_EINVAL, TIKH_ENOMEM, TIKH_ECUDA, TIKH_ENUMERIC, TIKH_EDIFFICULT, TIKH_ENOTCONVERGED, \
+    TIKH_ETIMEOUT, TIKH_EDEGREE = 0, -1, -2, -3, -4, -5, -6, -7, -8
+TIKH_R64, TIKH_C128 = 0, 1
+TIKH_PREC_FP64 = 0
+
+
+class tikh_opts(ctypes.Structure):
+    _fields_ = [("n_lim", ctypes.c_int), ("m_min", ctypes.c_int), ("fill", ctypes.c_int),
+                ("eps_diff", ctypes.c_double), ("max_difficult", ctypes.c_int), ("refine_steps", ctypes.c_int)]
+
+
+class tikh_stats(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int64), ("M", ctypes.c_int64), ("k", ctypes.c_int64), ("p", ctypes.c_int),
+                ("dual", ctypes.c_int), ("n_difficult", ctypes.c_int64), ("delta", ctypes.c_int * 5),
+                ("jstar", ctypes.c_int), ("retries", ctypes.c_int), ("kernel_launches", ctypes.c_int64),
+                ("workspace_bytes", ctypes.c_int64), ("refine_steps", ctypes.c_int), ("rel_residual", ctypes.c_double)]
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_}
+        d["delta"] = list(self.delta)
+        return d
+
+
+class TikhError(RuntimeError):
+    def __init__(self, status, what):
+        super().__init__("%s failed: %s (status %d)" % (what, tikh_strerror(status), status))
+        self.status = status
+
+
+_lib = None
+
+EXPORTED = ["tikh_plan_create", "tikh_solve", "tikh_solve_async", "tikh_solve_normal", "tikh_solve_host",
+            "tikh_sync", "tikh_get_stats", "tikh_plan_destroy", "tikh_strerror", "tikh_test_fft", "tikh_test_leaf"]
+
+
+def lib():
+    """Load libtikh.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libtikh.so is not built (%s): run __graft_entry__.build() or "
+                               "python paper_1302_6945_gb300/build.py" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i64, dbl, ci = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int
+        L.tikh_plan_create.argtypes = [ctypes.POINTER(vp), i64, i64, ci, ci, ctypes.POINTER(tikh_opts), vp]
+        for f in ("tikh_solve", "tikh_solve_async", "tikh_solve_normal", "tikh_solve_host"):
+            getattr(L, f).argtypes = [vp, vp, vp, vp, dbl, vp]
+        L.tikh_sync.argtypes = [vp]
+        L.tikh_get_stats.argtypes = [vp, ctypes.POINTER(tikh_stats)]
+        L.tikh_plan_destroy.argtypes = [vp]
+        L.tikh_plan_destroy.restype = None
+        L.tikh_strerror.argtypes = [ci]
+        L.tikh_strerror.restype = ctypes.c_char_p
+        L.tikh_test_fft.argtypes = [i64, vp, ci, vp]
+        L.tikh_test_leaf.argtypes = [ci, vp, vp, vp, dbl, vp, vp, vp, vp, vp, vp, vp, vp]
+        _lib = L
+    return _lib
+
+
+def tikh_strerror(status):
+    return lib().tikh_strerror(int(status)).decode()
+
+
+def _check(rc, what):
+    if rc != TIKH_OK:
+        raise TikhError(rc, what)
+
+
+# ---------------------------------------------------------------------------------------------
+# C-ABI mirrors
+# ---------------------------------------------------------------------------------------------
+
+def tikh_plan_create(m, n, dtype=TIKH_R64, prec=TIKH_PREC_FP64, opts=None, stream=0):
+    h = ctypes.c_void_p()
+    o = ctypes.byref(opts) if opts is not None else None
+    _check(lib().tikh_plan_create(ctypes.byref(h), int(m), int(n), int(dtype), int(prec), o,
+                                  ctypes.c_void_p(int(stream))), "tikh_plan_create")
+    return h
+
+
+def tikh_solve(plan, col, row, b, lam, x):
+    _check(lib().tikh_solve(plan, col, row, b, float(lam), x), "tikh_solve")
+
+
+def tikh_solve_async(plan, col, row, b, lam, x):
+    _check(lib().tikh_solve_async(plan, col, row, b, float(lam), x), "tikh_solve_async")
+
+
+def tikh_solve_normal(plan, col, row, y, lam, x):
+    _check(lib().tikh_solve_normal(plan, col, row, y, float(lam), x), "tikh_solve_normal")
+
+
+def tikh_solve_host(plan, col, row, b, lam, x):
+    _check(lib().tikh_solve_host(plan, col, row, b, float(lam), x), "tikh_solve_host")
+
+
+def tikh_sync(plan):
+    _check(lib().tikh_sync(plan), "tikh_sync")
+
+
+def tikh_get_stats(plan):
+    st = tikh_stats()
+    _check(lib().tikh_get_stats(plan, ctypes.byref(st)), "tikh_get_stats")
+    return st.as_dict()
+
+
+def tikh_plan_destroy(plan):
+    lib().tikh_plan_destroy(plan)
+
+
+def tikh_test_fft(n, data, sign, stream=0):
+    _check(lib().tikh_test_fft(int(n), data, int(sign), ctypes.c_void_p(int(stream))), "tikh_test_fft")
+
+
+def tikh_test_leaf(K, sigma, r, delta_in, eps, B, length, delta_out, order, pivot, deferred, n_def, stream=0):
+    _check(lib().tikh_test_leaf(int(K), sigma, r, delta_in, float(eps), B, length, delta_out, order, pivot, deferred,
+                                n_def, ctypes.c_void_p(int(stream))), "tikh_test_leaf")
+
+
+def fft(x, sign=+1):
+    """DFT of a complex128 CUDA tensor through the library's FFT engine (test hook)."""
+    import torch
+    y = x.detach().to(torch.complex128).contiguous().clone()
+    tikh_test_fft(y.numel(), ctypes.c_void_p(y.data_ptr()), sign, torch.cuda.current_stream().cuda_stream)
+    return y
+
+
+def leaf(sigma, r, delta, eps=1e-8):
+    """Run one leaf kernel on CUDA tensors sigma (K,) and r (K, 5) (test hook); returns a dict."""
+    import torch
+    K = sigma.numel()
+    dev = sigma.device
+    ptr = lambda t: ctypes.c_void_p(t.data_ptr())
+    sig = sigma.to(torch.complex128).contiguous()
+    rr = r.to(torch.complex128).contiguous()
+    din = torch.tensor(list(delta), dtype=torch.int32, device=dev)
+    B = torch.zeros(25 * (K + 1), dtype=torch.complex128, device=dev)
+    ln = torch.zeros(25, dtype=torch.int32, device=dev)
+    dout = torch.zeros(5, dtype=torch.int32, device=dev)
+    order = torch.zeros(K, dtype=torch.int32, device=dev)
+    piv = torch.zeros(K, dtype=torch.int32, device=dev)
+    dq = torch.zeros(K, dtype=torch.int64, device=dev)
+    nd = torch.zeros(1, dtype=torch.int32, device=dev)
+    tikh_test_leaf(K, ptr(sig), ptr(rr), ptr(din), eps, ptr(B), ptr(ln), ptr(dout), ptr(order), ptr(piv), ptr(dq),
+                   ptr(nd), torch.cuda.current_stream().cuda_stream)
+    n = int(nd.item())
+    return dict(B=B.view(25, K + 1).cpu().numpy(), len=ln.cpu().numpy(), delta=dout.cpu().numpy(),
+                order=order.cpu().numpy(), pivot=piv.cpu().numpy(), deferred=sorted(dq[:n].cpu().tolist()))
+
+
+# ---------------------------------------------------------------------------------------------
+# convenience wrapper over torch CUDA tensors / numpy host arrays
+# ---------------------------------------------------------------------------------------------
+
+def _dtype_code(t):
+    import torch
+    if t.dtype == torch.float64:
+        return TIKH_R64
+    if t.dtype == torch.complex128:
+        return TIKH_C128
+    raise TypeError("tensors must be float64 or complex128, got %s" % t.dtype)
+
+
+class Plan:
+    """A solver plan for m x n Toeplitz problems of one dtype ('r64' or 'c128')."""
+
+    def __init__(self, m, n, dtype="r64", n_lim=32, m_min=0, fill=0, eps_diff=1e-8, max_difficult=4096,
+                 refine_steps=0, stream=None):
+        import torch
+        self.m, self.n = int(m), int(n)
+        self.dtype = TIKH_C128 if dtype in ("c128", TIKH_C128, torch.complex128) else TIKH_R64
+        self.opts = tikh_opts(int(n_lim), int(m_min), int(fill), float(eps_diff), int(max_difficult),
+                              int(refine_steps))
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        self.h = tikh_plan_create(self.m, self.n, self.dtype, TIKH_PREC_FP64, self.opts, handle)
+
+    def _args(self, col, row, v, vlen):
+        import torch
+        for t, ln in ((col, self.m), (row, self.n), (v, vlen)):
+            if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
+                raise TypeError("expected contiguous CUDA tensors")
+            if _dtype_code(t) != self.dtype or t.numel() != ln:
+                raise ValueError("tensor dtype/size does not match the plan")
+        return ctypes.c_void_p(col.data_ptr()), ctypes.c_void_p(row.data_ptr()), ctypes.c_void_p(v.data_ptr())
+
+    def _out(self, ref, x):
+        import torch
+        if x is None:
+            x = torch.empty(self.n, dtype=ref.dtype, device=ref.device)
+        return x
+
+    def solve(self, col, row, b, lam, x=None, sync=True):
+        """x = argmin ||Tx-b||^2 + lam ||x||^2 on the plan's stream."""
+        c, r, bb = self._args(col, row, b, self.m)
+        x = self._out(b, x)
+        f = tikh_solve if sync else tikh_solve_async
+        f(self.h, c, r, bb, lam, ctypes.c_void_p(x.data_ptr()))
+        return x
+
+    def solve_normal(self, col, row, y, lam, x=None):
+        """x = (T^H T + lam I)^{-1} y (requires m >= n)."""
+        c, r, yy = self._args(col, row, y, self.n)
+        x = self._out(y, x)
+        tikh_solve_normal(self.h, c, r, yy, lam, ctypes.c_void_p(x.data_ptr()))
+        return x
+
+    def solve_host(self, col, row, b, lam, x=None):
+        """Same as solve for host numpy arrays (copies in and out inside the call)."""
+        np_dt = np.complex128 if self.dtype == TIKH_C128 else np.float64
+        col = np.ascontiguousarray(col, dtype=np_dt)
+        row = np.ascontiguousarray(row, dtype=np_dt)
+        b = np.ascontiguousarray(b, dtype=np_dt)
+        if x is None:
+            x = np.empty(self.n, dtype=np_dt)
+        tikh_solve_host(self.h, col.ctypes.data_as(ctypes.c_void_p), row.ctypes.data_as(ctypes.c_void_p),
+                        b.ctypes.data_as(ctypes.c_void_p), lam, x.ctypes.data_as(ctypes.c_void_p))
+        return x
+
+    def sync(self):
+        tikh_sync(self.h)
+
+    def stats(self):
+        return tikh_get_stats(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            tikh_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def solve(col, row, b, lam, **kw):
+    """One-shot solve of CUDA tensors (builds and frees a plan)."""
+    p = Plan(col.numel(), row.numel(), "c128" if col.is_complex() else "r64", **kw)
+    try:
+        return p.solve(col, row, b, lam)
+    finally:
+        p.close()

@@ -1,0 +1,181 @@
+"""Parity of the CUDA path (through the C-ABI) with the CPU oracle.
+
+Tolerance: relative 2-norm error <= 1e-9 in FP64 (lambda >= 1e-6), on the same seeded inputs.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1302_6945_gb300 import tikh
+from paper_1302_6945_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-9
+DEV = "cuda:0"
+
+
+def relerr(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300))
+
+
+def gpu_solve(P, cplx, **kw):
+    dt = torch.complex128 if cplx else torch.float64
+    col = torch.tensor(P["col"], dtype=dt, device=DEV)
+    row = torch.tensor(P["row"], dtype=dt, device=DEV)
+    b = torch.tensor(P["b"], dtype=dt, device=DEV)
+    plan = tikh.Plan(len(P["col"]), len(P["row"]), "c128" if cplx else "r64", **kw)
+    x = plan.solve(col, row, b, P["lam"]).cpu().numpy()
+    st = plan.stats()
+    plan.close()
+    return x, st
+
+
+@pytest.mark.parametrize("m,n", [(1, 1), (2, 1), (1, 2), (5, 3), (3, 5), (17, 17), (64, 40), (40, 64),
+                                 (100, 100), (131, 77), (300, 200), (257, 511)])
+@pytest.mark.parametrize("cplx", [True, False])
+def test_small_random_vs_oracle(m, n, cplx):
+    P = W.random_problem(m, n, 1e-2, seed=13 * m + n, complex_data=cplx)
+    x, st = gpu_solve(P, cplx)
+    xo, sto = oracle.solve(P["col"], P["row"], P["b"], P["lam"], is_complex=int(cplx))
+    if not cplx:
+        xo = xo.real
+    assert relerr(x, xo) <= TOL, (relerr(x, xo), st, sto)
+    assert (st["N"], st["k"], st["p"]) == (sto["N"], sto["k"], sto["p"])
+    assert sorted(st["delta"]) == [0, 1, 1, 1, 1]
+
+
+@pytest.mark.parametrize("nlim", [8, 16, 32, 64])
+@pytest.mark.parametrize("lam", [1e-6, 1e-4, 1e-3, 1.0])
+def test_psf_vs_oracle_nlim_lambda(nlim, lam):
+    # m = n = 1024: N = 2048 = 2^p M for every N_lim, extension k = 1.  Where the plain method's own
+    # forward error (oracle vs dense QR) exceeds 1e-9 -- small lambda with large leaves -- the two
+    # implementations agree to a small multiple of it; the refined solves then meet 1e-9.
+    P = W.deconvolution_problem(1024, 1024, 4.0, 16, 1e-6, 1e-6, lam, seed=nlim)
+    x, st = gpu_solve(P, False, n_lim=nlim)
+    xo, sto = oracle.solve(P["col"], P["row"], P["b"], lam, nlim=nlim, is_complex=0)
+    xd = oracle.dense_solve(P["col"], P["row"], P["b"], lam).real
+    assert st["k"] == 1
+    method_err = relerr(xo.real, xd)
+    assert relerr(x, xo.real) <= max(TOL, 20 * method_err), (relerr(x, xo.real), method_err, st)
+    if method_err <= 1e-11:
+        assert relerr(x, xo.real) <= TOL
+    assert st["n_difficult"] == sto["n_difficult"]
+
+
+@pytest.mark.parametrize("nlim", [16, 64])
+@pytest.mark.parametrize("shape", [(1024, 1024), (900, 640), (700, 1000)])
+def test_refined_small_lambda_meets_tolerance(nlim, shape):
+    # one FP64 refinement correction (S9) on lambda = 1e-6 deconvolution problems, k = 1 and k >> 1
+    m, n = shape
+    P = W.deconvolution_problem(m, n, 4.0, 16, 1e-6, 1e-6, 1e-6, seed=nlim + m)
+    x, st = gpu_solve(P, False, n_lim=nlim, refine_steps=1)
+    xo, sto, rr = oracle.solve_refined(P["col"], P["row"], P["b"], P["lam"], steps=1, nlim=nlim, is_complex=0)
+    xd = oracle.dense_solve(P["col"], P["row"], P["b"], P["lam"]).real
+    assert st["refine_steps"] == 1 and 0 <= st["rel_residual"] < 1e-13, st
+    assert relerr(x, xo.real) <= TOL, relerr(x, xo.real)
+    assert relerr(x, xd) <= TOL, relerr(x, xd)
+
+
+def test_refined_complex_rectangular():
+    P = W.deconvolution_problem(3000, 2048, 8.0, 32, 1e-6, 1e-4, 1e-5, seed=3, complex_data=True, signal="smooth")
+    x, st = gpu_solve(P, True, refine_steps=2)
+    xo, _, _ = oracle.solve_refined(P["col"], P["row"], P["b"], P["lam"], steps=2)
+    assert relerr(x, xo) <= TOL and st["rel_residual"] < 1e-13
+
+
+@pytest.mark.parametrize("nlim", [16, 64])
+def test_large_extension_small_lambda_within_method_error(nlim):
+    # Algorithm 2 quantises N = 2^p M: here k is 15-30 % of N and, at lam = 1e-6, the method's own
+    # forward error (oracle vs dense QR) is far above 1e-9; both implementations of the same algorithm
+    # then agree to a small multiple of that error
+    P = W.deconvolution_problem(900, 640, 4.0, 16, 1e-6, 1e-6, 1e-6, seed=nlim)
+    x, st = gpu_solve(P, False, n_lim=nlim)
+    xo, sto = oracle.solve(P["col"], P["row"], P["b"], P["lam"], nlim=nlim, is_complex=0)
+    xd = oracle.dense_solve(P["col"], P["row"], P["b"], P["lam"]).real
+    assert st["k"] > 100
+    assert relerr(x, xo.real) <= max(TOL, 20 * relerr(xo.real, xd)), (relerr(x, xo.real), relerr(xo.real, xd))
+
+
+@pytest.mark.parametrize("m_min,fill", [(12, 0), (20, 0), (12, 1)])
+def test_large_extension_vs_oracle(m_min, fill):
+    P = W.deconvolution_problem(500, 377, 3.0, 12, 1e-6, 1e-6, 1e-3, seed=7)
+    x, st = gpu_solve(P, False, n_lim=32, m_min=m_min, fill=fill)
+    xo, sto = oracle.solve(P["col"], P["row"], P["b"], P["lam"], nlim=32, m_min=m_min, fill=fill, is_complex=0)
+    assert st["k"] == sto["k"] and st["k"] > 10
+    assert relerr(x, xo.real) <= TOL
+
+
+def test_c1_config_vs_oracle_and_dense():
+    P = W.config_c1()
+    x, st = gpu_solve(P, False)
+    xo, sto = oracle.solve(P["col"], P["row"], P["b"], P["lam"], is_complex=0)
+    xd = oracle.dense_solve(P["col"], P["row"], P["b"], P["lam"]).real
+    assert (st["N"], st["k"]) == (2048, 1)
+    assert relerr(x, xo.real) <= TOL
+    assert relerr(x, xd) <= 1e-9
+
+
+def test_solve_normal_paper_workload():
+    # Sec. 6.1: known x, y = (T^H T + lam I) x
+    P = W.paper_problem(512, seed=3)
+    T = oracle.toeplitz_dense(P["col"], P["row"])
+    y = T.conj().T @ (T @ P["x_true"]) + P["lam"] * P["x_true"]
+    plan = tikh.Plan(512, 512, "c128")
+    t = lambda a: torch.tensor(a, dtype=torch.complex128, device=DEV)
+    x = plan.solve_normal(t(P["col"]), t(P["row"]), t(y), P["lam"]).cpu().numpy()
+    plan.close()
+    xo, _ = oracle.solve_normal(P["col"], P["row"], y, P["lam"])
+    assert relerr(x, xo) <= TOL
+    assert np.abs(x - P["x_true"]).max() <= 10 * 1.55e-11   # Table 1, n = 512
+
+
+def test_solve_host_matches_device():
+    P = W.deconvolution_problem(777, 512, 5.0, 20, 1e-6, 1e-6, 1e-4, seed=2, complex_data=True, signal="smooth")
+    xd, _ = gpu_solve(P, True)
+    plan = tikh.Plan(777, 512, "c128")
+    xh = plan.solve_host(P["col"], P["row"], P["b"], P["lam"])
+    plan.close()
+    assert relerr(xh, xd) <= 1e-14
+
+
+def test_difficult_points_match_oracle():
+    # a high threshold forces deferrals; both sides process them against the final basis.  The
+    # deferral trajectories may diverge once one near-threshold decision flips, so the comparison is
+    # on x, to a small multiple of the method's own error
+    P = W.deconvolution_problem(200, 150, 3.0, 12, 1e-6, 1e-6, 1e-2, seed=9)
+    xd = oracle.dense_solve(P["col"], P["row"], P["b"], P["lam"]).real
+    for eps in (0.05, 0.2):
+        x, st = gpu_solve(P, False, n_lim=16, eps_diff=eps)
+        xo, sto = oracle.solve(P["col"], P["row"], P["b"], P["lam"], nlim=16, eps_diff=eps, is_complex=0)
+        assert sto["n_difficult"] > 0 and st["n_difficult"] > 0, (st, sto)
+        assert relerr(x, xd) <= max(1e-7, 20 * relerr(xo.real, xd)), (relerr(x, xd), relerr(xo.real, xd))
+
+
+def test_invalid_arguments_raise():
+    with pytest.raises(tikh.TikhError):
+        tikh.Plan(0, 5)
+    with pytest.raises(tikh.TikhError):
+        tikh.Plan(5, 5, n_lim=1000)
+    plan = tikh.Plan(8, 8)
+    z = torch.zeros(8, dtype=torch.float64, device=DEV)
+    with pytest.raises(tikh.TikhError):
+        plan.solve(z, z, z, -1.0)
+    plan.close()
+
+
+def test_c2_full_size_vs_oracle():
+    # the benchmark workload: complex128, m = 98304, n = 65536, lambda = 1e-4.  Plain solve: agreement
+    # within a small multiple of the plain method's own error (its normal-equation residual); one FP64
+    # refinement correction: 1e-9.
+    P = W.config_c2()
+    x, st = gpu_solve(P, True)
+    assert (st["N"], st["k"]) == (163840, 1)
+    xo, _ = oracle.solve(P["col"], P["row"], P["b"], P["lam"])
+    r = oracle.apply_th(P["col"], P["row"], P["b"] - oracle.apply_t(P["col"], P["row"], xo)) - P["lam"] * xo
+    method_res = np.linalg.norm(r) / np.linalg.norm(oracle.apply_th(P["col"], P["row"], P["b"]))
+    assert relerr(x, xo) <= max(TOL, 20 * method_res), (relerr(x, xo), method_res)
+    xr, st = gpu_solve(P, True, refine_steps=1)
+    xor, _, rr = oracle.solve_refined(P["col"], P["row"], P["b"], P["lam"], steps=1)
+    assert st["rel_residual"] < 1e-13 and rr < 1e-13
+    assert relerr(xr, xor) <= TOL, relerr(xr, xor)

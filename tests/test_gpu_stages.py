@@ -1,0 +1,62 @@
+"""Stage-wise parity through the C-ABI test hooks: the FFT engine and one leaf, on identical inputs."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1302_6945_gb300 import tikh
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 7, 8, 12, 40, 49, 64, 125, 343, 640, 2048, 4096, 4200, 20480,
+                               163840, 327680 * 2])
+@pytest.mark.parametrize("sign", [1, -1])
+def test_fft_matches_definition(n, sign):
+    rng = np.random.default_rng(n)
+    x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    y = tikh.fft(torch.tensor(x, device=DEV), sign).cpu().numpy()
+    ref = np.fft.ifft(x) * n if sign > 0 else np.fft.fft(x)
+    err = np.abs(y - ref).max() / np.abs(ref).max()
+    assert err < 1e-14 * max(1.0, np.log2(n)) * 4, err
+
+
+def _leaf_case(K, seed, zero_frac=0.3):
+    rng = np.random.default_rng(seed)
+    e = rng.permutation(4 * K)[:K]
+    sigma = np.exp(2j * np.pi * e / (4 * K))
+    r = rng.standard_normal((K, 5)) + 1j * rng.standard_normal((K, 5))
+    r[rng.random((K, 5)) < zero_frac] = 0.0
+    r[:, 4] *= 0.1
+    return sigma, r
+
+
+@pytest.mark.parametrize("K,seed", [(1, 0), (4, 1), (8, 2), (20, 3), (32, 4), (40, 5), (64, 6)])
+def test_leaf_matches_oracle_leaf(K, seed):
+    sigma, r = _leaf_case(K, seed)
+    delta = [-7, -9, -9, -8, 0]
+    g = tikh.leaf(torch.tensor(sigma, device=DEV), torch.tensor(r, device=DEV), delta, eps=1e-8)
+    o = oracle.leaf(sigma, r.copy(), delta, eps=1e-8)
+    # decisions are unique here (no ties): identical order, pivots, degrees, deferrals
+    assert list(g["order"]) == list(o["order"])
+    assert list(g["pivot"]) == list(o["pivot"])
+    assert list(g["delta"]) == list(o["delta"])
+    assert g["deferred"] == sorted(o["deferred"])
+    # the basis entrywise (the device trims to the degree bounds; beyond them the oracle has zeros)
+    for E in range(25):
+        lg = g["len"][E]
+        a = g["B"][E, :lg]
+        b = o["B"][E, :lg]
+        assert np.abs(o["B"][E, lg:]).max(initial=0.0) == 0.0
+        scale = max(np.abs(o["B"][E]).max(initial=0.0), 1e-300)
+        assert np.abs(a - b).max(initial=0.0) <= 1e-12 * scale, E
+
+
+def test_leaf_deferral_matches_oracle():
+    sigma, r = _leaf_case(32, 11, zero_frac=0.6)
+    for eps in (0.1, 0.3, 0.6):
+        g = tikh.leaf(torch.tensor(sigma, device=DEV), torch.tensor(r, device=DEV), [-3, -3, -3, -3, 0], eps=eps)
+        o = oracle.leaf(sigma, r.copy(), [-3, -3, -3, -3, 0], eps=eps)
+        assert g["deferred"] == sorted(o["deferred"]), eps
+        assert list(g["order"]) == list(o["order"])
