@@ -91,9 +91,12 @@ def dist_setup():
     return world, rank, local
 
 
-def workload(seed_offset=0):
+def workload(seed_offset=0, n=None):
+    """c2: m = 98304, n = 65536; with n given, the same recipe at m = 1.5 n (the metric's n sweep)."""
     from paper_1302_6945_gb300 import workloads as W
-    return W.config_c2(seed=1 + seed_offset)
+    if n is None:
+        return W.config_c2(seed=1 + seed_offset)
+    return W.config_c2(seed=1 + seed_offset, m=3 * n // 2, n=n)
 
 
 def run_reference(args, world, rank):
@@ -103,7 +106,7 @@ def run_reference(args, world, rank):
     import numpy as np
     import oracle
     oracle.build()
-    P = workload()
+    P = workload(n=args.n)
     times = []
     for s in range(args.warmup + args.steps):
         t0 = time.perf_counter()
@@ -116,7 +119,7 @@ def run_reference(args, world, rank):
     out = {"metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "c128", "data": "synthetic", "impl": "reference",
-           "config": {"workload": "c2 deconvolution m=98304 n=65536 complex128 lambda=1e-4", "m": P["m"],
+           "config": {"workload": "deconvolution m=%d n=%d complex128 lambda=1e-4 (c2 recipe)" % (P["m"], P["n"]), "m": P["m"],
                       "n": P["n"], "n_lim": args.n_lim, "l2": "working set > L2"},
            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
                             "sample": "full c2 solve per step, single thread"},
@@ -133,6 +136,7 @@ def main():
     ap.add_argument("--n-lim", type=int, default=32)
     ap.add_argument("--refine", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=None, help="sweep point: n unknowns, m = 1.5 n (default: c2)")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -148,7 +152,7 @@ def main():
     if world > 1:
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
-    P = workload(seed_offset=rank)
+    P = workload(seed_offset=rank, n=args.n)
     m, n = P["m"], P["n"]
     col = torch.tensor(P["col"], dtype=torch.complex128, device=dev)
     row = torch.tensor(P["row"], dtype=torch.complex128, device=dev)
@@ -230,13 +234,13 @@ def main():
         tc = time.perf_counter() - t0
         err = float(np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo))
         cpu = {"value": 1.0 / tc, "unit": "solves/s", "cores": 1, "kind": "oracle",
-               "sample": "one full c2 solve (m=98304, n=65536), single thread", "gpu_vs_oracle_rel_err": err}
+               "sample": "one full solve of the same problem (m=%d, n=%d), single thread" % (m, n), "gpu_vs_oracle_rel_err": err}
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": t_max, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": "c128", "data": "synthetic",
-               "config": {"workload": "c2 deconvolution m=98304 n=65536 complex128 lambda=1e-4", "m": m, "n": n,
+               "config": {"workload": "deconvolution m=%d n=%d complex128 lambda=1e-4 (c2 recipe)" % (m, n), "m": m, "n": n,
                           "N": st["N"], "p": st["p"], "M": st["M"], "n_lim": args.n_lim,
                           "refine_steps": args.refine, "precision": "fp64",
                           "l2": "256 MB flush between steps; working set > L2"},
