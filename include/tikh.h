@@ -61,6 +61,8 @@ typedef struct tikh_plan_s* tikh_plan;
  *            method; 0..8).  Each correction recomputes r = y - (T^H T + lambda I) x by FFT matrix-
  *            vector products (Sec. 6.3) and solves for the correction with the same algorithm
  *            (Sec. 6.2: the result "can be further improved with iterative refinement").
+ *  batch     largest number of same-shape problems per tikh_solve_batched call (default 1); the
+ *            plan's workspace scales with it.
  */
 typedef struct {
   int n_lim;
@@ -69,6 +71,7 @@ typedef struct {
   double eps_diff;
   int max_difficult;
   int refine_steps;
+  int batch;
 } tikh_opts;
 
 typedef struct {
@@ -82,7 +85,8 @@ typedef struct {
   int64_t kernel_launches; /* kernels enqueued by the last solve */
   int64_t workspace_bytes; /* device bytes owned by the plan */
   int refine_steps;        /* corrections applied in the last solve */
-  double rel_residual;     /* ||y - (T^H T + lambda I) x|| / ||y|| after refinement (-1 if none) */
+  double rel_residual;     /* largest ||y - (T^H T + lambda I) x|| / ||y|| after refinement (-1 if none) */
+  int batch;               /* problems in the last call */
 } tikh_stats;
 
 /* Build a plan for an m x n problem: sizing by Algorithm 2 (Sec. 5.2), the recursion schedule of
@@ -106,6 +110,17 @@ int tikh_solve_async(tikh_plan plan, const void* col, const void* row, const voi
 /* x = (T^H T + lambda I)^{-1} y for a given right-hand side y (n entries, device), the form the
  * paper's experiments solve (Sec. 6.1).  Requires m >= n (the tall, stable formulation). */
 int tikh_solve_normal(tikh_plan plan, const void* col, const void* row, const void* y, double lambda, void* x);
+
+/* `batch` problems of the plan's shape in one pass: every step of the method is one launch for all of
+ * them (a batch shares the recursion schedule; each problem keeps its own tau-degrees, pivots and
+ * basis).  Problem i reads col + i*col_stride, row + i*row_stride, b + i*b_stride and lambdas[i]
+ * (HOST array of batch doubles) and writes x + i*x_stride; strides count elements of the plan's
+ * dtype, and a stride of 0 shares one array across the batch (e.g. a regularisation path: one T and
+ * b, many lambdas).  1 <= batch <= opts.batch; x_stride >= n when batch > 1.  Synchronises like
+ * tikh_solve; the status is the OR over the batch. */
+int tikh_solve_batched(tikh_plan plan, int batch, const void* col, int64_t col_stride, const void* row,
+                       int64_t row_stride, const void* b, int64_t b_stride, const double* lambdas, void* x,
+                       int64_t x_stride);
 
 /* tikh_solve with HOST arrays: copies col, row, b to the plan's device staging buffers, solves and
  * copies x back, all on the plan's stream; returns after x is in host memory. */

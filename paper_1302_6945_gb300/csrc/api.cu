@@ -6,9 +6,10 @@
 // Algorithm 1 is laid out once on the host as a list of steps; product transform lengths come from
 // a water-filling model of the tau-degrees (every condition raises the lowest column) plus slack,
 // and the device checks the real degrees against them (TIKH_EDEGREE triggers a re-plan and re-run).
+// A plan serves up to opts.batch problems of one shape per call: every step is one launch for all.
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
-#include <cmath>
 #include <cstring>
 #include <new>
 
@@ -138,9 +139,10 @@ void build_steps(Plan& P, int depth, int64_t a, int64_t s, int64_t L, int side, 
   P.Pmax = std::max(P.Pmax, Pn);
 }
 
-// (re)build the schedule and the product scratch for the current slack
+// (re)build the schedule, the product scratch and the basis buffers for the current slack
 int make_schedule(Plan& P) {
   int err = 0;
+  const size_t nb = (size_t)P.batch_max;
   P.sched.clear();
   int sd[5] = {-(int)(P.cn - 1), -(int)(P.cm - 1), -(int)(P.cm + P.k - 2), -(int)(P.cn + P.k - 2), 0};
   uint64_t pending = 0;
@@ -149,7 +151,7 @@ int make_schedule(Plan& P) {
   build_steps(P, 0, 0, 2, P.N / 2, 0, sd, pending, slack, err);
   if (err) return err;
   if (P.Pmax > oldP || !P.FA) {
-    size_t n25 = 25 * (size_t)std::max<int64_t>(P.Pmax, 1);
+    size_t n25 = 25 * (size_t)std::max<int64_t>(P.Pmax, 1) * nb;
     P.FA = (cd*)dalloc(P, sizeof(cd) * n25, err);
     P.FB = (cd*)dalloc(P, sizeof(cd) * n25, err);
     P.FC = (cd*)dalloc(P, sizeof(cd) * n25, err);
@@ -168,10 +170,13 @@ int make_schedule(Plan& P) {
       BasisBuf& B = P.buf[d][side];
       if (B.cap >= need[d]) continue;
       B.cap = need[d];
-      B.c = (cd*)dalloc(P, sizeof(cd) * 25 * (size_t)B.cap, err);
-      if (!B.len) B.len = (int*)dalloc(P, sizeof(int) * 32, err);
-      if (!B.colmax) B.colmax = (unsigned long long*)dalloc(P, sizeof(unsigned long long) * 8, err);
-      if (d == 0) P.dscr = (cd*)dalloc(P, sizeof(cd) * (5 * (size_t)B.cap + (size_t)P.opts.max_difficult), err);
+      B.c = (cd*)dalloc(P, sizeof(cd) * 25 * (size_t)B.cap * nb, err);
+      if (!B.len) B.len = (int*)dalloc(P, sizeof(int) * 32 * nb, err);
+      if (!B.colmax) B.colmax = (unsigned long long*)dalloc(P, sizeof(unsigned long long) * 8 * nb, err);
+      if (d == 0) {
+        P.dscr_stride = 5 * B.cap + P.opts.max_difficult;
+        P.dscr = (cd*)dalloc(P, sizeof(cd) * (size_t)P.dscr_stride * nb, err);
+      }
     }
   return err;
 }
@@ -183,13 +188,13 @@ int status_to_code(int st) {
   return TIKH_OK;
 }
 
-// one superfast solve of the core system with right-hand side y, solution into out
-int enqueue_core(Plan& P, const cd* y, double lam, cd* out, int64_t& nl) {
+// one superfast solve of every problem's core system with right-hand side y, solution into out
+int enqueue_core(Plan& P, const cd* y, cd* out, int64_t& nl) {
   int r;
-  if ((r = launch_conditions(P, y, lam)) < 0) return r;
+  if ((r = launch_conditions(P, y)) < 0) return r;
   nl += r;
   for (const Step& st : P.sched) {
-    if (st.kind == STEP_LEAF) r = launch_leaf(P, st, 0);
+    if (st.kind == STEP_LEAF) r = launch_leaf(P, st);
     else if (st.kind == STEP_EVAL) r = launch_eval(P, st);
     else r = launch_prod(P, st);
     if (r < 0) return r;
@@ -202,29 +207,33 @@ int enqueue_core(Plan& P, const cd* y, double lam, cd* out, int64_t& nl) {
   return TIKH_OK;
 }
 
-int enqueue_solve(Plan& P, const void* col, const void* row, const void* rhs, int rhs_is_y, double lam, void* x) {
+int enqueue_solve(Plan& P, const UserArrays& u, int rhs_is_y, const double* lams, int nb) {
   int64_t nl = 0;
   int r;
+  if (nb < 1 || nb > P.batch_max) return TIKH_EINVAL;
+  P.nb = nb;
+  if (cudaMemcpyAsync(P.lam, lams, sizeof(double) * (size_t)nb, cudaMemcpyHostToDevice, P.stream) != cudaSuccess)
+    return TIKH_ECUDA;
   if (cudaMemsetAsync(P.status, 0, sizeof(int), P.stream) != cudaSuccess) return TIKH_ECUDA;
-  if ((r = launch_spectrum(P, col, row)) < 0) return r;
+  if ((r = launch_spectrum(P, u)) < 0) return r;
   nl += r;
   // for m < n the core problem (T T^H + lam I) v = b takes b itself as its right-hand side
-  if ((r = launch_rhs(P, rhs, P.dual ? 1 : rhs_is_y)) < 0) return r;
+  if ((r = launch_rhs(P, u, P.dual ? 1 : rhs_is_y)) < 0) return r;
   nl += r;
-  if ((r = enqueue_core(P, P.ybuf, lam, P.xcore, nl)) < 0) return r;
+  if ((r = enqueue_core(P, P.ybuf, P.xcore, nl)) < 0) return r;
   // iterative refinement on the core system: v <- v + A^{-1}(y - A v)
   for (int it = 0; it < P.opts.refine_steps; ++it) {
-    if ((r = launch_residual(P, P.ybuf, P.xcore, P.rbuf, lam)) < 0) return r;
+    if ((r = launch_residual(P, P.ybuf, P.xcore, P.rbuf)) < 0) return r;
     nl += r;
-    if ((r = enqueue_core(P, P.rbuf, lam, P.dx, nl)) < 0) return r;
+    if ((r = enqueue_core(P, P.rbuf, P.dx, nl)) < 0) return r;
     if ((r = launch_axpy(P, P.xcore, P.dx)) < 0) return r;
     nl += r;
   }
   if (P.opts.refine_steps > 0) {  // residual of the refined solution, reported in the stats
-    if ((r = launch_residual(P, P.ybuf, P.xcore, P.rbuf, lam)) < 0) return r;
+    if ((r = launch_residual(P, P.ybuf, P.xcore, P.rbuf)) < 0) return r;
     nl += r;
   }
-  if ((r = launch_output(P, P.xcore, x)) < 0) return r;
+  if ((r = launch_output(P, P.xcore, u)) < 0) return r;
   nl += r;
   P.launches = nl;
   return TIKH_OK;
@@ -232,35 +241,44 @@ int enqueue_solve(Plan& P, const void* col, const void* row, const void* rhs, in
 
 int sync_status(Plan& P) {
   if (cudaStreamSynchronize(P.stream) != cudaSuccess) { cudaGetLastError(); return TIKH_ECUDA; }
-  int st = 0, nd = 0, dl[5];
+  int st = 0;
   if (cudaMemcpy(&st, P.status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return TIKH_ECUDA;
-  cudaMemcpy(&nd, P.ndiff, sizeof(int), cudaMemcpyDeviceToHost);
-  cudaMemcpy(dl, P.delta, sizeof(dl), cudaMemcpyDeviceToHost);
-  P.last.n_difficult = nd;
-  memcpy(P.last.delta, dl, sizeof(dl));
+  std::vector<int> nd(4 * (size_t)P.nb), dl(8 * (size_t)P.nb);
+  cudaMemcpy(nd.data(), P.ndiff, sizeof(int) * nd.size(), cudaMemcpyDeviceToHost);
+  cudaMemcpy(dl.data(), P.delta, sizeof(int) * dl.size(), cudaMemcpyDeviceToHost);
+  int64_t total = 0;
+  for (int b = 0; b < P.nb; ++b) total += nd[4 * b];
+  P.last.n_difficult = total;
+  memcpy(P.last.delta, dl.data(), sizeof(int) * 5);
   P.last.jstar = -1;
   for (int j = 0; j < 5; ++j)
     if (dl[j] == 0) P.last.jstar = j;
   P.last.kernel_launches = P.launches;
   P.last.refine_steps = P.opts.refine_steps;
+  P.last.batch = P.nb;
   P.last.rel_residual = -1.0;
-  if (P.opts.refine_steps > 0) {
-    double nr[2] = {0.0, 0.0};
-    cudaMemcpy(nr, P.norms, sizeof(nr), cudaMemcpyDeviceToHost);
-    P.last.rel_residual = nr[1] > 0.0 ? sqrt(nr[0] / nr[1]) : sqrt(nr[0]);
+  if (P.opts.refine_steps > 0) {  // largest relative residual of the batch
+    std::vector<double> nr(4 * (size_t)P.nb);
+    cudaMemcpy(nr.data(), P.norms, sizeof(double) * nr.size(), cudaMemcpyDeviceToHost);
+    double worst = 0.0;
+    for (int b = 0; b < P.nb; ++b) {
+      double v = nr[4 * b + 1] > 0.0 ? sqrt(nr[4 * b] / nr[4 * b + 1]) : sqrt(nr[4 * b]);
+      worst = std::max(worst, v);
+    }
+    P.last.rel_residual = worst;
   }
   int zero = 0;
   cudaMemcpy(P.status, &zero, sizeof(int), cudaMemcpyHostToDevice);
   return status_to_code(st);
 }
 
-int solve_with_retry(Plan& P, const void* col, const void* row, const void* rhs, int rhs_is_y, double lam, void* x,
-                     bool host_copy_back, void* x_host, size_t xbytes) {
+int solve_with_retry(Plan& P, const UserArrays& u, int rhs_is_y, const double* lams, int nb, void* x_host,
+                     size_t xbytes) {
   P.last.retries = 0;
   for (int attempt = 0;; ++attempt) {
-    int rc = enqueue_solve(P, col, row, rhs, rhs_is_y, lam, x);
+    int rc = enqueue_solve(P, u, rhs_is_y, lams, nb);
     if (rc) return rc;
-    if (host_copy_back && cudaMemcpyAsync(x_host, x, xbytes, cudaMemcpyDeviceToHost, P.stream) != cudaSuccess)
+    if (x_host && cudaMemcpyAsync(x_host, u.x, xbytes, cudaMemcpyDeviceToHost, P.stream) != cudaSuccess)
       return TIKH_ECUDA;
     rc = sync_status(P);
     if (rc != TIKH_EDEGREE || attempt >= 3) return rc;
@@ -272,6 +290,15 @@ int solve_with_retry(Plan& P, const void* col, const void* row, const void* rhs,
 
 bool valid_lambda(double lam) { return lam > 0.0 && lam < 1e300; }
 
+UserArrays single(const Plan& P, const void* col, const void* row, const void* rhs, void* x) {
+  UserArrays u;
+  u.col = col;
+  u.row = row;
+  u.rhs = rhs;
+  u.x = x;
+  return u;
+}
+
 }  // namespace
 
 extern "C" {
@@ -280,11 +307,11 @@ int tikh_plan_create(tikh_plan* out, int64_t m, int64_t n, int dtype, int prec, 
   if (!out) return TIKH_EINVAL;
   *out = nullptr;
   if (m < 1 || n < 1 || (dtype != TIKH_R64 && dtype != TIKH_C128) || prec != TIKH_PREC_FP64) return TIKH_EINVAL;
-  tikh_opts o{32, 0, 0, 1e-8, 4096, 0};
+  tikh_opts o{32, 0, 0, 1e-8, 4096, 0, 1};
   if (opts) o = *opts;
   if (o.n_lim < 4 || o.n_lim > 64 || o.m_min < 0 || o.m_min > 32 || (o.fill != 0 && o.fill != 1) ||
       !(o.eps_diff >= 0.0) || o.max_difficult < 1 || o.max_difficult > (1 << 20) || o.refine_steps < 0 ||
-      o.refine_steps > 8)
+      o.refine_steps > 8 || o.batch < 1 || o.batch > 65535)
     return TIKH_EINVAL;
   tikh_plan h = new (std::nothrow) tikh_plan_s;
   if (!h) return TIKH_ENOMEM;
@@ -293,6 +320,7 @@ int tikh_plan_create(tikh_plan* out, int64_t m, int64_t n, int dtype, int prec, 
   P.n = n;
   P.dtype = dtype;
   P.opts = o;
+  P.batch_max = o.batch;
   P.stream = (cudaStream_t)stream;
   P.dual = m < n ? 1 : 0;
   P.cm = P.dual ? n : m;
@@ -311,32 +339,33 @@ int tikh_plan_create(tikh_plan* out, int64_t m, int64_t n, int dtype, int prec, 
   if (pv >= MAX_DEPTH - 1 || 4 * (Mv / 2) > 64 || P.N > (int64_t)1 << 31) { delete h; return TIKH_EINVAL; }
 
   int err = 0;
-  size_t N = (size_t)P.N;
+  const size_t N = (size_t)P.N, nb = (size_t)P.batch_max;
   if (fft_index(P, P.N, err) < 0 && !err) err = TIKH_EINVAL;
   P.wN = P.twiddle_of_len[P.N];
-  P.specT = (cd*)dalloc(P, sizeof(cd) * N, err);
-  P.work = (cd*)dalloc(P, sizeof(cd) * N, err);
-  P.work2 = (cd*)dalloc(P, sizeof(cd) * N, err);
-  P.ftmpN = (cd*)dalloc(P, sizeof(cd) * N, err);
-  P.R = (cd*)dalloc(P, sizeof(cd) * 10 * N, err);
-  P.Phi = (cd*)dalloc(P, sizeof(cd) * 10 * N, err);
-  P.delta = (int*)dalloc(P, sizeof(int) * 8, err);
-  P.dstack = (int*)dalloc(P, sizeof(int) * 5 * MAX_DEPTH, err);
+  P.specT = (cd*)dalloc(P, sizeof(cd) * N * nb, err);
+  P.work = (cd*)dalloc(P, sizeof(cd) * N * nb, err);
+  P.work2 = (cd*)dalloc(P, sizeof(cd) * N * nb, err);
+  P.ftmpN = (cd*)dalloc(P, sizeof(cd) * N * nb, err);
+  P.R = (cd*)dalloc(P, sizeof(cd) * 10 * N * nb, err);
+  P.Phi = (cd*)dalloc(P, sizeof(cd) * 10 * N * nb, err);
+  P.delta = (int*)dalloc(P, sizeof(int) * 8 * nb, err);
+  P.dstack = (int*)dalloc(P, sizeof(int) * 5 * MAX_DEPTH * nb, err);
   P.status = (int*)dalloc(P, sizeof(int) * 4, err);
-  P.ndiff = (int*)dalloc(P, sizeof(int) * 4, err);
-  P.diff = (int64_t*)dalloc(P, sizeof(int64_t) * (size_t)o.max_difficult, err);
-  P.diffr = (cd*)dalloc(P, sizeof(cd) * 5 * (size_t)o.max_difficult, err);
-  P.peak = (unsigned long long*)dalloc(P, 16, err);
+  P.ndiff = (int*)dalloc(P, sizeof(int) * 4 * nb, err);
+  P.diff = (int64_t*)dalloc(P, sizeof(int64_t) * (size_t)o.max_difficult * nb, err);
+  P.diffr = (cd*)dalloc(P, sizeof(cd) * 5 * (size_t)o.max_difficult * nb, err);
+  P.peak = (unsigned long long*)dalloc(P, sizeof(unsigned long long) * nb, err);
+  P.lam = (double*)dalloc(P, sizeof(double) * nb, err);
   if (!err) err = make_schedule(P);
   if (!err) {
-    size_t nl = 50 * (size_t)std::max<int64_t>(P.Lrmax, 1);
+    size_t nl = 50 * (size_t)std::max<int64_t>(P.Lrmax, 1) * nb;
     P.evalv = (cd*)dalloc(P, sizeof(cd) * nl, err);
     P.etmp = (cd*)dalloc(P, sizeof(cd) * nl, err);
-    P.ybuf = (cd*)dalloc(P, sizeof(cd) * (size_t)P.cn, err);
-    P.rbuf = (cd*)dalloc(P, sizeof(cd) * (size_t)P.cn, err);
-    P.xcore = (cd*)dalloc(P, sizeof(cd) * (size_t)P.cn, err);
-    P.dx = (cd*)dalloc(P, sizeof(cd) * (size_t)P.cn, err);
-    P.norms = (double*)dalloc(P, sizeof(double) * 4, err);
+    P.ybuf = (cd*)dalloc(P, sizeof(cd) * (size_t)P.cn * nb, err);
+    P.rbuf = (cd*)dalloc(P, sizeof(cd) * (size_t)P.cn * nb, err);
+    P.xcore = (cd*)dalloc(P, sizeof(cd) * (size_t)P.cn * nb, err);
+    P.dx = (cd*)dalloc(P, sizeof(cd) * (size_t)P.cn * nb, err);
+    P.norms = (double*)dalloc(P, sizeof(double) * 4 * nb, err);
     size_t es = dtype == TIKH_C128 ? 16 : 8;
     P.d_in = dalloc(P, es * (size_t)(2 * m + 2 * n) + 64, err);
   }
@@ -352,23 +381,43 @@ int tikh_plan_create(tikh_plan* out, int64_t m, int64_t n, int dtype, int prec, 
   P.last.k = P.k;
   P.last.p = P.p;
   P.last.dual = P.dual;
+  P.last.batch = 1;
   *out = h;
   return TIKH_OK;
 }
 
 int tikh_solve(tikh_plan h, const void* col, const void* row, const void* b, double lambda, void* x) {
   if (!h || !col || !row || !b || !x || !valid_lambda(lambda)) return TIKH_EINVAL;
-  return solve_with_retry(h->P, col, row, b, 0, lambda, x, false, nullptr, 0);
+  return solve_with_retry(h->P, single(h->P, col, row, b, x), 0, &lambda, 1, nullptr, 0);
 }
 
 int tikh_solve_async(tikh_plan h, const void* col, const void* row, const void* b, double lambda, void* x) {
   if (!h || !col || !row || !b || !x || !valid_lambda(lambda)) return TIKH_EINVAL;
-  return enqueue_solve(h->P, col, row, b, 0, lambda, x);
+  return enqueue_solve(h->P, single(h->P, col, row, b, x), 0, &lambda, 1);
 }
 
 int tikh_solve_normal(tikh_plan h, const void* col, const void* row, const void* y, double lambda, void* x) {
   if (!h || !col || !row || !y || !x || !valid_lambda(lambda) || h->P.dual) return TIKH_EINVAL;
-  return solve_with_retry(h->P, col, row, y, 1, lambda, x, false, nullptr, 0);
+  return solve_with_retry(h->P, single(h->P, col, row, y, x), 1, &lambda, 1, nullptr, 0);
+}
+
+int tikh_solve_batched(tikh_plan h, int batch, const void* col, int64_t col_stride, const void* row,
+                       int64_t row_stride, const void* b, int64_t b_stride, const double* lambdas, void* x,
+                       int64_t x_stride) {
+  if (!h || !col || !row || !b || !x || !lambdas || batch < 1 || batch > h->P.batch_max) return TIKH_EINVAL;
+  if (col_stride < 0 || row_stride < 0 || b_stride < 0 || (batch > 1 && x_stride < h->P.n)) return TIKH_EINVAL;
+  for (int i = 0; i < batch; ++i)
+    if (!valid_lambda(lambdas[i])) return TIKH_EINVAL;
+  UserArrays u;
+  u.col = col;
+  u.row = row;
+  u.rhs = b;
+  u.x = x;
+  u.col_stride = col_stride;
+  u.row_stride = row_stride;
+  u.rhs_stride = b_stride;
+  u.x_stride = x_stride;
+  return solve_with_retry(h->P, u, 0, lambdas, batch, nullptr, 0);
 }
 
 int tikh_solve_host(tikh_plan h, const void* col, const void* row, const void* b, double lambda, void* x) {
@@ -384,7 +433,7 @@ int tikh_solve_host(tikh_plan h, const void* col, const void* row, const void* b
       cudaMemcpyAsync(drow, row, es * P.n, cudaMemcpyHostToDevice, P.stream) != cudaSuccess ||
       cudaMemcpyAsync(db, b, es * P.m, cudaMemcpyHostToDevice, P.stream) != cudaSuccess)
     return TIKH_ECUDA;
-  return solve_with_retry(P, dcol, drow, db, 0, lambda, dx, true, x, es * P.n);
+  return solve_with_retry(P, single(P, dcol, drow, db, dx), 0, &lambda, 1, x, es * P.n);
 }
 
 int tikh_sync(tikh_plan h) {

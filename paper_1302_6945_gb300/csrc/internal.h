@@ -1,4 +1,9 @@
 // internal.h -- plan structure and kernel launchers shared by the translation units of libtikh.
+//
+// Every per-problem device array carries a leading problem index: a plan is built for up to
+// `batch_max` problems of the same shape, and every kernel processes all problems of a call at once
+// (grid.y, or the transform index of the FFT engine), so the launch count of a batched solve equals
+// that of a single solve.
 #pragma once
 #include <cstdint>
 #include <map>
@@ -12,13 +17,18 @@ namespace tikh {
 
 constexpr int MAX_DEPTH = 40;
 
-// one basis matrix B(z): 25 polynomials (entry (i,j) at c + (5i+j)*cap), device-side lengths and the
-// per-column max |Re|,|Im| (bit pattern) that fixes the lazy power-of-two column scaling
+// one basis matrix B(z) per problem: 25 polynomials (entry (i,j) at c + pb*cstride + (5i+j)*cap),
+// device-side lengths (32 per problem) and per-column max |Re|,|Im| bit patterns (8 per problem)
+// that fix the lazy power-of-two column scaling
 struct BasisBuf {
   cd* c = nullptr;
-  int* len = nullptr;                   // 25
-  unsigned long long* colmax = nullptr;  // 5
+  int* len = nullptr;
+  unsigned long long* colmax = nullptr;
   int64_t cap = 0;
+  __host__ __device__ int64_t cstride() const { return 25 * cap; }
+  __device__ cd* cp(int pb) const { return c + pb * cstride(); }
+  __device__ int* lp(int pb) const { return len + pb * 32; }
+  __device__ unsigned long long* mp(int pb) const { return colmax + pb * 8; }
 };
 
 // DFS schedule of Algorithm 1: a node (a, s, L) at `depth` has nodes omega^{a + c + s j}, c in {0,1},
@@ -34,6 +44,15 @@ struct Step {
   uint64_t save_mask;  // STEP_LEAF: depths whose delta_in is this leaf's delta_in
 };
 
+// per-problem user arrays of a call: element i of problem pb at base + pb * stride + i
+struct UserArrays {
+  const void* col = nullptr;
+  const void* row = nullptr;
+  const void* rhs = nullptr;
+  void* x = nullptr;
+  int64_t col_stride = 0, row_stride = 0, rhs_stride = 0, x_stride = 0;
+};
+
 struct Plan {
   // problem
   int64_t m = 0, n = 0;
@@ -44,6 +63,8 @@ struct Plan {
   int64_t cm = 0, cn = 0;  // core (tall) problem: cm >= cn
   int64_t N = 0, M = 0, k = 0;
   int p = 0;
+  int batch_max = 1;
+  int nb = 1;          // problems in the current call
   int slack_mult = 1;  // degree-prediction slack multiplier (raised after TIKH_EDEGREE)
 
   std::vector<Step> sched;
@@ -52,36 +73,38 @@ struct Plan {
   std::map<int64_t, cd*> twiddle_of_len;
   int64_t Pmax = 0, Lrmax = 0;
 
-  // device memory
+  // device memory (per-problem arrays: leading problem index)
   std::vector<void*> allocs;
   int64_t bytes = 0;
-  cd* wN = nullptr;     // omega^e, e < N
-  cd* specT = nullptr;  // DFT of the circulant generator of the core T
-  cd* work = nullptr;   // N
-  cd* work2 = nullptr;  // N
-  cd* ftmpN = nullptr;  // N (four-step temp for length-N transforms)
-  cd* R = nullptr;      // residual rows [N][2][5]
-  cd* Phi = nullptr;    // original condition rows [N][2][5]
-  int* delta = nullptr;   // 5
-  int* dstack = nullptr;  // MAX_DEPTH * 5
-  int* status = nullptr;  // 1
-  int* ndiff = nullptr;   // 1
-  int64_t* diff = nullptr;  // max_difficult condition ids 2e + f
-  cd* diffr = nullptr;      // max_difficult * 5 residuals
+  cd* wN = nullptr;     // omega^e, e < N (shared)
+  cd* specT = nullptr;  // [nb][N] DFT of the circulant generator of the core T
+  cd* work = nullptr;   // [nb][N]
+  cd* work2 = nullptr;  // [nb][N]
+  cd* ftmpN = nullptr;  // [nb][N] four-step temp for length-N transforms
+  cd* R = nullptr;      // [nb][N][2][5] residual rows
+  cd* Phi = nullptr;    // [nb][N][2][5] original condition rows
+  int* delta = nullptr;   // [nb][8]
+  int* dstack = nullptr;  // [nb][MAX_DEPTH][5]
+  int* status = nullptr;  // 1 (shared by the batch)
+  int* ndiff = nullptr;   // [nb][4]
+  int64_t* diff = nullptr;  // [nb][max_difficult] condition ids 2e + f
+  cd* diffr = nullptr;      // [nb][max_difficult][5] residuals
   BasisBuf buf[MAX_DEPTH][2];
-  cd* evalv = nullptr;  // 50 * Lrmax
-  cd* etmp = nullptr;   // 50 * Lrmax (four-step temp)
-  cd* FA = nullptr;     // 25 * Pmax spectra of B_L
-  cd* FB = nullptr;     // 25 * Pmax spectra of B_R
-  cd* FC = nullptr;     // 25 * Pmax products
-  cd* ptmp = nullptr;   // 50 * Pmax (four-step temp)
-  unsigned long long* peak = nullptr;  // fill magnitude (bit pattern of a non-negative double)
-  cd* ybuf = nullptr;    // core right-hand side (cn)
-  cd* rbuf = nullptr;    // refinement residual (cn)
-  cd* xcore = nullptr;   // core solution (cn)
-  cd* dx = nullptr;      // refinement correction (cn)
-  double* norms = nullptr;  // ||r||^2, ||y||^2 of the last residual
-  cd* dscr = nullptr;    // difficult-point scratch: 5 * buf[0][0].cap + max_difficult
+  cd* evalv = nullptr;  // [nb][50][Lrmax]
+  cd* etmp = nullptr;   // [nb][50][Lrmax] (four-step temp)
+  cd* FA = nullptr;     // [nb][25][Pmax] spectra of B_L
+  cd* FB = nullptr;     // [nb][25][Pmax] spectra of B_R
+  cd* FC = nullptr;     // [nb][25][Pmax] products
+  cd* ptmp = nullptr;   // [nb][50][Pmax] (four-step temp)
+  unsigned long long* peak = nullptr;  // [nb] fill magnitude (bit pattern of a non-negative double)
+  double* lam = nullptr;  // [nb] regularisation weights of the current call
+  cd* ybuf = nullptr;    // [nb][cn] core right-hand side
+  cd* rbuf = nullptr;    // [nb][cn] refinement residual
+  cd* xcore = nullptr;   // [nb][cn] core solution
+  cd* dx = nullptr;      // [nb][cn] refinement correction
+  double* norms = nullptr;  // [nb][4]: ||r||^2, ||y||^2 of the last residual
+  cd* dscr = nullptr;    // [nb][dscr_stride] difficult-point scratch
+  int64_t dscr_stride = 0;
   void* d_in = nullptr;  // staging for tikh_solve_host: col | row | b | x
   int64_t launches = 0;
 
@@ -90,14 +113,14 @@ struct Plan {
 
 // launchers (return the number of kernels enqueued, or a negative TIKH_E* code)
 int launch_twiddle(cd* tab, int64_t L, cudaStream_t s);
-int launch_spectrum(Plan& P, const void* col, const void* row);
-int launch_rhs(Plan& P, const void* rhs, int rhs_is_y);
-int launch_conditions(Plan& P, const cd* y, double lam);
+int launch_spectrum(Plan& P, const UserArrays& u);
+int launch_rhs(Plan& P, const UserArrays& u, int rhs_is_y);
+int launch_conditions(Plan& P, const cd* y);
 int launch_extract(Plan& P, cd* out);
-int launch_residual(Plan& P, const cd* y, const cd* x, cd* r, double lam);
+int launch_residual(Plan& P, const cd* y, const cd* x, cd* r);
 int launch_axpy(Plan& P, cd* x, const cd* dx);
-int launch_output(Plan& P, const cd* v, void* x);
-int launch_leaf(Plan& P, const Step& st, int nlim_threads);
+int launch_output(Plan& P, const cd* v, const UserArrays& u);
+int launch_leaf(Plan& P, const Step& st);
 int launch_eval(Plan& P, const Step& st);
 int launch_prod(Plan& P, const Step& st);
 int launch_difficult(Plan& P);

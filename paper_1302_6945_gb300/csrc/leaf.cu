@@ -7,7 +7,14 @@
 //    ties: larger |r|^2, then lower column index;
 //  - next condition: largest |r_pivot|^2 / ||r||^2; ties: lowest list position (4j + 2c + f);
 //  - if that best ratio is below eps^2, the leaf's remaining conditions are deferred.
-// Decisions are taken in FP64.
+// Decisions are taken in FP64 values; the comparisons use the IEEE bit patterns of the non-negative
+// doubles as integers (same order, no FP64 instruction).
+//
+// Cost model on GB300: an FP64 warp instruction occupies its SM sub-partition for 64 cycles whatever
+// the number of active lanes (measured), FP32 ~4.5 cycles.  The pivot chain of a leaf therefore keeps
+// only the FP64 work that decides the next step (scores, the multipliers mu, the residual update);
+// the basis B_leaf = E_1 E_2 ... E_K is rebuilt after the chain from the recorded (pivot, sigma, mu)
+// of every step, with the 25 (row, column) entries spread over all warps.
 #include "internal.h"
 
 namespace tikh {
@@ -16,43 +23,51 @@ constexpr int LEAF_KMAX = 64;
 constexpr int LEAF_THREADS = 128;
 constexpr int LEAF_CAP = LEAF_KMAX + 1;
 
+// pick: (score bits, position, pivot); larger score wins, then lower position
 struct Pick {
-  double score;
+  unsigned long long sb;
   int idx, piv;
 };
-__device__ __forceinline__ Pick pick_better(Pick a, Pick b) {
-  if (b.score > a.score || (b.score == a.score && b.idx < a.idx)) return b;
-  return a;
+__device__ __forceinline__ bool pick_better(const Pick& b, const Pick& a) {
+  return b.sb > a.sb || (b.sb == a.sb && b.idx < a.idx);
 }
 __device__ __forceinline__ Pick warp_pick(Pick p) {
   for (int o = 16; o > 0; o >>= 1) {
     Pick q;
-    q.score = __shfl_xor_sync(0xffffffffu, p.score, o);
+    q.sb = __shfl_xor_sync(0xffffffffu, p.sb, o);
     q.idx = __shfl_xor_sync(0xffffffffu, p.idx, o);
     q.piv = __shfl_xor_sync(0xffffffffu, p.piv, o);
-    p = pick_better(p, q);
+    if (pick_better(q, p)) p = q;
   }
   return p;
 }
+constexpr unsigned long long NO_PICK = 0ULL;  // every real score bit pattern is > 0 (score > 0)
 
-// pivot column and score of one residual row
+// pivot column and score of one residual row (score > 0 for a row with a non-zero entry)
 __device__ __forceinline__ Pick score_row(const cd* r, const int* dl, int q) {
-  double mag[5], tot = 0.0;
+  unsigned long long mb[5];
+  double mag[5], tot;
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    mag[i] = fma(r[i].x, r[i].x, r[i].y * r[i].y);
+    mb[i] = (unsigned long long)__double_as_longlong(mag[i]);
+  }
+  tot = ((mag[0] + mag[1]) + (mag[2] + mag[3])) + mag[4];
   int pi = -1;
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
-    mag[i] = r[i].x * r[i].x + r[i].y * r[i].y;
-    tot += mag[i];
-  }
-#pragma unroll
-  for (int i = 0; i < 5; ++i) {
     if (!cnonzero(r[i])) continue;
-    if (pi < 0 || dl[i] < dl[pi] || (dl[i] == dl[pi] && mag[i] > mag[pi])) pi = i;
+    if (pi < 0 || dl[i] < dl[pi] || (dl[i] == dl[pi] && mb[i] > mb[pi])) pi = i;
   }
   Pick p;
   p.idx = q;
   p.piv = pi;
-  p.score = pi < 0 ? -2.0 : mag[pi] / tot;
+  p.sb = NO_PICK;
+  if (pi >= 0) {
+    double sc = mag[pi] / tot;
+    p.sb = (unsigned long long)__double_as_longlong(sc);
+    if (p.sb == 0ULL) p.sb = 1ULL;  // an underflowed ratio still ranks above "no candidate"
+  }
   return p;
 }
 
@@ -69,26 +84,27 @@ __device__ __forceinline__ int entry_bound(const int* din, const int* dout, int 
   return min(acc, dout[j] - din[i]);
 }
 
-// condition source of a leaf: the recursion node (a, s, L) in the residual rows R, with position
-// q = 4j + 2c + f <-> node e = a + c + s j, condition f; deferred conditions are recorded as 2e + f
+// condition source of a leaf: the recursion node (a, s, L) in problem pb's residual rows, with
+// position q = 4j + 2c + f <-> node e = a + c + s j, condition f; deferred ids are 2e + f
 struct SrcNodes {
   const cd* R;
   const cd* wN;
-  int64_t a, s;
-  __device__ void get(int q, cd* r, cd& sig, int64_t& id) const {
+  int64_t N, a, s;
+  __device__ void get(int pb, int q, cd* r, cd& sig, int64_t& id) const {
     int j = q / 4, c = (q / 2) % 2, f = q % 2;
     int64_t e = a + c + s * j;
     id = 2 * e + f;
+    const cd* row = R + ((int64_t)pb * N + e) * 10 + f * 5;
 #pragma unroll
-    for (int i = 0; i < 5; ++i) r[i] = R[e * 10 + f * 5 + i];
+    for (int i = 0; i < 5; ++i) r[i] = row[i];
     sig = wN[e];
   }
 };
-// explicit arrays (test hook): sigma[q], r[5q..5q+4]; deferred conditions are recorded as q
+// explicit arrays (test hook, one problem): sigma[q], r[5q..5q+4]; deferred ids are q
 struct SrcArrays {
   const cd* sigma;
   const cd* rr;
-  __device__ void get(int q, cd* r, cd& sig, int64_t& id) const {
+  __device__ void get(int, int q, cd* r, cd& sig, int64_t& id) const {
     id = q;
 #pragma unroll
     for (int i = 0; i < 5; ++i) r[i] = rr[q * 5 + i];
@@ -96,6 +112,7 @@ struct SrcArrays {
   }
 };
 
+// one CTA per problem (blockIdx.x)
 template <class Src>
 __global__ void __launch_bounds__(LEAF_THREADS) k_leaf(Src src, int K, int* delta, int* dstack,
                                                         unsigned long long save_mask, double eps, BasisBuf out,
@@ -103,100 +120,124 @@ __global__ void __launch_bounds__(LEAF_THREADS) k_leaf(Src src, int K, int* delt
                                                         int* rec_order, int* rec_pivot) {
   __shared__ cd Bs[25][LEAF_CAP];
   __shared__ cd oldc[5][LEAF_CAP];
+  __shared__ cd rec_mu[LEAF_KMAX][5];
+  __shared__ cd rec_sig[LEAF_KMAX];
+  __shared__ int rec_piv[LEAF_KMAX];
+  __shared__ cd win_r[5];
   __shared__ int blen[25];
   __shared__ int dl[5], din[5];
   __shared__ Pick wpick[LEAF_THREADS / 32];
-  __shared__ Pick best;
-  __shared__ cd mu[5];
-  __shared__ cd sig_best;
-  const int tid = threadIdx.x;
+  __shared__ int nsteps_s;
+  const int tid = threadIdx.x, pb = blockIdx.x;
+  int* dlt = delta + 8 * pb;
 
-  if (tid < 5) { dl[tid] = delta[tid]; din[tid] = delta[tid]; }
-  if (tid < 25) blen[tid] = (tid % 6 == 0) ? 1 : 0;
-  for (int idx = tid; idx < 25 * LEAF_CAP; idx += blockDim.x) {
-    int e = idx / LEAF_CAP, t = idx % LEAF_CAP;
-    Bs[e][t] = (t == 0 && e % 6 == 0) ? mkc(1.0, 0.0) : mkc(0.0, 0.0);
-  }
+  if (tid < 5) { dl[tid] = dlt[tid]; din[tid] = dlt[tid]; }
   // the leaf's own residual row and node
   cd r[5];
   cd sig = mkc(0.0, 0.0);
   bool active = tid < K;
   int64_t eid = -1;
-  if (active) src.get(tid, r, sig, eid);
+  if (active) src.get(pb, tid, r, sig, eid);
   __syncthreads();
   if (tid < 5 && dstack) {
     for (int d = 0; d < 64; ++d)
-      if (save_mask >> d & 1ULL) dstack[d * 5 + tid] = din[tid];
+      if (save_mask >> d & 1ULL) dstack[((int64_t)pb * MAX_DEPTH + d) * 5 + tid] = din[tid];
   }
+  const unsigned long long eps_bits = (unsigned long long)__double_as_longlong(eps * eps);
+  const int nwarps = (K + 31) / 32;
 
-  for (int step = 0; step < K; ++step) {
+  // ---- pivot chain: decisions, multipliers and residual updates only ----
+  int step = 0;
+  for (; step < K; ++step) {
     Pick p;
-    p.score = -1.0;
+    p.sb = NO_PICK;
     p.idx = 1 << 30;
     p.piv = -1;
     if (active) {
       p = score_row(r, dl, tid);
-      if (p.piv < 0) { active = false; p.score = -1.0; p.idx = 1 << 30; }  // already satisfied
+      if (p.piv < 0) { active = false; p.sb = NO_PICK; p.idx = 1 << 30; }  // already satisfied
     }
-    p = warp_pick(p);
-    if ((tid & 31) == 0) wpick[tid >> 5] = p;
-    __syncthreads();
-    if (tid == 0) {
-      Pick b = wpick[0];
-      for (int w = 1; w < LEAF_THREADS / 32; ++w) b = pick_better(b, wpick[w]);
-      best = b;
+    if (tid < 32 * nwarps) {
+      p = warp_pick(p);
+      if ((tid & 31) == 0) wpick[tid >> 5] = p;
     }
     __syncthreads();
-    const Pick b = best;
-    if (b.score < 0.0) break;
-    if (b.score < eps * eps) {  // difficult: defer the rest of the leaf
+    Pick b = wpick[0];
+    for (int w = 1; w < nwarps; ++w)
+      if (pick_better(wpick[w], b)) b = wpick[w];
+    if (b.sb == NO_PICK) break;
+    if (b.sb < eps_bits) {  // difficult: defer the rest of the leaf
       if (active) {
-        int slot = atomicAdd(ndiff, 1);
-        if (slot < maxdiff) diff[slot] = eid;
+        int slot = atomicAdd(ndiff + 4 * pb, 1);
+        if (slot < maxdiff) diff[(int64_t)pb * maxdiff + slot] = eid;
         else set_status(status, ST_DIFFICULT);
         active = false;
       }
       break;
     }
     const int pi = b.piv;
-    if (tid == 0 && rec_order) { rec_order[step] = b.idx; rec_pivot[step] = pi; }
     if (tid == b.idx) {
-      double den = r[pi].x * r[pi].x + r[pi].y * r[pi].y;
-      cd inv = mkc(r[pi].x / den, -r[pi].y / den);
 #pragma unroll
-      for (int i = 0; i < 5; ++i) {
-        cd m = (i == pi) ? mkc(0.0, 0.0) : cmul(r[i], inv);
-        mu[i] = mkc(-m.x, -m.y);
-      }
-      sig_best = sig;
+      for (int i = 0; i < 5; ++i) win_r[i] = r[i];
+      rec_sig[step] = sig;
+      rec_piv[step] = pi;
+      if (rec_order) { rec_order[step] = b.idx; rec_pivot[step] = pi; }
       active = false;
     }
-    // snapshot of the pivot column before the update
-    for (int idx = tid; idx < 5 * LEAF_CAP; idx += blockDim.x) {
-      int i = idx / LEAF_CAP, t = idx % LEAF_CAP;
+    __syncthreads();
+    if (tid < 5) {  // mu_i = -r_i / r_pi, division as r_i * conj(r_pi) / |r_pi|^2, one lane per i
+      cd rp = win_r[pi];
+      double den = fma(rp.x, rp.x, rp.y * rp.y);
+      cd inv = mkc(rp.x / den, -rp.y / den);
+      cd m = (tid == pi) ? mkc(0.0, 0.0) : cmul(win_r[tid], inv);
+      rec_mu[step][tid] = mkc(-m.x, -m.y);
+    }
+    if (tid == 0) dl[pi] += 1;
+    __syncthreads();
+    if (active) {  // r <- r E(sigma): column pi times (sigma - sb), others += mu_i r_pi
+      const cd sb = rec_sig[step];
+      const cd rp = r[pi];
+      const cd* mu = rec_mu[step];
+#pragma unroll
+      for (int i = 0; i < 5; ++i) {
+        cd base = (i == pi) ? mkc(0.0, 0.0) : r[i];
+        cd fac = (i == pi) ? csub(sig, sb) : mu[i];
+        r[i] = cfma(fac, rp, base);
+      }
+    }
+  }
+  if (tid == 0) nsteps_s = step;
+  // ---- basis reconstruction B = E_1 ... E_steps (off the pivot chain) ----
+  if (tid < 25) blen[tid] = (tid % 6 == 0) ? 1 : 0;
+  for (int idx = tid; idx < 25 * LEAF_CAP; idx += blockDim.x) {
+    int e = idx / LEAF_CAP, t = idx % LEAF_CAP;
+    Bs[e][t] = (t == 0 && e % 6 == 0) ? mkc(1.0, 0.0) : mkc(0.0, 0.0);
+  }
+  __syncthreads();
+  const int nsteps = nsteps_s;
+  for (int s = 0; s < nsteps; ++s) {
+    const int pi = rec_piv[s];
+    const cd sb = rec_sig[s];
+    int lmax = 0;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) lmax = max(lmax, blen[i * 5 + pi]);
+    for (int idx = tid; idx < 5 * lmax; idx += blockDim.x) {
+      int i = idx / lmax, t = idx % lmax;
       oldc[i][t] = Bs[i * 5 + pi][t];
     }
     __syncthreads();
-    const cd sb = sig_best;
-    if (active) {  // r <- r E(sigma): column pi times (sigma - sb), others += mu_i r_pi
-      cd rp = r[pi];
-#pragma unroll
-      for (int i = 0; i < 5; ++i)
-        if (i != pi) r[i] = cfma(mu[i], rp, r[i]);
-      r[pi] = cmul(rp, csub(sig, sb));
-    }
-    // B <- B E: column pi <- (z - sb) column pi, column i += mu_i * old column pi
-    for (int idx = tid; idx < 5 * LEAF_CAP; idx += blockDim.x) {
-      int i = idx / LEAF_CAP, t = idx % LEAF_CAP;
+    // item (row i, column j, coefficient t): column pi <- (z - sb) column pi, column j += mu_j old pi
+    for (int idx = tid; idx < 25 * (lmax + 1); idx += blockDim.x) {
+      int e = idx / (lmax + 1), t = idx % (lmax + 1);
+      int i = e / 5, j = e % 5;
       int lo = blen[i * 5 + pi];
       if (lo == 0 || t > lo) continue;
       cd o = t < lo ? oldc[i][t] : mkc(0.0, 0.0);
-      cd prev = t >= 1 ? oldc[i][t - 1] : mkc(0.0, 0.0);
-      Bs[i * 5 + pi][t] = csub(prev, cmul(sb, o));
-      if (t < lo) {
-#pragma unroll
-        for (int j = 0; j < 5; ++j)
-          if (j != pi) Bs[i * 5 + j][t] = cfma(mu[j], o, Bs[i * 5 + j][t]);
+      if (j == pi) {
+        cd prev = t >= 1 ? oldc[i][t - 1] : mkc(0.0, 0.0);
+        Bs[e][t] = csub(prev, cmul(sb, o));
+      } else if (t < lo) {
+        Bs[e][t] = cfma(rec_mu[s][j], o, Bs[e][t]);
       }
     }
     __syncthreads();
@@ -208,13 +249,11 @@ __global__ void __launch_bounds__(LEAF_THREADS) k_leaf(Src src, int K, int* delt
         blen[i * 5 + pi] = lo + 1;
       }
     }
-    if (tid == 0) dl[pi] += 1;
     __syncthreads();
   }
-  __syncthreads();
-  // trim to the degree bounds, record column maxima, write out
-  __shared__ double cmax[5];
-  if (tid < 5) cmax[tid] = 0.0;
+  // ---- trim to the degree bounds, record column maxima, write out ----
+  __shared__ unsigned long long cmax[5];
+  if (tid < 5) cmax[tid] = 0ULL;
   if (tid < 25) {
     int i = tid / 5, j = tid % 5;
     int bnd = entry_bound(din, dl, i, j);
@@ -222,34 +261,35 @@ __global__ void __launch_bounds__(LEAF_THREADS) k_leaf(Src src, int K, int* delt
     if (blen[tid] > want) blen[tid] = want;
   }
   __syncthreads();
+  cd* oc = out.cp(pb);
   for (int idx = tid; idx < 25 * LEAF_CAP; idx += blockDim.x) {
     int e = idx / LEAF_CAP, t = idx % LEAF_CAP;
     if (t < blen[e]) {
       cd v = Bs[e][t];
-      out.c[(int64_t)e * out.cap + t] = v;
+      oc[(int64_t)e * out.cap + t] = v;
       double m = fmax(fabs(v.x), fabs(v.y));
-      if (m > 0.0) atomicMax((unsigned long long*)&cmax[e % 5], (unsigned long long)__double_as_longlong(m));
+      if (m > 0.0) atomicMax(&cmax[e % 5], (unsigned long long)__double_as_longlong(m));
     }
   }
   __syncthreads();
-  if (tid < 25) out.len[tid] = blen[tid];
+  if (tid < 25) out.lp(pb)[tid] = blen[tid];
   if (tid < 5) {
-    out.colmax[tid] = (unsigned long long)__double_as_longlong(cmax[tid]);
-    delta[tid] = dl[tid];
+    out.mp(pb)[tid] = cmax[tid];
+    dlt[tid] = dl[tid];
   }
 }
 
-int launch_leaf(Plan& P, const Step& st, int) {
+int launch_leaf(Plan& P, const Step& st) {
   int K = (int)(4 * st.L);
   if (K > LEAF_KMAX) return TIKH_EINVAL;
-  k_leaf<SrcNodes><<<1, LEAF_THREADS, 0, P.stream>>>(SrcNodes{P.R, P.wN, st.a, st.s}, K, P.delta, P.dstack,
-                                                     st.save_mask, P.opts.eps_diff, P.buf[st.depth][st.side], P.ndiff,
-                                                     P.diff, P.opts.max_difficult, P.status, nullptr, nullptr);
+  k_leaf<SrcNodes><<<P.nb, LEAF_THREADS, 0, P.stream>>>(SrcNodes{P.R, P.wN, P.N, st.a, st.s}, K, P.delta, P.dstack,
+                                                        st.save_mask, P.opts.eps_diff, P.buf[st.depth][st.side],
+                                                        P.ndiff, P.diff, P.opts.max_difficult, P.status, nullptr,
+                                                        nullptr);
   return cudaGetLastError() == cudaSuccess ? 1 : TIKH_ECUDA;
 }
 
-// test hook: one leaf on explicit device arrays; ws holds delta(8) status(4) ndiff(4) ints, then
-// 25*(K+1) coefficients, len(32), colmax(8), diff(K) -- see tikh_test_leaf
+// test hook: one leaf (one problem) on explicit device arrays
 int launch_leaf_arrays(int K, const cd* sigma, const cd* r, int* delta, double eps, cd* B, int* len,
                        unsigned long long* colmax, int* ndiff, int64_t* diff, int* status, int* order, int* pivot,
                        cudaStream_t s) {
@@ -268,19 +308,22 @@ int launch_leaf_arrays(int K, const cd* sigma, const cd* r, int* delta, double e
 // difficult points (Sec. 4.4): residual against the final basis B*, then serial processing.
 // ------------------------------------------------------------------------------------------------
 
-// r_q = Phi_q B*(sigma_q) for every deferred condition (B* with its column scales applied)
+// r_q = Phi_q B*(sigma_q) for every deferred condition (B* with its column scales applied);
+// grid (blocks, problems)
 __global__ void k_diff_eval(BasisBuf B, const cd* __restrict__ Phi, const cd* __restrict__ wN, int64_t N,
                             const int* ndiff, const int64_t* diff, int maxdiff, cd* diffr) {
   __shared__ cd red[32];
   __shared__ cd vals[25];
-  int nd = min(*ndiff, maxdiff);
+  const int pb = blockIdx.y;
+  const int nd = min(ndiff[4 * pb], maxdiff);
+  const cd* bc = B.cp(pb);
+  const int* bl = B.lp(pb);
   for (int q = blockIdx.x; q < nd; q += gridDim.x) {
-    int64_t id = diff[q], e = id / 2, f = id % 2;
+    int64_t id = diff[(int64_t)pb * maxdiff + q], e = id / 2, f = id % 2;
     for (int E = 0; E < 25; ++E) {
       cd acc = mkc(0.0, 0.0);
-      int64_t L = B.len[E];
-      for (int64_t t = threadIdx.x; t < L; t += blockDim.x)
-        acc = cfma(B.c[E * B.cap + t], tw_at(wN, (e * t) % N), acc);
+      int64_t L = bl[E];
+      for (int64_t t = threadIdx.x; t < L; t += blockDim.x) acc = cfma(bc[E * B.cap + t], tw_at(wN, (e * t) % N), acc);
       for (int o = 16; o > 0; o >>= 1) {
         acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
         acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
@@ -290,61 +333,68 @@ __global__ void k_diff_eval(BasisBuf B, const cd* __restrict__ Phi, const cd* __
       if (threadIdx.x == 0) {
         cd sum = mkc(0.0, 0.0);
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum = cadd(sum, red[w]);
-        vals[E] = cscale(sum, col_scale_from_bits(B.colmax[E % 5]));
+        vals[E] = cscale(sum, col_scale_from_bits(B.mp(pb)[E % 5]));
       }
       __syncthreads();
     }
     if (threadIdx.x < 5) {
       int j = threadIdx.x;
       cd acc = mkc(0.0, 0.0);
-      for (int i = 0; i < 5; ++i) acc = cfma(Phi[e * 10 + f * 5 + i], vals[i * 5 + j], acc);
-      diffr[(int64_t)q * 5 + j] = acc;
+      for (int i = 0; i < 5; ++i) acc = cfma(Phi[((int64_t)pb * N + e) * 10 + f * 5 + i], vals[i * 5 + j], acc);
+      diffr[((int64_t)pb * maxdiff + q) * 5 + j] = acc;
     }
     __syncthreads();
   }
 }
 
-// serial processing of the deferred conditions against B* (one CTA; no further deferral)
+// serial processing of the deferred conditions against B* (one CTA per problem; no further deferral)
 __global__ void __launch_bounds__(1024) k_diff_serial(BasisBuf B, const cd* __restrict__ wN, const int* ndiff,
                                                      const int64_t* diff, int maxdiff, cd* diffr, int* delta,
-                                                     int* status, cd* scratch) {
+                                                     int* status, cd* scratch, int64_t scr_stride) {
   __shared__ int dl[5];
   __shared__ Pick wpick[32];
   __shared__ Pick best;
   __shared__ cd mu[5];
   __shared__ int blen[25];
   __shared__ double scl[5];
-  const int nd = min(*ndiff, maxdiff);
+  const int pb = blockIdx.x;
+  const int nd = min(ndiff[4 * pb], maxdiff);
   if (nd == 0) return;
   const int tid = threadIdx.x;
-  if (tid < 5) { dl[tid] = delta[tid]; scl[tid] = col_scale_from_bits(B.colmax[tid]); }
-  if (tid < 25) blen[tid] = B.len[tid];
+  cd* bc = B.cp(pb);
+  cd* scr = scratch + (int64_t)pb * scr_stride;
+  cd* dr = diffr + (int64_t)pb * maxdiff * 5;
+  const int64_t* did = diff + (int64_t)pb * maxdiff;
+  int* dlt = delta + 8 * pb;
+  if (tid < 5) { dl[tid] = dlt[tid]; scl[tid] = col_scale_from_bits(B.mp(pb)[tid]); }
+  if (tid < 25) blen[tid] = B.lp(pb)[tid];
   __syncthreads();
   // materialise the column scales so that B* is plain
   for (int E = 0; E < 25; ++E)
-    for (int64_t t = tid; t < blen[E]; t += blockDim.x) B.c[E * B.cap + t] = cscale(B.c[E * B.cap + t], scl[E % 5]);
+    for (int64_t t = tid; t < blen[E]; t += blockDim.x) bc[E * B.cap + t] = cscale(bc[E * B.cap + t], scl[E % 5]);
   __syncthreads();
-  unsigned char* done = (unsigned char*)(scratch + 5 * B.cap);  // nd flags
+  unsigned char* done = (unsigned char*)(scr + 5 * B.cap);  // nd flags
   for (int q = tid; q < nd; q += blockDim.x) done[q] = 0;
   __syncthreads();
   for (int step = 0; step < nd; ++step) {
     Pick p;
-    p.score = -1.0; p.idx = 1 << 30; p.piv = -1;
+    p.sb = NO_PICK; p.idx = 1 << 30; p.piv = -1;
     for (int q = tid; q < nd; q += blockDim.x) {
       if (done[q]) continue;
-      Pick c = score_row(diffr + (int64_t)q * 5, dl, q);
+      Pick c = score_row(dr + (int64_t)q * 5, dl, q);
       if (c.piv < 0) { done[q] = 1; continue; }
-      p = pick_better(p, c);
+      if (pick_better(c, p)) p = c;
     }
     p = warp_pick(p);
     if ((tid & 31) == 0) wpick[tid >> 5] = p;
     __syncthreads();
     if (tid == 0) {
       Pick b = wpick[0];
-      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) b = pick_better(b, wpick[w]);
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+        if (pick_better(wpick[w], b)) b = wpick[w];
       best = b;
-      if (b.score >= 0.0) {
-        const cd* rs = diffr + (int64_t)b.idx * 5;
+      if (b.sb != NO_PICK) {
+        const cd* rs = dr + (int64_t)b.idx * 5;
         int pi = b.piv;
         double den = rs[pi].x * rs[pi].x + rs[pi].y * rs[pi].y;
         cd inv = mkc(rs[pi].x / den, -rs[pi].y / den);
@@ -357,36 +407,36 @@ __global__ void __launch_bounds__(1024) k_diff_serial(BasisBuf B, const cd* __re
     }
     __syncthreads();
     const Pick b = best;
-    if (b.score < 0.0) break;
+    if (b.sb == NO_PICK) break;
     const int pi = b.piv;
-    const cd sb = tw_at(wN, diff[b.idx] / 2);
+    const cd sb = tw_at(wN, did[b.idx] / 2);
     for (int q = tid; q < nd; q += blockDim.x) {
       if (done[q]) continue;
-      cd* rq = diffr + (int64_t)q * 5;
+      cd* rq = dr + (int64_t)q * 5;
       cd rp = rq[pi];
       for (int i = 0; i < 5; ++i)
         if (i != pi) rq[i] = cfma(mu[i], rp, rq[i]);
-      rq[pi] = cmul(rp, csub(tw_at(wN, diff[q] / 2), sb));
+      rq[pi] = cmul(rp, csub(tw_at(wN, did[q] / 2), sb));
     }
     // B* <- B* E
     int lmax = 0;
     for (int i = 0; i < 5; ++i) lmax = max(lmax, blen[i * 5 + pi]);
     for (int idx = tid; idx < 5 * (lmax + 1); idx += blockDim.x) {
       int i = idx / (lmax + 1), t = idx % (lmax + 1);
-      scratch[(int64_t)i * B.cap + t] = t < blen[i * 5 + pi] ? B.c[(int64_t)(i * 5 + pi) * B.cap + t] : mkc(0.0, 0.0);
+      scr[(int64_t)i * B.cap + t] = t < blen[i * 5 + pi] ? bc[(int64_t)(i * 5 + pi) * B.cap + t] : mkc(0.0, 0.0);
     }
     __syncthreads();
     for (int idx = tid; idx < 5 * (lmax + 1); idx += blockDim.x) {
       int i = idx / (lmax + 1), t = idx % (lmax + 1);
       int lo = blen[i * 5 + pi];
       if (lo == 0 || t > lo || t >= B.cap) continue;
-      cd o = t < lo ? scratch[(int64_t)i * B.cap + t] : mkc(0.0, 0.0);
-      cd prev = t >= 1 ? scratch[(int64_t)i * B.cap + t - 1] : mkc(0.0, 0.0);
-      B.c[(int64_t)(i * 5 + pi) * B.cap + t] = csub(prev, cmul(sb, o));
+      cd o = t < lo ? scr[(int64_t)i * B.cap + t] : mkc(0.0, 0.0);
+      cd prev = t >= 1 ? scr[(int64_t)i * B.cap + t - 1] : mkc(0.0, 0.0);
+      bc[(int64_t)(i * 5 + pi) * B.cap + t] = csub(prev, cmul(sb, o));
       if (t < lo)
         for (int j = 0; j < 5; ++j) {
           if (j == pi) continue;
-          cd* dst = B.c + (int64_t)(i * 5 + j) * B.cap + t;
+          cd* dst = bc + (int64_t)(i * 5 + j) * B.cap + t;
           cd cur = t < blen[i * 5 + j] ? *dst : mkc(0.0, 0.0);
           *dst = cfma(mu[j], o, cur);
         }
@@ -404,19 +454,19 @@ __global__ void __launch_bounds__(1024) k_diff_serial(BasisBuf B, const cd* __re
     if (tid == 0) dl[pi] += 1;
     __syncthreads();
   }
-  if (tid < 25) B.len[tid] = blen[tid];
+  if (tid < 25) B.lp(pb)[tid] = blen[tid];
   if (tid < 5) {
-    delta[tid] = dl[tid];
-    B.colmax[tid] = (unsigned long long)__double_as_longlong(0.5);  // scale 1
+    dlt[tid] = dl[tid];
+    B.mp(pb)[tid] = (unsigned long long)__double_as_longlong(0.5);  // scale 1
   }
 }
 
 int launch_difficult(Plan& P) {
-  int grid = std::min(P.opts.max_difficult, 128);
-  k_diff_eval<<<grid, 256, 0, P.stream>>>(P.buf[0][0], P.Phi, P.wN, P.N, P.ndiff, P.diff, P.opts.max_difficult,
-                                          P.diffr);
-  k_diff_serial<<<1, 1024, 0, P.stream>>>(P.buf[0][0], P.wN, P.ndiff, P.diff, P.opts.max_difficult, P.diffr,
-                                          P.delta, P.status, P.dscr);
+  int grid = std::min(P.opts.max_difficult, 64);
+  k_diff_eval<<<dim3(grid, P.nb), 256, 0, P.stream>>>(P.buf[0][0], P.Phi, P.wN, P.N, P.ndiff, P.diff,
+                                                      P.opts.max_difficult, P.diffr);
+  k_diff_serial<<<P.nb, 1024, 0, P.stream>>>(P.buf[0][0], P.wN, P.ndiff, P.diff, P.opts.max_difficult, P.diffr,
+                                             P.delta, P.status, P.dscr, P.dscr_stride);
   return cudaGetLastError() == cudaSuccess ? 2 : TIKH_ECUDA;
 }
 

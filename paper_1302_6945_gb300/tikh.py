@@ -20,14 +20,16 @@ TIKH_PREC_FP64 = 0
 
 class tikh_opts(ctypes.Structure):
     _fields_ = [("n_lim", ctypes.c_int), ("m_min", ctypes.c_int), ("fill", ctypes.c_int),
-                ("eps_diff", ctypes.c_double), ("max_difficult", ctypes.c_int), ("refine_steps", ctypes.c_int)]
+                ("eps_diff", ctypes.c_double), ("max_difficult", ctypes.c_int), ("refine_steps", ctypes.c_int),
+                ("batch", ctypes.c_int)]
 
 
 class tikh_stats(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int64), ("M", ctypes.c_int64), ("k", ctypes.c_int64), ("p", ctypes.c_int),
                 ("dual", ctypes.c_int), ("n_difficult", ctypes.c_int64), ("delta", ctypes.c_int * 5),
                 ("jstar", ctypes.c_int), ("retries", ctypes.c_int), ("kernel_launches", ctypes.c_int64),
-                ("workspace_bytes", ctypes.c_int64), ("refine_steps", ctypes.c_int), ("rel_residual", ctypes.c_double)]
+                ("workspace_bytes", ctypes.c_int64), ("refine_steps", ctypes.c_int), ("rel_residual", ctypes.c_double),
+                ("batch", ctypes.c_int)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}
@@ -44,6 +46,7 @@ class TikhError(RuntimeError):
 _lib = None
 
 EXPORTED = ["tikh_plan_create", "tikh_solve", "tikh_solve_async", "tikh_solve_normal", "tikh_solve_host",
+            "tikh_solve_batched",
             "tikh_sync", "tikh_get_stats", "tikh_plan_destroy", "tikh_strerror", "tikh_test_fft", "tikh_test_leaf"]
 
 
@@ -59,6 +62,7 @@ def lib():
         L.tikh_plan_create.argtypes = [ctypes.POINTER(vp), i64, i64, ci, ci, ctypes.POINTER(tikh_opts), vp]
         for f in ("tikh_solve", "tikh_solve_async", "tikh_solve_normal", "tikh_solve_host"):
             getattr(L, f).argtypes = [vp, vp, vp, vp, dbl, vp]
+        L.tikh_solve_batched.argtypes = [vp, ci, vp, i64, vp, i64, vp, i64, vp, vp, i64]
         L.tikh_sync.argtypes = [vp]
         L.tikh_get_stats.argtypes = [vp, ctypes.POINTER(tikh_stats)]
         L.tikh_plan_destroy.argtypes = [vp]
@@ -102,6 +106,12 @@ def tikh_solve_async(plan, col, row, b, lam, x):
 
 def tikh_solve_normal(plan, col, row, y, lam, x):
     _check(lib().tikh_solve_normal(plan, col, row, y, float(lam), x), "tikh_solve_normal")
+
+
+def tikh_solve_batched(plan, batch, col, col_stride, row, row_stride, b, b_stride, lambdas, x, x_stride):
+    lam = np.ascontiguousarray(lambdas, dtype=np.float64)
+    _check(lib().tikh_solve_batched(plan, int(batch), col, int(col_stride), row, int(row_stride), b, int(b_stride),
+                                    lam.ctypes.data_as(ctypes.c_void_p), x, int(x_stride)), "tikh_solve_batched")
 
 
 def tikh_solve_host(plan, col, row, b, lam, x):
@@ -179,12 +189,13 @@ class Plan:
     """A solver plan for m x n Toeplitz problems of one dtype ('r64' or 'c128')."""
 
     def __init__(self, m, n, dtype="r64", n_lim=32, m_min=0, fill=0, eps_diff=1e-8, max_difficult=4096,
-                 refine_steps=0, stream=None):
+                 refine_steps=0, batch=1, stream=None):
         import torch
         self.m, self.n = int(m), int(n)
         self.dtype = TIKH_C128 if dtype in ("c128", TIKH_C128, torch.complex128) else TIKH_R64
+        self.batch = int(batch)
         self.opts = tikh_opts(int(n_lim), int(m_min), int(fill), float(eps_diff), int(max_difficult),
-                              int(refine_steps))
+                              int(refine_steps), self.batch)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
@@ -212,6 +223,28 @@ class Plan:
         x = self._out(b, x)
         f = tikh_solve if sync else tikh_solve_async
         f(self.h, c, r, bb, lam, ctypes.c_void_p(x.data_ptr()))
+        return x
+
+    def solve_batched(self, col, row, b, lams, x=None):
+        """Solve a batch: col (B, m) or (m,), row (B, n) or (n,), b (B, m) or (m,), lams (B,) on the host.
+        A 1-D argument is shared by every problem of the batch (stride 0)."""
+        import torch
+        lams = np.ascontiguousarray(np.asarray(lams, dtype=np.float64).reshape(-1))
+        B = lams.size
+
+        def arg(t, ln):
+            if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
+                raise TypeError("expected contiguous CUDA tensors")
+            if _dtype_code(t) != self.dtype or t.shape[-1] != ln or (t.dim() == 2 and t.shape[0] != B) or t.dim() > 2:
+                raise ValueError("tensor dtype/shape does not match the plan and batch")
+            return ctypes.c_void_p(t.data_ptr()), (ln if t.dim() == 2 else 0)
+
+        c, cs = arg(col, self.m)
+        r, rs = arg(row, self.n)
+        bb, bs = arg(b, self.m)
+        if x is None:
+            x = torch.empty((B, self.n), dtype=b.dtype, device=b.device)
+        tikh_solve_batched(self.h, B, c, cs, r, rs, bb, bs, lams, ctypes.c_void_p(x.data_ptr()), self.n)
         return x
 
     def solve_normal(self, col, row, y, lam, x=None):
