@@ -156,6 +156,26 @@ int tikh_test_fft(int64_t n, void* data, int sign, void* stream);
 int tikh_test_leaf(int K, const void* sigma, const void* r, const int* delta_in, double eps, void* B, int* len,
                    int* delta_out, int* order, int* pivot, int64_t* deferred, int* n_def, void* stream);
 
+/* ---- allocation-free variant ---- */
+
+/* The DFT of tikh_test_fft (same transform, same kernels, same result) for callers that must not
+ * allocate device memory during the call: code running while a stream is being captured into a CUDA
+ * graph (cudaMalloc is not allowed there), code whose device memory is owned by another allocator or
+ * a fixed budget, and latency-critical loops that cannot afford an allocation.  The paper has no
+ * counterpart; this is an interface convenience.
+ * Its scratch (twiddle tables and the four-step temporary, about 2.2 MB) is one file-scope device
+ * array that every GPU loading the library keeps until process exit; nothing is allocated or freed
+ * per call (no cudaMalloc, cudaFree or allocating library routine).
+ * n must factor into 2, 3, 5, 7 and be at most 65536 (larger n returns TIKH_EINVAL: use
+ * tikh_test_fft).  data: n complex128 values on the device, transformed in place; the call
+ * synchronises the stream.
+ * The first call on each device looks up the scratch array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.  Every call rewrites the
+ * parts of the scratch it reads, so nothing needs clearing, but all calls share the one array: calls
+ * that overlap on the GPU (other streams, other host threads) race and must be serialised by the
+ * caller. */
+int tikh_fft_noalloc(int64_t n, void* data, int sign, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -47,7 +47,8 @@ _lib = None
 
 EXPORTED = ["tikh_plan_create", "tikh_solve", "tikh_solve_async", "tikh_solve_normal", "tikh_solve_host",
             "tikh_solve_batched",
-            "tikh_sync", "tikh_get_stats", "tikh_plan_destroy", "tikh_strerror", "tikh_test_fft", "tikh_test_leaf"]
+            "tikh_sync", "tikh_get_stats", "tikh_plan_destroy", "tikh_strerror", "tikh_test_fft", "tikh_test_leaf",
+            "tikh_fft_noalloc"]
 
 
 def lib():
@@ -70,6 +71,7 @@ def lib():
         L.tikh_strerror.argtypes = [ci]
         L.tikh_strerror.restype = ctypes.c_char_p
         L.tikh_test_fft.argtypes = [i64, vp, ci, vp]
+        L.tikh_fft_noalloc.argtypes = [i64, vp, ci, vp]
         L.tikh_test_leaf.argtypes = [ci, vp, vp, vp, dbl, vp, vp, vp, vp, vp, vp, vp, vp]
         _lib = L
     return _lib
@@ -134,6 +136,10 @@ def tikh_plan_destroy(plan):
 
 def tikh_test_fft(n, data, sign, stream=0):
     _check(lib().tikh_test_fft(int(n), data, int(sign), ctypes.c_void_p(int(stream))), "tikh_test_fft")
+
+
+def tikh_fft_noalloc(n, data, sign, stream=0):
+    _check(lib().tikh_fft_noalloc(int(n), data, int(sign), ctypes.c_void_p(int(stream))), "tikh_fft_noalloc")
 
 
 def tikh_test_leaf(K, sigma, r, delta_in, eps, B, length, delta_out, order, pivot, deferred, n_def, stream=0):
