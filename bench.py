@@ -138,6 +138,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=None, help="sweep point: n unknowns, m = 1.5 n (default: c2)")
     ap.add_argument("--batch", type=int, default=1, help="independent problems per step (tikh_solve_batched)")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -225,13 +226,15 @@ def main():
     hrow = torch.tensor(P["row"], dtype=torch.complex128).pin_memory().numpy()
     hb = torch.tensor(P["b"], dtype=torch.complex128).pin_memory().numpy()
     hx = torch.empty(n, dtype=torch.complex128).pin_memory().numpy()
-    plan.solve_host(hcol, hrow, hb, P["lam"], hx)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
+    e2e_t = float("nan")
+    if not args.no_e2e:
         plan.solve_host(hcol, hrow, hb, P["lam"], hx)
-    e2e_t = (time.perf_counter() - t0) / args.steps
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            plan.solve_host(hcol, hrow, hb, P["lam"], hx)
+        e2e_t = (time.perf_counter() - t0) / args.steps
     e2e_v = 1.0 / e2e_t  # host-buffer path solves one problem per call
-    if world > 1:
+    if world > 1 and not args.no_e2e:
         tt = torch.tensor([e2e_t], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         e2e_v = world / float(tt.item())

@@ -66,6 +66,8 @@ struct Plan {
   int batch_max = 1;
   int nb = 1;          // problems in the current call
   int slack_mult = 1;  // degree-prediction slack multiplier (raised after TIKH_EDEGREE)
+  int64_t eval_direct_max = 32;  // step 2 by Horner when the right child has <= this many nodes per coset
+  int64_t prod_direct_max = 64;  // step 4 by schoolbook products when the planned length P <= this
 
   std::vector<Step> sched;
   std::map<int64_t, int> fft_of_len;

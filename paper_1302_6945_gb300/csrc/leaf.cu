@@ -12,9 +12,10 @@
 //
 // Cost model on GB300: an FP64 warp instruction occupies its SM sub-partition for 64 cycles whatever
 // the number of active lanes (measured), FP32 ~4.5 cycles.  The pivot chain of a leaf therefore keeps
-// only the FP64 work that decides the next step (scores, the multipliers mu, the residual update);
-// the basis B_leaf = E_1 E_2 ... E_K is rebuilt after the chain from the recorded (pivot, sigma, mu)
-// of every step, with the 25 (row, column) entries spread over all warps.
+// only the FP64 work that decides the next step (scores, the multipliers mu, the residual update) and,
+// for K <= 32, runs warp-synchronously in one warp (shuffles, no block barrier inside a step); the
+// basis B_leaf = E_1 E_2 ... E_K is rebuilt by the other warps from the recorded (pivot, sigma, mu) of
+// each step, one step behind, on the other SM sub-partitions.
 #include "internal.h"
 
 namespace tikh {
@@ -43,6 +44,10 @@ __device__ __forceinline__ Pick warp_pick(Pick p) {
 }
 constexpr unsigned long long NO_PICK = 0ULL;  // every real score bit pattern is > 0 (score > 0)
 
+// non-zero test on the bit pattern (no FP64 instruction): +0.0 and -0.0 are zero
+__device__ __forceinline__ bool nz_bits(double v) { return ((unsigned long long)__double_as_longlong(v) << 1) != 0ULL; }
+__device__ __forceinline__ bool cnz(cd a) { return nz_bits(a.x) || nz_bits(a.y); }
+
 // pivot column and score of one residual row (score > 0 for a row with a non-zero entry)
 __device__ __forceinline__ Pick score_row(const cd* r, const int* dl, int q) {
   unsigned long long mb[5];
@@ -54,17 +59,19 @@ __device__ __forceinline__ Pick score_row(const cd* r, const int* dl, int q) {
   }
   tot = ((mag[0] + mag[1]) + (mag[2] + mag[3])) + mag[4];
   int pi = -1;
+  unsigned long long mpi = 0ULL;
+  double magpi = 0.0;
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
-    if (!cnonzero(r[i])) continue;
-    if (pi < 0 || dl[i] < dl[pi] || (dl[i] == dl[pi] && mb[i] > mb[pi])) pi = i;
+    if (!cnz(r[i])) continue;
+    if (pi < 0 || dl[i] < dl[pi] || (dl[i] == dl[pi] && mb[i] > mpi)) { pi = i; mpi = mb[i]; magpi = mag[i]; }
   }
   Pick p;
   p.idx = q;
   p.piv = pi;
   p.sb = NO_PICK;
   if (pi >= 0) {
-    double sc = mag[pi] / tot;
+    double sc = magpi / tot;
     p.sb = (unsigned long long)__double_as_longlong(sc);
     if (p.sb == 0ULL) p.sb = 1ULL;  // an underflowed ratio still ranks above "no candidate"
   }
@@ -112,27 +119,51 @@ struct SrcArrays {
   }
 };
 
-// one CTA per problem (blockIdx.x)
-template <class Src>
+__device__ __forceinline__ cd pick5(const cd* v, int i) {  // v[i] with a runtime i, by selects
+  cd o = v[0];
+  o = i == 1 ? v[1] : o;
+  o = i == 2 ? v[2] : o;
+  o = i == 3 ? v[3] : o;
+  o = i == 4 ? v[4] : o;
+  return o;
+}
+__device__ __forceinline__ cd shfl_cd(cd v, int src) {
+  return mkc(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+__device__ __forceinline__ void named_sync(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// One CTA per problem (blockIdx.x).  Warps [0, CW) run the pivot chain (one condition per lane,
+// K <= 32 * CW); warps [CW, 4) rebuild B from the step records, one step behind the chain, on the
+// other SM sub-partitions.  One __syncthreads per step hands the records over.
+template <int CW, class Src>
 __global__ void __launch_bounds__(LEAF_THREADS) k_leaf(Src src, int K, int* delta, int* dstack,
                                                         unsigned long long save_mask, double eps, BasisBuf out,
                                                         int* ndiff, int64_t* diff, int maxdiff, int* status,
                                                         int* rec_order, int* rec_pivot) {
+  constexpr int NCHAIN = 32 * CW, NREC = LEAF_THREADS - NCHAIN;
   __shared__ cd Bs[25][LEAF_CAP];
   __shared__ cd oldc[5][LEAF_CAP];
   __shared__ cd rec_mu[LEAF_KMAX][5];
   __shared__ cd rec_sig[LEAF_KMAX];
   __shared__ int rec_piv[LEAF_KMAX];
   __shared__ cd win_r[5];
+  __shared__ cd mu_s[5];
   __shared__ int blen[25];
-  __shared__ int dl[5], din[5];
-  __shared__ Pick wpick[LEAF_THREADS / 32];
-  __shared__ int nsteps_s;
-  const int tid = threadIdx.x, pb = blockIdx.x;
+  __shared__ int din[5], dl_out[5];
+  __shared__ Pick wpick[2];
+  __shared__ int done_s, nsteps_s;
+  const int tid = threadIdx.x, lane = tid & 31, pb = blockIdx.x;
   int* dlt = delta + 8 * pb;
 
-  if (tid < 5) { dl[tid] = dlt[tid]; din[tid] = dlt[tid]; }
-  // the leaf's own residual row and node
+  if (tid < 5) din[tid] = dlt[tid];
+  if (tid == 0) { done_s = 0; nsteps_s = 0; }
+  if (tid < 25) blen[tid] = (tid % 6 == 0) ? 1 : 0;
+  for (int idx = tid; idx < 25 * LEAF_CAP; idx += blockDim.x) {
+    int e = idx / LEAF_CAP, t = idx % LEAF_CAP;
+    Bs[e][t] = (t == 0 && e % 6 == 0) ? mkc(1.0, 0.0) : mkc(0.0, 0.0);
+  }
   cd r[5];
   cd sig = mkc(0.0, 0.0);
   bool active = tid < K;
@@ -143,120 +174,153 @@ __global__ void __launch_bounds__(LEAF_THREADS) k_leaf(Src src, int K, int* delt
     for (int d = 0; d < 64; ++d)
       if (save_mask >> d & 1ULL) dstack[((int64_t)pb * MAX_DEPTH + d) * 5 + tid] = din[tid];
   }
+  int dl[5];  // chain lanes keep the tau-degrees in registers
+#pragma unroll
+  for (int i = 0; i < 5; ++i) dl[i] = din[i];
   const unsigned long long eps_bits = (unsigned long long)__double_as_longlong(eps * eps);
-  const int nwarps = (K + 31) / 32;
 
-  // ---- pivot chain: decisions, multipliers and residual updates only ----
-  int step = 0;
-  for (; step < K; ++step) {
-    Pick p;
-    p.sb = NO_PICK;
-    p.idx = 1 << 30;
-    p.piv = -1;
-    if (active) {
-      p = score_row(r, dl, tid);
-      if (p.piv < 0) { active = false; p.sb = NO_PICK; p.idx = 1 << 30; }  // already satisfied
-    }
-    if (tid < 32 * nwarps) {
-      p = warp_pick(p);
-      if ((tid & 31) == 0) wpick[tid >> 5] = p;
-    }
-    __syncthreads();
-    Pick b = wpick[0];
-    for (int w = 1; w < nwarps; ++w)
-      if (pick_better(wpick[w], b)) b = wpick[w];
-    if (b.sb == NO_PICK) break;
-    if (b.sb < eps_bits) {  // difficult: defer the rest of the leaf
-      if (active) {
-        int slot = atomicAdd(ndiff + 4 * pb, 1);
-        if (slot < maxdiff) diff[(int64_t)pb * maxdiff + slot] = eid;
-        else set_status(status, ST_DIFFICULT);
-        active = false;
-      }
-      break;
-    }
-    const int pi = b.piv;
-    if (tid == b.idx) {
+  for (int step = 0;; ++step) {
+    if (tid < NCHAIN) {
+      // ---- one pivot step: decide, record, update ----
+      if (!done_s) {
+        Pick p;
+        p.sb = NO_PICK;
+        p.idx = 1 << 30;
+        p.piv = -1;
+        if (active) {
+          p = score_row(r, dl, tid);
+          if (p.piv < 0) { active = false; p.sb = NO_PICK; p.idx = 1 << 30; }  // already satisfied
+        }
+        p = warp_pick(p);
+        if (CW > 1) {
+          if (lane == 0) wpick[tid >> 5] = p;
+          named_sync(2, NCHAIN);
+          p = pick_better(wpick[1], wpick[0]) ? wpick[1] : wpick[0];
+        }
+        bool finish = false;
+        if (p.sb == NO_PICK) {
+          finish = true;
+        } else if (p.sb < eps_bits) {  // difficult: defer the rest of the leaf
+          if (active) {
+            int slot = atomicAdd(ndiff + 4 * pb, 1);
+            if (slot < maxdiff) diff[(int64_t)pb * maxdiff + slot] = eid;
+            else set_status(status, ST_DIFFICULT);
+            active = false;
+          }
+          finish = true;
+        }
+        if (finish) {
+          if (tid == 0) { done_s = 1; nsteps_s = step; }
+        } else {
+          const int pi = p.piv, w = p.idx;
+          cd rw[5], sw, mu[5];
+          if (CW == 1) {
 #pragma unroll
-      for (int i = 0; i < 5; ++i) win_r[i] = r[i];
-      rec_sig[step] = sig;
-      rec_piv[step] = pi;
-      if (rec_order) { rec_order[step] = b.idx; rec_pivot[step] = pi; }
-      active = false;
-    }
-    __syncthreads();
-    if (tid < 5) {  // mu_i = -r_i / r_pi, division as r_i * conj(r_pi) / |r_pi|^2, one lane per i
-      cd rp = win_r[pi];
-      double den = fma(rp.x, rp.x, rp.y * rp.y);
-      cd inv = mkc(rp.x / den, -rp.y / den);
-      cd m = (tid == pi) ? mkc(0.0, 0.0) : cmul(win_r[tid], inv);
-      rec_mu[step][tid] = mkc(-m.x, -m.y);
-    }
-    if (tid == 0) dl[pi] += 1;
-    __syncthreads();
-    if (active) {  // r <- r E(sigma): column pi times (sigma - sb), others += mu_i r_pi
-      const cd sb = rec_sig[step];
-      const cd rp = r[pi];
-      const cd* mu = rec_mu[step];
+            for (int i = 0; i < 5; ++i) rw[i] = shfl_cd(r[i], w);
+            sw = shfl_cd(sig, w);
+          } else {
+            if (tid == w) {
 #pragma unroll
-      for (int i = 0; i < 5; ++i) {
-        cd base = (i == pi) ? mkc(0.0, 0.0) : r[i];
-        cd fac = (i == pi) ? csub(sig, sb) : mu[i];
-        r[i] = cfma(fac, rp, base);
+              for (int i = 0; i < 5; ++i) win_r[i] = r[i];
+              rec_sig[step] = sig;
+            }
+            named_sync(2, NCHAIN);
+#pragma unroll
+            for (int i = 0; i < 5; ++i) rw[i] = win_r[i];
+            sw = rec_sig[step];
+          }
+          // mu_i = -r_i / r_pi as r_i * conj(r_pi) / |r_pi|^2: lane i of warp 0 computes mu_i
+          cd m = mkc(0.0, 0.0);
+          if (lane < 5 && lane != pi) {
+            cd rp = pick5(rw, pi);
+            double rd = 1.0 / fma(rp.x, rp.x, rp.y * rp.y);
+            cd inv = mkc(rp.x * rd, -rp.y * rd);
+            m = cmul(pick5(rw, lane), inv);
+            m = mkc(-m.x, -m.y);
+          }
+          if (CW == 1) {
+#pragma unroll
+            for (int i = 0; i < 5; ++i) mu[i] = shfl_cd(m, i);
+          } else {
+            if (tid < 5) mu_s[tid] = m;
+            named_sync(2, NCHAIN);
+#pragma unroll
+            for (int i = 0; i < 5; ++i) mu[i] = mu_s[i];
+          }
+          if (tid == w) active = false;
+          if (tid < 5) rec_mu[step][tid] = mu[tid];
+          if (tid == 0) {
+            rec_piv[step] = pi;
+            rec_sig[step] = sw;
+            if (rec_order) { rec_order[step] = w; rec_pivot[step] = pi; }
+          }
+          dl[pi] += 1;
+          if (active) {  // r <- r E(sigma): column pi times (sigma - sw), others += mu_i r_pi
+            const cd rp = pick5(r, pi);
+            const cd ds = csub(sig, sw);
+#pragma unroll
+            for (int i = 0; i < 5; ++i) {
+              cd base = (i == pi) ? mkc(0.0, 0.0) : r[i];
+              cd fac = (i == pi) ? ds : mu[i];
+              r[i] = cfma(fac, rp, base);
+            }
+          }
+          if (CW > 1) named_sync(2, NCHAIN);  // wpick / win_r / mu_s are rewritten next step
+        }
       }
+    } else if (step >= 1) {
+      // ---- rebuild B <- B E_{step-1} from the records ----
+      const int s = step - 1;
+      const int rt = tid - NCHAIN;
+      const int pi = rec_piv[s];
+      const cd sb = rec_sig[s];
+      int lmax = 0;
+#pragma unroll
+      for (int i = 0; i < 5; ++i) lmax = max(lmax, blen[i * 5 + pi]);
+      for (int idx = rt; idx < 5 * lmax; idx += NREC) {
+        int i = idx / lmax, t = idx % lmax;
+        oldc[i][t] = Bs[i * 5 + pi][t];
+      }
+      named_sync(1, NREC);
+      // item (row i, column j, coefficient t): column pi <- (z - sb) column pi, column j += mu_j old pi
+      for (int idx = rt; idx < 25 * (lmax + 1); idx += NREC) {
+        int e = idx / (lmax + 1), t = idx % (lmax + 1);
+        int i = e / 5, j = e % 5;
+        int lo = blen[i * 5 + pi];
+        if (lo == 0 || t > lo) continue;
+        cd o = t < lo ? oldc[i][t] : mkc(0.0, 0.0);
+        if (j == pi) {
+          cd prev = t >= 1 ? oldc[i][t - 1] : mkc(0.0, 0.0);
+          Bs[e][t] = csub(prev, cmul(sb, o));
+        } else if (t < lo) {
+          Bs[e][t] = cfma(rec_mu[s][j], o, Bs[e][t]);
+        }
+      }
+      named_sync(1, NREC);
+      if (rt < 5) {
+        int i = rt, lo = blen[i * 5 + pi];
+        if (lo > 0) {
+          for (int j = 0; j < 5; ++j)
+            if (j != pi && blen[i * 5 + j] < lo) blen[i * 5 + j] = lo;
+          blen[i * 5 + pi] = lo + 1;
+        }
+      }
+      named_sync(1, NREC);
     }
+    __syncthreads();
+    // the chain is done (it always is by step K: every step processes or drops a condition) and every
+    // recorded step 0 .. nsteps-1 has been rebuilt; done_s / nsteps_s were written before the barrier
+    if (done_s && step >= nsteps_s) break;
+    __syncthreads();
   }
-  if (tid == 0) nsteps_s = step;
-  // ---- basis reconstruction B = E_1 ... E_steps (off the pivot chain) ----
-  if (tid < 25) blen[tid] = (tid % 6 == 0) ? 1 : 0;
-  for (int idx = tid; idx < 25 * LEAF_CAP; idx += blockDim.x) {
-    int e = idx / LEAF_CAP, t = idx % LEAF_CAP;
-    Bs[e][t] = (t == 0 && e % 6 == 0) ? mkc(1.0, 0.0) : mkc(0.0, 0.0);
-  }
+  if (tid < 5) dl_out[tid] = dl[tid];  // lanes 0..4 of the chain hold the final degrees
   __syncthreads();
-  const int nsteps = nsteps_s;
-  for (int s = 0; s < nsteps; ++s) {
-    const int pi = rec_piv[s];
-    const cd sb = rec_sig[s];
-    int lmax = 0;
-#pragma unroll
-    for (int i = 0; i < 5; ++i) lmax = max(lmax, blen[i * 5 + pi]);
-    for (int idx = tid; idx < 5 * lmax; idx += blockDim.x) {
-      int i = idx / lmax, t = idx % lmax;
-      oldc[i][t] = Bs[i * 5 + pi][t];
-    }
-    __syncthreads();
-    // item (row i, column j, coefficient t): column pi <- (z - sb) column pi, column j += mu_j old pi
-    for (int idx = tid; idx < 25 * (lmax + 1); idx += blockDim.x) {
-      int e = idx / (lmax + 1), t = idx % (lmax + 1);
-      int i = e / 5, j = e % 5;
-      int lo = blen[i * 5 + pi];
-      if (lo == 0 || t > lo) continue;
-      cd o = t < lo ? oldc[i][t] : mkc(0.0, 0.0);
-      if (j == pi) {
-        cd prev = t >= 1 ? oldc[i][t - 1] : mkc(0.0, 0.0);
-        Bs[e][t] = csub(prev, cmul(sb, o));
-      } else if (t < lo) {
-        Bs[e][t] = cfma(rec_mu[s][j], o, Bs[e][t]);
-      }
-    }
-    __syncthreads();
-    if (tid < 5) {
-      int i = tid, lo = blen[i * 5 + pi];
-      if (lo > 0) {
-        for (int j = 0; j < 5; ++j)
-          if (j != pi && blen[i * 5 + j] < lo) blen[i * 5 + j] = lo;
-        blen[i * 5 + pi] = lo + 1;
-      }
-    }
-    __syncthreads();
-  }
   // ---- trim to the degree bounds, record column maxima, write out ----
   __shared__ unsigned long long cmax[5];
   if (tid < 5) cmax[tid] = 0ULL;
   if (tid < 25) {
     int i = tid / 5, j = tid % 5;
-    int bnd = entry_bound(din, dl, i, j);
+    int bnd = entry_bound(din, dl_out, i, j);
     int want = bnd < 0 ? 0 : bnd + 1;
     if (blen[tid] > want) blen[tid] = want;
   }
@@ -275,18 +339,29 @@ __global__ void __launch_bounds__(LEAF_THREADS) k_leaf(Src src, int K, int* delt
   if (tid < 25) out.lp(pb)[tid] = blen[tid];
   if (tid < 5) {
     out.mp(pb)[tid] = cmax[tid];
-    dlt[tid] = dl[tid];
+    dlt[tid] = dl_out[tid];
   }
+}
+
+template <class Src>
+static int launch_leaf_t(const Src& src, int K, int nb, int* delta, int* dstack, unsigned long long mask, double eps,
+                         const BasisBuf& out, int* ndiff, int64_t* diff, int maxdiff, int* status, int* order,
+                         int* pivot, cudaStream_t s) {
+  if (K <= 32)
+    k_leaf<1, Src><<<nb, LEAF_THREADS, 0, s>>>(src, K, delta, dstack, mask, eps, out, ndiff, diff, maxdiff, status,
+                                               order, pivot);
+  else
+    k_leaf<2, Src><<<nb, LEAF_THREADS, 0, s>>>(src, K, delta, dstack, mask, eps, out, ndiff, diff, maxdiff, status,
+                                               order, pivot);
+  return cudaGetLastError() == cudaSuccess ? 1 : TIKH_ECUDA;
 }
 
 int launch_leaf(Plan& P, const Step& st) {
   int K = (int)(4 * st.L);
   if (K > LEAF_KMAX) return TIKH_EINVAL;
-  k_leaf<SrcNodes><<<P.nb, LEAF_THREADS, 0, P.stream>>>(SrcNodes{P.R, P.wN, P.N, st.a, st.s}, K, P.delta, P.dstack,
-                                                        st.save_mask, P.opts.eps_diff, P.buf[st.depth][st.side],
-                                                        P.ndiff, P.diff, P.opts.max_difficult, P.status, nullptr,
-                                                        nullptr);
-  return cudaGetLastError() == cudaSuccess ? 1 : TIKH_ECUDA;
+  return launch_leaf_t(SrcNodes{P.R, P.wN, P.N, st.a, st.s}, K, P.nb, P.delta, P.dstack, st.save_mask,
+                       P.opts.eps_diff, P.buf[st.depth][st.side], P.ndiff, P.diff, P.opts.max_difficult, P.status,
+                       nullptr, nullptr, P.stream);
 }
 
 // test hook: one leaf (one problem) on explicit device arrays
@@ -299,9 +374,8 @@ int launch_leaf_arrays(int K, const cd* sigma, const cd* r, int* delta, double e
   out.len = len;
   out.colmax = colmax;
   out.cap = K + 1;
-  k_leaf<SrcArrays><<<1, LEAF_THREADS, 0, s>>>(SrcArrays{sigma, r}, K, delta, nullptr, 0ULL, eps, out, ndiff, diff, K,
-                                               status, order, pivot);
-  return cudaGetLastError() == cudaSuccess ? 1 : TIKH_ECUDA;
+  return launch_leaf_t(SrcArrays{sigma, r}, K, 1, delta, nullptr, 0ULL, eps, out, ndiff, diff, K, status, order, pivot,
+                       s);
 }
 
 // ------------------------------------------------------------------------------------------------

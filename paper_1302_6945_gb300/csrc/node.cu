@@ -29,10 +29,13 @@ __device__ __forceinline__ int entry_bound_dev(const int* din, const int* dout, 
 // ------------------------------------------------------------------------------------------------
 struct LoadTwistFold {  // transform t = 50 pb + 2E + c
   BasisBuf B;
+  BasisBuf OUT;  // this node's output slot: its column maxima are reset here, before the product
   const cd* wN;
   int64_t N, Lr, beta0;
   __device__ cd operator()(int t, int64_t u) const {
     int pb = t / 50, b = t % 50;
+    if (b == 0 && u == 0)
+      for (int j = 0; j < 5; ++j) OUT.mp(pb)[j] = 0ULL;
     int E = b >> 1, c = b & 1;
     int64_t beta = beta0 + c;
     int64_t len = B.lp(pb)[E];
@@ -75,11 +78,65 @@ __global__ void k_eval_update(cd* R, const cd* __restrict__ vals, int64_t N, int
   }
 }
 
+// Small nodes: B_L evaluated by Horner at each right-child node (thread per (node, entry)), then the
+// residual update of that node's two conditions, in one launch.  Block = 8 nodes x 25 entries.
+constexpr int EVD_NODES = 8;
+__global__ void __launch_bounds__(256) k_eval_direct(BasisBuf BL, BasisBuf OUT, cd* R, const cd* __restrict__ wN,
+                                                     int64_t N, int64_t a0, int64_t s2, int64_t Lr) {
+  __shared__ cd V[EVD_NODES][25];
+  __shared__ cd Rs[EVD_NODES][10];
+  __shared__ double scl[5];
+  const int pb = blockIdx.y, tid = threadIdx.x;
+  if (tid < 5) scl[tid] = col_scale_from_bits(BL.mp(pb)[tid]);
+  if (blockIdx.x == 0 && tid >= 32 && tid < 37) OUT.mp(pb)[tid - 32] = 0ULL;
+  const int64_t g0 = (int64_t)blockIdx.x * EVD_NODES;  // first node (g = 2j + c) of this block
+  if (tid < EVD_NODES * 10) {  // stage the two residual rows of each node
+    int ln = tid / 10, k = tid % 10;
+    int64_t g = g0 + ln;
+    if (g < 2 * Lr) {
+      int64_t e = a0 + (g & 1) + s2 * (g >> 1);
+      Rs[ln][k] = R[((int64_t)pb * N + e) * 10 + k];
+    }
+  }
+  __syncthreads();
+  if (tid < EVD_NODES * 25) {
+    int ln = tid / 25, E = tid % 25;
+    int64_t g = g0 + ln;
+    if (g < 2 * Lr) {
+      int64_t e = a0 + (g & 1) + s2 * (g >> 1);
+      cd z = wN[e];
+      const cd* c = BL.cp(pb) + (int64_t)E * BL.cap;
+      int len = BL.lp(pb)[E];
+      cd v = mkc(0.0, 0.0);
+      for (int t = len - 1; t >= 0; --t) v = cfma(v, z, c[t]);
+      V[ln][E] = cscale(v, scl[E % 5]);
+    }
+  }
+  __syncthreads();
+  if (tid < EVD_NODES * 10) {  // (node, condition f, column): phi <- phi B_L(sigma)
+    int ln = tid / 10, f = (tid / 5) % 2, col = tid % 5;
+    int64_t g = g0 + ln;
+    if (g < 2 * Lr) {
+      int64_t e = a0 + (g & 1) + s2 * (g >> 1);
+      cd acc = mkc(0.0, 0.0);
+#pragma unroll
+      for (int i = 0; i < 5; ++i) acc = cfma(Rs[ln][f * 5 + i], V[ln][i * 5 + col], acc);
+      R[((int64_t)pb * N + e) * 10 + f * 5 + col] = acc;
+    }
+  }
+}
+
 int launch_eval(Plan& P, const Step& st) {
-  const FftPlan& F = P.ffts[st.fft];
   const int64_t Lr = st.L / 2;
   const BasisBuf& BL = P.buf[st.depth + 1][0];
-  int r = fft_run(F, 50 * P.nb, +1, LoadTwistFold{BL, P.wN, P.N, Lr, st.a + st.s}, StoreEval{P.evalv, Lr}, P.etmp,
+  const BasisBuf& OUT = P.buf[st.depth][st.side];
+  if (Lr <= P.eval_direct_max) {
+    dim3 grid((unsigned)((2 * Lr + EVD_NODES - 1) / EVD_NODES), (unsigned)P.nb);
+    k_eval_direct<<<grid, 256, 0, P.stream>>>(BL, OUT, P.R, P.wN, P.N, st.a + st.s, 2 * st.s, Lr);
+    return cudaGetLastError() == cudaSuccess ? 1 : TIKH_ECUDA;
+  }
+  const FftPlan& F = P.ffts[st.fft];
+  int r = fft_run(F, 50 * P.nb, +1, LoadTwistFold{BL, OUT, P.wN, P.N, Lr, st.a + st.s}, StoreEval{P.evalv, Lr}, P.etmp,
                   P.stream);
   if (r < 0) return TIKH_ECUDA;
   dim3 grid((unsigned)std::min<int64_t>((2 * Lr + 127) / 128, 4096), (unsigned)P.nb);
@@ -181,11 +238,66 @@ __global__ void k_prod_finish(const cd* __restrict__ FC, int64_t P, BasisBuf OUT
   }
 }
 
+// Small nodes: schoolbook product, one block per (output entry, problem), thread per coefficient,
+// trimmed to the degree bound, column maxima accumulated (reset by this node's evaluation step).
+__global__ void __launch_bounds__(256) k_prod_direct(BasisBuf BL, BasisBuf BR, BasisBuf OUT, const int* dstack,
+                                                     int depth, const int* delta, int* status) {
+  const int E = blockIdx.x, i = E / 5, j = E % 5, pb = blockIdx.y, tid = threadIdx.x;
+  __shared__ double sl[5], sr;
+  __shared__ int want_s, ll[5], lr[5];
+  __shared__ double red[8];
+  if (tid < 5) {
+    sl[tid] = col_scale_from_bits(BL.mp(pb)[tid]);
+    ll[tid] = BL.lp(pb)[i * 5 + tid];
+    lr[tid] = BR.lp(pb)[tid * 5 + j];
+  }
+  if (tid == 0) {
+    sr = col_scale_from_bits(BR.mp(pb)[j]);
+    int bnd = entry_bound_dev(dstack + (pb * MAX_DEPTH + depth) * 5, delta + 8 * pb, i, j);
+    int want = bnd < 0 ? 0 : bnd + 1;
+    if (want > OUT.cap) { set_status(status, ST_DEGREE); want = (int)OUT.cap; }
+    want_s = want;
+    OUT.lp(pb)[E] = want;
+  }
+  __syncthreads();
+  const int want = want_s;
+  const cd* lc = BL.cp(pb) + (int64_t)(i * 5) * BL.cap;
+  const cd* rc = BR.cp(pb) + (int64_t)j * BR.cap;
+  cd* dst = OUT.cp(pb) + (int64_t)E * OUT.cap;
+  double mx = 0.0;
+  for (int t = tid; t < want; t += blockDim.x) {
+    cd acc = mkc(0.0, 0.0);
+    for (int u = 0; u < 5; ++u) {
+      const cd* a = lc + (int64_t)u * BL.cap;
+      const cd* b = rc + (int64_t)(u * 5) * BR.cap;
+      int la = ll[u], lb = lr[u];
+      int s0 = max(0, t - lb + 1), s1 = min(t, la - 1);
+      cd part = mkc(0.0, 0.0);
+      for (int q = s0; q <= s1; ++q) part = cfma(a[q], b[t - q], part);
+      acc = cfma(part, mkc(sl[u] * sr, 0.0), acc);
+    }
+    dst[t] = acc;
+    mx = fmax(mx, fmax(fabs(acc.x), fabs(acc.y)));
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((tid & 31) == 0) red[tid >> 5] = mx;
+  __syncthreads();
+  if (tid == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, red[w]);
+    if (mx > 0.0) atomicMax(OUT.mp(pb) + j, (unsigned long long)__double_as_longlong(mx));
+  }
+}
+
 int launch_prod(Plan& P, const Step& st) {
-  const FftPlan& F = P.ffts[st.fft];
   const BasisBuf& BL = P.buf[st.depth + 1][0];
   const BasisBuf& BR = P.buf[st.depth + 1][1];
   const BasisBuf& OUT = P.buf[st.depth][st.side];
+  if (st.P <= P.prod_direct_max) {
+    int threads = (int)std::min<int64_t>(256, ((st.P + 31) / 32) * 32);
+    k_prod_direct<<<dim3(25, P.nb), threads, 0, P.stream>>>(BL, BR, OUT, P.dstack, st.depth, P.delta, P.status);
+    return cudaGetLastError() == cudaSuccess ? 1 : TIKH_ECUDA;
+  }
+  const FftPlan& F = P.ffts[st.fft];
   int nl = 0, r;
   LoadPad lp{BL, BR, OUT, P.dstack, P.delta, st.depth, P.status, st.P};
   if ((r = fft_run(F, 50 * P.nb, +1, lp, StoreSpec{P.FA, P.FB, st.P}, P.ptmp, P.stream)) < 0) return TIKH_ECUDA;
