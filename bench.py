@@ -24,6 +24,22 @@ sys.path.insert(0, ROOT)
 
 METRIC = "solves/s and n*solves/s at n=2^16..2^20 vs plain FP64 GPU at rel err<=1e-8; HBM %"
 
+# FP64 peak of GB300 from its unit counts: 152 SMs x 4 sub-partitions x 0.5 DFMA/clk x 2 flop x clock
+# (the sub-partition rate was measured: one FP64 warp instruction per 64 cycles).
+FP64_PEAK_GFLOPS = 152 * 4 * 0.5 * 2 * 2.070
+
+
+def leaf_model_flops(K):
+    """Algorithmic FP64 flops of one leaf of K conditions (serial single-point construction):
+    pivot chain sum_s [60 (K - s) + 60] (score 20 + update 40 per remaining condition, mu 60 per step)
+    plus the basis rebuild ~20 K^2 (5 rows x ~K/10 coefficients x 40 flops per step)."""
+    return 30 * K * K + 90 * K + 20 * K * K
+
+
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_leaf launch (K = 20, one problem), from
+# profiles/k_leaf_c2recipe_n4096.md; None once the kernel changes after that capture
+LEAF_TRAFFIC_BYTES = 52224
+
 
 def peaks():
     try:
@@ -212,6 +228,17 @@ def main():
     plan.sync()
     clocks = clk.stop()
     step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
+
+    # dominant kernel (the leaf): every launch timed with a CUDA event pair on the plan's stream, over
+    # the same number of steps right after the timed region (events are not in the timed steps)
+    plan.set_profiling(1)
+    with torch.cuda.stream(stream):
+        for i in range(args.steps):
+            flush.zero_()
+            step(sync=True)
+    plan.sync()
+    pst = plan.stats()
+    plan.set_profiling(0)
     t_step = sum(step_ms) / len(step_ms)
     t_max = t_step
     if world > 1:
@@ -240,6 +267,17 @@ def main():
         e2e_v = world / float(tt.item())
 
     pk, pk_kind = peaks()
+    K_leaf = 2 * int(st["M"])
+    leaf_launches = max(1, int(pst["prof_leaf_launches"]))
+    leaf_ms = max(pst["prof_leaf_ms"] / leaf_launches, 1e-9)
+    leaf_gflops = leaf_model_flops(K_leaf) * B / (leaf_ms * 1e-3) / 1e9
+    roofline = {"bound": "alu", "kernel": "k_leaf (FP64 serial single-point construction)",
+                "achieved": leaf_gflops, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                "frac": leaf_gflops / FP64_PEAK_GFLOPS, "peak_kind": "derived from unit counts and max clock",
+                "traffic": LEAF_TRAFFIC_BYTES, "avg_launch_ms": leaf_ms,
+                "launches_per_step": leaf_launches / args.steps,
+                "share_of_step": (pst["prof_leaf_ms"] / args.steps) / t_step,
+                "flops_per_launch": leaf_model_flops(K_leaf) * B}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
@@ -267,6 +305,7 @@ def main():
                "gpu_launches": int(st["kernel_launches"]) * args.steps,
                "clocks": clocks,
                "peaks": {"hbm_gbs": pk.get("hbm_gbs"), "kind": pk_kind},
+               "roofline": roofline,
                "cpu_baseline": cpu}
         print(json.dumps(out))
     plan.close()

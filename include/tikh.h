@@ -87,6 +87,8 @@ typedef struct {
   int refine_steps;        /* corrections applied in the last solve */
   double rel_residual;     /* largest ||y - (T^H T + lambda I) x|| / ||y|| after refinement (-1 if none) */
   int batch;               /* problems in the last call */
+  double prof_leaf_ms;     /* with profiling on: summed duration of the leaf launches since it was switched on */
+  int64_t prof_leaf_launches; /* with profiling on: leaf launches timed since it was switched on */
 } tikh_stats;
 
 /* Build a plan for an m x n problem: sizing by Algorithm 2 (Sec. 5.2), the recursion schedule of
@@ -132,6 +134,12 @@ int tikh_sync(tikh_plan plan);
 
 /* Statistics of the plan and of the last synchronised solve. */
 int tikh_get_stats(tikh_plan plan, tikh_stats* out);
+
+/* Profiling switch: flags = 1 records a CUDA event pair around every leaf launch (Eq. (spbasis)
+ * kernel) on the plan's stream; every synchronising call adds them to tikh_stats.prof_leaf_ms and
+ * prof_leaf_launches, which this call resets.  flags = 0 turns it off.  The events add a little host
+ * and device time. */
+int tikh_set_profiling(tikh_plan plan, int flags);
 
 /* Release all device and host memory of the plan.  NULL is ignored. */
 void tikh_plan_destroy(tikh_plan plan);

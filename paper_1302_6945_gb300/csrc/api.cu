@@ -194,9 +194,26 @@ int enqueue_core(Plan& P, const cd* y, cd* out, int64_t& nl) {
   if ((r = launch_conditions(P, y)) < 0) return r;
   nl += r;
   for (const Step& st : P.sched) {
-    if (st.kind == STEP_LEAF) r = launch_leaf(P, st);
-    else if (st.kind == STEP_EVAL) r = launch_eval(P, st);
-    else r = launch_prod(P, st);
+    if (st.kind == STEP_LEAF) {
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      if (P.prof_leaf) {
+        while (P.ev_pool.size() < P.ev_used + 2) {
+          cudaEvent_t e;
+          if (cudaEventCreate(&e) != cudaSuccess) return TIKH_ECUDA;
+          P.ev_pool.push_back(e);
+        }
+        e0 = P.ev_pool[P.ev_used];
+        e1 = P.ev_pool[P.ev_used + 1];
+        P.ev_used += 2;
+        cudaEventRecord(e0, P.stream);
+      }
+      r = launch_leaf(P, st);
+      if (e1) cudaEventRecord(e1, P.stream);
+    } else if (st.kind == STEP_EVAL) {
+      r = launch_eval(P, st);
+    } else {
+      r = launch_prod(P, st);
+    }
     if (r < 0) return r;
     nl += r;
   }
@@ -266,6 +283,16 @@ int sync_status(Plan& P) {
       worst = std::max(worst, v);
     }
     P.last.rel_residual = worst;
+  }
+  if (P.prof_leaf) {  // average leaf duration from the event pairs recorded since the last sync
+    double ms = 0.0;
+    for (size_t i = 0; i + 1 < P.ev_used; i += 2) {
+      float t = 0.0f;
+      if (cudaEventElapsedTime(&t, P.ev_pool[i], P.ev_pool[i + 1]) == cudaSuccess) ms += t;
+    }
+    P.last.prof_leaf_ms += ms;  // accumulated until tikh_set_profiling re-arms it
+    P.last.prof_leaf_launches += (int64_t)(P.ev_used / 2);
+    P.ev_used = 0;
   }
   int zero = 0;
   cudaMemcpy(P.status, &zero, sizeof(int), cudaMemcpyHostToDevice);
@@ -448,9 +475,19 @@ int tikh_get_stats(tikh_plan h, tikh_stats* out) {
   return TIKH_OK;
 }
 
+int tikh_set_profiling(tikh_plan h, int flags) {
+  if (!h || flags < 0 || flags > 1) return TIKH_EINVAL;
+  h->P.prof_leaf = flags & 1;
+  h->P.ev_used = 0;
+  h->P.last.prof_leaf_ms = 0.0;
+  h->P.last.prof_leaf_launches = 0;
+  return TIKH_OK;
+}
+
 void tikh_plan_destroy(tikh_plan h) {
   if (!h) return;
   cudaStreamSynchronize(h->P.stream);
+  for (cudaEvent_t e : h->P.ev_pool) cudaEventDestroy(e);
   for (void* p : h->P.allocs) cudaFree(p);
   delete h;
 }

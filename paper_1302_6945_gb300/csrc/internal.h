@@ -110,6 +110,11 @@ struct Plan {
   void* d_in = nullptr;  // staging for tikh_solve_host: col | row | b | x
   int64_t launches = 0;
 
+  // optional timing of every leaf launch with a CUDA event pair on the plan's stream
+  int prof_leaf = 0;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+
   tikh_stats last{};
 };
 

@@ -29,7 +29,7 @@ class tikh_stats(ctypes.Structure):
                 ("dual", ctypes.c_int), ("n_difficult", ctypes.c_int64), ("delta", ctypes.c_int * 5),
                 ("jstar", ctypes.c_int), ("retries", ctypes.c_int), ("kernel_launches", ctypes.c_int64),
                 ("workspace_bytes", ctypes.c_int64), ("refine_steps", ctypes.c_int), ("rel_residual", ctypes.c_double),
-                ("batch", ctypes.c_int)]
+                ("batch", ctypes.c_int), ("prof_leaf_ms", ctypes.c_double), ("prof_leaf_launches", ctypes.c_int64)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}
@@ -48,7 +48,7 @@ _lib = None
 EXPORTED = ["tikh_plan_create", "tikh_solve", "tikh_solve_async", "tikh_solve_normal", "tikh_solve_host",
             "tikh_solve_batched",
             "tikh_sync", "tikh_get_stats", "tikh_plan_destroy", "tikh_strerror", "tikh_test_fft", "tikh_test_leaf",
-            "tikh_fft_noalloc"]
+            "tikh_fft_noalloc", "tikh_set_profiling"]
 
 
 def lib():
@@ -65,6 +65,7 @@ def lib():
             getattr(L, f).argtypes = [vp, vp, vp, vp, dbl, vp]
         L.tikh_solve_batched.argtypes = [vp, ci, vp, i64, vp, i64, vp, i64, vp, vp, i64]
         L.tikh_sync.argtypes = [vp]
+        L.tikh_set_profiling.argtypes = [vp, ci]
         L.tikh_get_stats.argtypes = [vp, ctypes.POINTER(tikh_stats)]
         L.tikh_plan_destroy.argtypes = [vp]
         L.tikh_plan_destroy.restype = None
@@ -132,6 +133,10 @@ def tikh_get_stats(plan):
 
 def tikh_plan_destroy(plan):
     lib().tikh_plan_destroy(plan)
+
+
+def tikh_set_profiling(plan, flags):
+    _check(lib().tikh_set_profiling(plan, int(flags)), "tikh_set_profiling")
 
 
 def tikh_test_fft(n, data, sign, stream=0):
@@ -274,6 +279,9 @@ class Plan:
 
     def sync(self):
         tikh_sync(self.h)
+
+    def set_profiling(self, flags):
+        tikh_set_profiling(self.h, flags)
 
     def stats(self):
         return tikh_get_stats(self.h)
