@@ -237,3 +237,33 @@ def dense_solve_normal(col, row, y, lam):
     T = toeplitz_dense(col, row)
     n = T.shape[1]
     return np.linalg.solve(T.conj().T @ T + lam * np.eye(n), _c128(y))
+
+
+# ---------------------------------------------------------------------------------------------
+# Adjoint of x = (T^H T + lam I)^{-1} T^H b, m >= n (conjugate-Wirtinger convention: dL = Re(G^H dx)).
+# ---------------------------------------------------------------------------------------------
+
+def solve_normal_refined(col, row, y, lam, steps=1, nlim=32):
+    """(T^H T + lam I)^{-1} y by the superfast solve plus `steps` refinement corrections."""
+    col, row, y = _c128(col), _c128(row), _c128(y)
+    v, _ = solve_normal(col, row, y, lam, nlim=nlim)
+    for _ in range(steps):
+        res = y - (apply_th(col, row, apply_t(col, row, v)) + lam * v)
+        dv, _ = solve_normal(col, row, res, lam, nlim=nlim)
+        v = v + dv
+    return v
+
+
+def adjoint(col, row, b, lam, x, G, steps=1, nlim=32):
+    """(dL/dcol, dL/drow, dL/db, dL/dlam) for dL/dx = G:  g = A^{-1} G, u = T g, r = b - T x,
+    dL/db = u, dL/dlam = -Re(g^H x), dL/da_d = sum_j r_{j+d} conj(g_j) - u_{j+d} conj(x_j)."""
+    col, row, b, x, G = _c128(col), _c128(row), _c128(b), _c128(x), _c128(G)
+    m, n = col.size, row.size
+    g = solve_normal_refined(col, row, G, lam, steps=steps, nlim=nlim)
+    u = apply_t(col, row, g)
+    r = b - apply_t(col, row, x)
+    c = np.correlate(r, g, mode="full") - np.correlate(u, x, mode="full")  # index d + n - 1, d in [-(n-1), m-1]
+    dcol = c[n - 1:n - 1 + m]
+    drow = np.zeros(n, np.complex128)
+    drow[1:] = c[n - 2::-1][:n - 1]
+    return dcol, drow, u, float(-np.real(np.vdot(g, x)))
