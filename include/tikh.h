@@ -113,6 +113,17 @@ int tikh_solve_async(tikh_plan plan, const void* col, const void* row, const voi
  * paper's experiments solve (Sec. 6.1).  Requires m >= n (the tall, stable formulation). */
 int tikh_solve_normal(tikh_plan plan, const void* col, const void* row, const void* y, double lambda, void* x);
 
+/* Adjoint of x = (T^H T + lambda I)^{-1} T^H b for a real loss L (m >= n; TIKH_EINVAL otherwise).
+ * Inputs (device, plan dtype): col, row, b, lambda as in tikh_solve, x = the solution, dLdx = dL/dx in
+ * the conjugate-Wirtinger convention (dL = Re(dLdx^H dx), PyTorch's convention).  With A = T^H T +
+ * lambda I and g = A^{-1} dLdx -- one more superfast solve with dLdx as its right-hand side, refined
+ * like tikh_solve --:  dLdb = T g;  *dLdlambda = -Re(g^H x) (host double);  dLdcol[d] = sum_j
+ * r_{j+d} conj(g_j) - u_{j+d} conj(x_j) for the diagonal a_d (d >= 0), dLdrow[d] the same for a_{-d}
+ * (d >= 1), dLdrow[0] = 0, with r = b - T x and u = T g, evaluated as two FFT cross-correlations.
+ * Real dtype returns real parts.  The first call allocates the adjoint workspace; synchronises. */
+int tikh_solve_grad(tikh_plan plan, const void* col, const void* row, const void* b, double lambda, const void* x,
+                    const void* dLdx, void* dLdcol, void* dLdrow, void* dLdb, double* dLdlambda);
+
 /* `batch` problems of the plan's shape in one pass: every step of the method is one launch for all of
  * them (a batch shares the recursion schedule; each problem keeps its own tau-degrees, pivots and
  * basis).  Problem i reads col + i*col_stride, row + i*row_stride, b + i*b_stride and lambdas[i]

@@ -224,19 +224,9 @@ int enqueue_core(Plan& P, const cd* y, cd* out, int64_t& nl) {
   return TIKH_OK;
 }
 
-int enqueue_solve(Plan& P, const UserArrays& u, int rhs_is_y, const double* lams, int nb) {
-  int64_t nl = 0;
+// core solve of A v = y (y in P.ybuf) into P.xcore, then opts.refine_steps corrections
+int enqueue_core_refined(Plan& P, int64_t& nl) {
   int r;
-  if (nb < 1 || nb > P.batch_max) return TIKH_EINVAL;
-  P.nb = nb;
-  if (cudaMemcpyAsync(P.lam, lams, sizeof(double) * (size_t)nb, cudaMemcpyHostToDevice, P.stream) != cudaSuccess)
-    return TIKH_ECUDA;
-  if (cudaMemsetAsync(P.status, 0, sizeof(int), P.stream) != cudaSuccess) return TIKH_ECUDA;
-  if ((r = launch_spectrum(P, u)) < 0) return r;
-  nl += r;
-  // for m < n the core problem (T T^H + lam I) v = b takes b itself as its right-hand side
-  if ((r = launch_rhs(P, u, P.dual ? 1 : rhs_is_y)) < 0) return r;
-  nl += r;
   if ((r = enqueue_core(P, P.ybuf, P.xcore, nl)) < 0) return r;
   // iterative refinement on the core system: v <- v + A^{-1}(y - A v)
   for (int it = 0; it < P.opts.refine_steps; ++it) {
@@ -250,6 +240,29 @@ int enqueue_solve(Plan& P, const UserArrays& u, int rhs_is_y, const double* lams
     if ((r = launch_residual(P, P.ybuf, P.xcore, P.rbuf)) < 0) return r;
     nl += r;
   }
+  return TIKH_OK;
+}
+
+int enqueue_prologue(Plan& P, const UserArrays& u, int rhs_is_y, const double* lams, int nb, int64_t& nl) {
+  int r;
+  if (nb < 1 || nb > P.batch_max) return TIKH_EINVAL;
+  P.nb = nb;
+  if (cudaMemcpyAsync(P.lam, lams, sizeof(double) * (size_t)nb, cudaMemcpyHostToDevice, P.stream) != cudaSuccess)
+    return TIKH_ECUDA;
+  if (cudaMemsetAsync(P.status, 0, sizeof(int), P.stream) != cudaSuccess) return TIKH_ECUDA;
+  if ((r = launch_spectrum(P, u)) < 0) return r;
+  nl += r;
+  // for m < n the core problem (T T^H + lam I) v = b takes b itself as its right-hand side
+  if ((r = launch_rhs(P, u, P.dual ? 1 : rhs_is_y)) < 0) return r;
+  nl += r;
+  return TIKH_OK;
+}
+
+int enqueue_solve(Plan& P, const UserArrays& u, int rhs_is_y, const double* lams, int nb) {
+  int64_t nl = 0;
+  int r;
+  if ((r = enqueue_prologue(P, u, rhs_is_y, lams, nb, nl)) < 0) return r;
+  if ((r = enqueue_core_refined(P, nl)) < 0) return r;
   if ((r = launch_output(P, P.xcore, u)) < 0) return r;
   nl += r;
   P.launches = nl;
@@ -445,6 +458,31 @@ int tikh_solve_batched(tikh_plan h, int batch, const void* col, int64_t col_stri
   u.rhs_stride = b_stride;
   u.x_stride = x_stride;
   return solve_with_retry(h->P, u, 0, lambdas, batch, nullptr, 0);
+}
+
+int tikh_solve_grad(tikh_plan h, const void* col, const void* row, const void* b, double lambda, const void* x,
+                    const void* dLdx, void* dLdcol, void* dLdrow, void* dLdb, double* dLdlambda) {
+  if (!h || !col || !row || !b || !x || !dLdx || !dLdcol || !dLdrow || !dLdb || !dLdlambda || !valid_lambda(lambda))
+    return TIKH_EINVAL;
+  Plan& P = h->P;
+  if (P.dual) return TIKH_EINVAL;  // the adjoint is implemented for m >= n
+  int err = 0;
+  if (!P.gbuf) {  // adjoint workspace, allocated by the first gradient call
+    P.gbuf = (cd*)dalloc(P, sizeof(cd) * (size_t)(4 * P.N + 2 * P.cm) * (size_t)P.batch_max, err);
+    P.gdl = (double*)dalloc(P, sizeof(double) * (size_t)P.batch_max, err);
+    if (err) return err;
+  }
+  UserArrays u = single(P, col, row, dLdx, nullptr);
+  int64_t nl = 0;
+  int r;
+  if ((r = enqueue_prologue(P, u, 1, &lambda, 1, nl)) < 0) return r;  // right-hand side y = dL/dx
+  if ((r = enqueue_core_refined(P, nl)) < 0) return r;                // g = A^{-1} dL/dx
+  if ((r = launch_grad(P, x, 0, b, 0, dLdcol, 0, dLdrow, 0, dLdb, 0, P.gdl, P.gbuf)) < 0) return r;
+  nl += r;
+  P.launches = nl;
+  if (cudaMemcpyAsync(dLdlambda, P.gdl, sizeof(double), cudaMemcpyDeviceToHost, P.stream) != cudaSuccess)
+    return TIKH_ECUDA;
+  return sync_status(P);
 }
 
 int tikh_solve_host(tikh_plan h, const void* col, const void* row, const void* b, double lambda, void* x) {

@@ -108,6 +108,8 @@ struct Plan {
   cd* dscr = nullptr;    // [nb][dscr_stride] difficult-point scratch
   int64_t dscr_stride = 0;
   void* d_in = nullptr;  // staging for tikh_solve_host: col | row | b | x
+  cd* gbuf = nullptr;    // [nb][4N + 2cm] adjoint workspace (first gradient call)
+  double* gdl = nullptr; // [nb] dL/dlambda
   int64_t launches = 0;
 
   // optional timing of every leaf launch with a CUDA event pair on the plan's stream
@@ -131,6 +133,9 @@ int launch_leaf(Plan& P, const Step& st);
 int launch_eval(Plan& P, const Step& st);
 int launch_prod(Plan& P, const Step& st);
 int launch_difficult(Plan& P);
+int launch_grad(Plan& P, const void* x, int64_t x_stride, const void* b, int64_t b_stride, void* dcol,
+                int64_t dcol_stride, void* drow, int64_t drow_stride, void* db, int64_t db_stride, double* dlam,
+                cd* gbuf);
 int launch_leaf_arrays(int K, const cd* sigma, const cd* r, int* delta, double eps, cd* B, int* len,
                        unsigned long long* colmax, int* ndiff, int64_t* diff, int* status, int* order, int* pivot,
                        cudaStream_t s);

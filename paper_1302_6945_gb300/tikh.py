@@ -48,7 +48,7 @@ _lib = None
 EXPORTED = ["tikh_plan_create", "tikh_solve", "tikh_solve_async", "tikh_solve_normal", "tikh_solve_host",
             "tikh_solve_batched",
             "tikh_sync", "tikh_get_stats", "tikh_plan_destroy", "tikh_strerror", "tikh_test_fft", "tikh_test_leaf",
-            "tikh_fft_noalloc", "tikh_set_profiling"]
+            "tikh_fft_noalloc", "tikh_set_profiling", "tikh_solve_grad"]
 
 
 def lib():
@@ -66,6 +66,7 @@ def lib():
         L.tikh_solve_batched.argtypes = [vp, ci, vp, i64, vp, i64, vp, i64, vp, vp, i64]
         L.tikh_sync.argtypes = [vp]
         L.tikh_set_profiling.argtypes = [vp, ci]
+        L.tikh_solve_grad.argtypes = [vp, vp, vp, vp, dbl, vp, vp, vp, vp, vp, ctypes.POINTER(dbl)]
         L.tikh_get_stats.argtypes = [vp, ctypes.POINTER(tikh_stats)]
         L.tikh_plan_destroy.argtypes = [vp]
         L.tikh_plan_destroy.restype = None
@@ -115,6 +116,13 @@ def tikh_solve_batched(plan, batch, col, col_stride, row, row_stride, b, b_strid
     lam = np.ascontiguousarray(lambdas, dtype=np.float64)
     _check(lib().tikh_solve_batched(plan, int(batch), col, int(col_stride), row, int(row_stride), b, int(b_stride),
                                     lam.ctypes.data_as(ctypes.c_void_p), x, int(x_stride)), "tikh_solve_batched")
+
+
+def tikh_solve_grad(plan, col, row, b, lam, x, dldx, dcol, drow, db):
+    out = ctypes.c_double()
+    _check(lib().tikh_solve_grad(plan, col, row, b, float(lam), x, dldx, dcol, drow, db, ctypes.byref(out)),
+           "tikh_solve_grad")
+    return out.value
 
 
 def tikh_solve_host(plan, col, row, b, lam, x):
@@ -258,6 +266,16 @@ class Plan:
         tikh_solve_batched(self.h, B, c, cs, r, rs, bb, bs, lams, ctypes.c_void_p(x.data_ptr()), self.n)
         return x
 
+    def grad(self, col, row, b, lam, x, dldx):
+        """Adjoint: returns (dL/dcol, dL/drow, dL/db, dL/dlambda) for dL/dx = dldx (m >= n)."""
+        c, r, bb = self._args(col, row, b, self.m)
+        _, _, xx = self._args(col, row, x, self.n)
+        _, _, gg = self._args(col, row, dldx.contiguous(), self.n)
+        dcol, drow, db = torch_empty_like(col), torch_empty_like(row), torch_empty_like(b)
+        dlam = tikh_solve_grad(self.h, c, r, bb, lam, xx, gg, ctypes.c_void_p(dcol.data_ptr()),
+                               ctypes.c_void_p(drow.data_ptr()), ctypes.c_void_p(db.data_ptr()))
+        return dcol, drow, db, dlam
+
     def solve_normal(self, col, row, y, lam, x=None):
         """x = (T^H T + lam I)^{-1} y (requires m >= n)."""
         c, r, yy = self._args(col, row, y, self.n)
@@ -296,6 +314,48 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def torch_empty_like(t):
+    import torch
+    return torch.empty_like(t)
+
+
+_autograd_fn = None
+
+
+def _make_autograd():
+    import torch
+
+    class TikhSolve(torch.autograd.Function):
+        """x = argmin ||Tx - b||^2 + lam ||x||^2 with the library's hand-written adjoint as backward."""
+
+        @staticmethod
+        def forward(ctx, col, row, b, lam, plan):
+            lam_v = float(lam)
+            x = plan.solve(col.contiguous(), row.contiguous(), b.contiguous(), lam_v)
+            ctx.save_for_backward(col, row, b, x)
+            ctx.plan, ctx.lam = plan, lam_v
+            ctx.lam_is_tensor = isinstance(lam, torch.Tensor)
+            return x
+
+        @staticmethod
+        def backward(ctx, gx):
+            col, row, b, x = ctx.saved_tensors
+            dcol, drow, db, dlam = ctx.plan.grad(col.contiguous(), row.contiguous(), b.contiguous(), ctx.lam, x,
+                                                 gx.contiguous())
+            glam = torch.tensor(dlam, dtype=torch.float64, device=col.device) if ctx.lam_is_tensor else None
+            return dcol, drow, db, glam, None
+
+    return TikhSolve
+
+
+def tikh_solve_autograd(col, row, b, lam, plan):
+    """Differentiable solve: gradients flow to col, row, b and (if a tensor) lam."""
+    global _autograd_fn
+    if _autograd_fn is None:
+        _autograd_fn = _make_autograd()
+    return _autograd_fn.apply(col, row, b, lam, plan)
 
 
 def solve(col, row, b, lam, **kw):
