@@ -155,6 +155,7 @@ def main():
     ap.add_argument("--n", type=int, default=None, help="sweep point: n unknowns, m = 1.5 n (default: c2)")
     ap.add_argument("--batch", type=int, default=1, help="independent problems per step (tikh_solve_batched)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
+    ap.add_argument("--graph", type=int, default=1, help="1 (default): replay each solve as one captured CUDA graph; 0: stream launches")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -182,7 +183,8 @@ def main():
     xb = torch.empty((B, n), dtype=torch.complex128, device=dev)
     x = xb[0]
     stream = torch.cuda.Stream(device=dev)
-    plan = tikh.Plan(m, n, "c128", n_lim=args.n_lim, refine_steps=args.refine, batch=B, stream=stream)
+    plan = tikh.Plan(m, n, "c128", n_lim=args.n_lim, refine_steps=args.refine, batch=B, graph=bool(args.graph),
+                     stream=stream)
 
     def step(sync=True):
         if B == 1:
@@ -296,6 +298,7 @@ def main():
                "config": {"workload": "deconvolution m=%d n=%d complex128 lambda=1e-4 (c2 recipe)" % (m, n), "m": m, "n": n,
                           "N": st["N"], "p": st["p"], "M": st["M"], "n_lim": args.n_lim,
                           "refine_steps": args.refine, "precision": "fp64", "batch": B,
+                          "cuda_graph": bool(st["graph"]),
                           "l2": "256 MB flush between steps; working set > L2"},
                "n_solves_per_s": value * n,
                "solves_per_s_per_problem_stream": value / B,

@@ -63,6 +63,10 @@ typedef struct tikh_plan_s* tikh_plan;
  *            (Sec. 6.2: the result "can be further improved with iterative refinement").
  *  batch     largest number of same-shape problems per tikh_solve_batched call (default 1); the
  *            plan's workspace scales with it.
+ *  graph     1: tikh_solve / tikh_solve_async / tikh_solve_batched capture the whole solve (every
+ *            kernel of every recursion node) into one CUDA graph on the first call and replay it while
+ *            the pointer and stride arguments stay the same (lambda may change); 0 (default): stream
+ *            launches.  Not used with profiling on.
  */
 typedef struct {
   int n_lim;
@@ -72,6 +76,7 @@ typedef struct {
   int max_difficult;
   int refine_steps;
   int batch;
+  int graph;
 } tikh_opts;
 
 typedef struct {
@@ -89,6 +94,7 @@ typedef struct {
   int batch;               /* problems in the last call */
   double prof_leaf_ms;     /* with profiling on: summed duration of the leaf launches since it was switched on */
   int64_t prof_leaf_launches; /* with profiling on: leaf launches timed since it was switched on */
+  int graph;                  /* 1 if the last solve ran as a (captured or replayed) CUDA graph */
 } tikh_stats;
 
 /* Build a plan for an m x n problem: sizing by Algorithm 2 (Sec. 5.2), the recursion schedule of

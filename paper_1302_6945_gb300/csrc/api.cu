@@ -247,7 +247,8 @@ int enqueue_prologue(Plan& P, const UserArrays& u, int rhs_is_y, const double* l
   int r;
   if (nb < 1 || nb > P.batch_max) return TIKH_EINVAL;
   P.nb = nb;
-  if (cudaMemcpyAsync(P.lam, lams, sizeof(double) * (size_t)nb, cudaMemcpyHostToDevice, P.stream) != cudaSuccess)
+  if (lams &&
+      cudaMemcpyAsync(P.lam, lams, sizeof(double) * (size_t)nb, cudaMemcpyHostToDevice, P.stream) != cudaSuccess)
     return TIKH_ECUDA;
   if (cudaMemsetAsync(P.status, 0, sizeof(int), P.stream) != cudaSuccess) return TIKH_ECUDA;
   if ((r = launch_spectrum(P, u)) < 0) return r;
@@ -267,6 +268,65 @@ int enqueue_solve(Plan& P, const UserArrays& u, int rhs_is_y, const double* lams
   nl += r;
   P.launches = nl;
   return TIKH_OK;
+}
+
+bool same_args(const UserArrays& a, const UserArrays& b) {
+  return a.col == b.col && a.row == b.row && a.rhs == b.rhs && a.x == b.x && a.col_stride == b.col_stride &&
+         a.row_stride == b.row_stride && a.rhs_stride == b.rhs_stride && a.x_stride == b.x_stride;
+}
+
+void drop_graph(Plan& P) {
+  if (P.graph_exec) cudaGraphExecDestroy(P.graph_exec);
+  P.graph_exec = nullptr;
+  P.graph_nb = 0;
+}
+
+// the solve as a CUDA graph: lambda is uploaded outside the graph; the rest (status reset, transform,
+// every node of the recursion, refinement, output) is captured once per argument set and replayed
+int enqueue_solve_graph(Plan& P, const UserArrays& u, int rhs_is_y, const double* lams, int nb) {
+  if (nb < 1 || nb > P.batch_max) return TIKH_EINVAL;
+  if (cudaMemcpyAsync(P.lam, lams, sizeof(double) * (size_t)nb, cudaMemcpyHostToDevice, P.stream) != cudaSuccess)
+    return TIKH_ECUDA;
+  if (!P.graph_exec || P.graph_nb != nb || P.graph_rhs_is_y != rhs_is_y || !same_args(P.graph_key, u)) {
+    drop_graph(P);
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(P.stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();  // e.g. the legacy default stream, which cannot be captured
+      P.opts.graph = 0;
+      return enqueue_solve(P, u, rhs_is_y, nullptr, nb);
+    }
+    int rc = enqueue_solve(P, u, rhs_is_y, nullptr, nb);
+    cudaError_t ce = cudaStreamEndCapture(P.stream, &g);
+    if (rc || ce != cudaSuccess || !g) {
+      cudaGetLastError();
+      if (g) cudaGraphDestroy(g);
+      P.opts.graph = 0;  // capture not possible here: plain stream launches from now on
+      return rc ? rc : enqueue_solve(P, u, rhs_is_y, nullptr, nb);
+    }
+    ce = cudaGraphInstantiate(&P.graph_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess) {
+      cudaGetLastError();
+      P.graph_exec = nullptr;
+      P.opts.graph = 0;
+      return enqueue_solve(P, u, rhs_is_y, nullptr, nb);
+    }
+    P.graph_key = u;
+    P.graph_nb = nb;
+    P.graph_rhs_is_y = rhs_is_y;
+  }
+  P.nb = nb;
+  return cudaGraphLaunch(P.graph_exec, P.stream) == cudaSuccess ? TIKH_OK : TIKH_ECUDA;
+}
+
+int enqueue_any(Plan& P, const UserArrays& u, int rhs_is_y, const double* lams, int nb) {
+  P.last.graph = 0;
+  if (P.opts.graph && !P.prof_leaf) {
+    int rc = enqueue_solve_graph(P, u, rhs_is_y, lams, nb);
+    P.last.graph = P.graph_exec && P.opts.graph ? 1 : 0;
+    return rc;
+  }
+  return enqueue_solve(P, u, rhs_is_y, lams, nb);
 }
 
 int sync_status(Plan& P) {
@@ -316,7 +376,7 @@ int solve_with_retry(Plan& P, const UserArrays& u, int rhs_is_y, const double* l
                      size_t xbytes) {
   P.last.retries = 0;
   for (int attempt = 0;; ++attempt) {
-    int rc = enqueue_solve(P, u, rhs_is_y, lams, nb);
+    int rc = enqueue_any(P, u, rhs_is_y, lams, nb);
     if (rc) return rc;
     if (x_host && cudaMemcpyAsync(x_host, u.x, xbytes, cudaMemcpyDeviceToHost, P.stream) != cudaSuccess)
       return TIKH_ECUDA;
@@ -324,6 +384,7 @@ int solve_with_retry(Plan& P, const UserArrays& u, int rhs_is_y, const double* l
     if (rc != TIKH_EDEGREE || attempt >= 3) return rc;
     P.slack_mult *= 16;
     P.last.retries = attempt + 1;
+    drop_graph(P);
     if ((rc = make_schedule(P))) return rc;
   }
 }
@@ -347,11 +408,11 @@ int tikh_plan_create(tikh_plan* out, int64_t m, int64_t n, int dtype, int prec, 
   if (!out) return TIKH_EINVAL;
   *out = nullptr;
   if (m < 1 || n < 1 || (dtype != TIKH_R64 && dtype != TIKH_C128) || prec != TIKH_PREC_FP64) return TIKH_EINVAL;
-  tikh_opts o{32, 0, 0, 1e-8, 4096, 0, 1};
+  tikh_opts o{32, 0, 0, 1e-8, 4096, 0, 1, 0};
   if (opts) o = *opts;
   if (o.n_lim < 4 || o.n_lim > 64 || o.m_min < 0 || o.m_min > 32 || (o.fill != 0 && o.fill != 1) ||
       !(o.eps_diff >= 0.0) || o.max_difficult < 1 || o.max_difficult > (1 << 20) || o.refine_steps < 0 ||
-      o.refine_steps > 8 || o.batch < 1 || o.batch > 65535)
+      o.refine_steps > 8 || o.batch < 1 || o.batch > 65535 || (o.graph != 0 && o.graph != 1))
     return TIKH_EINVAL;
   tikh_plan h = new (std::nothrow) tikh_plan_s;
   if (!h) return TIKH_ENOMEM;
@@ -433,7 +494,7 @@ int tikh_solve(tikh_plan h, const void* col, const void* row, const void* b, dou
 
 int tikh_solve_async(tikh_plan h, const void* col, const void* row, const void* b, double lambda, void* x) {
   if (!h || !col || !row || !b || !x || !valid_lambda(lambda)) return TIKH_EINVAL;
-  return enqueue_solve(h->P, single(h->P, col, row, b, x), 0, &lambda, 1);
+  return enqueue_any(h->P, single(h->P, col, row, b, x), 0, &lambda, 1);
 }
 
 int tikh_solve_normal(tikh_plan h, const void* col, const void* row, const void* y, double lambda, void* x) {
@@ -525,6 +586,7 @@ int tikh_set_profiling(tikh_plan h, int flags) {
 void tikh_plan_destroy(tikh_plan h) {
   if (!h) return;
   cudaStreamSynchronize(h->P.stream);
+  drop_graph(h->P);
   for (cudaEvent_t e : h->P.ev_pool) cudaEventDestroy(e);
   for (void* p : h->P.allocs) cudaFree(p);
   delete h;

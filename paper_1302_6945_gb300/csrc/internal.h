@@ -112,6 +112,11 @@ struct Plan {
   double* gdl = nullptr; // [nb] dL/dlambda
   int64_t launches = 0;
 
+  // optional CUDA graph of the whole solve, replayed while the call's arguments stay the same
+  cudaGraphExec_t graph_exec = nullptr;
+  UserArrays graph_key{};
+  int graph_nb = 0, graph_rhs_is_y = -1;
+
   // optional timing of every leaf launch with a CUDA event pair on the plan's stream
   int prof_leaf = 0;
   std::vector<cudaEvent_t> ev_pool;

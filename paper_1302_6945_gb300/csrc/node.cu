@@ -41,7 +41,14 @@ struct LoadTwistFold {  // transform t = 50 pb + 2E + c
     int64_t len = B.lp(pb)[E];
     const cd* src = B.cp(pb) + E * B.cap;
     cd acc = mkc(0.0, 0.0);
-    for (int64_t q = u; q < len; q += Lr) acc = cfma(src[q], tw_at(wN, (beta * q) % N), acc);
+    // twiddle index (beta q) mod N advanced by (beta Lr) mod N per fold term (one 64-bit modulo each)
+    int64_t ix = (beta * u) % N;
+    const int64_t stepx = (beta * Lr) % N;
+    for (int64_t q = u; q < len; q += Lr) {
+      acc = cfma(src[q], tw_at(wN, ix), acc);
+      ix += stepx;
+      if (ix >= N) ix -= N;
+    }
     return cscale(acc, col_scale_from_bits(B.mp(pb)[E % 5]));
   }
 };

@@ -21,7 +21,7 @@ TIKH_PREC_FP64 = 0
 class tikh_opts(ctypes.Structure):
     _fields_ = [("n_lim", ctypes.c_int), ("m_min", ctypes.c_int), ("fill", ctypes.c_int),
                 ("eps_diff", ctypes.c_double), ("max_difficult", ctypes.c_int), ("refine_steps", ctypes.c_int),
-                ("batch", ctypes.c_int)]
+                ("batch", ctypes.c_int), ("graph", ctypes.c_int)]
 
 
 class tikh_stats(ctypes.Structure):
@@ -29,7 +29,8 @@ class tikh_stats(ctypes.Structure):
                 ("dual", ctypes.c_int), ("n_difficult", ctypes.c_int64), ("delta", ctypes.c_int * 5),
                 ("jstar", ctypes.c_int), ("retries", ctypes.c_int), ("kernel_launches", ctypes.c_int64),
                 ("workspace_bytes", ctypes.c_int64), ("refine_steps", ctypes.c_int), ("rel_residual", ctypes.c_double),
-                ("batch", ctypes.c_int), ("prof_leaf_ms", ctypes.c_double), ("prof_leaf_launches", ctypes.c_int64)]
+                ("batch", ctypes.c_int), ("prof_leaf_ms", ctypes.c_double), ("prof_leaf_launches", ctypes.c_int64),
+                ("graph", ctypes.c_int)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}
@@ -208,13 +209,13 @@ class Plan:
     """A solver plan for m x n Toeplitz problems of one dtype ('r64' or 'c128')."""
 
     def __init__(self, m, n, dtype="r64", n_lim=32, m_min=0, fill=0, eps_diff=1e-8, max_difficult=4096,
-                 refine_steps=0, batch=1, stream=None):
+                 refine_steps=0, batch=1, graph=False, stream=None):
         import torch
         self.m, self.n = int(m), int(n)
         self.dtype = TIKH_C128 if dtype in ("c128", TIKH_C128, torch.complex128) else TIKH_R64
         self.batch = int(batch)
         self.opts = tikh_opts(int(n_lim), int(m_min), int(fill), float(eps_diff), int(max_difficult),
-                              int(refine_steps), self.batch)
+                              int(refine_steps), self.batch, 1 if graph else 0)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
