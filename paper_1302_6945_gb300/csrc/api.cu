@@ -185,6 +185,7 @@ int status_to_code(int st) {
   if (st & ST_DEGREE) return TIKH_EDEGREE;
   if (st & ST_DIFFICULT) return TIKH_EDIFFICULT;
   if (st & ST_NUMERIC) return TIKH_ENUMERIC;
+  if (st & ST_WAIT) return TIKH_ETIMEOUT;
   return TIKH_OK;
 }
 

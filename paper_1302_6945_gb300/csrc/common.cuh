@@ -25,6 +25,7 @@ enum : int {
   ST_NUMERIC = 1,    // final degree pattern wrong / zero pivot
   ST_DEGREE = 2,     // a basis degree exceeded the planned transform length
   ST_DIFFICULT = 4,  // deferred-condition list overflow
+  ST_WAIT = 8,       // a bounded in-kernel wait gave up
 };
 
 __device__ __forceinline__ void set_status(int* st, int bit) { atomicOr(st, bit); }

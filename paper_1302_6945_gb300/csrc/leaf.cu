@@ -12,16 +12,16 @@
 //
 // Cost model on GB300: an FP64 warp instruction occupies its SM sub-partition for 64 cycles whatever
 // the number of active lanes (measured), FP32 ~4.5 cycles.  The pivot chain of a leaf therefore keeps
-// only the FP64 work that decides the next step (scores, the multipliers mu, the residual update) and,
-// for K <= 32, runs warp-synchronously in one warp (shuffles, no block barrier inside a step); the
-// basis B_leaf = E_1 E_2 ... E_K is rebuilt by the other warps from the recorded (pivot, sigma, mu) of
-// each step, one step behind, on the other SM sub-partitions.
+// only the FP64 work that decides the next step (scores, the multipliers mu, the residual update), and
+// spreads each residual row over five lanes ("component lanes") so that the per-entry work of a step
+// is one warp instruction on each of the four sub-partitions; the basis B_leaf = E_1 E_2 ... E_K is
+// rebuilt by four more warps from the recorded (pivot, sigma, mu) of each step as soon as the chain
+// publishes it.
 #include "internal.h"
 
 namespace tikh {
 
 constexpr int LEAF_KMAX = 64;
-constexpr int LEAF_THREADS = 128;
 constexpr int LEAF_CAP = LEAF_KMAX + 1;
 
 // pick: (score bits, position, pivot); larger score wins, then lower position
@@ -106,6 +106,13 @@ struct SrcNodes {
     for (int i = 0; i < 5; ++i) r[i] = row[i];
     sig = wN[e];
   }
+  __device__ void get1(int pb, int q, int jcol, cd& rj, cd& sig, int64_t& id) const {
+    int j = q / 4, c = (q / 2) % 2, f = q % 2;
+    int64_t e = a + c + s * j;
+    id = 2 * e + f;
+    rj = R[((int64_t)pb * N + e) * 10 + f * 5 + jcol];
+    sig = wN[e];
+  }
 };
 // explicit arrays (test hook, one problem): sigma[q], r[5q..5q+4]; deferred ids are q
 struct SrcArrays {
@@ -117,16 +124,13 @@ struct SrcArrays {
     for (int i = 0; i < 5; ++i) r[i] = rr[q * 5 + i];
     sig = sigma[q];
   }
+  __device__ void get1(int, int q, int jcol, cd& rj, cd& sig, int64_t& id) const {
+    id = q;
+    rj = rr[q * 5 + jcol];
+    sig = sigma[q];
+  }
 };
 
-__device__ __forceinline__ cd pick5(const cd* v, int i) {  // v[i] with a runtime i, by selects
-  cd o = v[0];
-  o = i == 1 ? v[1] : o;
-  o = i == 2 ? v[2] : o;
-  o = i == 3 ? v[3] : o;
-  o = i == 4 ? v[4] : o;
-  return o;
-}
 __device__ __forceinline__ cd shfl_cd(cd v, int src) {
   return mkc(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
 }
@@ -134,169 +138,200 @@ __device__ __forceinline__ void named_sync(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
-// One CTA per problem (blockIdx.x).  Warps [0, CW) run the pivot chain (one condition per lane,
-// K <= 32 * CW); warps [CW, 4) rebuild B from the step records, one step behind the chain, on the
-// other SM sub-partitions.  One __syncthreads per step hands the records over.
-template <int CW, class Src>
-__global__ void __launch_bounds__(LEAF_THREADS) k_leaf(Src src, int K, int* delta, int* dstack,
-                                                        unsigned long long save_mask, double eps, BasisBuf out,
-                                                        int* ndiff, int64_t* diff, int maxdiff, int* status,
-                                                        int* rec_order, int* rec_pivot) {
-  constexpr int NCHAIN = 32 * CW, NREC = LEAF_THREADS - NCHAIN;
+// One CTA per problem (blockIdx.x), "component lanes": chain warp w holds residual rows 6w .. 6w+5,
+// lane 5 rr + j holding entry j of row 6w + rr (lanes 30, 31 idle), so the FP64 work of a step that is
+// per entry (magnitudes, the update) is one warp instruction spread over CWN warps on all four SM
+// sub-partitions.  Each step: magnitudes -> row scores (every lane of a row gathers its five
+// magnitudes) -> per-warp pick -> one named barrier among the chain warps -> the same global pick in
+// every chain warp -> multipliers mu_j (lane j's own column) -> update.  Chain warp 0 publishes the
+// records of step s and then the count s + 1; the four rebuild warps (one per sub-partition) apply
+// B <- B E_s as soon as step s is published, so the chain never waits for the rebuild.
+constexpr int L4_ROWS = 6;
+constexpr int L4_NREC = 128;
+constexpr int CHAIN_DONE = 1 << 30;
+constexpr int L4_SPIN_LIMIT = 1 << 24;  // polls of the rebuild warps before they give up (ST_WAIT)
+
+__device__ __forceinline__ int ld_volatile(const int* p) { return *(const volatile int*)p; }
+__device__ __forceinline__ void st_volatile(int* p, int v) { *(volatile int*)p = v; }
+
+template <int CWN, class Src>
+__global__ void __launch_bounds__(32 * CWN + L4_NREC) k_leaf(Src src, int K, int* delta, int* dstack,
+                                                              unsigned long long save_mask, double eps, BasisBuf out,
+                                                              int* ndiff, int64_t* diff, int maxdiff, int* status,
+                                                              int* rec_order, int* rec_pivot) {
+  constexpr int NCHAIN = 32 * CWN, NT = NCHAIN + L4_NREC;
   __shared__ cd Bs[25][LEAF_CAP];
   __shared__ cd oldc[5][LEAF_CAP];
   __shared__ cd rec_mu[LEAF_KMAX][5];
   __shared__ cd rec_sig[LEAF_KMAX];
   __shared__ int rec_piv[LEAF_KMAX];
-  __shared__ cd win_r[5];
-  __shared__ cd mu_s[5];
+  __shared__ cd rowbuf[LEAF_KMAX][5];  // a row is written only while it is active: the step's winner row
+                                       // is never rewritten, so one buffer serves every step
+  __shared__ cd sigbuf[LEAF_KMAX];
+  __shared__ Pick cand[2][CWN];  // per-warp picks, by step parity
   __shared__ int blen[25];
   __shared__ int din[5], dl_out[5];
-  __shared__ Pick wpick[2];
-  __shared__ int done_s, nsteps_s;
-  const int tid = threadIdx.x, lane = tid & 31, pb = blockIdx.x;
+  __shared__ int chain_state;  // steps recorded so far, | CHAIN_DONE once the chain has stopped
+  __shared__ int rb_cmd;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, pb = blockIdx.x;
   int* dlt = delta + 8 * pb;
 
   if (tid < 5) din[tid] = dlt[tid];
-  if (tid == 0) { done_s = 0; nsteps_s = 0; }
+  if (tid == 0) chain_state = 0;
   if (tid < 25) blen[tid] = (tid % 6 == 0) ? 1 : 0;
-  for (int idx = tid; idx < 25 * LEAF_CAP; idx += blockDim.x) {
+  for (int idx = tid; idx < 25 * LEAF_CAP; idx += NT) {
     int e = idx / LEAF_CAP, t = idx % LEAF_CAP;
     Bs[e][t] = (t == 0 && e % 6 == 0) ? mkc(1.0, 0.0) : mkc(0.0, 0.0);
   }
-  cd r[5];
-  cd sig = mkc(0.0, 0.0);
-  bool active = tid < K;
+  const int rr = lane / 5, jc = lane - 5 * rr, rbase = 5 * rr;
+  const int q = wid * L4_ROWS + rr;
+  bool active = tid < NCHAIN && rr < L4_ROWS && q < K;
+  cd r = mkc(0.0, 0.0), sig = mkc(0.0, 0.0);
   int64_t eid = -1;
-  if (active) src.get(pb, tid, r, sig, eid);
+  if (active) {
+    src.get1(pb, q, jc, r, sig, eid);
+    if (jc == 0) sigbuf[q] = sig;
+  }
   __syncthreads();
   if (tid < 5 && dstack) {
     for (int d = 0; d < 64; ++d)
       if (save_mask >> d & 1ULL) dstack[((int64_t)pb * MAX_DEPTH + d) * 5 + tid] = din[tid];
   }
-  int dl[5];  // chain lanes keep the tau-degrees in registers
-#pragma unroll
-  for (int i = 0; i < 5; ++i) dl[i] = din[i];
-  const unsigned long long eps_bits = (unsigned long long)__double_as_longlong(eps * eps);
 
-  for (int step = 0;; ++step) {
-    if (tid < NCHAIN) {
-      // ---- one pivot step: decide, record, update ----
-      if (!done_s) {
-        Pick p;
-        p.sb = NO_PICK;
-        p.idx = 1 << 30;
-        p.piv = -1;
-        if (active) {
-          p = score_row(r, dl, tid);
-          if (p.piv < 0) { active = false; p.sb = NO_PICK; p.idx = 1 << 30; }  // already satisfied
+  if (tid < NCHAIN) {
+    int dl[5];  // tau-degrees of the five columns, identical in every chain lane
+#pragma unroll
+    for (int i = 0; i < 5; ++i) dl[i] = din[i];
+    const unsigned long long eps_bits = (unsigned long long)__double_as_longlong(eps * eps);
+    for (int step = 0;; ++step) {
+      const int par = step & 1;
+      // ---- score of every active row (same arithmetic as the row-per-lane form) ----
+      const double mag = fma(r.x, r.x, r.y * r.y);
+      const unsigned nzm = __ballot_sync(0xffffffffu, active && cnz(r));
+      const unsigned rownz = (nzm >> rbase) & 31u;
+      double mg[5];
+#pragma unroll
+      for (int c = 0; c < 5; ++c) mg[c] = __shfl_sync(0xffffffffu, mag, (rbase + c) & 31);
+      if (active && rownz == 0u) active = false;  // every entry zero: the condition already holds
+      Pick p;
+      p.sb = NO_PICK;
+      p.idx = 1 << 30;
+      p.piv = -1;
+      if (active && jc == 0) {
+        int pi = -1, dpi = 0;
+        unsigned long long mpi = 0ULL;
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+          if (!((rownz >> c) & 1u)) continue;
+          const unsigned long long mb = (unsigned long long)__double_as_longlong(mg[c]);
+          if (pi < 0 || dl[c] < dpi || (dl[c] == dpi && mb > mpi)) { pi = c; mpi = mb; dpi = dl[c]; }
         }
-        p = warp_pick(p);
-        if (CW > 1) {
-          if (lane == 0) wpick[tid >> 5] = p;
-          named_sync(2, NCHAIN);
-          p = pick_better(wpick[1], wpick[0]) ? wpick[1] : wpick[0];
-        }
-        bool finish = false;
-        if (p.sb == NO_PICK) {
-          finish = true;
-        } else if (p.sb < eps_bits) {  // difficult: defer the rest of the leaf
-          if (active) {
-            int slot = atomicAdd(ndiff + 4 * pb, 1);
-            if (slot < maxdiff) diff[(int64_t)pb * maxdiff + slot] = eid;
-            else set_status(status, ST_DIFFICULT);
-            active = false;
-          }
-          finish = true;
-        }
-        if (finish) {
-          if (tid == 0) { done_s = 1; nsteps_s = step; }
-        } else {
-          const int pi = p.piv, w = p.idx;
-          cd rw[5], sw, mu[5];
-          if (CW == 1) {
-#pragma unroll
-            for (int i = 0; i < 5; ++i) rw[i] = shfl_cd(r[i], w);
-            sw = shfl_cd(sig, w);
-          } else {
-            if (tid == w) {
-#pragma unroll
-              for (int i = 0; i < 5; ++i) win_r[i] = r[i];
-              rec_sig[step] = sig;
-            }
-            named_sync(2, NCHAIN);
-#pragma unroll
-            for (int i = 0; i < 5; ++i) rw[i] = win_r[i];
-            sw = rec_sig[step];
-          }
-          // mu_i = -r_i / r_pi as r_i * conj(r_pi) / |r_pi|^2: lane i of warp 0 computes mu_i
-          cd m = mkc(0.0, 0.0);
-          if (lane < 5 && lane != pi) {
-            cd rp = pick5(rw, pi);
-            double rd = 1.0 / fma(rp.x, rp.x, rp.y * rp.y);
-            cd inv = mkc(rp.x * rd, -rp.y * rd);
-            m = cmul(pick5(rw, lane), inv);
-            m = mkc(-m.x, -m.y);
-          }
-          if (CW == 1) {
-#pragma unroll
-            for (int i = 0; i < 5; ++i) mu[i] = shfl_cd(m, i);
-          } else {
-            if (tid < 5) mu_s[tid] = m;
-            named_sync(2, NCHAIN);
-#pragma unroll
-            for (int i = 0; i < 5; ++i) mu[i] = mu_s[i];
-          }
-          if (tid == w) active = false;
-          if (tid < 5) rec_mu[step][tid] = mu[tid];
-          if (tid == 0) {
-            rec_piv[step] = pi;
-            rec_sig[step] = sw;
-            if (rec_order) { rec_order[step] = w; rec_pivot[step] = pi; }
-          }
-          dl[pi] += 1;
-          if (active) {  // r <- r E(sigma): column pi times (sigma - sw), others += mu_i r_pi
-            const cd rp = pick5(r, pi);
-            const cd ds = csub(sig, sw);
-#pragma unroll
-            for (int i = 0; i < 5; ++i) {
-              cd base = (i == pi) ? mkc(0.0, 0.0) : r[i];
-              cd fac = (i == pi) ? ds : mu[i];
-              r[i] = cfma(fac, rp, base);
-            }
-          }
-          if (CW > 1) named_sync(2, NCHAIN);  // wpick / win_r / mu_s are rewritten next step
-        }
+        const double tot = ((mg[0] + mg[1]) + (mg[2] + mg[3])) + mg[4];
+        const double sc = __longlong_as_double((long long)mpi) / tot;
+        p.sb = (unsigned long long)__double_as_longlong(sc);
+        if (p.sb == 0ULL) p.sb = 1ULL;  // an underflowed ratio still ranks above "no candidate"
+        p.idx = q;
+        p.piv = pi;
       }
-    } else if (step >= 1) {
-      // ---- rebuild B <- B E_{step-1} from the records ----
-      const int s = step - 1;
-      const int rt = tid - NCHAIN;
+      p = warp_pick(p);
+      if (lane == 0) cand[par][wid] = p;
+      if (active) rowbuf[q][jc] = r;
+      named_sync(2, NCHAIN);
+      Pick b = cand[par][0];
+#pragma unroll
+      for (int w2 = 1; w2 < CWN; ++w2)
+        if (pick_better(cand[par][w2], b)) b = cand[par][w2];
+      if (b.sb == NO_PICK || b.sb < eps_bits) {  // done, or difficult: defer the rest of the leaf
+        if (b.sb != NO_PICK && active && jc == 0) {
+          int slot = atomicAdd(ndiff + 4 * pb, 1);
+          if (slot < maxdiff) diff[(int64_t)pb * maxdiff + slot] = eid;
+          else set_status(status, ST_DIFFICULT);
+        }
+        if (tid == 0) {
+          __threadfence_block();
+          st_volatile(&chain_state, step | CHAIN_DONE);
+        }
+        break;
+      }
+      const int pi = b.piv, w = b.idx;
+      // ---- mu_j = -r_wj / r_wpi as r_wj conj(r_wpi) / |r_wpi|^2, lane j's own column ----
+      const cd rp = rowbuf[w][pi];
+      const cd sw = sigbuf[w];
+      cd mu = mkc(0.0, 0.0);
+      if (jc != pi) {
+        const double rd = 1.0 / fma(rp.x, rp.x, rp.y * rp.y);
+        const cd inv = mkc(rp.x * rd, -rp.y * rd);
+        mu = cmul(rowbuf[w][jc], inv);
+        mu = mkc(-mu.x, -mu.y);
+      }
+      if (wid == 0) {  // records of this step, then its publication to the rebuild warps
+        if (lane < 5) rec_mu[step][lane] = mu;
+        if (lane == 0) {
+          rec_piv[step] = pi;
+          rec_sig[step] = sw;
+          if (rec_order) { rec_order[step] = w; rec_pivot[step] = pi; }
+        }
+        __threadfence_block();
+        __syncwarp();
+        if (lane == 0) st_volatile(&chain_state, step + 1);
+      }
+      if (q == w) active = false;
+#pragma unroll
+      for (int c = 0; c < 5; ++c) dl[c] += (c == pi) ? 1 : 0;
+      // ---- r <- r E(sigma): column pi times (sigma - sw), the others += mu_j r_pi ----
+      const cd rpo = shfl_cd(r, (rbase + pi) & 31);
+      if (active) {
+        const cd ds = csub(sig, sw);
+        const cd fac = (jc == pi) ? ds : mu;
+        const cd base = (jc == pi) ? mkc(0.0, 0.0) : r;
+        r = cfma(fac, rpo, base);
+      }
+    }
+    if (tid < 5) dl_out[tid] = dl[tid];
+  } else {
+    // ---- rebuild B <- B E_s for s = 0, 1, ... as the chain publishes them ----
+    const int rt = tid - NCHAIN;
+    for (int s = 0;; ++s) {
+      if (rt == 0) {
+        int cmd = 2;  // 0: step s is recorded, 1: the chain stopped before s, 2: gave up waiting
+        for (int it = 0; it < L4_SPIN_LIMIT; ++it) {
+          const int st = ld_volatile(&chain_state);
+          if ((st & ~CHAIN_DONE) > s) { cmd = 0; break; }
+          if (st & CHAIN_DONE) { cmd = 1; break; }
+          __nanosleep(20);
+        }
+        __threadfence_block();
+        if (cmd == 2) set_status(status, ST_WAIT);
+        rb_cmd = cmd;
+      }
+      named_sync(1, L4_NREC);
+      if (rb_cmd != 0) break;
       const int pi = rec_piv[s];
       const cd sb = rec_sig[s];
+      const cd nsb = mkc(-sb.x, -sb.y);
       int lmax = 0;
 #pragma unroll
       for (int i = 0; i < 5; ++i) lmax = max(lmax, blen[i * 5 + pi]);
-      for (int idx = rt; idx < 5 * lmax; idx += NREC) {
+      for (int idx = rt; idx < 5 * lmax; idx += L4_NREC) {
         int i = idx / lmax, t = idx % lmax;
         oldc[i][t] = Bs[i * 5 + pi][t];
       }
-      named_sync(1, NREC);
-      // item (row i, column j, coefficient t): column pi <- (z - sb) column pi, column j += mu_j old pi
-      for (int idx = rt; idx < 25 * (lmax + 1); idx += NREC) {
-        int e = idx / (lmax + 1), t = idx % (lmax + 1);
-        int i = e / 5, j = e % 5;
-        int lo = blen[i * 5 + pi];
+      named_sync(1, L4_NREC);
+      // item (entry e = (i, j), coefficient t): column pi <- (z - sb) column pi, column j += mu_j old pi
+      for (int idx = rt; idx < 25 * (lmax + 1); idx += L4_NREC) {
+        const int e = idx / (lmax + 1), t = idx % (lmax + 1);
+        const int i = e / 5, j = e % 5;
+        const int lo = blen[i * 5 + pi];
         if (lo == 0 || t > lo) continue;
-        cd o = t < lo ? oldc[i][t] : mkc(0.0, 0.0);
+        const cd o = t < lo ? oldc[i][t] : mkc(0.0, 0.0);
         if (j == pi) {
-          cd prev = t >= 1 ? oldc[i][t - 1] : mkc(0.0, 0.0);
-          Bs[e][t] = csub(prev, cmul(sb, o));
+          const cd prev = t >= 1 ? oldc[i][t - 1] : mkc(0.0, 0.0);
+          Bs[e][t] = cfma(nsb, o, prev);
         } else if (t < lo) {
           Bs[e][t] = cfma(rec_mu[s][j], o, Bs[e][t]);
         }
       }
-      named_sync(1, NREC);
+      named_sync(1, L4_NREC);
       if (rt < 5) {
         int i = rt, lo = blen[i * 5 + pi];
         if (lo > 0) {
@@ -305,15 +340,9 @@ __global__ void __launch_bounds__(LEAF_THREADS) k_leaf(Src src, int K, int* delt
           blen[i * 5 + pi] = lo + 1;
         }
       }
-      named_sync(1, NREC);
+      // the next poll's barrier orders these blen writes before the next step reads them
     }
-    __syncthreads();
-    // the chain is done (it always is by step K: every step processes or drops a condition) and every
-    // recorded step 0 .. nsteps-1 has been rebuilt; done_s / nsteps_s were written before the barrier
-    if (done_s && step >= nsteps_s) break;
-    __syncthreads();
   }
-  if (tid < 5) dl_out[tid] = dl[tid];  // lanes 0..4 of the chain hold the final degrees
   __syncthreads();
   // ---- trim to the degree bounds, record column maxima, write out ----
   __shared__ unsigned long long cmax[5];
@@ -326,7 +355,7 @@ __global__ void __launch_bounds__(LEAF_THREADS) k_leaf(Src src, int K, int* delt
   }
   __syncthreads();
   cd* oc = out.cp(pb);
-  for (int idx = tid; idx < 25 * LEAF_CAP; idx += blockDim.x) {
+  for (int idx = tid; idx < 25 * LEAF_CAP; idx += NT) {
     int e = idx / LEAF_CAP, t = idx % LEAF_CAP;
     if (t < blen[e]) {
       cd v = Bs[e][t];
@@ -347,12 +376,15 @@ template <class Src>
 static int launch_leaf_t(const Src& src, int K, int nb, int* delta, int* dstack, unsigned long long mask, double eps,
                          const BasisBuf& out, int* ndiff, int64_t* diff, int maxdiff, int* status, int* order,
                          int* pivot, cudaStream_t s) {
-  if (K <= 32)
-    k_leaf<1, Src><<<nb, LEAF_THREADS, 0, s>>>(src, K, delta, dstack, mask, eps, out, ndiff, diff, maxdiff, status,
-                                               order, pivot);
+  if (K <= 4 * L4_ROWS)
+    k_leaf<4, Src><<<nb, 32 * 4 + L4_NREC, 0, s>>>(src, K, delta, dstack, mask, eps, out, ndiff, diff, maxdiff,
+                                                   status, order, pivot);
+  else if (K <= 8 * L4_ROWS)
+    k_leaf<8, Src><<<nb, 32 * 8 + L4_NREC, 0, s>>>(src, K, delta, dstack, mask, eps, out, ndiff, diff, maxdiff,
+                                                   status, order, pivot);
   else
-    k_leaf<2, Src><<<nb, LEAF_THREADS, 0, s>>>(src, K, delta, dstack, mask, eps, out, ndiff, diff, maxdiff, status,
-                                               order, pivot);
+    k_leaf<11, Src><<<nb, 32 * 11 + L4_NREC, 0, s>>>(src, K, delta, dstack, mask, eps, out, ndiff, diff, maxdiff,
+                                                     status, order, pivot);
   return cudaGetLastError() == cudaSuccess ? 1 : TIKH_ECUDA;
 }
 
