@@ -146,6 +146,56 @@ __device__ __forceinline__ void named_sync(int id, int nthreads) {
 // every chain warp -> multipliers mu_j (lane j's own column) -> update.  Chain warp 0 publishes the
 // records of step s and then the count s + 1; the four rebuild warps (one per sub-partition) apply
 // B <- B E_s as soon as step s is published, so the chain never waits for the rebuild.
+constexpr long long KEY_NONE = -0x7fffffffffffffffLL - 1;
+constexpr long long KEY_BAND = 16;  // units of 2^-23 in log2 scale; the key's error is below 6 units
+constexpr long long KEY_SPEC = 0x7fffffffffffffffLL;  // a warp holding a special row (FP64 path)
+
+// Approximate key of the row score |r_pi|^2 / ||r||^2 from the exact FP64 magnitudes' bit patterns,
+// in FP32 and integer arithmetic: key = 2^23 (floor(log2 R) + 127) + (23 leading mantissa bits of R),
+// monotone in R.  Magnitudes are re-based to the row's largest exponent (terms more than 2^60 below it
+// are dropped), truncated to 23 mantissa bits, summed in FP32 and divided to 2 ulp, so the key is
+// within 6 units of the exact ratio's; two keys more than KEY_BAND apart order the FP64 scores the
+// same way.  special: zero
+// or sub-normal pivot magnitude, or a row too small or too large for the re-basing (FP64 path instead).
+__device__ __forceinline__ long long approx_key(const double* mg, unsigned long long mpi, bool& special) {
+  unsigned long long mb[5];
+  int emax = 0;
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    mb[c] = (unsigned long long)__double_as_longlong(mg[c]);
+    emax = max(emax, (int)(mb[c] >> 52));
+  }
+  const int epi = (int)(mpi >> 52);
+  special = epi == 0 || emax <= 61 || emax >= 2046;
+  float f[5];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    const int ec = (int)(mb[c] >> 52), d = ec - emax;
+    f[c] = (d < -60 || ec == 0) ? 0.0f : __int_as_float(((127 + d) << 23) | (int)((mb[c] >> 29) & 0x7fffffULL));
+  }
+  const float tot = ((f[0] + f[1]) + (f[2] + f[3])) + f[4];  // in [1, 10)
+  const float mp = __int_as_float((127 << 23) | (int)((mpi >> 29) & 0x7fffffULL));  // in [1, 2)
+  const float qf = __fdividef(mp, tot);  // normal, in (0.1, 2); within 2 ulp
+  return ((long long)(epi - emax) << 23) + (long long)__float_as_int(qf);
+}
+
+// 1/d for a positive normal d with biased exponent in (2, 2044): seed y0 from the FP32 approximate
+// reciprocal of d's 23 leading mantissa bits (relative error e0 below 2^-21), then one third-order
+// step of the series 1/d = y0 / (1 - e) = y0 (1 + e + e^2 + ...), e = 1 - d y0: the truncation error
+// e^3 is below 2^-63, under FP64 rounding
+__device__ __forceinline__ double rcp_series(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const int E = (int)(b >> 52);
+  float rf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(__int_as_float((127 << 23) | (int)((b >> 29) & 0x7fffffULL))));
+  const int fb = __float_as_int(rf);  // rf in [0.5, 1]
+  const long long ye = (long long)(((fb >> 23) - 127) - (E - 1023) + 1023);
+  const double y = __longlong_as_double((long long)(((unsigned long long)ye << 52) | ((unsigned long long)(fb & 0x7fffff) << 29)));
+  const double e = fma(-d, y, 1.0);
+  return fma(y, fma(e, e, e), y);
+}
+
+
 constexpr int L4_ROWS = 6;
 constexpr int L4_NREC = 128;
 constexpr int CHAIN_DONE = 1 << 30;
@@ -155,20 +205,20 @@ __device__ __forceinline__ int ld_volatile(const int* p) { return *(const volati
 __device__ __forceinline__ void st_volatile(int* p, int v) { *(volatile int*)p = v; }
 
 template <int CWN, class Src>
-__global__ void __launch_bounds__(32 * CWN + L4_NREC) k_leaf(Src src, int K, int* delta, int* dstack,
+__global__ void __launch_bounds__(32 * CWN + L4_NREC, CWN <= 4 ? 4 : (CWN <= 8 ? 2 : 1)) k_leaf(Src src, int K, int* delta, int* dstack,
                                                               unsigned long long save_mask, double eps, BasisBuf out,
                                                               int* ndiff, int64_t* diff, int maxdiff, int* status,
                                                               int* rec_order, int* rec_pivot) {
   constexpr int NCHAIN = 32 * CWN, NT = NCHAIN + L4_NREC;
   __shared__ cd Bs[25][LEAF_CAP];
   __shared__ cd oldc[5][LEAF_CAP];
-  __shared__ cd rec_mu[LEAF_KMAX][5];
-  __shared__ cd rec_sig[LEAF_KMAX];
-  __shared__ int rec_piv[LEAF_KMAX];
-  __shared__ cd rowbuf[LEAF_KMAX][5];  // a row is written only while it is active: the step's winner row
-                                       // is never rewritten, so one buffer serves every step
+  __shared__ int rec_w[LEAF_KMAX], rec_piv[LEAF_KMAX];  // winner row and pivot column of each step
+  __shared__ cd muspec[LEAF_KMAX][5];  // each active row's would-be multipliers; a row is written only
+                                       // while it is active, so a step's winner row stays as it was
   __shared__ cd sigbuf[LEAF_KMAX];
-  __shared__ Pick cand[2][CWN];  // per-warp picks, by step parity
+  __shared__ longlong2 cand2[2][CWN];  // per-warp two largest packed keys ((key * 64 + 63 - row) * 8 +
+                                      // pivot column; KEY_SPEC: a special row), by step parity
+  __shared__ Pick cand[2][CWN];    // per-warp exact picks (FP64 path), by step parity
   __shared__ int blen[25];
   __shared__ int din[5], dl_out[5];
   __shared__ int chain_state;  // steps recorded so far, | CHAIN_DONE once the chain has stopped
@@ -203,6 +253,11 @@ __global__ void __launch_bounds__(32 * CWN + L4_NREC) k_leaf(Src src, int K, int
 #pragma unroll
     for (int i = 0; i < 5; ++i) dl[i] = din[i];
     const unsigned long long eps_bits = (unsigned long long)__double_as_longlong(eps * eps);
+    // eps^2 as a key (the same scale as approx_key); for zero or sub-normal eps^2 the key of 2^-1022
+    const int eexp = (int)(eps_bits >> 52);
+    const bool eps_normal = eexp > 0 && eexp < 2047;
+    const long long key_eps = eps_normal ? ((long long)(eexp - 1023 + 127) << 23) + (long long)((eps_bits >> 29) & 0x7fffffULL)
+                                         : ((long long)(-1022 + 127) << 23);
     for (int step = 0;; ++step) {
       const int par = step & 1;
       // ---- score of every active row (same arithmetic as the row-per-lane form) ----
@@ -213,36 +268,96 @@ __global__ void __launch_bounds__(32 * CWN + L4_NREC) k_leaf(Src src, int K, int
 #pragma unroll
       for (int c = 0; c < 5; ++c) mg[c] = __shfl_sync(0xffffffffu, mag, (rbase + c) & 31);
       if (active && rownz == 0u) active = false;  // every entry zero: the condition already holds
-      Pick p;
-      p.sb = NO_PICK;
-      p.idx = 1 << 30;
-      p.piv = -1;
-      if (active && jc == 0) {
-        int pi = -1, dpi = 0;
-        unsigned long long mpi = 0ULL;
+      // the row's pivot column, in each of its five lanes
+      int rpi = -1, dpi = 0;
+      unsigned long long mpi = 0ULL;
 #pragma unroll
-        for (int c = 0; c < 5; ++c) {
-          if (!((rownz >> c) & 1u)) continue;
-          const unsigned long long mb = (unsigned long long)__double_as_longlong(mg[c]);
-          if (pi < 0 || dl[c] < dpi || (dl[c] == dpi && mb > mpi)) { pi = c; mpi = mb; dpi = dl[c]; }
-        }
-        const double tot = ((mg[0] + mg[1]) + (mg[2] + mg[3])) + mg[4];
-        const double sc = __longlong_as_double((long long)mpi) / tot;
-        p.sb = (unsigned long long)__double_as_longlong(sc);
-        if (p.sb == 0ULL) p.sb = 1ULL;  // an underflowed ratio still ranks above "no candidate"
-        p.idx = q;
-        p.piv = pi;
+      for (int c = 0; c < 5; ++c) {
+        if (!((rownz >> c) & 1u)) continue;
+        const unsigned long long mb = (unsigned long long)__double_as_longlong(mg[c]);
+        if (rpi < 0 || dl[c] < dpi || (dl[c] == dpi && mb > mpi)) { rpi = c; mpi = mb; dpi = dl[c]; }
       }
-      p = warp_pick(p);
-      if (lane == 0) cand[par][wid] = p;
-      if (active) rowbuf[q][jc] = r;
-      named_sync(2, NCHAIN);
-      Pick b = cand[par][0];
+      // the multipliers this row would give if it wins, mu_j = -r_j conj(r_pi) / |r_pi|^2 (lane j's
+      // column), computed before the pick so that their FP64 latency overlaps the pick's integer work
+      const cd rpr = shfl_cd(r, (rbase + max(rpi, 0)) & 31);
+      {
+        const int de = (int)(mpi >> 52);
+        const double dw = __longlong_as_double((long long)mpi);  // |r_pi|^2 exactly as scored
+        const bool slow = active && !(de > 2 && de < 2044);
+        double rd = rcp_series(dw);
+        if (__any_sync(0xffffffffu, slow)) {  // zero, sub-normal or extreme |r_pi|^2: the FP64 division
+          if (slow) rd = 1.0 / dw;
+        }
+        // r_j conj(r_pi) does not wait for the reciprocal
+        const cd t = mkc(fma(r.x, rpr.x, r.y * rpr.y), fma(r.y, rpr.x, -(r.x * rpr.y)));
+        if (active && jc != rpi) muspec[q][jc] = mkc(-(t.x * rd), -(t.y * rd));
+      }
+      long long p1 = KEY_NONE, p2 = KEY_NONE;
+      if (active && jc == 0) {
+        bool spec;
+        p1 = (approx_key(mg, mpi, spec) * 64 + (63 - q)) * 8 + rpi;
+        if (spec) p1 = KEY_SPEC;
+      }
+      // the two largest over the candidate lanes 0, 5, ..., 25 (three rounds; the result in lane 0)
 #pragma unroll
-      for (int w2 = 1; w2 < CWN; ++w2)
-        if (pick_better(cand[par][w2], b)) b = cand[par][w2];
-      if (b.sb == NO_PICK || b.sb < eps_bits) {  // done, or difficult: defer the rest of the leaf
-        if (b.sb != NO_PICK && active && jc == 0) {
+      for (int o = 5; o <= 20; o *= 2) {
+        long long a1 = __shfl_down_sync(0xffffffffu, p1, o), a2 = __shfl_down_sync(0xffffffffu, p2, o);
+        if (lane + o >= 32) { a1 = KEY_NONE; a2 = KEY_NONE; }
+        const long long hi = max(p1, a1), lo = min(p1, a1);
+        p2 = max(lo, max(p2, a2));
+        p1 = hi;
+      }
+      if (lane == 0) cand2[par][wid] = make_longlong2(p1, p2);
+      named_sync(2, NCHAIN);
+      long long g1 = KEY_NONE, g2 = KEY_NONE;
+#pragma unroll
+      for (int w2 = 0; w2 < CWN; ++w2) {
+        const longlong2 c = cand2[par][w2];
+        const long long hi = max(g1, c.x), lo = min(g1, c.x);
+        g2 = max(lo, max(g2, c.y));
+        g1 = hi;
+      }
+      bool exact = g1 == KEY_SPEC;
+      if (!exact && g1 != KEY_NONE) {
+        const long long k1 = g1 >> 9;
+        if (g2 != KEY_NONE && k1 - (g2 >> 9) <= KEY_BAND) exact = true;  // a near tie
+        if (k1 <= key_eps + KEY_BAND && (k1 >= key_eps - KEY_BAND || !eps_normal)) exact = true;
+      }
+      int outcome, w = -1, pi = -1;  // outcome 0: pivot step, 1: no condition left, 2: difficult
+      if (!exact) {
+        if (g1 == KEY_NONE) {
+          outcome = 1;
+        } else {
+          w = 63 - (int)((g1 >> 3) & 63);
+          pi = (int)(g1 & 7);
+          outcome = (g1 >> 9) < key_eps ? 2 : 0;
+        }
+      } else {  // FP64 scores of every candidate, as the approximate keys could not decide
+        Pick p;
+        p.sb = NO_PICK;
+        p.idx = 1 << 30;
+        p.piv = -1;
+        if (active && jc == 0) {
+          const double tot = ((mg[0] + mg[1]) + (mg[2] + mg[3])) + mg[4];
+          const double sc = __longlong_as_double((long long)mpi) / tot;
+          p.sb = (unsigned long long)__double_as_longlong(sc);
+          if (p.sb == 0ULL) p.sb = 1ULL;  // an underflowed ratio still ranks above "no candidate"
+          p.idx = q;
+          p.piv = rpi;
+        }
+        p = warp_pick(p);
+        if (lane == 0) cand[par][wid] = p;
+        named_sync(2, NCHAIN);
+        Pick b = cand[par][0];
+#pragma unroll
+        for (int w2 = 1; w2 < CWN; ++w2)
+          if (pick_better(cand[par][w2], b)) b = cand[par][w2];
+        outcome = b.sb == NO_PICK ? 1 : (b.sb < eps_bits ? 2 : 0);
+        w = b.idx;
+        pi = b.piv;
+      }
+      if (outcome != 0) {  // done, or difficult: defer the rest of the leaf
+        if (outcome == 2 && active && jc == 0) {
           int slot = atomicAdd(ndiff + 4 * pb, 1);
           if (slot < maxdiff) diff[(int64_t)pb * maxdiff + slot] = eid;
           else set_status(status, ST_DIFFICULT);
@@ -253,27 +368,14 @@ __global__ void __launch_bounds__(32 * CWN + L4_NREC) k_leaf(Src src, int K, int
         }
         break;
       }
-      const int pi = b.piv, w = b.idx;
-      // ---- mu_j = -r_wj / r_wpi as r_wj conj(r_wpi) / |r_wpi|^2, lane j's own column ----
-      const cd rp = rowbuf[w][pi];
       const cd sw = sigbuf[w];
-      cd mu = mkc(0.0, 0.0);
-      if (jc != pi) {
-        const double rd = 1.0 / fma(rp.x, rp.x, rp.y * rp.y);
-        const cd inv = mkc(rp.x * rd, -rp.y * rd);
-        mu = cmul(rowbuf[w][jc], inv);
-        mu = mkc(-mu.x, -mu.y);
-      }
-      if (wid == 0) {  // records of this step, then its publication to the rebuild warps
-        if (lane < 5) rec_mu[step][lane] = mu;
-        if (lane == 0) {
-          rec_piv[step] = pi;
-          rec_sig[step] = sw;
-          if (rec_order) { rec_order[step] = w; rec_pivot[step] = pi; }
-        }
+      const cd muw = muspec[w][jc];
+      if (tid == 0) {  // this step's record, then its publication to the rebuild warps
+        rec_w[step] = w;
+        rec_piv[step] = pi;
+        if (rec_order) { rec_order[step] = w; rec_pivot[step] = pi; }
         __threadfence_block();
-        __syncwarp();
-        if (lane == 0) st_volatile(&chain_state, step + 1);
+        st_volatile(&chain_state, step + 1);
       }
       if (q == w) active = false;
 #pragma unroll
@@ -282,7 +384,7 @@ __global__ void __launch_bounds__(32 * CWN + L4_NREC) k_leaf(Src src, int K, int
       const cd rpo = shfl_cd(r, (rbase + pi) & 31);
       if (active) {
         const cd ds = csub(sig, sw);
-        const cd fac = (jc == pi) ? ds : mu;
+        const cd fac = (jc == pi) ? ds : muw;
         const cd base = (jc == pi) ? mkc(0.0, 0.0) : r;
         r = cfma(fac, rpo, base);
       }
@@ -306,8 +408,8 @@ __global__ void __launch_bounds__(32 * CWN + L4_NREC) k_leaf(Src src, int K, int
       }
       named_sync(1, L4_NREC);
       if (rb_cmd != 0) break;
-      const int pi = rec_piv[s];
-      const cd sb = rec_sig[s];
+      const int pi = rec_piv[s], ws = rec_w[s];
+      const cd sb = sigbuf[ws];
       const cd nsb = mkc(-sb.x, -sb.y);
       int lmax = 0;
 #pragma unroll
@@ -323,13 +425,12 @@ __global__ void __launch_bounds__(32 * CWN + L4_NREC) k_leaf(Src src, int K, int
         const int i = e / 5, j = e % 5;
         const int lo = blen[i * 5 + pi];
         if (lo == 0 || t > lo) continue;
+        const bool isp = j == pi;
+        if (!isp && t == lo) continue;
         const cd o = t < lo ? oldc[i][t] : mkc(0.0, 0.0);
-        if (j == pi) {
-          const cd prev = t >= 1 ? oldc[i][t - 1] : mkc(0.0, 0.0);
-          Bs[e][t] = cfma(nsb, o, prev);
-        } else if (t < lo) {
-          Bs[e][t] = cfma(rec_mu[s][j], o, Bs[e][t]);
-        }
+        const cd fac = isp ? nsb : muspec[ws][j];
+        const cd base = isp ? (t >= 1 ? oldc[i][t - 1] : mkc(0.0, 0.0)) : Bs[e][t];
+        Bs[e][t] = cfma(fac, o, base);
       }
       named_sync(1, L4_NREC);
       if (rt < 5) {
