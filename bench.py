@@ -233,7 +233,7 @@ def main():
 
     # dominant kernel (the leaf): every launch timed with a CUDA event pair on the plan's stream, over
     # the same number of steps right after the timed region (events are not in the timed steps)
-    plan.set_profiling(1)
+    plan.set_profiling(3)
     with torch.cuda.stream(stream):
         for i in range(args.steps):
             flush.zero_()
@@ -241,6 +241,9 @@ def main():
     plan.sync()
     pst = plan.stats()
     plan.set_profiling(0)
+    kinds = ("leaf", "evaluation", "product", "other")
+    breakdown = {k: {"ms_per_step": pst["prof_kind_ms"][i] / args.steps,
+                     "groups_per_step": pst["prof_kind_count"][i] / args.steps} for i, k in enumerate(kinds)}
     t_step = sum(step_ms) / len(step_ms)
     t_max = t_step
     if world > 1:
@@ -309,6 +312,7 @@ def main():
                "clocks": clocks,
                "peaks": {"hbm_gbs": pk.get("hbm_gbs"), "kind": pk_kind},
                "roofline": roofline,
+               "step_breakdown": breakdown,
                "cpu_baseline": cpu}
         print(json.dumps(out))
     plan.close()

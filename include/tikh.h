@@ -95,6 +95,12 @@ typedef struct {
   double prof_leaf_ms;     /* with profiling on: summed duration of the leaf launches since it was switched on */
   int64_t prof_leaf_launches; /* with profiling on: leaf launches timed since it was switched on */
   int graph;                  /* 1 if the last solve ran as a (captured or replayed) CUDA graph */
+  /* with profiling flag 2: summed event-timed duration and count of the schedule's launch groups since
+   * profiling was switched on, by kind: [0] leaves, [1] evaluations (Sec. 5.1 updates of a right
+   * child's conditions), [2] basis products, [3] the rest (transform, conditions, difficult points,
+   * extraction, refinement, output) */
+  double prof_kind_ms[4];
+  int64_t prof_kind_count[4];
 } tikh_stats;
 
 /* Build a plan for an m x n problem: sizing by Algorithm 2 (Sec. 5.2), the recursion schedule of
@@ -152,10 +158,12 @@ int tikh_sync(tikh_plan plan);
 /* Statistics of the plan and of the last synchronised solve. */
 int tikh_get_stats(tikh_plan plan, tikh_stats* out);
 
-/* Profiling switch: flags = 1 records a CUDA event pair around every leaf launch (Eq. (spbasis)
+/* Profiling switch: flags bit 0 records a CUDA event pair around every leaf launch (Eq. (spbasis)
  * kernel) on the plan's stream; every synchronising call adds them to tikh_stats.prof_leaf_ms and
- * prof_leaf_launches, which this call resets.  flags = 0 turns it off.  The events add a little host
- * and device time. */
+ * prof_leaf_launches.  Bit 1 records a pair around every launch group of the solve and sums them by
+ * kind into prof_kind_ms / prof_kind_count.  This call resets all of them; flags = 0 turns profiling
+ * off.  Profiled solves run as stream launches (no graph replay); the events add a little host and
+ * device time.  TIKH_EINVAL for flags outside 0..3. */
 int tikh_set_profiling(tikh_plan plan, int flags);
 
 /* Release all device and host memory of the plan.  NULL is ignored. */

@@ -189,38 +189,57 @@ int status_to_code(int st) {
   return TIKH_OK;
 }
 
+// profiling: an event pair around one launch group, kind 0..3 (leaf, evaluation, product, other)
+struct ProfScope {
+  Plan& P;
+  cudaEvent_t e1 = nullptr;
+  ProfScope(Plan& p, int kind) : P(p) {
+    const bool on = (P.prof_leaf & 2) || (kind == 0 && (P.prof_leaf & 1));
+    if (!on) return;
+    while (P.ev_pool.size() < P.ev_used + 2) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return;
+      P.ev_pool.push_back(e);
+    }
+    if (P.ev_kind.size() < P.ev_pool.size() / 2) P.ev_kind.resize(P.ev_pool.size() / 2);
+    cudaEventRecord(P.ev_pool[P.ev_used], P.stream);
+    e1 = P.ev_pool[P.ev_used + 1];
+    P.ev_kind[P.ev_used / 2] = (signed char)kind;
+    P.ev_used += 2;
+  }
+  ~ProfScope() {
+    if (e1) cudaEventRecord(e1, P.stream);
+  }
+};
+
 // one superfast solve of every problem's core system with right-hand side y, solution into out
 int enqueue_core(Plan& P, const cd* y, cd* out, int64_t& nl) {
   int r;
-  if ((r = launch_conditions(P, y)) < 0) return r;
+  {
+    ProfScope ps(P, 3);
+    if ((r = launch_conditions(P, y)) < 0) return r;
+  }
   nl += r;
   for (const Step& st : P.sched) {
     if (st.kind == STEP_LEAF) {
-      cudaEvent_t e0 = nullptr, e1 = nullptr;
-      if (P.prof_leaf) {
-        while (P.ev_pool.size() < P.ev_used + 2) {
-          cudaEvent_t e;
-          if (cudaEventCreate(&e) != cudaSuccess) return TIKH_ECUDA;
-          P.ev_pool.push_back(e);
-        }
-        e0 = P.ev_pool[P.ev_used];
-        e1 = P.ev_pool[P.ev_used + 1];
-        P.ev_used += 2;
-        cudaEventRecord(e0, P.stream);
-      }
+      ProfScope ps(P, 0);
       r = launch_leaf(P, st);
-      if (e1) cudaEventRecord(e1, P.stream);
     } else if (st.kind == STEP_EVAL) {
+      ProfScope ps(P, 1);
       r = launch_eval(P, st);
     } else {
+      ProfScope ps(P, 2);
       r = launch_prod(P, st);
     }
     if (r < 0) return r;
     nl += r;
   }
-  if ((r = launch_difficult(P)) < 0) return r;
-  nl += r;
-  if ((r = launch_extract(P, out)) < 0) return r;
+  {
+    ProfScope ps(P, 3);
+    if ((r = launch_difficult(P)) < 0) return r;
+    nl += r;
+    if ((r = launch_extract(P, out)) < 0) return r;
+  }
   nl += r;
   return TIKH_OK;
 }
@@ -231,13 +250,20 @@ int enqueue_core_refined(Plan& P, int64_t& nl) {
   if ((r = enqueue_core(P, P.ybuf, P.xcore, nl)) < 0) return r;
   // iterative refinement on the core system: v <- v + A^{-1}(y - A v)
   for (int it = 0; it < P.opts.refine_steps; ++it) {
-    if ((r = launch_residual(P, P.ybuf, P.xcore, P.rbuf)) < 0) return r;
+    {
+      ProfScope ps(P, 3);
+      if ((r = launch_residual(P, P.ybuf, P.xcore, P.rbuf)) < 0) return r;
+    }
     nl += r;
     if ((r = enqueue_core(P, P.rbuf, P.dx, nl)) < 0) return r;
-    if ((r = launch_axpy(P, P.xcore, P.dx)) < 0) return r;
+    {
+      ProfScope ps(P, 3);
+      if ((r = launch_axpy(P, P.xcore, P.dx)) < 0) return r;
+    }
     nl += r;
   }
   if (P.opts.refine_steps > 0) {  // residual of the refined solution, reported in the stats
+    ProfScope ps(P, 3);
     if ((r = launch_residual(P, P.ybuf, P.xcore, P.rbuf)) < 0) return r;
     nl += r;
   }
@@ -252,6 +278,7 @@ int enqueue_prologue(Plan& P, const UserArrays& u, int rhs_is_y, const double* l
       cudaMemcpyAsync(P.lam, lams, sizeof(double) * (size_t)nb, cudaMemcpyHostToDevice, P.stream) != cudaSuccess)
     return TIKH_ECUDA;
   if (cudaMemsetAsync(P.status, 0, sizeof(int), P.stream) != cudaSuccess) return TIKH_ECUDA;
+  ProfScope ps(P, 3);
   if ((r = launch_spectrum(P, u)) < 0) return r;
   nl += r;
   // for m < n the core problem (T T^H + lam I) v = b takes b itself as its right-hand side
@@ -265,7 +292,10 @@ int enqueue_solve(Plan& P, const UserArrays& u, int rhs_is_y, const double* lams
   int r;
   if ((r = enqueue_prologue(P, u, rhs_is_y, lams, nb, nl)) < 0) return r;
   if ((r = enqueue_core_refined(P, nl)) < 0) return r;
-  if ((r = launch_output(P, P.xcore, u)) < 0) return r;
+  {
+    ProfScope ps(P, 3);
+    if ((r = launch_output(P, P.xcore, u)) < 0) return r;
+  }
   nl += r;
   P.launches = nl;
   return TIKH_OK;
@@ -358,14 +388,21 @@ int sync_status(Plan& P) {
     }
     P.last.rel_residual = worst;
   }
-  if (P.prof_leaf) {  // average leaf duration from the event pairs recorded since the last sync
-    double ms = 0.0;
+  if (P.prof_leaf) {  // durations of the event pairs recorded since the last sync, accumulated until
+                      // tikh_set_profiling re-arms it
     for (size_t i = 0; i + 1 < P.ev_used; i += 2) {
       float t = 0.0f;
-      if (cudaEventElapsedTime(&t, P.ev_pool[i], P.ev_pool[i + 1]) == cudaSuccess) ms += t;
+      if (cudaEventElapsedTime(&t, P.ev_pool[i], P.ev_pool[i + 1]) != cudaSuccess) continue;
+      const int kind = P.ev_kind[i / 2];
+      if (kind == 0) {
+        P.last.prof_leaf_ms += t;
+        P.last.prof_leaf_launches += 1;
+      }
+      if (P.prof_leaf & 2) {
+        P.last.prof_kind_ms[kind] += t;
+        P.last.prof_kind_count[kind] += 1;
+      }
     }
-    P.last.prof_leaf_ms += ms;  // accumulated until tikh_set_profiling re-arms it
-    P.last.prof_leaf_launches += (int64_t)(P.ev_used / 2);
     P.ev_used = 0;
   }
   int zero = 0;
@@ -576,11 +613,15 @@ int tikh_get_stats(tikh_plan h, tikh_stats* out) {
 }
 
 int tikh_set_profiling(tikh_plan h, int flags) {
-  if (!h || flags < 0 || flags > 1) return TIKH_EINVAL;
-  h->P.prof_leaf = flags & 1;
+  if (!h || flags < 0 || flags > 3) return TIKH_EINVAL;
+  h->P.prof_leaf = flags & 3;
   h->P.ev_used = 0;
   h->P.last.prof_leaf_ms = 0.0;
   h->P.last.prof_leaf_launches = 0;
+  for (int k = 0; k < 4; ++k) {
+    h->P.last.prof_kind_ms[k] = 0.0;
+    h->P.last.prof_kind_count[k] = 0;
+  }
   return TIKH_OK;
 }
 

@@ -66,8 +66,8 @@ struct Plan {
   int batch_max = 1;
   int nb = 1;          // problems in the current call
   int slack_mult = 1;  // degree-prediction slack multiplier (raised after TIKH_EDEGREE)
-  int64_t eval_direct_max = 32;  // step 2 by Horner when the right child has <= this many nodes per coset
-  int64_t prod_direct_max = 64;  // step 4 by schoolbook products when the planned length P <= this
+  int64_t eval_direct_max = 80;  // step 2 by direct evaluation when the right child has <= this many nodes per coset
+  int64_t prod_direct_max = 360;  // step 4 by schoolbook products when the planned length P <= this
 
   std::vector<Step> sched;
   std::map<int64_t, int> fft_of_len;
@@ -118,8 +118,9 @@ struct Plan {
   int graph_nb = 0, graph_rhs_is_y = -1;
 
   // optional timing of every leaf launch with a CUDA event pair on the plan's stream
-  int prof_leaf = 0;
+  int prof_leaf = 0;  // profiling flags (bit 0: leaves, bit 1: every launch group by kind)
   std::vector<cudaEvent_t> ev_pool;
+  std::vector<signed char> ev_kind;  // kind of each recorded pair (-1: a leaf timed for bit 0 only)
   size_t ev_used = 0;
 
   tikh_stats last{};

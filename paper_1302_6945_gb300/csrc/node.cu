@@ -85,51 +85,47 @@ __global__ void k_eval_update(cd* R, const cd* __restrict__ vals, int64_t N, int
   }
 }
 
-// Small nodes: B_L evaluated by Horner at each right-child node (thread per (node, entry)), then the
-// residual update of that node's two conditions, in one launch.  Block = 8 nodes x 25 entries.
-constexpr int EVD_NODES = 8;
-__global__ void __launch_bounds__(256) k_eval_direct(BasisBuf BL, BasisBuf OUT, cd* R, const cd* __restrict__ wN,
-                                                     int64_t N, int64_t a0, int64_t s2, int64_t Lr) {
-  __shared__ cd V[EVD_NODES][25];
-  __shared__ cd Rs[EVD_NODES][10];
-  __shared__ double scl[5];
+// Small nodes: B_L evaluated at each right-child node, then the residual update of that node's two
+// conditions, in one launch.  Block = one node (g = 2j + c), 25 entries x G lanes: lane gl evaluates
+// the coefficient chunk [gl C, gl C + C) of its entry by Horner, multiplies by z^(gl C) (twiddle
+// table) and the G lanes are added by shuffles; then ten threads form phi <- phi B_L(sigma).
+template <int G>
+__global__ void __launch_bounds__(25 * G) k_eval_direct(BasisBuf BL, BasisBuf OUT, cd* R, const cd* __restrict__ wN,
+                                                        int64_t N, int64_t a0, int64_t s2) {
+  __shared__ cd V[25];
+  __shared__ cd Rs[10];
   const int pb = blockIdx.y, tid = threadIdx.x;
-  if (tid < 5) scl[tid] = col_scale_from_bits(BL.mp(pb)[tid]);
-  if (blockIdx.x == 0 && tid >= 32 && tid < 37) OUT.mp(pb)[tid - 32] = 0ULL;
-  const int64_t g0 = (int64_t)blockIdx.x * EVD_NODES;  // first node (g = 2j + c) of this block
-  if (tid < EVD_NODES * 10) {  // stage the two residual rows of each node
-    int ln = tid / 10, k = tid % 10;
-    int64_t g = g0 + ln;
-    if (g < 2 * Lr) {
-      int64_t e = a0 + (g & 1) + s2 * (g >> 1);
-      Rs[ln][k] = R[((int64_t)pb * N + e) * 10 + k];
-    }
-  }
-  __syncthreads();
-  if (tid < EVD_NODES * 25) {
-    int ln = tid / 25, E = tid % 25;
-    int64_t g = g0 + ln;
-    if (g < 2 * Lr) {
-      int64_t e = a0 + (g & 1) + s2 * (g >> 1);
-      cd z = wN[e];
-      const cd* c = BL.cp(pb) + (int64_t)E * BL.cap;
-      int len = BL.lp(pb)[E];
-      cd v = mkc(0.0, 0.0);
-      for (int t = len - 1; t >= 0; --t) v = cfma(v, z, c[t]);
-      V[ln][E] = cscale(v, scl[E % 5]);
-    }
-  }
-  __syncthreads();
-  if (tid < EVD_NODES * 10) {  // (node, condition f, column): phi <- phi B_L(sigma)
-    int ln = tid / 10, f = (tid / 5) % 2, col = tid % 5;
-    int64_t g = g0 + ln;
-    if (g < 2 * Lr) {
-      int64_t e = a0 + (g & 1) + s2 * (g >> 1);
-      cd acc = mkc(0.0, 0.0);
+  const int64_t g = blockIdx.x;
+  const int64_t e = a0 + (g & 1) + s2 * (g >> 1);
+  if (g == 0 && tid < 5) OUT.mp(pb)[tid] = 0ULL;  // the parent's column maxima, rebuilt by its product
+  if (tid < 10) Rs[tid] = R[((int64_t)pb * N + e) * 10 + tid];
+  const int E = tid / G, gl = tid - E * G;
+  const int len = BL.lp(pb)[E];
+  const int C = (len + G - 1) / G;
+  const int cnt = min(C, len - gl * C);
+  const cd z = wN[e];
+  const cd* c = BL.cp(pb) + (int64_t)E * BL.cap + (int64_t)gl * C;
+  cd v = mkc(0.0, 0.0);
+  for (int t = cnt - 1; t >= 0; --t) v = cfma(v, z, c[t]);
+  if (G > 1) {
+    if (gl > 0 && cnt > 0) v = cmul(v, tw_at(wN, (e * (int64_t)(gl * C)) % N));
+    const int wbase = tid & ~31;
+    const int nw = min(32, (int)blockDim.x - wbase);
+    const unsigned mask = nw == 32 ? 0xffffffffu : ((1u << nw) - 1u);
 #pragma unroll
-      for (int i = 0; i < 5; ++i) acc = cfma(Rs[ln][f * 5 + i], V[ln][i * 5 + col], acc);
-      R[((int64_t)pb * N + e) * 10 + f * 5 + col] = acc;
+    for (int o = G / 2; o > 0; o >>= 1) {
+      v.x += __shfl_xor_sync(mask, v.x, o);
+      v.y += __shfl_xor_sync(mask, v.y, o);
     }
+  }
+  if (gl == 0) V[E] = cscale(v, col_scale_from_bits(BL.mp(pb)[E % 5]));
+  __syncthreads();
+  if (tid < 10) {  // (condition f, column): phi <- phi B_L(sigma)
+    const int f = tid / 5, col = tid % 5;
+    cd acc = mkc(0.0, 0.0);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) acc = cfma(Rs[f * 5 + i], V[i * 5 + col], acc);
+    R[((int64_t)pb * N + e) * 10 + f * 5 + col] = acc;
   }
 }
 
@@ -138,8 +134,15 @@ int launch_eval(Plan& P, const Step& st) {
   const BasisBuf& BL = P.buf[st.depth + 1][0];
   const BasisBuf& OUT = P.buf[st.depth][st.side];
   if (Lr <= P.eval_direct_max) {
-    dim3 grid((unsigned)((2 * Lr + EVD_NODES - 1) / EVD_NODES), (unsigned)P.nb);
-    k_eval_direct<<<grid, 256, 0, P.stream>>>(BL, OUT, P.R, P.wN, P.N, st.a + st.s, 2 * st.s, Lr);
+    const dim3 grid((unsigned)(2 * Lr), (unsigned)P.nb);
+    const int64_t cap = BL.cap, a0 = st.a + st.s, s2 = 2 * st.s;
+    cudaStream_t s = P.stream;
+    if (cap <= 8) k_eval_direct<1><<<grid, 25, 0, s>>>(BL, OUT, P.R, P.wN, P.N, a0, s2);
+    else if (cap <= 24) k_eval_direct<2><<<grid, 50, 0, s>>>(BL, OUT, P.R, P.wN, P.N, a0, s2);
+    else if (cap <= 48) k_eval_direct<4><<<grid, 100, 0, s>>>(BL, OUT, P.R, P.wN, P.N, a0, s2);
+    else if (cap <= 96) k_eval_direct<8><<<grid, 200, 0, s>>>(BL, OUT, P.R, P.wN, P.N, a0, s2);
+    else if (cap <= 192) k_eval_direct<16><<<grid, 400, 0, s>>>(BL, OUT, P.R, P.wN, P.N, a0, s2);
+    else k_eval_direct<32><<<grid, 800, 0, s>>>(BL, OUT, P.R, P.wN, P.N, a0, s2);
     return cudaGetLastError() == cudaSuccess ? 1 : TIKH_ECUDA;
   }
   const FftPlan& F = P.ffts[st.fft];
@@ -245,52 +248,83 @@ __global__ void k_prod_finish(const cd* __restrict__ FC, int64_t P, BasisBuf OUT
   }
 }
 
-// Small nodes: schoolbook product, one block per (output entry, problem), thread per coefficient,
-// trimmed to the degree bound, column maxima accumulated (reset by this node's evaluation step).
-__global__ void __launch_bounds__(256) k_prod_direct(BasisBuf BL, BasisBuf BR, BasisBuf OUT, const int* dstack,
-                                                     int depth, const int* delta, int* status) {
-  const int E = blockIdx.x, i = E / 5, j = E % 5, pb = blockIdx.y, tid = threadIdx.x;
-  __shared__ double sl[5], sr;
+// Small nodes: schoolbook product B = B_L B_R.  Block = (output entry E = (i, j), tile of PD_TC
+// coefficients, problem); warp w computes coefficient t = tile PD_TC + w, its lanes splitting the
+// terms (u, q) of sum_u sum_q a_iu[q] b_uj[t - q] and a shuffle reduction adding them, so each lane's
+// FP64 chain is short and the product spreads over 25 ceil(P / PD_TC) blocks.  Row i of B_L and
+// column j of B_R are staged in shared memory with their column scales applied.  Output trimmed to
+// the degree bound; column maxima accumulated (reset by this node's evaluation step).
+constexpr int PD_TC = 8;
+__global__ void __launch_bounds__(32 * PD_TC) k_prod_direct(BasisBuf BL, BasisBuf BR, BasisBuf OUT, const int* dstack,
+                                                             int depth, const int* delta, int* status, int ntile) {
+  extern __shared__ cd pd_sh[];  // A: 5 x BL.cap, then B: 5 x BR.cap
+  const int E = blockIdx.x / ntile, tile = blockIdx.x % ntile;
+  const int i = E / 5, j = E % 5, pb = blockIdx.y, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   __shared__ int want_s, ll[5], lr[5];
-  __shared__ double red[8];
+  __shared__ double red[PD_TC];
   if (tid < 5) {
-    sl[tid] = col_scale_from_bits(BL.mp(pb)[tid]);
     ll[tid] = BL.lp(pb)[i * 5 + tid];
     lr[tid] = BR.lp(pb)[tid * 5 + j];
   }
   if (tid == 0) {
-    sr = col_scale_from_bits(BR.mp(pb)[j]);
     int bnd = entry_bound_dev(dstack + (pb * MAX_DEPTH + depth) * 5, delta + 8 * pb, i, j);
     int want = bnd < 0 ? 0 : bnd + 1;
     if (want > OUT.cap) { set_status(status, ST_DEGREE); want = (int)OUT.cap; }
     want_s = want;
-    OUT.lp(pb)[E] = want;
+    if (tile == 0) OUT.lp(pb)[E] = want;
   }
   __syncthreads();
-  const int want = want_s;
-  const cd* lc = BL.cp(pb) + (int64_t)(i * 5) * BL.cap;
-  const cd* rc = BR.cp(pb) + (int64_t)j * BR.cap;
-  cd* dst = OUT.cp(pb) + (int64_t)E * OUT.cap;
-  double mx = 0.0;
-  for (int t = tid; t < want; t += blockDim.x) {
-    cd acc = mkc(0.0, 0.0);
-    for (int u = 0; u < 5; ++u) {
-      const cd* a = lc + (int64_t)u * BL.cap;
-      const cd* b = rc + (int64_t)(u * 5) * BR.cap;
-      int la = ll[u], lb = lr[u];
-      int s0 = max(0, t - lb + 1), s1 = min(t, la - 1);
-      cd part = mkc(0.0, 0.0);
-      for (int q = s0; q <= s1; ++q) part = cfma(a[q], b[t - q], part);
-      acc = cfma(part, mkc(sl[u] * sr, 0.0), acc);
-    }
-    dst[t] = acc;
-    mx = fmax(mx, fmax(fabs(acc.x), fabs(acc.y)));
+  const int want = want_s, t0 = tile * PD_TC;
+  if (t0 >= want) return;  // block-uniform
+  const int tmax = min(want, t0 + PD_TC);
+  const int capL = (int)BL.cap, capR = (int)BR.cap;
+  cd* As = pd_sh;
+  cd* Bs = pd_sh + 5 * capL;
+  for (int idx = tid; idx < 5 * capL; idx += blockDim.x) {
+    const int u = idx / capL, q = idx - u * capL;
+    if (q < min(ll[u], tmax))
+      As[idx] = cscale(BL.cp(pb)[(int64_t)(i * 5 + u) * capL + q], col_scale_from_bits(BL.mp(pb)[u]));
   }
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((tid & 31) == 0) red[tid >> 5] = mx;
+  const double sr = col_scale_from_bits(BR.mp(pb)[j]);
+  for (int idx = tid; idx < 5 * capR; idx += blockDim.x) {
+    const int u = idx / capR, q = idx - u * capR;
+    if (q < min(lr[u], tmax)) Bs[idx] = cscale(BR.cp(pb)[(int64_t)(u * 5 + j) * capR + q], sr);
+  }
+  __syncthreads();
+  double mx = 0.0;
+  const int t = t0 + w;
+  if (t < tmax) {  // warp-uniform
+    int lo[5], pre[5], tot = 0;
+#pragma unroll
+    for (int u = 0; u < 5; ++u) {
+      lo[u] = max(0, t - lr[u] + 1);
+      const int hi = min(t, ll[u] - 1);
+      pre[u] = tot;
+      tot += max(0, hi - lo[u] + 1);
+    }
+    cd acc = mkc(0.0, 0.0);
+    for (int k = lane; k < tot; k += 32) {
+      int u = 0, base = 0, l0 = lo[0];
+#pragma unroll
+      for (int v = 1; v < 5; ++v)
+        if (k >= pre[v]) { u = v; base = pre[v]; l0 = lo[v]; }
+      const int q = l0 + (k - base);
+      acc = cfma(As[u * capL + q], Bs[u * capR + (t - q)], acc);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+    }
+    if (lane == 0) {
+      OUT.cp(pb)[(int64_t)E * OUT.cap + t] = acc;
+      mx = fmax(fabs(acc.x), fabs(acc.y));
+    }
+  }
+  if (lane == 0) red[w] = mx;
   __syncthreads();
   if (tid == 0) {
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, red[w]);
+    for (int v = 1; v < PD_TC; ++v) mx = fmax(mx, red[v]);
     if (mx > 0.0) atomicMax(OUT.mp(pb) + j, (unsigned long long)__double_as_longlong(mx));
   }
 }
@@ -299,9 +333,11 @@ int launch_prod(Plan& P, const Step& st) {
   const BasisBuf& BL = P.buf[st.depth + 1][0];
   const BasisBuf& BR = P.buf[st.depth + 1][1];
   const BasisBuf& OUT = P.buf[st.depth][st.side];
-  if (st.P <= P.prod_direct_max) {
-    int threads = (int)std::min<int64_t>(256, ((st.P + 31) / 32) * 32);
-    k_prod_direct<<<dim3(25, P.nb), threads, 0, P.stream>>>(BL, BR, OUT, P.dstack, st.depth, P.delta, P.status);
+  const size_t smem = sizeof(cd) * 5 * (size_t)(BL.cap + BR.cap);
+  if (st.P <= P.prod_direct_max && smem <= 48 * 1024) {
+    const int ntile = (int)((st.P + PD_TC - 1) / PD_TC);
+    k_prod_direct<<<dim3(25 * ntile, P.nb), 32 * PD_TC, smem, P.stream>>>(BL, BR, OUT, P.dstack, st.depth, P.delta,
+                                                                          P.status, ntile);
     return cudaGetLastError() == cudaSuccess ? 1 : TIKH_ECUDA;
   }
   const FftPlan& F = P.ffts[st.fft];

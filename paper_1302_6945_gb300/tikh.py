@@ -30,11 +30,12 @@ class tikh_stats(ctypes.Structure):
                 ("jstar", ctypes.c_int), ("retries", ctypes.c_int), ("kernel_launches", ctypes.c_int64),
                 ("workspace_bytes", ctypes.c_int64), ("refine_steps", ctypes.c_int), ("rel_residual", ctypes.c_double),
                 ("batch", ctypes.c_int), ("prof_leaf_ms", ctypes.c_double), ("prof_leaf_launches", ctypes.c_int64),
-                ("graph", ctypes.c_int)]
+                ("graph", ctypes.c_int), ("prof_kind_ms", ctypes.c_double * 4), ("prof_kind_count", ctypes.c_int64 * 4)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}
-        d["delta"] = list(self.delta)
+        for f in ("delta", "prof_kind_ms", "prof_kind_count"):
+            d[f] = list(getattr(self, f))
         return d
 
 

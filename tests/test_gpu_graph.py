@@ -74,3 +74,20 @@ def test_graph_batched_and_default_stream_fallback():
     assert relerr(x.cpu().numpy(), ref.solve(col, row, b, 1e-3).cpu().numpy()) <= 1e-14
     d.close()
     ref.close()
+
+
+def test_profiling_by_kind_covers_the_schedule():
+    m, n = 1024, 1024
+    P = W.deconvolution_problem(m, n, 3.0, 12, 1e-6, 1e-6, 1e-3, seed=2)
+    t = lambda a: torch.tensor(a, dtype=torch.float64, device=DEV)
+    plan = tikh.Plan(m, n, "r64", graph=True)
+    plan.set_profiling(3)
+    plan.solve(t(P["col"]), t(P["row"]), t(P["b"]), 1e-3)
+    st = plan.stats()
+    plan.close()
+    assert st["graph"] == 0  # profiled solves run as stream launches
+    leaves = st["prof_kind_count"][0]
+    assert leaves >= 2 and st["prof_leaf_launches"] == leaves
+    assert st["prof_kind_count"][1] == leaves - 1 and st["prof_kind_count"][2] == leaves - 1  # one per inner node
+    assert all(v > 0 for v in st["prof_kind_ms"])
+    assert abs(st["prof_kind_ms"][0] - st["prof_leaf_ms"]) <= 1e-9 * max(1.0, st["prof_leaf_ms"])
