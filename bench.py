@@ -38,7 +38,17 @@ def leaf_model_flops(K):
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_leaf launch (K = 20, one problem), from
 # profiles/k_leaf_c2recipe_n4096.md; None once the kernel changes after that capture
-LEAF_TRAFFIC_BYTES = 52224
+# dram__bytes_read.sum + dram__bytes_write.sum of one leaf launch from an ncu capture of the current
+# kernel (profiles/k_leaf_*.md); None while the kernel has changed since the last capture
+LEAF_TRAFFIC_BYTES = None
+
+
+def model_bytes_per_solve(N, p):
+    """Algorithmic HBM words of one solve (c128, 16 B each): per split level the left basis read
+    for the evaluation (~5N), the right residuals read and written (~10N), both bases into the product
+    (~10N) and the product out (~10N), about 35N; the leaves read their conditions and write their
+    bases (~10N)."""
+    return 16 * (35 * N * p + 10 * N)
 
 
 def peaks():
@@ -214,6 +224,15 @@ def main():
 
     res = normal_residual(x)
 
+    # forward error of the benchmarked solution against a solve of the same problem with two FP64
+    # refinement corrections (outside the timed region)
+    ref_plan = tikh.Plan(m, n, "c128", n_lim=args.n_lim, refine_steps=max(2, args.refine + 1), stream=stream)
+    with torch.cuda.stream(stream):
+        x_ref = ref_plan.solve(col[0], row[0], bb[0], lams[0])
+    ref_res = normal_residual(x_ref)
+    rel_err_ref = float(torch.linalg.norm(x - x_ref) / torch.linalg.norm(x_ref))
+    ref_plan.close()
+
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -306,12 +325,19 @@ def main():
                "n_solves_per_s": value * n,
                "solves_per_s_per_problem_stream": value / B,
                "normal_eq_rel_residual": res,
+               "rel_err_vs_refined": {"value": rel_err_ref, "reference": "same problem, %d FP64 refinement "
+                                      "corrections" % max(2, args.refine + 1), "reference_normal_eq_rel_residual":
+                                      ref_res},
                "e2e": {"value": e2e_v, "unit": "solves/s", "h2d_bytes_per_step": 16 * (2 * m + n),
                        "d2h_bytes_per_step": 16 * n},
                "gpu_launches": int(st["kernel_launches"]) * args.steps,
                "clocks": clocks,
                "peaks": {"hbm_gbs": pk.get("hbm_gbs"), "kind": pk_kind},
                "roofline": roofline,
+               "hbm": {"model_bytes_per_solve": model_bytes_per_solve(st["N"], st["p"]),
+                       "achieved_gbs": model_bytes_per_solve(st["N"], st["p"]) * B / (t_max / 1e3) / 1e9,
+                       "pct_of_measured": 100.0 * model_bytes_per_solve(st["N"], st["p"]) * B / (t_max / 1e3) / 1e9
+                       / pk.get("hbm_gbs", 6788.3)},
                "step_breakdown": breakdown,
                "cpu_baseline": cpu}
         print(json.dumps(out))
