@@ -38,9 +38,9 @@ def leaf_model_flops(K):
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_leaf launch (K = 20, one problem), from
 # profiles/k_leaf_c2recipe_n4096.md; None once the kernel changes after that capture
-# dram__bytes_read.sum + dram__bytes_write.sum of one leaf launch from an ncu capture of the current
-# kernel (profiles/k_leaf_*.md); None while the kernel has changed since the last capture
-LEAF_TRAFFIC_BYTES = None
+# dram__bytes_read.sum + dram__bytes_write.sum of one leaf launch (K = 20) from an ncu capture of the
+# current kernel (profiles/k_leaf_c2recipe_n4096.md); None whenever the kernel changes until recaptured
+LEAF_TRAFFIC_BYTES = 45056
 
 
 def model_bytes_per_solve(N, p):
