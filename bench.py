@@ -165,6 +165,8 @@ def main():
     ap.add_argument("--n", type=int, default=None, help="sweep point: n unknowns, m = 1.5 n (default: c2)")
     ap.add_argument("--batch", type=int, default=1, help="independent problems per step (tikh_solve_batched)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
+    ap.add_argument("--prod-direct-max", type=int, default=0, help="direct products up to this P (0: automatic)")
+    ap.add_argument("--eval-direct-max", type=int, default=0, help="direct evaluations up to this size (0: automatic)")
     ap.add_argument("--graph", type=int, default=1, help="1 (default): replay each solve as one captured CUDA graph; 0: stream launches")
     args = ap.parse_args()
     world, rank, local = dist_setup()
@@ -194,7 +196,7 @@ def main():
     x = xb[0]
     stream = torch.cuda.Stream(device=dev)
     plan = tikh.Plan(m, n, "c128", n_lim=args.n_lim, refine_steps=args.refine, batch=B, graph=bool(args.graph),
-                     stream=stream)
+                     prod_direct_max=args.prod_direct_max, eval_direct_max=args.eval_direct_max, stream=stream)
 
     def step(sync=True):
         if B == 1:
@@ -321,6 +323,7 @@ def main():
                           "N": st["N"], "p": st["p"], "M": st["M"], "n_lim": args.n_lim,
                           "refine_steps": args.refine, "precision": "fp64", "batch": B,
                           "cuda_graph": bool(st["graph"]),
+                          "prod_direct_max": args.prod_direct_max or "auto", "eval_direct_max": args.eval_direct_max or "auto",
                           "l2": "256 MB flush between steps; working set > L2"},
                "n_solves_per_s": value * n,
                "solves_per_s_per_problem_stream": value / B,

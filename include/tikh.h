@@ -67,6 +67,12 @@ typedef struct tikh_plan_s* tikh_plan;
  *            kernel of every recursion node) into one CUDA graph on the first call and replay it while
  *            the pointer and stride arguments stay the same (lambda may change); 0 (default): stream
  *            launches.  Not used with profiling on.
+ *  prod_direct_max  step-4 products (Alg. 1) of planned length P <= this are computed directly
+ *            (schoolbook, one warp per output coefficient), longer ones by FFT; 0 (default): automatic
+ *            (360 for batch = 1, where a small node is latency-bound; smaller for batches, where the
+ *            O(P^2) direct product is FP64-throughput-bound).  0..4096.
+ *  eval_direct_max  step-2 evaluations of B_L at <= this many nodes per coset are computed directly
+ *            (chunked Horner), larger ones by FFT; 0 (default): automatic (80 for batch = 1).  0..4096.
  */
 typedef struct {
   int n_lim;
@@ -77,6 +83,8 @@ typedef struct {
   int refine_steps;
   int batch;
   int graph;
+  int prod_direct_max;
+  int eval_direct_max;
 } tikh_opts;
 
 typedef struct {

@@ -133,7 +133,10 @@ void build_steps(Plan& P, int depth, int64_t a, int64_t s, int64_t L, int side, 
   int D = -1;
   for (int i = 0; i < 5; ++i)
     for (int j = 0; j < 5; ++j) D = std::max(D, entry_bound_host(din, sd, i, j));
-  int64_t Pn = smooth_at_least((int64_t)D + 1 + slack);
+  // the product of the bases of 4L conditions has degree <= 4L whatever the tau-degree bound and the
+  // slack say, and each child's stored entries are at most 2L + 1 long (they are trimmed to the same
+  // kind of bound), which the transform must hold
+  int64_t Pn = smooth_at_least(std::max<int64_t>(2 * L + 1, std::min<int64_t>((int64_t)D + 1 + slack, 4 * L + 1)));
   Step pr{STEP_PROD, depth, side, a, s, L, fft_index(P, Pn, err), Pn, 0};
   P.sched.push_back(pr);
   P.Pmax = std::max(P.Pmax, Pn);
@@ -446,11 +449,12 @@ int tikh_plan_create(tikh_plan* out, int64_t m, int64_t n, int dtype, int prec, 
   if (!out) return TIKH_EINVAL;
   *out = nullptr;
   if (m < 1 || n < 1 || (dtype != TIKH_R64 && dtype != TIKH_C128) || prec != TIKH_PREC_FP64) return TIKH_EINVAL;
-  tikh_opts o{32, 0, 0, 1e-8, 4096, 0, 1, 0};
+  tikh_opts o{32, 0, 0, 1e-8, 4096, 0, 1, 0, 0, 0};
   if (opts) o = *opts;
   if (o.n_lim < 4 || o.n_lim > 64 || o.m_min < 0 || o.m_min > 32 || (o.fill != 0 && o.fill != 1) ||
       !(o.eps_diff >= 0.0) || o.max_difficult < 1 || o.max_difficult > (1 << 20) || o.refine_steps < 0 ||
-      o.refine_steps > 8 || o.batch < 1 || o.batch > 65535 || (o.graph != 0 && o.graph != 1))
+      o.refine_steps > 8 || o.batch < 1 || o.batch > 65535 || (o.graph != 0 && o.graph != 1) ||
+      o.prod_direct_max < 0 || o.prod_direct_max > 4096 || o.eval_direct_max < 0 || o.eval_direct_max > 4096)
     return TIKH_EINVAL;
   tikh_plan h = new (std::nothrow) tikh_plan_s;
   if (!h) return TIKH_ENOMEM;
@@ -460,6 +464,11 @@ int tikh_plan_create(tikh_plan* out, int64_t m, int64_t n, int dtype, int prec, 
   P.dtype = dtype;
   P.opts = o;
   P.batch_max = o.batch;
+  // direct vs FFT forms of steps 2 and 4: a single problem is latency-bound at small nodes (direct forms
+  // spread over more SMs with short chains); a batch is FP64-throughput-bound, where the O(P^2) direct
+  // product loses to the O(P log P) FFT product at much smaller P (measured on GB300)
+  P.prod_direct_max = o.prod_direct_max > 0 ? o.prod_direct_max : (o.batch == 1 ? 360 : BATCH_PROD_DIRECT_MAX);
+  P.eval_direct_max = o.eval_direct_max > 0 ? o.eval_direct_max : (o.batch == 1 ? 80 : BATCH_EVAL_DIRECT_MAX);
   P.stream = (cudaStream_t)stream;
   P.dual = m < n ? 1 : 0;
   P.cm = P.dual ? n : m;
@@ -493,6 +502,7 @@ int tikh_plan_create(tikh_plan* out, int64_t m, int64_t n, int dtype, int prec, 
   P.ndiff = (int*)dalloc(P, sizeof(int) * 4 * nb, err);
   P.diff = (int64_t*)dalloc(P, sizeof(int64_t) * (size_t)o.max_difficult * nb, err);
   P.diffr = (cd*)dalloc(P, sizeof(cd) * 5 * (size_t)o.max_difficult * nb, err);
+  P.dvals = (cd*)dalloc(P, sizeof(cd) * 25 * (size_t)o.max_difficult * nb, err);
   P.peak = (unsigned long long*)dalloc(P, sizeof(unsigned long long) * nb, err);
   P.lam = (double*)dalloc(P, sizeof(double) * nb, err);
   if (!err) err = make_schedule(P);

@@ -34,6 +34,9 @@ struct BasisBuf {
 // DFS schedule of Algorithm 1: a node (a, s, L) at `depth` has nodes omega^{a + c + s j}, c in {0,1},
 // j < L (s L = N) and 4L conditions.
 enum StepKind { STEP_LEAF = 0, STEP_EVAL = 1, STEP_PROD = 2 };
+constexpr int BATCH_PROD_DIRECT_MAX = 36;  // automatic thresholds for plans with batch > 1 (measured)
+constexpr int BATCH_EVAL_DIRECT_MAX = 10;
+
 struct Step {
   int kind;
   int depth;
@@ -66,7 +69,7 @@ struct Plan {
   int batch_max = 1;
   int nb = 1;          // problems in the current call
   int slack_mult = 1;  // degree-prediction slack multiplier (raised after TIKH_EDEGREE)
-  int64_t eval_direct_max = 80;  // step 2 by direct evaluation when the right child has <= this many nodes per coset
+  int64_t eval_direct_max = 80;   // step 2 by direct evaluation when the right child has <= this many nodes per coset
   int64_t prod_direct_max = 360;  // step 4 by schoolbook products when the planned length P <= this
 
   std::vector<Step> sched;
@@ -91,6 +94,7 @@ struct Plan {
   int* ndiff = nullptr;   // [nb][4]
   int64_t* diff = nullptr;  // [nb][max_difficult] condition ids 2e + f
   cd* diffr = nullptr;      // [nb][max_difficult][5] residuals
+  cd* dvals = nullptr;      // [nb][max_difficult][25] B*(sigma) of the deferred conditions
   BasisBuf buf[MAX_DEPTH][2];
   cd* evalv = nullptr;  // [nb][50][Lrmax]
   cd* etmp = nullptr;   // [nb][50][Lrmax] (four-step temp)

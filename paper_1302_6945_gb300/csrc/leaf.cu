@@ -515,46 +515,56 @@ int launch_leaf_arrays(int K, const cd* sigma, const cd* r, int* delta, double e
 // difficult points (Sec. 4.4): residual against the final basis B*, then serial processing.
 // ------------------------------------------------------------------------------------------------
 
-// r_q = Phi_q B*(sigma_q) for every deferred condition (B* with its column scales applied);
-// grid (blocks, problems)
-__global__ void k_diff_eval(BasisBuf B, const cd* __restrict__ Phi, const cd* __restrict__ wN, int64_t N,
-                            const int* ndiff, const int64_t* diff, int maxdiff, cd* diffr) {
-  __shared__ cd red[32];
-  __shared__ cd vals[25];
-  const int pb = blockIdx.y;
+// B*(sigma_q) for every deferred condition q (column scales applied): block (entry E, slot, problem),
+// threads over the coefficients with the twiddle index advanced incrementally, a block reduction per q
+__global__ void __launch_bounds__(256) k_diff_values(BasisBuf B, const cd* __restrict__ wN, int64_t N,
+                                                     const int* ndiff, const int64_t* diff, int maxdiff, cd* vals) {
+  __shared__ cd red[8];
+  const int E = blockIdx.x, pb = blockIdx.z, tid = threadIdx.x;
   const int nd = min(ndiff[4 * pb], maxdiff);
-  const cd* bc = B.cp(pb);
-  const int* bl = B.lp(pb);
-  for (int q = blockIdx.x; q < nd; q += gridDim.x) {
-    int64_t id = diff[(int64_t)pb * maxdiff + q], e = id / 2, f = id % 2;
-    for (int E = 0; E < 25; ++E) {
-      cd acc = mkc(0.0, 0.0);
-      int64_t L = bl[E];
-      for (int64_t t = threadIdx.x; t < L; t += blockDim.x) acc = cfma(bc[E * B.cap + t], tw_at(wN, (e * t) % N), acc);
-      for (int o = 16; o > 0; o >>= 1) {
-        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
-      }
-      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        cd sum = mkc(0.0, 0.0);
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum = cadd(sum, red[w]);
-        vals[E] = cscale(sum, col_scale_from_bits(B.mp(pb)[E % 5]));
-      }
-      __syncthreads();
+  const cd* bc = B.cp(pb) + (int64_t)E * B.cap;
+  const int64_t L = B.lp(pb)[E];
+  const double scl = col_scale_from_bits(B.mp(pb)[E % 5]);
+  for (int q = blockIdx.y; q < nd; q += gridDim.y) {
+    const int64_t e = diff[(int64_t)pb * maxdiff + q] / 2;
+    int64_t ix = (e * (int64_t)tid) % N;
+    const int64_t stp = (e * (int64_t)blockDim.x) % N;
+    cd acc = mkc(0.0, 0.0);
+    for (int64_t t = tid; t < L; t += blockDim.x) {
+      acc = cfma(bc[t], tw_at(wN, ix), acc);
+      ix += stp;
+      if (ix >= N) ix -= N;
     }
-    if (threadIdx.x < 5) {
-      int j = threadIdx.x;
-      cd acc = mkc(0.0, 0.0);
-      for (int i = 0; i < 5; ++i) acc = cfma(Phi[((int64_t)pb * N + e) * 10 + f * 5 + i], vals[i * 5 + j], acc);
-      diffr[((int64_t)pb * maxdiff + q) * 5 + j] = acc;
+    for (int o = 16; o > 0; o >>= 1) {
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+    }
+    if ((tid & 31) == 0) red[tid >> 5] = acc;
+    __syncthreads();
+    if (tid == 0) {
+      cd sum = red[0];
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) sum = cadd(sum, red[w]);
+      vals[((int64_t)pb * maxdiff + q) * 25 + E] = cscale(sum, scl);
     }
     __syncthreads();
   }
 }
 
-// serial processing of the deferred conditions against B* (one CTA per problem; no further deferral)
+// r_q = Phi_q B*(sigma_q): thread per (deferred condition, column)
+__global__ void k_diff_rows(const cd* __restrict__ Phi, int64_t N, const int* ndiff, const int64_t* diff, int maxdiff,
+                            const cd* __restrict__ vals, cd* diffr) {
+  const int pb = blockIdx.y;
+  const int nd = min(ndiff[4 * pb], maxdiff);
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < 5 * nd; idx += gridDim.x * blockDim.x) {
+    const int q = idx / 5, j = idx % 5;
+    const int64_t id = diff[(int64_t)pb * maxdiff + q], e = id / 2, f = id % 2;
+    const cd* v = vals + ((int64_t)pb * maxdiff + q) * 25;
+    cd acc = mkc(0.0, 0.0);
+    for (int i = 0; i < 5; ++i) acc = cfma(Phi[((int64_t)pb * N + e) * 10 + f * 5 + i], v[i * 5 + j], acc);
+    diffr[((int64_t)pb * maxdiff + q) * 5 + j] = acc;
+  }
+}
+
 __global__ void __launch_bounds__(1024) k_diff_serial(BasisBuf B, const cd* __restrict__ wN, const int* ndiff,
                                                      const int64_t* diff, int maxdiff, cd* diffr, int* delta,
                                                      int* status, cd* scratch, int64_t scr_stride) {
@@ -669,12 +679,14 @@ __global__ void __launch_bounds__(1024) k_diff_serial(BasisBuf B, const cd* __re
 }
 
 int launch_difficult(Plan& P) {
-  int grid = std::min(P.opts.max_difficult, 64);
-  k_diff_eval<<<dim3(grid, P.nb), 256, 0, P.stream>>>(P.buf[0][0], P.Phi, P.wN, P.N, P.ndiff, P.diff,
-                                                      P.opts.max_difficult, P.diffr);
+  const int slots = std::min(P.opts.max_difficult, 64);
+  k_diff_values<<<dim3(25, slots, P.nb), 256, 0, P.stream>>>(P.buf[0][0], P.wN, P.N, P.ndiff, P.diff,
+                                                             P.opts.max_difficult, P.dvals);
+  k_diff_rows<<<dim3((unsigned)std::min(64, (5 * P.opts.max_difficult + 255) / 256), P.nb), 256, 0, P.stream>>>(
+      P.Phi, P.N, P.ndiff, P.diff, P.opts.max_difficult, P.dvals, P.diffr);
   k_diff_serial<<<P.nb, 1024, 0, P.stream>>>(P.buf[0][0], P.wN, P.ndiff, P.diff, P.opts.max_difficult, P.diffr,
                                              P.delta, P.status, P.dscr, P.dscr_stride);
-  return cudaGetLastError() == cudaSuccess ? 2 : TIKH_ECUDA;
+  return cudaGetLastError() == cudaSuccess ? 3 : TIKH_ECUDA;
 }
 
 }  // namespace tikh

@@ -158,6 +158,17 @@ int launch_eval(Plan& P, const Step& st) {
 // ------------------------------------------------------------------------------------------------
 // step 4
 // ------------------------------------------------------------------------------------------------
+// length bound of entry (i, j) of B_L B_R from the operands' lengths: max_u len(a_iu) + len(b_uj) - 1 (the
+// tau-degree bound can be far looser when the extension k is large)
+__device__ __forceinline__ int prod_len_bound(const BasisBuf& BL, const BasisBuf& BR, int pb, int i, int j) {
+  int L = 0;
+  for (int u = 0; u < 5; ++u) {
+    const int la = BL.lp(pb)[i * 5 + u], lb = BR.lp(pb)[u * 5 + j];
+    if (la > 0 && lb > 0) L = max(L, la + lb - 1);
+  }
+  return L;
+}
+
 struct LoadPad {  // transform t = 50 pb + b; b < 25: B_L entry b; b >= 25: B_R entry b - 25; zero-padded to P
   BasisBuf BL, BR, OUT;
   const int* dstack;  // + pb * MAX_DEPTH * 5 + depth * 5: delta_in of the node
@@ -168,13 +179,13 @@ struct LoadPad {  // transform t = 50 pb + b; b < 25: B_L entry b; b >= 25: B_R 
   __device__ cd operator()(int t, int64_t q) const {
     int pb = t / 50, b = t % 50;
     if (b == 0 && q == 0) {
-      // guard: the transform length must exceed every entry degree of the product
+      // guard: the transform length must exceed every entry degree of the product (no wrap-around)
       const int* din = dstack + (pb * MAX_DEPTH + depth) * 5;
       const int* dout = delta + 8 * pb;
       int D = -1;
       for (int i = 0; i < 5; ++i)
-        for (int j = 0; j < 5; ++j) D = max(D, entry_bound_dev(din, dout, i, j));
-      for (int E = 0; E < 25; ++E) D = max(D, max(BL.lp(pb)[E], BR.lp(pb)[E]) - 1);
+        for (int j = 0; j < 5; ++j) D = max(D, min(entry_bound_dev(din, dout, i, j), prod_len_bound(BL, BR, pb, i, j) - 1));
+      for (int E = 0; E < 25; ++E) D = max(D, max(BL.lp(pb)[E], BR.lp(pb)[E]) - 1);  // operands fit the transform
       if (D >= P) set_status(status, ST_DEGREE);
       for (int j = 0; j < 5; ++j) OUT.mp(pb)[j] = 0ULL;
     }
@@ -215,14 +226,15 @@ struct LoadProduct {  // transform t = 25 pb + 5i + j: sum_u FA[5i+u] FB[5u+j]
 };
 
 // trim to the degree bounds, scale by 1/P, record column maxima and lengths
-__global__ void k_prod_finish(const cd* __restrict__ FC, int64_t P, BasisBuf OUT, const int* dstack, int depth,
-                              const int* delta, int* status) {
+__global__ void k_prod_finish(const cd* __restrict__ FC, int64_t P, BasisBuf BL, BasisBuf BR, BasisBuf OUT,
+                              const int* dstack, int depth, const int* delta, int* status) {
   const int E = blockIdx.y, i = E / 5, j = E % 5, pb = blockIdx.z;
   __shared__ int want_s;
   __shared__ double red[32];
   if (threadIdx.x == 0) {
     int bnd = entry_bound_dev(dstack + (pb * MAX_DEPTH + depth) * 5, delta + 8 * pb, i, j);
     int64_t want = bnd < 0 ? 0 : (int64_t)bnd + 1;
+    want = min(want, (int64_t)prod_len_bound(BL, BR, pb, i, j));
     if (want > P) want = P;
     if (want > OUT.cap) { set_status(status, ST_DEGREE); want = OUT.cap; }
     want_s = (int)want;
@@ -269,6 +281,7 @@ __global__ void __launch_bounds__(32 * PD_TC) k_prod_direct(BasisBuf BL, BasisBu
   if (tid == 0) {
     int bnd = entry_bound_dev(dstack + (pb * MAX_DEPTH + depth) * 5, delta + 8 * pb, i, j);
     int want = bnd < 0 ? 0 : bnd + 1;
+    want = min(want, prod_len_bound(BL, BR, pb, i, j));
     if (want > OUT.cap) { set_status(status, ST_DEGREE); want = (int)OUT.cap; }
     want_s = want;
     if (tile == 0) OUT.lp(pb)[E] = want;
@@ -349,7 +362,8 @@ int launch_prod(Plan& P, const Step& st) {
     return TIKH_ECUDA;
   nl += r;
   int bx = (int)std::min<int64_t>((st.P + 255) / 256, 64);
-  k_prod_finish<<<dim3(bx, 25, P.nb), 256, 0, P.stream>>>(P.FC, st.P, OUT, P.dstack, st.depth, P.delta, P.status);
+  k_prod_finish<<<dim3(bx, 25, P.nb), 256, 0, P.stream>>>(P.FC, st.P, BL, BR, OUT, P.dstack, st.depth, P.delta,
+                                                          P.status);
   if (cudaGetLastError() != cudaSuccess) return TIKH_ECUDA;
   return nl + 1;
 }

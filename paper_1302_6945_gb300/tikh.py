@@ -21,7 +21,8 @@ TIKH_PREC_FP64 = 0
 class tikh_opts(ctypes.Structure):
     _fields_ = [("n_lim", ctypes.c_int), ("m_min", ctypes.c_int), ("fill", ctypes.c_int),
                 ("eps_diff", ctypes.c_double), ("max_difficult", ctypes.c_int), ("refine_steps", ctypes.c_int),
-                ("batch", ctypes.c_int), ("graph", ctypes.c_int)]
+                ("batch", ctypes.c_int), ("graph", ctypes.c_int),
+                ("prod_direct_max", ctypes.c_int), ("eval_direct_max", ctypes.c_int)]
 
 
 class tikh_stats(ctypes.Structure):
@@ -210,13 +211,14 @@ class Plan:
     """A solver plan for m x n Toeplitz problems of one dtype ('r64' or 'c128')."""
 
     def __init__(self, m, n, dtype="r64", n_lim=32, m_min=0, fill=0, eps_diff=1e-8, max_difficult=4096,
-                 refine_steps=0, batch=1, graph=False, stream=None):
+                 refine_steps=0, batch=1, graph=False, prod_direct_max=0, eval_direct_max=0, stream=None):
         import torch
         self.m, self.n = int(m), int(n)
         self.dtype = TIKH_C128 if dtype in ("c128", TIKH_C128, torch.complex128) else TIKH_R64
         self.batch = int(batch)
         self.opts = tikh_opts(int(n_lim), int(m_min), int(fill), float(eps_diff), int(max_difficult),
-                              int(refine_steps), self.batch, 1 if graph else 0)
+                              int(refine_steps), self.batch, 1 if graph else 0, int(prod_direct_max),
+                              int(eval_direct_max))
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
@@ -367,3 +369,74 @@ def solve(col, row, b, lam, **kw):
         return p.solve(col, row, b, lam)
     finally:
         p.close()
+
+
+# ---- tuning ----------------------------------------------------------------------------------------
+
+TUNE_SPACE = {
+    "n_lim": (24, 32, 40),
+    "prod_direct_max": (36, 72, 192, 360),
+    "eval_direct_max": (10, 20, 40, 80),
+}
+
+
+def coordinate_search(time_fn, start, space=None):
+    """Minimise time_fn(opts) one key at a time (n_lim, then the product and evaluation thresholds),
+    keeping the best value of each key before moving to the next.  Returns (best opts, {opts: time})."""
+    space = space or TUNE_SPACE
+    best = dict(start)
+    seen = {}
+
+    def t(o):
+        k = tuple(sorted(o.items()))
+        if k not in seen:
+            seen[k] = float(time_fn(dict(o)))
+        return seen[k]
+
+    best_t = t(best)
+    for key in ("n_lim", "prod_direct_max", "eval_direct_max"):
+        for v in space[key]:
+            cand = dict(best)
+            cand[key] = v
+            ct = t(cand)
+            if ct < best_t:
+                best, best_t = cand, ct
+    return best, {k: v for k, v in seen.items()}
+
+
+def autotune(m, n, dtype="c128", batch=1, refine_steps=0, reps=2, seed=0, time_fn=None):
+    """Pick N_lim and the direct/FFT thresholds of steps 2 and 4 for m x n problems solved `batch` at a
+    time: each candidate plan solves a seeded random Toeplitz problem of that shape (generated on the
+    device), timed with CUDA events on the plan's stream after one warm-up solve, best of `reps`.
+    Returns (Plan keyword arguments, {candidate: seconds}).  time_fn replaces the timing (for tests)."""
+    import torch
+    if time_fn is None:
+        g = torch.Generator(device="cuda").manual_seed(int(seed))
+        tdt = torch.complex128 if dtype in ("c128", TIKH_C128) else torch.float64
+        B = int(batch)
+        col = torch.randn((B, m), generator=g, device="cuda", dtype=tdt)
+        row = torch.randn((B, n), generator=g, device="cuda", dtype=tdt)
+        b = torch.randn((B, m), generator=g, device="cuda", dtype=tdt)
+        lams = [1e-2] * B
+        stream = torch.cuda.Stream()
+
+        def time_fn(o):
+            with torch.cuda.stream(stream):
+                p = Plan(m, n, dtype, refine_steps=refine_steps, batch=B, graph=True, stream=stream, **o)
+                try:
+                    x = torch.empty((B, n), dtype=tdt, device="cuda")
+                    p.solve_batched(col, row, b, lams, x)
+                    best = float("inf")
+                    for _ in range(max(1, int(reps))):
+                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                        p.solve_batched(col, row, b, lams, x)
+                        e1.record(stream)
+                        e1.synchronize()
+                        best = min(best, e0.elapsed_time(e1) * 1e-3)
+                    return best
+                finally:
+                    p.close()
+
+    start = {"n_lim": 32, "prod_direct_max": 0, "eval_direct_max": 0}
+    return coordinate_search(time_fn, start)

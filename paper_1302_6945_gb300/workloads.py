@@ -95,6 +95,12 @@ def config_c4(seed=3, m=1572864, n=1048576):
     return deconvolution_problem(m, n, 12.0, 48, 1e-7, 1e-7, 1e-5, seed)
 
 
+def config_c5(seed=4, m=327680, n=262144):
+    """real, m = 327680, n = 262144, PSF sigma 8, lam 1e-3 (the differentiation configuration; the loss
+    is ||x - x_true||^2)."""
+    return deconvolution_problem(m, n, 8.0, 32, 1e-6, 1e-6, 1e-3, seed)
+
+
 def sweep_problem(n, seed=5):
     """metric sweep point: n = 2^e, m = 1.5 n, PSF sigma 8, real."""
     return deconvolution_problem(int(1.5 * n), n, 8.0, 32, 1e-6, 1e-6, 1e-4, seed)

@@ -29,3 +29,4 @@ def test_strerror_and_invalid_plan_without_gpu():
     assert tikh.tikh_strerror(tikh.TIKH_EINVAL) == "invalid argument"
     with pytest.raises(tikh.TikhError):
         tikh.tikh_plan_create(0, 4)
+
