@@ -117,6 +117,27 @@ def dist_setup():
     return world, rank, local
 
 
+def rank_seed_offsets(rank, batch):
+    """Weak scaling: rank r solves the problems with seed offsets r B .. r B + B - 1 (disjoint ranks)."""
+    return [rank * batch + i for i in range(batch)]
+
+
+def max_over_ranks(v, device=None):
+    """The largest v over all ranks, returned on every rank (v itself without a process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(v)
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, units_per_rank, t_max_s):
+    """Units all ranks processed divided by the slowest rank's time."""
+    return world * units_per_rank / t_max_s
+
+
 def workload(seed_offset=0, n=None):
     """c2: m = 98304, n = 65536; with n given, the same recipe at m = 1.5 n (the metric's n sweep)."""
     from paper_1302_6945_gb300 import workloads as W
@@ -184,7 +205,7 @@ def main():
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
     B = max(1, args.batch)
-    probs = [workload(seed_offset=rank * B + i, n=args.n) for i in range(B)]
+    probs = [workload(seed_offset=o, n=args.n) for o in rank_seed_offsets(rank, B)]
     P = probs[0]
     m, n = P["m"], P["n"]
     col = torch.tensor(np.stack([q["col"] for q in probs]), dtype=torch.complex128, device=dev)
@@ -266,13 +287,10 @@ def main():
     breakdown = {k: {"ms_per_step": pst["prof_kind_ms"][i] / args.steps,
                      "groups_per_step": pst["prof_kind_count"][i] / args.steps} for i, k in enumerate(kinds)}
     t_step = sum(step_ms) / len(step_ms)
-    t_max = t_step
+    t_max = max_over_ranks(t_step, dev)
     if world > 1:
-        tt = torch.tensor([t_step], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
         dist.barrier()
-    value = world * B / (t_max / 1e3)
+    value = whole_job_rate(world, B, t_max / 1e3)
 
     # e2e through the host-buffer entry point (pinned host arrays, copies inside the region)
     hcol = torch.tensor(P["col"], dtype=torch.complex128).pin_memory().numpy()
@@ -288,9 +306,7 @@ def main():
         e2e_t = (time.perf_counter() - t0) / args.steps
     e2e_v = 1.0 / e2e_t  # host-buffer path solves one problem per call
     if world > 1 and not args.no_e2e:
-        tt = torch.tensor([e2e_t], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_v = world / float(tt.item())
+        e2e_v = whole_job_rate(world, 1, max_over_ranks(e2e_t, dev))
 
     pk, pk_kind = peaks()
     K_leaf = 2 * int(st["M"])
