@@ -41,6 +41,8 @@ def leaf_model_flops(K):
 # dram__bytes_read.sum + dram__bytes_write.sum of one leaf launch (K = 20) from an ncu capture of the
 # current kernel (profiles/k_leaf_c2recipe_n4096.md); None whenever the kernel changes until recaptured
 LEAF_TRAFFIC_BYTES = 45056
+# sm__inst_executed_pipe_fp64 (fraction of the SM's peak while the leaf runs) from the same capture
+LEAF_FP64_PIPE_ACTIVE = 0.376
 
 
 def model_bytes_per_solve(N, p):
@@ -317,6 +319,9 @@ def main():
                 "achieved": leaf_gflops, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
                 "frac": leaf_gflops / FP64_PEAK_GFLOPS, "peak_kind": "derived from unit counts and max clock",
                 "traffic": LEAF_TRAFFIC_BYTES, "avg_launch_ms": leaf_ms,
+                # a leaf is one CTA: a single solve can use one SM's FP64 units at most
+                "peak_one_sm": FP64_PEAK_GFLOPS / 152, "frac_of_one_sm": leaf_gflops / B / (FP64_PEAK_GFLOPS / 152),
+                "fp64_pipe_active_ncu": LEAF_FP64_PIPE_ACTIVE,
                 "launches_per_step": leaf_launches / args.steps,
                 "share_of_step": (pst["prof_leaf_ms"] / args.steps) / t_step,
                 "flops_per_launch": leaf_model_flops(K_leaf) * B}
