@@ -122,7 +122,10 @@ int tikh_plan_create(tikh_plan* out, int64_t m, int64_t n, int dtype, int prec, 
 /* Tikhonov solution x (n entries) from device arrays col (m), row (n), b (m).  Enqueues the whole
  * path (Sec. 3-5: extension, DFT transformation, recursive basis construction, difficult points,
  * extraction x(z) = B*_1^{(j)}(z) / B*_5^{(j)}) and then synchronises the stream to report the
- * device status.  Returns TIKH_ENUMERIC / TIKH_EDIFFICULT when the device reported a failure. */
+ * device status.  A basis longer than its planned transform (TIKH_EDEGREE) re-plans with 16x the
+ * degree slack and re-runs, up to three times (tikh_stats.retries).  Returns TIKH_EINVAL for a NULL
+ * pointer or an invalid lambda, TIKH_ENUMERIC / TIKH_EDIFFICULT / TIKH_ETIMEOUT when the device
+ * reported a failure, TIKH_ECUDA when a launch failed.  With opts.graph the call replays its graph. */
 int tikh_solve(tikh_plan plan, const void* col, const void* row, const void* b, double lambda, void* x);
 
 /* As tikh_solve, without the final synchronisation: the status of this solve is returned by the
@@ -160,10 +163,12 @@ int tikh_solve_batched(tikh_plan plan, int batch, const void* col, int64_t col_s
 int tikh_solve_host(tikh_plan plan, const void* col, const void* row, const void* b, double lambda, void* x);
 
 /* Wait for the plan's stream and return (then clear) the device status of the solves since the last
- * synchronising call. */
+ * synchronising call: TIKH_OK, TIKH_ENUMERIC, TIKH_EDIFFICULT, TIKH_ETIMEOUT, TIKH_EDEGREE (not retried
+ * here) or TIKH_ECUDA. */
 int tikh_sync(tikh_plan plan);
 
-/* Statistics of the plan and of the last synchronised solve. */
+/* Statistics of the plan and of the last synchronised solve (*out is overwritten).  TIKH_EINVAL for a
+ * NULL plan or out. */
 int tikh_get_stats(tikh_plan plan, tikh_stats* out);
 
 /* Profiling switch: flags bit 0 records a CUDA event pair around every leaf launch (Eq. (spbasis)
