@@ -137,8 +137,9 @@ def leaf(sigma, r, delta, eps=1e-8, cap=None):
 
 
 def solve_normal(col, row, y, lam, nlim=32, eps_diff=1e-8, mode=AUTO, m_min=0, want_basis=False, fill=0,
-                 is_complex=None):
-    """x = (T^H T + lam I)^{-1} y by the superfast algorithm.  Returns (x, stats[, B, len])."""
+                 is_complex=None, want_deferred=False):
+    """x = (T^H T + lam I)^{-1} y by the superfast algorithm.  Returns (x, stats[, B, len]); with
+    want_deferred, stats["deferred"] lists the ids 2e + f of the conditions deferred as difficult."""
     if is_complex is None:
         is_complex = _is_complex(col, row)
     col, row, y = _c128(col), _c128(row), _c128(y)
@@ -153,13 +154,19 @@ def solve_normal(col, row, y, lam, nlim=32, eps_diff=1e-8, mode=AUTO, m_min=0, w
         bp, lp = _ptr(B), _ptr(ln)
     else:
         cap, B, ln, bp, lp = 0, None, None, None, None
-    rc = _lib().tikh_oracle_solve_normal(ctypes.c_int64(m), ctypes.c_int64(n), _ptr(col), _ptr(row), _ptr(y),
-                                         ctypes.c_double(lam), ctypes.byref(o), _ptr(x), ctypes.byref(st), bp,
-                                         ctypes.c_int64(cap), lp)
+    dcap = 2 * plan(m, n, nlim, m_min)[0] if want_deferred else 0
+    dq = np.zeros(max(dcap, 1), np.int64)
+    rc = _lib().tikh_oracle_solve_normal_ex(ctypes.c_int64(m), ctypes.c_int64(n), _ptr(col), _ptr(row), _ptr(y),
+                                            ctypes.c_double(lam), ctypes.byref(o), _ptr(x), ctypes.byref(st), bp,
+                                            ctypes.c_int64(cap), lp, _ptr(dq) if want_deferred else None,
+                                            ctypes.c_int64(dcap))
     _check(rc, "solve_normal")
+    sd = st.as_dict()
+    if want_deferred:
+        sd["deferred"] = [int(v) for v in dq[:min(sd["n_difficult"], dcap)]]
     if want_basis:
-        return x, st.as_dict(), B, ln
-    return x, st.as_dict()
+        return x, sd, B, ln
+    return x, sd
 
 
 def solve(col, row, b, lam, nlim=32, eps_diff=1e-8, mode=AUTO, m_min=0, fill=0, is_complex=None):

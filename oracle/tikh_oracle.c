@@ -16,14 +16,14 @@
  *     tau = [n-1, m-1, m+k-2, n+k-2, 0] (Eq. (taudef) is printed for k = 1, p = 7).
  *  R4 Algorithm 1 carries the absolute tau-degrees delta: the left child starts from delta_in,
  *     the right child from the left child's output (Theorem 1 with tau_{kappa->K} = -delta).
- *  R5 the k arbitrary entries (Sec. 5.2, "similar in value") are pseudo-random with the size of
+ *  R5 the k arbitrary entries (Sec. 6.2, "similar in value") are pseudo-random with the size of
  *     the known coefficients: a = peak * u, peak = max over known d of max(|Re a_d|, |Im a_d|),
  *     u uniform in [-1, 1) from the SplitMix64 generator (Steele, Lea, Flood 2014) used as a
  *     counter-based hash of the entry index (real u for real data, u + i u' for complex).  Zero-like
  *     fills (including a linear ramp between two near-zero PSF tails) lose accuracy for large k.
  *     The T^H extension uses the same periodic sequence.  fill = 1 selects the linear ramp.
  *  R6 Algorithm 2 for two condition sets with paired interleaving: halve M while 2M > N_lim,
- *     then round M up to even (Sec. 5.2) and further to a 7-smooth number (FFT lengths with
+ *     then round M up to even (Sec. 6.2) and further to a 7-smooth number (FFT lengths with
  *     factors 2, 3, 5, 7 only; the solution does not depend on k).
  *  R7 difficult point: the best remaining condition of a leaf has |r_pi| < eps ||r||_2; it and
  *     the rest of the leaf are deferred and processed serially against the final basis.
@@ -36,7 +36,7 @@
  *     by (largest delta_out of a pivoted column) - delta_in_i (diagonal: >= 0).  Products are
  *     trimmed to these bounds (what is cut is round-off).
  *  R11 m < n is solved as x = T^H (T T^H + lam I)^{-1} b with the same algorithm on T^H, whose
- *     right-hand-side term is b itself (Sec. 6.1 solves (G_T + G_L) x = y with y given).
+ *     right-hand-side term is b itself (Sec. 7.1 solves (G_T + G_L) x = y with y given).
  */
 #include "tikh_oracle.h"
 
@@ -455,7 +455,7 @@ static void scale_columns(pmat* B) {
 }
 
 /* ------------------------------------------------------------------------------------------ */
-/* The recursion (Algorithm 1 with paired interleaving, Sec. 5.1).                             */
+/* The recursion (Algorithm 1 with paired interleaving, Sec. 6.1).                             */
 /* A node is (a, s, L): its nodes are omega^{a + c + s j}, c in {0,1}, j < L; s L = N.         */
 /* Its conditions, in list order, are position 4j + 2c + f (f = 0: F, f = 1: G).              */
 /* ------------------------------------------------------------------------------------------ */
@@ -657,6 +657,13 @@ int tikh_oracle_conditions(int64_t m, int64_t n, const double* col, const double
 int tikh_oracle_solve_normal(int64_t m, int64_t n, const double* col, const double* row, const double* y,
                              double lam, const tikh_oracle_opts* opts, double* x, tikh_oracle_stats* stats,
                              double* Bout, int64_t cap, int64_t* lenout) {
+  return tikh_oracle_solve_normal_ex(m, n, col, row, y, lam, opts, x, stats, Bout, cap, lenout, NULL, 0);
+}
+
+int tikh_oracle_solve_normal_ex(int64_t m, int64_t n, const double* col, const double* row, const double* y,
+                                double lam, const tikh_oracle_opts* opts, double* x, tikh_oracle_stats* stats,
+                                double* Bout, int64_t cap, int64_t* lenout, int64_t* deferred_out,
+                                int64_t deferred_cap) {
   int64_t N, M, k;
   int p;
   int rc = tikh_oracle_plan(m, n, opts, &N, &M, &k, &p);
@@ -685,8 +692,10 @@ int tikh_oracle_solve_normal(int64_t m, int64_t n, const double* col, const doub
   int delta[5] = {-(int)(n - 1), -(int)(m - 1), -(int)(m + k - 2), -(int)(n + k - 2), 0};
   /* root node: all N nodes = omega^{0 + c + 2 j}, j < N/2 */
   if ((rc = rec_tanint(&st, 0, 2, N / 2, delta, &B))) goto done;
+  if (deferred_out)
+    for (int64_t q = 0; q < st.n_def && q < deferred_cap; ++q) deferred_out[q] = st.deferred[q];
   if (st.n_def > 0) {
-    /* difficult points (Sec. 4 end): residual against the final basis, then serial processing */
+    /* difficult points (Sec. 5): residual against the final basis, then serial processing */
     int K = (int)st.n_def;
     cx* sig = (cx*)malloc(sizeof(cx) * (size_t)K);
     cx* r = (cx*)malloc(sizeof(cx) * 5 * (size_t)K);
@@ -720,7 +729,7 @@ int tikh_oracle_solve_normal(int64_t m, int64_t n, const double* col, const doub
     stats->jstar = jstar; stats->dual = 0;
   }
   if (nzero != 1 || none != 4 || B.len[5 * 4 + jstar] < 1) { rc = TIKH_ORACLE_ENUMERIC; goto done; }
-  /* Sec. 4.4: x(z) = B*_1^{(j)}(z) / B*_5^{(j)} (the constant last component) */
+  /* Sec. 5: x(z) = B*_1^{(j)}(z) / B*_5^{(j)} (the constant last component) */
   {
     cx c5 = B.c[5 * 4 + jstar][0];
     const cx* b1 = B.c[jstar];
@@ -814,7 +823,7 @@ int tikh_oracle_solve(int64_t m, int64_t n, const double* col, const double* row
 }
 
 /* ------------------------------------------------------------------------------------------ */
-/* Iterative refinement (Sec. 6.2 notes that the direct solution "can be further improved with  */
+/* Iterative refinement (Sec. 7.2 notes that the direct solution "can be further improved with  */
 /* iterative refinement"): on the core system A v = y, A = T_c^H T_c + lam I (T_c the tall core */
 /* matrix, y its right-hand side), v <- v + A^{-1}(y - A v), each correction by the same        */
 /* superfast solve with the residual as right-hand side.                                       */

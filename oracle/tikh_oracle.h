@@ -33,9 +33,9 @@ extern "C" {
 #define TIKH_ORACLE_FFT 2    /* FFT evaluation and FFT products only */
 
 typedef struct {
-  int nlim;         /* leaf cutoff N_lim (Sec. 5.2); leaves hold <= 2*M conditions */
+  int nlim;         /* leaf cutoff N_lim (Sec. 6.2); leaves hold <= 2*M conditions */
   int m_min;        /* lower bound on M (forces a larger extension k); 0 = none */
-  double eps_diff;  /* difficult-point threshold on |r_pivot|/||r||_2 (Sec. 4 end) */
+  double eps_diff;  /* difficult-point threshold on |r_pivot|/||r||_2 (Sec. 5) */
   int mode;         /* TIKH_ORACLE_AUTO / DIRECT / FFT */
   int fill;         /* arbitrary extension entries: 0 = seeded pseudo-random of the coefficients' size,
                        1 = linear ramp between a_{m-1} and a_{-(n-1)} */
@@ -45,7 +45,7 @@ typedef struct {
 typedef struct {
   int64_t N, M, k; /* nodes, leaf size parameter, extension size */
   int p;           /* number of paired-interleaving splits */
-  int64_t n_difficult; /* conditions deferred to the end (Sec. 4, difficult points) */
+  int64_t n_difficult; /* conditions deferred to the end (Sec. 5, difficult points) */
   int64_t n_dropped;   /* conditions whose residual was exactly zero (already satisfied) */
   int delta[5];        /* final tau-degrees of the basis columns */
   int jstar;           /* the column with tau-degree 0 */
@@ -81,6 +81,13 @@ int tikh_oracle_leaf(int K, const double* sigma, double* r, int* delta, double e
 int tikh_oracle_solve_normal(int64_t m, int64_t n, const double* col, const double* row, const double* y,
                              double lam, const tikh_oracle_opts* opts, double* x, tikh_oracle_stats* stats,
                              double* B, int64_t cap, int64_t* len);
+
+/* tikh_oracle_solve_normal that also writes the ids 2e + f (node e, f = 0: F, 1: G) of the conditions
+ * the leaves deferred as difficult (Sec. 5), in the order they were deferred, to deferred_out (at most
+ * deferred_cap of them; stats->n_difficult is the full count). */
+int tikh_oracle_solve_normal_ex(int64_t m, int64_t n, const double* col, const double* row, const double* y,
+                                double lam, const tikh_oracle_opts* opts, double* x, tikh_oracle_stats* stats,
+                                double* B, int64_t cap, int64_t* len, int64_t* deferred_out, int64_t deferred_cap);
 
 /* Tikhonov solution x = argmin ||T x - b||^2 + lam ||x||^2  (Eq. (tik), (tiksol)).
  * m >= n: y = T^H b then solve_normal.  m < n: x = T^H v with (T T^H + lam I) v = b, solved by the

@@ -53,8 +53,8 @@ def _smooth7(v):
 def test_plan_alg2_properties(m, n, nlim):
     N, M, k, p = oracle.plan(m, n, nlim)
     Nt = m + n - 1
-    assert N == (M << p) and k == N - Nt and k >= 0          # criteria 1 and 3 (Sec. 5.2)
-    assert M % 2 == 0 and _smooth7(M)                        # M even (Sec. 5.2) and 7-smooth (R6)
+    assert N == (M << p) and k == N - Nt and k >= 0          # criteria 1 and 3 (Sec. 6.2)
+    assert M % 2 == 0 and _smooth7(M)                        # M even (Sec. 6.2) and 7-smooth (R6)
     # criterion 2 with s = 2 sets: the halving loop stops at the first M with 2M <= N_lim
     Mraw, praw = Nt, 0
     while 2 * Mraw > nlim:
@@ -107,7 +107,7 @@ def test_conditions_null_space_is_tikhonov_solution(m, n, lam, cplx, nlim):
 
 
 def test_conditions_adjoint_generator_identity():
-    # Sec. 6.3: the DFT of the T^H generator follows in O(n) from that of T: lam_H = w^{e(k-1)} conj(t_hat)
+    # Sec. 7.3: the DFT of the T^H generator follows in O(n) from that of T: lam_H = w^{e(k-1)} conj(t_hat)
     P = W.random_problem(37, 23, 1e-2, seed=3)
     F, G, tau, (N, M, k, p) = oracle.conditions(P["col"], P["row"], np.zeros(23), 1e-2, nlim=8, m_min=12)
     assert k > 1
@@ -211,6 +211,24 @@ def test_solve_matches_dense_qr(m, n, lam, cplx):
     assert sorted(st["delta"]) == [0, 1, 1, 1, 1]
 
 
+@pytest.mark.parametrize("m,n,cplx,eps", [(17, 11, True, 0.2), (40, 27, False, 0.2), (5, 3, True, 0.3),
+                                          (11, 17, True, 0.2), (27, 40, False, 0.3)])
+def test_difficult_points_processed_at_the_end_match_dense_qr(m, n, cplx, eps):
+    # Sec. 5: conditions whose best pivot is too small are deferred and processed serially against the
+    # final basis B* (residual Phi_q B*(sigma_q), then single-point steps with no further deferral).
+    # A large threshold forces many deferrals; x must still be the Tikhonov solution and the final
+    # tau-degrees one 0 and four 1s.  A wrong condition row (F for G), node or transposed B* fails this.
+    lam = 1e-2
+    P = W.random_problem(m, n, lam, seed=7 * m + n, complex_data=cplx)
+    xd = oracle.dense_solve(P["col"], P["row"], P["b"], lam)
+    x, st = oracle.solve(P["col"], P["row"], P["b"], lam, nlim=16, eps_diff=eps)
+    T = oracle.toeplitz_dense(P["col"], P["row"])
+    cond = np.linalg.cond(T.conj().T @ T + lam * np.eye(n))
+    assert st["n_difficult"] > 0
+    assert relerr(x, xd) <= 1e-13 * cond + 1e-12, (relerr(x, xd), cond, st)
+    assert sorted(st["delta"]) == [0, 1, 1, 1, 1]
+
+
 def test_scalar_closed_form():
     for a, b, lam in [(2.0 + 1j, 0.5 - 3j, 0.7), (-1e-3, 4.0, 1e-6), (0.0, 1.0, 2.0)]:
         x, _ = oracle.solve([a], [a], [b], lam)
@@ -287,7 +305,7 @@ def test_toeplitz_apply_matches_dense():
 
 
 def test_paper_known_x_within_table1_band():
-    # Sec. 6.1-6.2: y = (T^H T + |beta|^2 I) x for known x; Table 1 bounds the max error
+    # Sec. 7.1-7.2: y = (T^H T + |beta|^2 I) x for known x; Table 1 bounds the max error
     band = {}
     with open(os.path.join(GOLDEN, "table1_l2.txt")) as f:
         for line in f:
@@ -303,7 +321,7 @@ def test_paper_known_x_within_table1_band():
 
 
 def test_solution_independent_of_fill():
-    # Sec. 5.2: the arbitrary extension entries change only the conditioning, not the solution
+    # Sec. 6.2: the arbitrary extension entries change only the conditioning, not the solution
     P = W.deconvolution_problem(210, 150, 3.0, 12, 1e-6, 1e-6, 1e-2, seed=4)
     xd = oracle.dense_solve(P["col"], P["row"], P["b"], P["lam"])
     for fill in (0, 1):
@@ -313,7 +331,7 @@ def test_solution_independent_of_fill():
 
 
 # ----------------------------------------------------------------------------------------------
-# normal-equation form and refinement (Sec. 6.1 right-hand side; Sec. 6.2 refinement)
+# normal-equation form and refinement (Sec. 7.1 right-hand side; Sec. 7.2 refinement)
 # ----------------------------------------------------------------------------------------------
 def test_solve_normal_matches_dense_normal_equations():
     from scipy.linalg import toeplitz
