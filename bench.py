@@ -191,6 +191,8 @@ def main():
     ap.add_argument("--prod-direct-max", type=int, default=0, help="direct products up to this P (0: automatic)")
     ap.add_argument("--eval-direct-max", type=int, default=0, help="direct evaluations up to this size (0: automatic)")
     ap.add_argument("--graph", type=int, default=1, help="1 (default): replay each solve as one captured CUDA graph; 0: stream launches")
+    ap.add_argument("--single", action="store_true",
+                    help="build the plan, run one solve of the workload and exit (a short command for profiler captures)")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -226,6 +228,15 @@ def main():
             plan.solve(col[0], row[0], bb[0], lams[0], x, sync=sync)
         else:
             plan.solve_batched(col, row, bb, lams, xb)
+    if args.single:
+        with torch.cuda.stream(stream):
+            step()
+        torch.cuda.synchronize()
+        st = plan.stats()
+        print(json.dumps({"single_solve": True, "N": st["N"], "p": st["p"], "M": st["M"], "batch": B,
+                          "kernel_launches": st["kernel_launches"]}))
+        plan.close()
+        return
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # 256 MB > 129 MB L2
 
     with torch.cuda.stream(stream):

@@ -8,7 +8,7 @@
  *
  * for an m x n Toeplitz T = [a_{i-j}] (Sec. 2, l2-norm penalisation with L = beta I, lambda = |beta|^2),
  * by the extension-and-transformation of Sec. 3-4.1 and the divide-and-conquer tangential
- * interpolation of Sec. 4.3-5 (Algorithm 1 with paired interleaving, Algorithm 2 sizing).
+ * interpolation of Sec. 4.3-6 (Algorithm 1 with paired interleaving, Algorithm 2 sizing).
  * Every arithmetic step runs in CUDA kernels on the plan's stream.
  *
  * Conventions
@@ -49,18 +49,18 @@ typedef enum { TIKH_PREC_FP64 = 0 } tikh_prec;
 typedef struct tikh_plan_s* tikh_plan;
 
 /* Planner options (NULL -> defaults).
- *  n_lim     leaf cutoff N_lim (Sec. 5.2): leaves hold at most 2M <= n_lim (+ rounding) conditions.
+ *  n_lim     leaf cutoff N_lim (Sec. 6.2): leaves hold at most 2M <= n_lim (+ rounding) conditions.
  *            Default 32; valid 4..64.  Large serial leaves lose accuracy.
  *  m_min     lower bound on M in Algorithm 2 (forces a larger extension k); 0 = none.
- *  fill      extension entries "similar in value" (Sec. 5.2): 0 = seeded pseudo-random of the
+ *  fill      extension entries "similar in value" (Sec. 6.2): 0 = seeded pseudo-random of the
  *            coefficients' size (default), 1 = linear ramp between a_{m-1} and a_{-(n-1)}.
- *  eps_diff  difficult-point threshold (Sec. 4.4): a leaf defers its remaining conditions when the
+ *  eps_diff  difficult-point threshold (Sec. 5): a leaf defers its remaining conditions when the
  *            best one has |r_pivot| < eps_diff ||r||_2.  Default 1e-8.
  *  max_difficult  capacity of the deferred-condition list (default 4096).
  *  refine_steps   iterative-refinement corrections after the direct solve (default 0 = the plain
  *            method; 0..8).  Each correction recomputes r = y - (T^H T + lambda I) x by FFT matrix-
- *            vector products (Sec. 6.3) and solves for the correction with the same algorithm
- *            (Sec. 6.2: the result "can be further improved with iterative refinement").
+ *            vector products (Sec. 7.3) and solves for the correction with the same algorithm
+ *            (Sec. 7.2: the result "can be further improved with iterative refinement").
  *  batch     largest number of same-shape problems per tikh_solve_batched call (default 1); the
  *            plan's workspace scales with it.
  *  graph     1: tikh_solve / tikh_solve_async / tikh_solve_batched capture the whole solve (every
@@ -73,6 +73,9 @@ typedef struct tikh_plan_s* tikh_plan;
  *            O(P^2) direct product is FP64-throughput-bound).  0..4096.
  *  eval_direct_max  step-2 evaluations of B_L at <= this many nodes per coset are computed directly
  *            (chunked Horner), larger ones by FFT; 0 (default): automatic (80 for batch = 1).  0..4096.
+ *  wait_polls  bound on the one in-kernel wait (the leaf's basis-rebuild warps polling for the next
+ *            pivot step): after this many polls the wait gives up and the call returns TIKH_ETIMEOUT.
+ *            0 (default): 2^24 polls.  0..2^30.  A small value exists to exercise the failure path.
  */
 typedef struct {
   int n_lim;
@@ -85,6 +88,7 @@ typedef struct {
   int graph;
   int prod_direct_max;
   int eval_direct_max;
+  int wait_polls;
 } tikh_opts;
 
 typedef struct {
@@ -104,15 +108,15 @@ typedef struct {
   int64_t prof_leaf_launches; /* with profiling on: leaf launches timed since it was switched on */
   int graph;                  /* 1 if the last solve ran as a (captured or replayed) CUDA graph */
   /* with profiling flag 2: summed event-timed duration and count of the schedule's launch groups since
-   * profiling was switched on, by kind: [0] leaves, [1] evaluations (Sec. 5.1 updates of a right
+   * profiling was switched on, by kind: [0] leaves, [1] evaluations (Sec. 6.1 updates of a right
    * child's conditions), [2] basis products, [3] the rest (transform, conditions, difficult points,
    * extraction, refinement, output) */
   double prof_kind_ms[4];
   int64_t prof_kind_count[4];
 } tikh_stats;
 
-/* Build a plan for an m x n problem: sizing by Algorithm 2 (Sec. 5.2), the recursion schedule of
- * Algorithm 1 (Sec. 4.3, 5.1), transform lengths and all device workspace.  stream is a
+/* Build a plan for an m x n problem: sizing by Algorithm 2 (Sec. 6.2), the recursion schedule of
+ * Algorithm 1 (Sec. 4.3, 6.1), transform lengths and all device workspace.  stream is a
  * cudaStream_t (NULL = legacy default stream); every later call enqueues on it.
  * Returns TIKH_EINVAL for m < 1, n < 1, unknown dtype/prec or invalid opts; TIKH_ENOMEM / TIKH_ECUDA
  * when the workspace cannot be allocated.  On failure *out is NULL. */
@@ -133,7 +137,7 @@ int tikh_solve(tikh_plan plan, const void* col, const void* row, const void* b, 
 int tikh_solve_async(tikh_plan plan, const void* col, const void* row, const void* b, double lambda, void* x);
 
 /* x = (T^H T + lambda I)^{-1} y for a given right-hand side y (n entries, device), the form the
- * paper's experiments solve (Sec. 6.1).  Requires m >= n (the tall, stable formulation). */
+ * paper's experiments solve (Sec. 7.1).  Requires m >= n (the tall, stable formulation). */
 int tikh_solve_normal(tikh_plan plan, const void* col, const void* row, const void* y, double lambda, void* x);
 
 /* Adjoint of x = (T^H T + lambda I)^{-1} T^H b for a real loss L (m >= n; TIKH_EINVAL otherwise).
@@ -167,6 +171,13 @@ int tikh_solve_host(tikh_plan plan, const void* col, const void* row, const void
  * here) or TIKH_ECUDA. */
 int tikh_sync(tikh_plan plan);
 
+/* Conditions the leaves deferred as difficult points (Sec. 5) in the last solve of problem 0 of the
+ * call: *count = how many were deferred, ids[0 .. min(count, cap, opts.max_difficult)) = their ids
+ * 2e + f (node e, omega^e; f = 0: the F condition, 1: the G condition of Eq. (interp)), in no
+ * particular order.  ids is a HOST array of cap entries (NULL when cap = 0).  Synchronises the plan's
+ * stream.  TIKH_EINVAL for a NULL plan or count, or cap < 0. */
+int tikh_get_difficult(tikh_plan plan, int64_t* ids, int64_t cap, int64_t* count);
+
 /* Statistics of the plan and of the last synchronised solve (*out is overwritten).  TIKH_EINVAL for a
  * NULL plan or out. */
 int tikh_get_stats(tikh_plan plan, tikh_stats* out);
@@ -193,7 +204,7 @@ const char* tikh_strerror(int status);
 int tikh_test_fft(int64_t n, void* data, int sign, void* stream);
 
 /* One leaf of Algorithm 1: the serial single-point construction of Eq. (spbasis) (Sec. 4.3) with
- * condition pivoting and difficult-point deferral (Sec. 4.4) over K <= 64 conditions.
+ * condition pivoting and difficult-point deferral (Sec. 5) over K <= 64 conditions.
  * Inputs (device): sigma (K complex128 nodes), r (K x 5 complex128 residual rows), delta_in (5 ints,
  * starting tau-degrees), eps (deferral threshold).  Outputs (device): B (25 entries x (K+1) complex128,
  * entry (i,j) at (5i+j)(K+1), unscaled), len (25 ints, trimmed to the degree bounds), delta_out (5 ints),
@@ -202,13 +213,20 @@ int tikh_test_fft(int64_t n, void* data, int sign, void* stream);
 int tikh_test_leaf(int K, const void* sigma, const void* r, const int* delta_in, double eps, void* B, int* len,
                    int* delta_out, int* order, int* pivot, int64_t* deferred, int* n_def, void* stream);
 
+/* Measured peak FMA rate of the current device (the roofline denominator of FP64- and FP32-bound
+ * kernels): kind 0 = FP64 (DFMA), 1 = FP32 (FFMA).  A kernel of 4 CTAs x 256 threads per SM, each thread
+ * running 8 independent FMA chains with no memory traffic, timed with CUDA events on `stream` (best of
+ * three after a warm-up launch).  *gflops = 2 x FMAs / seconds / 1e9.  Synchronises the stream.
+ * TIKH_EINVAL for a NULL gflops or another kind. */
+int tikh_test_peak(int kind, double* gflops, void* stream);
+
 /* ---- allocation-free variant ---- */
 
 /* The DFT of tikh_test_fft (same transform, same kernels, same result) for callers that must not
- * allocate device memory during the call: code running while a stream is being captured into a CUDA
- * graph (cudaMalloc is not allowed there), code whose device memory is owned by another allocator or
- * a fixed budget, and latency-critical loops that cannot afford an allocation.  The paper has no
- * counterpart; this is an interface convenience.
+ * allocate device memory during the call: code whose device memory is owned by another allocator or
+ * a fixed budget (a cudaMalloc there would take memory the caller has promised elsewhere, or fail),
+ * and latency-critical loops that cannot afford an allocation and the synchronisation it implies.
+ * The paper has no counterpart; this is an interface convenience.
  * Its scratch (twiddle tables and the four-step temporary, about 2.2 MB) is one file-scope device
  * array that every GPU loading the library keeps until process exit; nothing is allocated or freed
  * per call (no cudaMalloc, cudaFree or allocating library routine).

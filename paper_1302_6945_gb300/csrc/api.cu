@@ -1,6 +1,6 @@
 // api.cu -- planning, workspace and the C-ABI entry points of include/tikh.h.
 //
-// Planning follows Algorithm 2 (OptExtend, Sec. 5.2) for two condition sets with paired
+// Planning follows Algorithm 2 (OptExtend, Sec. 6.2) for two condition sets with paired
 // interleaving: halve M while 2M > N_lim, make M even, and round it up to a 7-smooth value so every
 // transform length factors into radices 2, 3, 4, 5, 7, 8; N = 2^p M, k = N - (m+n-1).  The DFS of
 // Algorithm 1 is laid out once on the host as a list of steps; product transform lengths come from
@@ -184,11 +184,15 @@ int make_schedule(Plan& P) {
   return err;
 }
 
+// the root cause first: a wait that gave up or a non-finite input invalidates everything after it; a
+// full deferred list cannot be fixed by re-planning; a degree overflow (retried with more slack) can
+// itself cause the final degree pattern or extraction to fail
 int status_to_code(int st) {
-  if (st & ST_DEGREE) return TIKH_EDEGREE;
-  if (st & ST_DIFFICULT) return TIKH_EDIFFICULT;
-  if (st & ST_NUMERIC) return TIKH_ENUMERIC;
   if (st & ST_WAIT) return TIKH_ETIMEOUT;
+  if (st & ST_INPUT) return TIKH_ENUMERIC;
+  if (st & ST_DIFFICULT) return TIKH_EDIFFICULT;
+  if (st & ST_DEGREE) return TIKH_EDEGREE;
+  if (st & ST_NUMERIC) return TIKH_ENUMERIC;
   return TIKH_OK;
 }
 
@@ -282,7 +286,7 @@ int enqueue_prologue(Plan& P, const UserArrays& u, int rhs_is_y, const double* l
     return TIKH_ECUDA;
   if (cudaMemsetAsync(P.status, 0, sizeof(int), P.stream) != cudaSuccess) return TIKH_ECUDA;
   ProfScope ps(P, 3);
-  if ((r = launch_spectrum(P, u)) < 0) return r;
+  if ((r = launch_spectrum(P, u, rhs_is_y)) < 0) return r;
   nl += r;
   // for m < n the core problem (T T^H + lam I) v = b takes b itself as its right-hand side
   if ((r = launch_rhs(P, u, P.dual ? 1 : rhs_is_y)) < 0) return r;
@@ -449,12 +453,13 @@ int tikh_plan_create(tikh_plan* out, int64_t m, int64_t n, int dtype, int prec, 
   if (!out) return TIKH_EINVAL;
   *out = nullptr;
   if (m < 1 || n < 1 || (dtype != TIKH_R64 && dtype != TIKH_C128) || prec != TIKH_PREC_FP64) return TIKH_EINVAL;
-  tikh_opts o{32, 0, 0, 1e-8, 4096, 0, 1, 0, 0, 0};
+  tikh_opts o{32, 0, 0, 1e-8, 4096, 0, 1, 0, 0, 0, 0};
   if (opts) o = *opts;
   if (o.n_lim < 4 || o.n_lim > 64 || o.m_min < 0 || o.m_min > 32 || (o.fill != 0 && o.fill != 1) ||
       !(o.eps_diff >= 0.0) || o.max_difficult < 1 || o.max_difficult > (1 << 20) || o.refine_steps < 0 ||
       o.refine_steps > 8 || o.batch < 1 || o.batch > 65535 || (o.graph != 0 && o.graph != 1) ||
-      o.prod_direct_max < 0 || o.prod_direct_max > 4096 || o.eval_direct_max < 0 || o.eval_direct_max > 4096)
+      o.prod_direct_max < 0 || o.prod_direct_max > 4096 || o.eval_direct_max < 0 || o.eval_direct_max > 4096 ||
+      o.wait_polls < 0 || o.wait_polls > (1 << 30))
     return TIKH_EINVAL;
   tikh_plan h = new (std::nothrow) tikh_plan_s;
   if (!h) return TIKH_ENOMEM;
@@ -469,6 +474,7 @@ int tikh_plan_create(tikh_plan* out, int64_t m, int64_t n, int dtype, int prec, 
   // product loses to the O(P log P) FFT product at much smaller P (measured on GB300)
   P.prod_direct_max = o.prod_direct_max > 0 ? o.prod_direct_max : (o.batch == 1 ? 360 : BATCH_PROD_DIRECT_MAX);
   P.eval_direct_max = o.eval_direct_max > 0 ? o.eval_direct_max : (o.batch == 1 ? 80 : BATCH_EVAL_DIRECT_MAX);
+  P.wait_polls = o.wait_polls > 0 ? o.wait_polls : (1 << 24);
   P.stream = (cudaStream_t)stream;
   P.dual = m < n ? 1 : 0;
   P.cm = P.dual ? n : m;
@@ -500,6 +506,7 @@ int tikh_plan_create(tikh_plan* out, int64_t m, int64_t n, int dtype, int prec, 
   P.dstack = (int*)dalloc(P, sizeof(int) * 5 * MAX_DEPTH * nb, err);
   P.status = (int*)dalloc(P, sizeof(int) * 4, err);
   P.ndiff = (int*)dalloc(P, sizeof(int) * 4 * nb, err);
+  P.bad = (int*)dalloc(P, sizeof(int) * nb, err);
   P.diff = (int64_t*)dalloc(P, sizeof(int64_t) * (size_t)o.max_difficult * nb, err);
   P.diffr = (cd*)dalloc(P, sizeof(cd) * 5 * (size_t)o.max_difficult * nb, err);
   P.dvals = (cd*)dalloc(P, sizeof(cd) * 25 * (size_t)o.max_difficult * nb, err);
@@ -613,6 +620,19 @@ int tikh_solve_host(tikh_plan h, const void* col, const void* row, const void* b
 int tikh_sync(tikh_plan h) {
   if (!h) return TIKH_EINVAL;
   return sync_status(h->P);
+}
+
+int tikh_get_difficult(tikh_plan h, int64_t* ids, int64_t cap, int64_t* count) {
+  if (!h || !count || cap < 0 || (cap > 0 && !ids)) return TIKH_EINVAL;
+  Plan& P = h->P;
+  if (cudaStreamSynchronize(P.stream) != cudaSuccess) { cudaGetLastError(); return TIKH_ECUDA; }
+  int nd = 0;
+  if (cudaMemcpy(&nd, P.ndiff, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return TIKH_ECUDA;
+  *count = nd;
+  const int64_t stored = std::min<int64_t>(std::min<int64_t>(nd, P.opts.max_difficult), cap);
+  if (stored > 0 && cudaMemcpy(ids, P.diff, sizeof(int64_t) * (size_t)stored, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return TIKH_ECUDA;
+  return TIKH_OK;
 }
 
 int tikh_get_stats(tikh_plan h, tikh_stats* out) {

@@ -26,6 +26,7 @@ enum : int {
   ST_DEGREE = 2,     // a basis degree exceeded the planned transform length
   ST_DIFFICULT = 4,  // deferred-condition list overflow
   ST_WAIT = 8,       // a bounded in-kernel wait gave up
+  ST_INPUT = 16,     // a non-finite entry in col, row or the right-hand side
 };
 
 __device__ __forceinline__ void set_status(int* st, int bit) { atomicOr(st, bit); }

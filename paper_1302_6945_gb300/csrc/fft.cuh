@@ -12,6 +12,7 @@
 // the transform index as the contiguous dimension so global accesses coalesce.
 #pragma once
 #include <algorithm>
+#include <atomic>
 #include <vector>
 
 #include "common.cuh"
@@ -272,10 +273,17 @@ inline cudaError_t launch_tile(const FftDesc& d, int want_tb, int batch, int sig
   int tb, threads;
   fft_tile_geometry(d.L, want_tb, tb, threads);
   size_t smem = sizeof(cd) * (size_t)tb * d.L;
-  static bool attr_set = false;  // one per template instantiation
-  if (!attr_set) {
-    cudaFuncSetAttribute(fft_tile_kernel<LD, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8192 * (int)sizeof(cd));
-    attr_set = true;
+  // the dynamic shared-memory limit is a per-device function attribute: set it once per device (bit
+  // dev of a mask kept per template instantiation; devices beyond 63 set it on every launch)
+  static std::atomic<unsigned long long> attr_set{0ULL};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return cudaGetLastError();
+  const unsigned long long bit = dev < 64 ? (1ULL << dev) : 0ULL;
+  if (!bit || !(attr_set.load(std::memory_order_acquire) & bit)) {
+    cudaError_t e = cudaFuncSetAttribute(fft_tile_kernel<LD, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         8192 * (int)sizeof(cd));
+    if (e != cudaSuccess) return e;
+    attr_set.fetch_or(bit, std::memory_order_acq_rel);
   }
   int blocks = (batch + tb - 1) / tb;
   fft_tile_kernel<LD, ST><<<blocks, threads, smem, s>>>(d, tb, batch, sign, ljf, sjf, ld, st);

@@ -2,7 +2,7 @@
 //
 // With A = T^H T + lam I (Hermitian), an upstream gradient G = dL/dx (conjugate-Wirtinger
 // convention of PyTorch: dL = Re(G^H dx)) and g = A^{-1} G (one more superfast solve whose
-// right-hand side is G itself, Sec. 6.1's form):
+// right-hand side is G itself, Sec. 7.1's form):
 //   dL/db      = T g                                     (x is linear in b, adjoint T A^{-1})
 //   dL/dlambda = -Re(g^H x)                              (dx/dlambda = -A^{-1} x)
 //   dL/da_d    = sum_j r_{j+d} conj(g_j) - u_{j+d} conj(x_j),  r = b - T x, u = T g

@@ -1,5 +1,6 @@
 // hooks.cu -- test entry points of include/tikh.h that run one building block (the FFT engine, one
 // leaf) on caller data, so that each stage can be compared with the CPU oracle on identical inputs.
+#include <algorithm>
 #include <vector>
 
 #include "internal.h"
@@ -58,9 +59,62 @@ int launch_fft_test(int64_t L, cd* data, int sign, cudaStream_t s, int64_t* byte
   return rc;
 }
 
+// Peak FMA rate: every thread runs 8 independent FMA chains of `iters` steps (no memory traffic), on
+// 4 CTAs of 256 threads per SM, so every sub-partition always has an independent instruction ready.
+template <class T>
+__global__ void __launch_bounds__(256) k_fma_rate(T* out, int iters, T b, T c) {
+  T a[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) a[j] = (T)(threadIdx.x + j) * (T)1e-3;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] = fma(a[j], b, c);
+  }
+  T s = 0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) s += a[j];
+  if (s == (T)-1.2345) out[blockIdx.x] = s;  // never true for these inputs; keeps the chains live
+}
+
+template <class T>
+static int fma_rate(double* gflops, cudaStream_t s) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return TIKH_ECUDA;
+  T* out = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = TIKH_OK;
+  const int blocks = 4 * sms, threads = 256;
+  const int iters = sizeof(T) == 8 ? (1 << 14) : (1 << 18);
+  if (cudaMalloc(&out, sizeof(T) * blocks) != cudaSuccess) return TIKH_ENOMEM;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = TIKH_ECUDA;
+  float best = 1e30f;
+  for (int rep = 0; rep < 4 && !rc; ++rep) {  // the first launch warms up, the best of the rest counts
+    cudaEventRecord(e0, s);
+    k_fma_rate<T><<<blocks, threads, 0, s>>>(out, iters, (T)0.999999, (T)1e-7);
+    cudaEventRecord(e1, s);
+    if (cudaEventSynchronize(e1) != cudaSuccess) { rc = TIKH_ECUDA; break; }
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0) best = std::min(best, ms);
+  }
+  if (!rc) *gflops = 2.0 * 8.0 * (double)iters * blocks * threads / (best * 1e-3) / 1e9;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(out);
+  return rc;
+}
+
 }  // namespace tikh
 
 extern "C" {
+
+int tikh_test_peak(int kind, double* gflops, void* stream) {
+  if (!gflops || (kind != 0 && kind != 1)) return TIKH_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  return kind == 0 ? fma_rate<double>(gflops, s) : fma_rate<float>(gflops, s);
+}
+
 
 int tikh_test_fft(int64_t n, void* data, int sign, void* stream) {
   if (n < 1 || !data || (sign != 1 && sign != -1)) return TIKH_EINVAL;

@@ -71,6 +71,7 @@ struct Plan {
   int slack_mult = 1;  // degree-prediction slack multiplier (raised after TIKH_EDEGREE)
   int64_t eval_direct_max = 80;   // step 2 by direct evaluation when the right child has <= this many nodes per coset
   int64_t prod_direct_max = 360;  // step 4 by schoolbook products when the planned length P <= this
+  int wait_polls = 1 << 24;       // bounded wait of the leaf's rebuild warps (polls)
 
   std::vector<Step> sched;
   std::map<int64_t, int> fft_of_len;
@@ -92,6 +93,7 @@ struct Plan {
   int* dstack = nullptr;  // [nb][MAX_DEPTH][5]
   int* status = nullptr;  // 1 (shared by the batch)
   int* ndiff = nullptr;   // [nb][4]
+  int* bad = nullptr;     // [nb] 1: non-finite input (set by the prologue's check)
   int64_t* diff = nullptr;  // [nb][max_difficult] condition ids 2e + f
   cd* diffr = nullptr;      // [nb][max_difficult][5] residuals
   cd* dvals = nullptr;      // [nb][max_difficult][25] B*(sigma) of the deferred conditions
@@ -132,7 +134,7 @@ struct Plan {
 
 // launchers (return the number of kernels enqueued, or a negative TIKH_E* code)
 int launch_twiddle(cd* tab, int64_t L, cudaStream_t s);
-int launch_spectrum(Plan& P, const UserArrays& u);
+int launch_spectrum(Plan& P, const UserArrays& u, int rhs_is_y);
 int launch_rhs(Plan& P, const UserArrays& u, int rhs_is_y);
 int launch_conditions(Plan& P, const cd* y);
 int launch_extract(Plan& P, cd* out);

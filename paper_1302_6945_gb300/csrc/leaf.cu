@@ -1,5 +1,5 @@
 // leaf.cu -- leaves of Algorithm 1: the serial single-point construction of Eq. (spbasis) over the
-// K = 4L <= 64 conditions of a leaf node, with condition pivoting (Sec. 4.4) and difficult-point
+// K = 4L <= 64 conditions of a leaf node, with condition pivoting (Sec. 5) and difficult-point
 // deferral; and the end-of-run serial processing of the deferred conditions against B*.
 //
 // Pivot rules (shared reading of the paper):
@@ -23,6 +23,7 @@ namespace tikh {
 
 constexpr int LEAF_KMAX = 64;
 constexpr int LEAF_CAP = LEAF_KMAX + 1;
+constexpr int LEAF_SPIN_DEFAULT = 1 << 24;  // polls of the rebuild warps before they give up (ST_WAIT)
 
 // pick: (score bits, position, pivot); larger score wins, then lower position
 struct Pick {
@@ -199,7 +200,6 @@ __device__ __forceinline__ double rcp_series(double d) {
 constexpr int L4_ROWS = 6;
 constexpr int L4_NREC = 128;
 constexpr int CHAIN_DONE = 1 << 30;
-constexpr int L4_SPIN_LIMIT = 1 << 24;  // polls of the rebuild warps before they give up (ST_WAIT)
 
 __device__ __forceinline__ int ld_volatile(const int* p) { return *(const volatile int*)p; }
 __device__ __forceinline__ void st_volatile(int* p, int v) { *(volatile int*)p = v; }
@@ -208,7 +208,8 @@ template <int CWN, class Src>
 __global__ void __launch_bounds__(32 * CWN + L4_NREC, CWN <= 4 ? 4 : (CWN <= 8 ? 2 : 1)) k_leaf(Src src, int K, int* delta, int* dstack,
                                                               unsigned long long save_mask, double eps, BasisBuf out,
                                                               int* ndiff, int64_t* diff, int maxdiff, int* status,
-                                                              int* rec_order, int* rec_pivot) {
+                                                              int* rec_order, int* rec_pivot, const int* bad,
+                                                              int spin_limit) {
   constexpr int NCHAIN = 32 * CWN, NT = NCHAIN + L4_NREC;
   __shared__ cd Bs[25][LEAF_CAP];
   __shared__ cd oldc[5][LEAF_CAP];
@@ -235,7 +236,9 @@ __global__ void __launch_bounds__(32 * CWN + L4_NREC, CWN <= 4 ? 4 : (CWN <= 8 ?
   }
   const int rr = lane / 5, jc = lane - 5 * rr, rbase = 5 * rr;
   const int q = wid * L4_ROWS + rr;
-  bool active = tid < NCHAIN && rr < L4_ROWS && q < K;
+  // a problem whose input failed the prologue's finiteness check processes no condition
+  const bool skip = bad && bad[pb] != 0;
+  bool active = tid < NCHAIN && rr < L4_ROWS && q < K && !skip;
   cd r = mkc(0.0, 0.0), sig = mkc(0.0, 0.0);
   int64_t eid = -1;
   if (active) {
@@ -396,7 +399,7 @@ __global__ void __launch_bounds__(32 * CWN + L4_NREC, CWN <= 4 ? 4 : (CWN <= 8 ?
     for (int s = 0;; ++s) {
       if (rt == 0) {
         int cmd = 2;  // 0: step s is recorded, 1: the chain stopped before s, 2: gave up waiting
-        for (int it = 0; it < L4_SPIN_LIMIT; ++it) {
+        for (int it = 0; it < spin_limit; ++it) {
           const int st = ld_volatile(&chain_state);
           if ((st & ~CHAIN_DONE) > s) { cmd = 0; break; }
           if (st & CHAIN_DONE) { cmd = 1; break; }
@@ -476,16 +479,16 @@ __global__ void __launch_bounds__(32 * CWN + L4_NREC, CWN <= 4 ? 4 : (CWN <= 8 ?
 template <class Src>
 static int launch_leaf_t(const Src& src, int K, int nb, int* delta, int* dstack, unsigned long long mask, double eps,
                          const BasisBuf& out, int* ndiff, int64_t* diff, int maxdiff, int* status, int* order,
-                         int* pivot, cudaStream_t s) {
+                         int* pivot, const int* bad, int spin_limit, cudaStream_t s) {
   if (K <= 4 * L4_ROWS)
     k_leaf<4, Src><<<nb, 32 * 4 + L4_NREC, 0, s>>>(src, K, delta, dstack, mask, eps, out, ndiff, diff, maxdiff,
-                                                   status, order, pivot);
+                                                   status, order, pivot, bad, spin_limit);
   else if (K <= 8 * L4_ROWS)
     k_leaf<8, Src><<<nb, 32 * 8 + L4_NREC, 0, s>>>(src, K, delta, dstack, mask, eps, out, ndiff, diff, maxdiff,
-                                                   status, order, pivot);
+                                                   status, order, pivot, bad, spin_limit);
   else
     k_leaf<11, Src><<<nb, 32 * 11 + L4_NREC, 0, s>>>(src, K, delta, dstack, mask, eps, out, ndiff, diff, maxdiff,
-                                                     status, order, pivot);
+                                                     status, order, pivot, bad, spin_limit);
   return cudaGetLastError() == cudaSuccess ? 1 : TIKH_ECUDA;
 }
 
@@ -494,7 +497,7 @@ int launch_leaf(Plan& P, const Step& st) {
   if (K > LEAF_KMAX) return TIKH_EINVAL;
   return launch_leaf_t(SrcNodes{P.R, P.wN, P.N, st.a, st.s}, K, P.nb, P.delta, P.dstack, st.save_mask,
                        P.opts.eps_diff, P.buf[st.depth][st.side], P.ndiff, P.diff, P.opts.max_difficult, P.status,
-                       nullptr, nullptr, P.stream);
+                       nullptr, nullptr, P.bad, P.wait_polls, P.stream);
 }
 
 // test hook: one leaf (one problem) on explicit device arrays
@@ -508,11 +511,11 @@ int launch_leaf_arrays(int K, const cd* sigma, const cd* r, int* delta, double e
   out.colmax = colmax;
   out.cap = K + 1;
   return launch_leaf_t(SrcArrays{sigma, r}, K, 1, delta, nullptr, 0ULL, eps, out, ndiff, diff, K, status, order, pivot,
-                       s);
+                       nullptr, LEAF_SPIN_DEFAULT, s);
 }
 
 // ------------------------------------------------------------------------------------------------
-// difficult points (Sec. 4.4): residual against the final basis B*, then serial processing.
+// difficult points (Sec. 5): residual against the final basis B*, then serial processing.
 // ------------------------------------------------------------------------------------------------
 
 // B*(sigma_q) for every deferred condition q (column scales applied): block (entry E, slot, problem),

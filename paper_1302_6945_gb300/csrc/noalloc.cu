@@ -1,6 +1,8 @@
 // noalloc.cu -- the FFT engine without any allocation: its scratch (the twiddle tables and the
 // four-step temporary) lives in a file-scope device array of fixed size instead of cudaMalloc'd
 // memory, for callers that must not allocate (see tikh_fft_noalloc in include/tikh.h).
+#include <atomic>
+
 #include "internal.h"
 
 using namespace tikh;
@@ -26,18 +28,22 @@ struct NaStore {
 };
 
 // Device address of the scratch array for each device, fetched once with that device current.
-// Host code cannot use the symbol itself as a device pointer.
-static cd* g_na_addr[64] = {nullptr};
+// Host code cannot use the symbol itself as a device pointer.  Entries are atomic: host threads
+// making their first call on the same device at once may both look the address up (the lookup
+// returns the same value), but neither reads a torn or half-written entry.
+static std::atomic<cd*> g_na_addr[64];
 
 static int noalloc_scratch(cd** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) { cudaGetLastError(); return TIKH_ECUDA; }
-  if (!g_na_addr[dev]) {
+  cd* a = g_na_addr[dev].load(std::memory_order_acquire);
+  if (!a) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) { cudaGetLastError(); return TIKH_ECUDA; }
-    g_na_addr[dev] = (cd*)p;
+    a = (cd*)p;
+    g_na_addr[dev].store(a, std::memory_order_release);
   }
-  *out = g_na_addr[dev];
+  *out = a;
   return TIKH_OK;
 }
 

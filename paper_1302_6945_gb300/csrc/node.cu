@@ -1,9 +1,9 @@
-// node.cu -- internal nodes of Algorithm 1 with paired interleaving (Sec. 4.3, 5.1).
+// node.cu -- internal nodes of Algorithm 1 with paired interleaving (Sec. 4.3, 6.1).
 //
 // A node (a, s, L) splits into the left child (a, 2s, L/2) and the right child (a+s, 2s, L/2).
 // Step 2: the left basis B_L is evaluated at the right child's nodes omega^{beta + 2s j}, j < L/2,
 // beta in {a+s, a+s+1}: twist by omega^{beta t}, fold modulo L/2, DFT of length L/2 (the
-// cancellation of roots of unity that Sec. 4.3 and Sec. 5.1 rely on); then every right condition
+// cancellation of roots of unity that Sec. 4.3 and Sec. 6.1 rely on); then every right condition
 // phi <- phi B_L(sigma).
 // Step 4: B = B_L B_R by length-P DFTs, P > the largest entry degree allowed by the tau-degrees,
 // trimmed to entry (i,j) degree bounds and carried with power-of-two column scales.

@@ -1,5 +1,5 @@
-// transform.cu -- extension and transformation (Sec. 3.1, 3.3, 4.1), extraction (Sec. 4.4) and the
-// FFT matrix-vector products used by refinement (cf. Sec. 6.3).
+// transform.cu -- extension and transformation (Sec. 3.1, 3.3, 4.1), extraction (Sec. 5) and the
+// FFT matrix-vector products used by refinement (cf. Sec. 7.3).
 //
 // The core problem is tall (cm >= cn): (T^H T + lam I) x = y.  For m < n the core matrix is T^H
 // (a'_d = conj(a_{-d})) and its right-hand side is b itself; the answer is then x = T^H v.
@@ -7,7 +7,7 @@
 // Conditions at node e (omega = exp(+2 pi i / N)):
 //   F_e = [lam omega^{e(cm+k-1)}, lamH_e, 1, 0, yhat_e],  G_e = [-that_e, omega^{e(cn+k-1)}, 0, 1, 0]
 // with that = DFT(c_T), c_T[j] = a_{j-(cn+k-1)} over the N-periodic extended sequence,
-// lamH_e = omega^{e(k-1)} conj(that_e) (the T^H generator's DFT, obtained in O(N) as in Sec. 6.3),
+// lamH_e = omega^{e(k-1)} conj(that_e) (the T^H generator's DFT, obtained in O(N) as in Sec. 7.3),
 // yhat = DFT of -y placed after cm+k-1 zeros.
 //
 // Length-N transforms run one transform per problem (transform index = problem index).
@@ -66,17 +66,30 @@ __device__ __forceinline__ double splitmix_uniform(unsigned long long c) {
   return (double)(z >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
 }
 
-// peak = max over the known diagonals of max(|Re|, |Im|)  (exact, order independent)
-__global__ void k_peak(CoreDiag a, int64_t cm, int64_t cn, unsigned long long* peak) {
+// peak = max over the known diagonals of max(|Re|, |Im|)  (exact, order independent); and the input
+// check: a non-finite diagonal or right-hand-side entry marks the problem (bad[pb] = 1, whose leaves
+// then process no condition) and the call (ST_INPUT), so no kernel iterates on NaN or Inf
+__global__ void k_peak(CoreDiag a, int64_t cm, int64_t cn, unsigned long long* peak, const void* rhs,
+                       int64_t rhs_stride, int64_t rhs_len, int dtype, int* bad, int* status) {
   const int pb = blockIdx.y;
   double mx = 0.0;
+  bool fin = true;
   int64_t total = cm + cn - 1;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     cd v = a(pb, i - (cn - 1));
+    fin = fin && isfinite(v.x) && isfinite(v.y);
     mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+  }
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rhs_len; i += (int64_t)gridDim.x * blockDim.x) {
+    cd v = load_user(rhs, pb * rhs_stride + i, dtype);
+    fin = fin && isfinite(v.x) && isfinite(v.y);
   }
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if ((threadIdx.x & 31) == 0 && mx > 0.0) atomicMax(peak + pb, (unsigned long long)__double_as_longlong(mx));
+  if (!fin) {
+    bad[pb] = 1;
+    set_status(status, ST_INPUT);
+  }
 }
 
 // c_T[j] = a_{j-(cn+k-1)} over the periodic sequence; entries a_{cm-1+i}, i = 1..k, are the fill
@@ -127,7 +140,7 @@ struct LoadPadC {
   int64_t stride, len;
   __device__ cd operator()(int pb, int64_t j) const { return j < len ? v[pb * stride + j] : mkc(0.0, 0.0); }
 };
-// spectrum times lamH_e = omega^{e(k-1)} conj(that_e)  (adjoint generator, Sec. 6.3)
+// spectrum times lamH_e = omega^{e(k-1)} conj(that_e)  (adjoint generator, Sec. 7.3)
 struct StoreMulLamH {
   cd* out;
   const cd* that;
@@ -197,8 +210,11 @@ struct StoreConditions {
   }
 };
 
-__global__ void k_reset_peak(unsigned long long* peak, int nb) {
-  for (int i = threadIdx.x; i < nb; i += blockDim.x) peak[i] = 0ULL;
+__global__ void k_reset_peak(unsigned long long* peak, int* bad, int nb) {
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+    peak[i] = 0ULL;
+    bad[i] = 0;
+  }
 }
 __global__ void k_reset_tree(int* delta, int d0, int d1, int d2, int d3, int* ndiff, int nb) {
   for (int pb = threadIdx.x; pb < nb; pb += blockDim.x) {
@@ -213,13 +229,16 @@ static inline dim3 grid2(int64_t n, int nb, int threads = 256, int cap = 4096) {
 }
 
 // that = DFT(c_T) of each problem's core matrix (Sec. 3.1, Eq. (circdiag))
-int launch_spectrum(Plan& P, const UserArrays& u) {
+int launch_spectrum(Plan& P, const UserArrays& u, int rhs_is_y) {
   cudaStream_t s = P.stream;
   int nl = 0, r;
-  k_reset_peak<<<1, 256, 0, s>>>(P.peak, P.nb);
+  k_reset_peak<<<1, 256, 0, s>>>(P.peak, P.bad, P.nb);
   ++nl;
   CoreDiag a{u.col, u.row, u.col_stride, u.row_stride, P.dtype, P.dual};
-  k_peak<<<grid2(P.cm + P.cn, P.nb, 256, 1024), 256, 0, s>>>(a, P.cm, P.cn, P.peak);
+  // the user right-hand side: y (n entries) for the normal-equation form, else b (m entries)
+  const int64_t rhs_len = rhs_is_y ? P.n : P.m;
+  k_peak<<<grid2(P.cm + P.cn, P.nb, 256, 1024), 256, 0, s>>>(a, P.cm, P.cn, P.peak, u.rhs, u.rhs_stride, rhs_len,
+                                                              P.dtype, P.bad, P.status);
   ++nl;
   if (cudaGetLastError() != cudaSuccess) return TIKH_ECUDA;
   const FftPlan& FN = P.ffts[P.fft_of_len.at(P.N)];
@@ -270,7 +289,7 @@ int launch_conditions(Plan& P, const cd* y) {
 }
 
 // ------------------------------------------------------------------------------------------------
-// extraction: x(z) = B*_1^{(j)}(z) / B*_5^{(j)}, j the column of tau-degree 0 (Sec. 4.3 end, 4.4)
+// extraction: x(z) = B*_1^{(j)}(z) / B*_5^{(j)}, j the column of tau-degree 0 (Sec. 4.3 end, 5)
 // ------------------------------------------------------------------------------------------------
 __global__ void k_extract(BasisBuf B, const int* delta, int* status, int64_t cn, cd* out) {
   const int pb = blockIdx.y;
@@ -309,7 +328,7 @@ int launch_extract(Plan& P, cd* out) {
 }
 
 // ------------------------------------------------------------------------------------------------
-// refinement pieces: r = y - (T_c^H T_c x + lam x) by FFT matvecs (cf. Sec. 6.3), x += dx
+// refinement pieces: r = y - (T_c^H T_c x + lam x) by FFT matvecs (cf. Sec. 7.3), x += dx
 // ------------------------------------------------------------------------------------------------
 // keep the inverse-transform window [off, N) scaled at its own index, zero before
 struct StoreKeepFrom {

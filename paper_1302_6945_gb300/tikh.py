@@ -22,7 +22,7 @@ class tikh_opts(ctypes.Structure):
     _fields_ = [("n_lim", ctypes.c_int), ("m_min", ctypes.c_int), ("fill", ctypes.c_int),
                 ("eps_diff", ctypes.c_double), ("max_difficult", ctypes.c_int), ("refine_steps", ctypes.c_int),
                 ("batch", ctypes.c_int), ("graph", ctypes.c_int),
-                ("prod_direct_max", ctypes.c_int), ("eval_direct_max", ctypes.c_int)]
+                ("prod_direct_max", ctypes.c_int), ("eval_direct_max", ctypes.c_int), ("wait_polls", ctypes.c_int)]
 
 
 class tikh_stats(ctypes.Structure):
@@ -51,7 +51,7 @@ _lib = None
 EXPORTED = ["tikh_plan_create", "tikh_solve", "tikh_solve_async", "tikh_solve_normal", "tikh_solve_host",
             "tikh_solve_batched",
             "tikh_sync", "tikh_get_stats", "tikh_plan_destroy", "tikh_strerror", "tikh_test_fft", "tikh_test_leaf",
-            "tikh_fft_noalloc", "tikh_set_profiling", "tikh_solve_grad"]
+            "tikh_fft_noalloc", "tikh_set_profiling", "tikh_solve_grad", "tikh_get_difficult", "tikh_test_peak"]
 
 
 def lib():
@@ -71,12 +71,14 @@ def lib():
         L.tikh_set_profiling.argtypes = [vp, ci]
         L.tikh_solve_grad.argtypes = [vp, vp, vp, vp, dbl, vp, vp, vp, vp, vp, ctypes.POINTER(dbl)]
         L.tikh_get_stats.argtypes = [vp, ctypes.POINTER(tikh_stats)]
+        L.tikh_get_difficult.argtypes = [vp, vp, i64, ctypes.POINTER(i64)]
         L.tikh_plan_destroy.argtypes = [vp]
         L.tikh_plan_destroy.restype = None
         L.tikh_strerror.argtypes = [ci]
         L.tikh_strerror.restype = ctypes.c_char_p
         L.tikh_test_fft.argtypes = [i64, vp, ci, vp]
         L.tikh_fft_noalloc.argtypes = [i64, vp, ci, vp]
+        L.tikh_test_peak.argtypes = [ci, ctypes.POINTER(dbl), vp]
         L.tikh_test_leaf.argtypes = [ci, vp, vp, vp, dbl, vp, vp, vp, vp, vp, vp, vp, vp]
         _lib = L
     return _lib
@@ -142,6 +144,15 @@ def tikh_get_stats(plan):
     return st.as_dict()
 
 
+def tikh_get_difficult(plan, cap=1 << 16):
+    """(count, sorted ids 2e + f) of the conditions deferred as difficult in the last solve."""
+    ids = np.zeros(max(int(cap), 1), np.int64)
+    cnt = ctypes.c_int64()
+    _check(lib().tikh_get_difficult(plan, ids.ctypes.data_as(ctypes.c_void_p), int(cap), ctypes.byref(cnt)),
+           "tikh_get_difficult")
+    return int(cnt.value), sorted(int(v) for v in ids[:min(int(cnt.value), int(cap))])
+
+
 def tikh_plan_destroy(plan):
     lib().tikh_plan_destroy(plan)
 
@@ -152,6 +163,13 @@ def tikh_set_profiling(plan, flags):
 
 def tikh_test_fft(n, data, sign, stream=0):
     _check(lib().tikh_test_fft(int(n), data, int(sign), ctypes.c_void_p(int(stream))), "tikh_test_fft")
+
+
+def tikh_test_peak(kind, stream=0):
+    """Measured FMA rate of the device in GFLOP/s: kind 0 = FP64, 1 = FP32."""
+    out = ctypes.c_double()
+    _check(lib().tikh_test_peak(int(kind), ctypes.byref(out), ctypes.c_void_p(int(stream))), "tikh_test_peak")
+    return out.value
 
 
 def tikh_fft_noalloc(n, data, sign, stream=0):
@@ -211,14 +229,15 @@ class Plan:
     """A solver plan for m x n Toeplitz problems of one dtype ('r64' or 'c128')."""
 
     def __init__(self, m, n, dtype="r64", n_lim=32, m_min=0, fill=0, eps_diff=1e-8, max_difficult=4096,
-                 refine_steps=0, batch=1, graph=False, prod_direct_max=0, eval_direct_max=0, stream=None):
+                 refine_steps=0, batch=1, graph=False, prod_direct_max=0, eval_direct_max=0, wait_polls=0,
+                 stream=None):
         import torch
         self.m, self.n = int(m), int(n)
         self.dtype = TIKH_C128 if dtype in ("c128", TIKH_C128, torch.complex128) else TIKH_R64
         self.batch = int(batch)
         self.opts = tikh_opts(int(n_lim), int(m_min), int(fill), float(eps_diff), int(max_difficult),
                               int(refine_steps), self.batch, 1 if graph else 0, int(prod_direct_max),
-                              int(eval_direct_max))
+                              int(eval_direct_max), int(wait_polls))
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
@@ -307,6 +326,10 @@ class Plan:
 
     def stats(self):
         return tikh_get_stats(self.h)
+
+    def difficult(self):
+        """(count, sorted ids 2e + f) of the conditions deferred in the last solve (problem 0)."""
+        return tikh_get_difficult(self.h)
 
     def close(self):
         if getattr(self, "h", None):

@@ -12,7 +12,7 @@ Readings of the workload descriptions (all inputs synthetic; no dataset exists f
     theta_d ~ U[0, 2 pi), and draw complex noise with the stated deviation per real/imag part.
   * "piecewise constant with 8 random jumps": 8 distinct jump positions in [1, n-1], levels N(0,1).
   * "complex Gaussian smoothed by a width-32 box": same-size moving average of width 32.
-  * the paper-shaped workload (Sec. 6.1-6.2): complex standard-normal square T, known x,
+  * the paper-shaped workload (Sec. 7.1-7.2): complex standard-normal square T, known x,
     y = (T^H T + lam I) x with lam = |beta|^2 = sqrt(N), N read as m + n.
 """
 import math
@@ -122,7 +122,7 @@ def batch_c3(seed=2, count=512, nmin=256, nmax=65536, nlambda=16):
 
 
 def paper_problem(n, seed=0):
-    """Sec. 6.1: complex standard-normal square T, known x, y = (T^H T + lam I) x, lam = sqrt(2n)."""
+    """Sec. 7.1: complex standard-normal square T, known x, y = (T^H T + lam I) x, lam = sqrt(2n)."""
     rng = np.random.default_rng(seed)
     col = rng.standard_normal(n) + 1j * rng.standard_normal(n)
     row = rng.standard_normal(n) + 1j * rng.standard_normal(n)

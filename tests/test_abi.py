@@ -35,11 +35,12 @@ def test_strerror_and_invalid_plan_without_gpu():
 @pytest.mark.parametrize("field,value", [("n_lim", 3), ("n_lim", 65), ("m_min", 33), ("fill", 2), ("eps_diff", -1.0),
                                          ("max_difficult", 0), ("refine_steps", 9), ("batch", 0), ("graph", 2),
                                          ("prod_direct_max", -1), ("prod_direct_max", 4097),
-                                         ("eval_direct_max", -1), ("eval_direct_max", 4097)])
+                                         ("eval_direct_max", -1), ("eval_direct_max", 4097), ("wait_polls", -1),
+                                         ("wait_polls", (1 << 30) + 1)])
 def test_invalid_options_are_rejected_before_any_device_work(field, value):
     # argument checks come first, so they hold on a machine without a GPU
     from paper_1302_6945_gb300 import tikh
-    o = tikh.tikh_opts(32, 0, 0, 1e-8, 4096, 0, 1, 0, 0, 0)
+    o = tikh.tikh_opts(32, 0, 0, 1e-8, 4096, 0, 1, 0, 0, 0, 0)
     setattr(o, field, value)
     with pytest.raises(tikh.TikhError) as e:
         tikh.tikh_plan_create(64, 64, tikh.TIKH_R64, tikh.TIKH_PREC_FP64, o)

@@ -117,7 +117,7 @@ def test_c1_config_vs_oracle_and_dense():
 
 
 def test_solve_normal_paper_workload():
-    # Sec. 6.1: known x, y = (T^H T + lam I) x
+    # Sec. 7.1: known x, y = (T^H T + lam I) x
     P = W.paper_problem(512, seed=3)
     T = oracle.toeplitz_dense(P["col"], P["row"])
     y = T.conj().T @ (T @ P["x_true"]) + P["lam"] * P["x_true"]
@@ -152,6 +152,35 @@ def test_difficult_points_match_oracle():
         assert relerr(x, xd) <= max(1e-7, 20 * relerr(xo.real, xd)), (relerr(x, xd), relerr(xo.real, xd))
 
 
+@pytest.mark.parametrize("m,n,cplx,seed,eps", [(40, 27, False, 1, 0.036), (64, 40, True, 2, 0.003),
+                                               (200, 150, False, 9, 0.014)])
+def test_difficult_point_parity_with_well_separated_decisions(m, n, cplx, seed, eps):
+    # Sec. 5: each eps lies in the middle of a range (a factor of >= 1.6 either side) over which the
+    # oracle defers the same number of conditions, so no decision is near the threshold.  Both sides
+    # must defer the same conditions (ids 2e + f) and, processing them at the end against B*, reach the
+    # same x to 1e-9.
+    P = W.random_problem(m, n, 1e-2, seed=seed, complex_data=cplx)
+    y = oracle.apply_th(P["col"], P["row"], P["b"])
+    if not cplx:
+        y = y.real
+    xo, sto = oracle.solve_normal(P["col"], P["row"], y, P["lam"], nlim=16, eps_diff=eps, is_complex=int(cplx),
+                                  want_deferred=True)
+    dt = torch.complex128 if cplx else torch.float64
+    t = lambda a: torch.tensor(a, dtype=dt, device=DEV)
+    plan = tikh.Plan(m, n, "c128" if cplx else "r64", n_lim=16, eps_diff=eps)
+    x = plan.solve_normal(t(P["col"]), t(P["row"]), t(y), P["lam"]).cpu().numpy()
+    cnt, ids = plan.difficult()
+    st = plan.stats()
+    plan.close()
+    assert sto["n_difficult"] > 0
+    assert cnt == sto["n_difficult"] == st["n_difficult"]
+    assert ids == sorted(sto["deferred"])
+    if not cplx:
+        xo = xo.real
+    assert relerr(x, xo) <= TOL, relerr(x, xo)
+    assert sorted(st["delta"]) == [0, 1, 1, 1, 1]
+
+
 def test_invalid_arguments_raise():
     with pytest.raises(tikh.TikhError):
         tikh.Plan(0, 5)
@@ -165,17 +194,20 @@ def test_invalid_arguments_raise():
 
 
 def test_c2_full_size_vs_oracle():
-    # the benchmark workload: complex128, m = 98304, n = 65536, lambda = 1e-4.  Plain solve: agreement
-    # within a small multiple of the plain method's own error (its normal-equation residual); one FP64
-    # refinement correction: 1e-9.
+    # the benchmark workload: complex128, m = 98304, n = 65536, lambda = 1e-4.  x_ref = the oracle's
+    # solve with two FP64 refinement corrections (1e-14 from one correction).  The plain method's own
+    # forward error here is the oracle's distance from x_ref (6.5e-9 measured): the plain GPU solve must
+    # be as accurate as the oracle (within 2x of its error) and, where the oracle's error is <= 1e-10,
+    # within 1e-9 of it; with one correction the GPU solve is within 1e-9 of the refined oracle.
     P = W.config_c2()
     x, st = gpu_solve(P, True)
     assert (st["N"], st["k"]) == (163840, 1)
     xo, _ = oracle.solve(P["col"], P["row"], P["b"], P["lam"])
-    r = oracle.apply_th(P["col"], P["row"], P["b"] - oracle.apply_t(P["col"], P["row"], xo)) - P["lam"] * xo
-    method_res = np.linalg.norm(r) / np.linalg.norm(oracle.apply_th(P["col"], P["row"], P["b"]))
-    assert relerr(x, xo) <= max(TOL, 20 * method_res), (relerr(x, xo), method_res)
+    x_ref, _, rr2 = oracle.solve_refined(P["col"], P["row"], P["b"], P["lam"], steps=2)
+    oracle_err = relerr(xo, x_ref)
+    assert relerr(x, x_ref) <= 2 * oracle_err, (relerr(x, x_ref), oracle_err)
+    if oracle_err <= 1e-10:
+        assert relerr(x, xo) <= TOL
     xr, st = gpu_solve(P, True, refine_steps=1)
-    xor, _, rr = oracle.solve_refined(P["col"], P["row"], P["b"], P["lam"], steps=1)
-    assert st["rel_residual"] < 1e-13 and rr < 1e-13
-    assert relerr(xr, xor) <= TOL, relerr(xr, xor)
+    assert st["rel_residual"] < 1e-13 and rr2 < 1e-13
+    assert relerr(xr, x_ref) <= TOL, relerr(xr, x_ref)

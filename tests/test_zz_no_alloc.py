@@ -1,7 +1,8 @@
 """The allocation-free DFT entry point (tikh_fft_noalloc) against the allocating one (tikh_test_fft).
 
-Some callers cannot allocate device memory during a call (a stream being captured, a caller-owned
-memory budget); tikh_fft_noalloc serves them from a fixed device array.  This file runs last so that
+Some callers cannot allocate device memory during a call (their device memory belongs to another
+allocator or a fixed budget, or their inner loop cannot afford an allocation); tikh_fft_noalloc
+serves them from a fixed device array.  This file runs last so that
 a failure here leaves every other test already run.
 """
 import ctypes
