@@ -199,6 +199,35 @@ def solve_refined(col, row, b, lam, steps=1, nlim=32, eps_diff=1e-8, mode=AUTO, 
     return x, st.as_dict(), rr.value
 
 
+def solve_gramian(g, lcol, lrow, y, nlim=32, eps_diff=1e-8, mode=AUTO, m_min=0, fill=0, is_complex=None):
+    """Toeplitz-Gramian problem (Sec. 3.4): x = (G + L^H L)^{-1} y, G Hermitian Toeplitz with first column g,
+    L Toeplitz with first column lcol and first row lrow.  Returns (x, stats)."""
+    if is_complex is None:
+        is_complex = _is_complex(g, lcol, lrow)
+    g, lcol, lrow, y = _c128(g), _c128(lcol), _c128(lrow), _c128(y)
+    n, pl = g.size, lcol.size
+    x = np.zeros(n, np.complex128)
+    st = Stats()
+    o = opts(nlim=nlim, eps_diff=eps_diff, mode=mode, m_min=m_min, fill=fill, is_complex=is_complex)
+    _check(_lib().tikh_oracle_solve_gramian(ctypes.c_int64(n), ctypes.c_int64(pl), _ptr(g), _ptr(lcol), _ptr(lrow),
+                                            _ptr(y), ctypes.byref(o), _ptr(x), ctypes.byref(st)), "solve_gramian")
+    return x, st.as_dict()
+
+
+def hermitian_toeplitz_dense(g):
+    """G[i, j] = g_{i-j} with g_{-d} = conj(g_d)."""
+    g = _c128(g)
+    n = g.size
+    return toeplitz_dense(g, np.conj(g))
+
+
+def dense_solve_gramian(g, lcol, lrow, y):
+    """(G + L^H L)^{-1} y by a dense LAPACK solve."""
+    G = hermitian_toeplitz_dense(g)
+    L = toeplitz_dense(lcol, lrow)
+    return np.linalg.solve(G + L.conj().T @ L, _c128(y))
+
+
 def apply_t(col, row, x):
     col, row, x = _c128(col), _c128(row), _c128(x)
     u = np.zeros(col.size, np.complex128)

@@ -660,14 +660,48 @@ int tikh_oracle_solve_normal(int64_t m, int64_t n, const double* col, const doub
   return tikh_oracle_solve_normal_ex(m, n, col, row, y, lam, opts, x, stats, Bout, cap, lenout, NULL, 0);
 }
 
-int tikh_oracle_solve_normal_ex(int64_t m, int64_t n, const double* col, const double* row, const double* y,
-                                double lam, const tikh_oracle_opts* opts, double* x, tikh_oracle_stats* stats,
-                                double* Bout, int64_t cap, int64_t* lenout, int64_t* deferred_out,
-                                int64_t deferred_cap) {
-  int64_t N, M, k;
-  int p;
-  int rc = tikh_oracle_plan(m, n, opts, &N, &M, &k, &p);
-  if (rc) return rc;
+/* x-column of the first block row of the Toeplitz-Gramian system (Sec. 3.4, Eq. (gramblk)): the n x n
+ * Hermitian Toeplitz G (G[i][j] = g_{i-j}, g_{-d} = conj(g_d)) below N-n extension rows.  Its circulant
+ * generator is c11[(N-n+d) mod N] = g_d for |d| <= n-1; the other N-2n+1 entries are the arbitrary
+ * extension entries, filled as in R5 (peak of g times SplitMix64 uniforms, counters offset by 2^40 so they
+ * differ from L's).  Returns DFT(c11) (positive exponent) in out (N entries). */
+static int gram_column(int64_t n, int64_t N, const cx* g, int fill, int is_complex, cx* out) {
+  cx* gt = (cx*)malloc(sizeof(cx) * (size_t)N); /* gt[d mod N] = g_d */
+  if (!gt) return TIKH_ORACLE_ENOMEM;
+  for (int64_t d = 0; d < N; ++d) gt[d] = 0;
+  for (int64_t d = 0; d < n; ++d) gt[d] = g[d];
+  for (int64_t d = 1; d < n; ++d) gt[N - d] = conj(g[d]);
+  const int64_t nfill = N - 2 * n + 1; /* indices n .. N-n */
+  double peak = 0.0;
+  for (int64_t d = 0; d < n; ++d) {
+    if (fabs(creal(g[d])) > peak) peak = fabs(creal(g[d]));
+    if (fabs(cimag(g[d])) > peak) peak = fabs(cimag(g[d]));
+  }
+  for (int64_t i = 1; i <= nfill; ++i) {
+    cx v;
+    if (fill == 1) {
+      v = g[n - 1] + (conj(g[n - 1]) - g[n - 1]) * ((double)i / (double)(nfill + 1));
+    } else {
+      double re = peak * splitmix_uniform((uint64_t)(2 * i) + (1ULL << 40));
+      double im = is_complex ? peak * splitmix_uniform((uint64_t)(2 * i + 1) + (1ULL << 40)) : 0.0;
+      v = re + im * I;
+    }
+    gt[n - 1 + i] = v;
+  }
+  for (int64_t j = 0; j < N; ++j) out[j] = gt[((j - (N - n)) % N + N) % N];
+  free(gt);
+  return dft(out, N, +1);
+}
+
+/* The superfast solve from the plan (N, M, k, p) on: conditions, Algorithm 1, difficult points,
+ * extraction.  gram == NULL: the l2 system (Eq. (ex6)) for (T^H T + lam I) x = y; otherwise the
+ * Toeplitz-Gramian system (Eq. (ex7)) for (G + L^H L) x = y with L = [col, row] (m x n) in the role of T
+ * and G (first column gram) in place of lam I. */
+static int solve_core(int64_t m, int64_t n, const double* col, const double* row, const double* y, double lam,
+                      const double* gram, int64_t N, int64_t M, int64_t k, int p, const tikh_oracle_opts* opts,
+                      double* x, tikh_oracle_stats* stats, double* Bout, int64_t cap, int64_t* lenout,
+                      int64_t* deferred_out, int64_t deferred_cap) {
+  int rc;
   rstate st;
   memset(&st, 0, sizeof(st));
   st.N = N; st.M = M; st.eps = opts->eps_diff; st.mode = opts->mode;
@@ -683,6 +717,14 @@ int tikh_oracle_solve_normal_ex(int64_t m, int64_t n, const double* col, const d
   if ((rc = build_conditions(m, n, N, k, (const cx*)col, (const cx*)row, (const cx*)y, lam, opts->fill,
                              opts->is_complex, F, G)))
     goto done;
+  if (gram) { /* Toeplitz-Gramian: F's x component is the DFT of G's generator instead of lam w^{e(m+k-1)} */
+    cx* c11 = (cx*)malloc(sizeof(cx) * (size_t)N);
+    if (!c11) { rc = TIKH_ORACLE_ENOMEM; goto done; }
+    rc = gram_column(n, N, (const cx*)gram, opts->fill, opts->is_complex, c11);
+    for (int64_t e = 0; e < N && !rc; ++e) F[5 * e] = c11[e];
+    free(c11);
+    if (rc) goto done;
+  }
   for (int64_t e = 0; e < N; ++e) {
     memcpy(st.R + 10 * e, F + 5 * e, sizeof(cx) * 5);
     memcpy(st.R + 10 * e + 5, G + 5 * e, sizeof(cx) * 5);
@@ -749,6 +791,32 @@ done:
   pm_free(&B);
   free(F); free(G); free(Phi); free(st.R); free(st.deferred);
   return rc;
+}
+
+int tikh_oracle_solve_normal_ex(int64_t m, int64_t n, const double* col, const double* row, const double* y,
+                                double lam, const tikh_oracle_opts* opts, double* x, tikh_oracle_stats* stats,
+                                double* Bout, int64_t cap, int64_t* lenout, int64_t* deferred_out,
+                                int64_t deferred_cap) {
+  int64_t N, M, k;
+  int p;
+  int rc = tikh_oracle_plan(m, n, opts, &N, &M, &k, &p);
+  if (rc) return rc;
+  return solve_core(m, n, col, row, y, lam, NULL, N, M, k, p, opts, x, stats, Bout, cap, lenout, deferred_out,
+                    deferred_cap);
+}
+
+/* Sec. 3.4: q = max(n, pl); Algorithm 2 sizes N >= q + n - 1 (so the N-n extension rows of the first
+ * block row hold G's generator, N - 2n + 1 >= 0), and L's extension is k = N - (pl + n - 1). */
+int tikh_oracle_solve_gramian(int64_t n, int64_t pl, const double* g, const double* lcol, const double* lrow,
+                              const double* y, const tikh_oracle_opts* opts, double* x, tikh_oracle_stats* stats) {
+  if (n < 1 || pl < 1 || !opts) return TIKH_ORACLE_EINVAL;
+  const int64_t q = n > pl ? n : pl;
+  int64_t N, M, k0;
+  int p;
+  int rc = tikh_oracle_plan(q, n, opts, &N, &M, &k0, &p);
+  if (rc) return rc;
+  const int64_t k = N - (pl + n - 1);
+  return solve_core(pl, n, lcol, lrow, y, 0.0, g, N, M, k, p, opts, x, stats, NULL, 0, NULL, NULL, 0);
 }
 
 /* y = T^H v and u = T x through the circulant embedding of length >= m+n-1 (a plain DFT identity) */

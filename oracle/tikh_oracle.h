@@ -89,6 +89,14 @@ int tikh_oracle_solve_normal_ex(int64_t m, int64_t n, const double* col, const d
                                 double lam, const tikh_oracle_opts* opts, double* x, tikh_oracle_stats* stats,
                                 double* B, int64_t cap, int64_t* len, int64_t* deferred_out, int64_t deferred_cap);
 
+/* The Toeplitz-Gramian problem (Sec. 3.4, Eq. (gramblk), (ex7)): x = (G + L^H L)^{-1} y with G an n x n
+ * Hermitian Toeplitz matrix (a Gramian T^H T that is Toeplitz) given by its first column g (n complex;
+ * G[i][j] = g_{i-j}, g_{-d} = conj(g_d)) and L a pl x n Toeplitz regulariser given by its first column
+ * lcol (pl) and first row lrow (n; lrow[0] ignored).  Same algorithm as the l2 solve with L in place of T
+ * and G in place of lam I; N = 2^p M >= max(n, pl) + n - 1.  x: n complex. */
+int tikh_oracle_solve_gramian(int64_t n, int64_t pl, const double* g, const double* lcol, const double* lrow,
+                              const double* y, const tikh_oracle_opts* opts, double* x, tikh_oracle_stats* stats);
+
 /* Tikhonov solution x = argmin ||T x - b||^2 + lam ||x||^2  (Eq. (tik), (tiksol)).
  * m >= n: y = T^H b then solve_normal.  m < n: x = T^H v with (T T^H + lam I) v = b, solved by the
  * same algorithm on the tall matrix T^H.  b: m complex; x: n complex. */

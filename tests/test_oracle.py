@@ -363,3 +363,67 @@ def test_refinement_reaches_dense_accuracy_on_a_smoothing_psf():
     x2, _, _ = oracle.solve_refined(P["col"], P["row"], P["b"], lam, steps=2)
     assert relerr(x2.real, xd) <= 1e-9
     assert relerr(x2.real, xd) <= 1e-3 * relerr(x0.real, xd)
+
+
+# ----------------------------------------------------------------------------------------------
+# Toeplitz-Gramian problem (Sec. 3.4, Eq. (gramblk), (ex7)): (G + L^H L) x = y
+# ----------------------------------------------------------------------------------------------
+
+def _gramian_case(n, pl, cplx, seed, width=8):
+    rng = np.random.default_rng(seed)
+    h = rng.standard_normal(width) + (1j * rng.standard_normal(width) if cplx else 0.0)
+    # G = the autocorrelation Toeplitz of h: Hermitian positive semidefinite, as a Gramian is
+    g = np.array([np.vdot(h[d:], h[:width - d]) if d < width else 0.0 for d in range(n)], dtype=complex)
+    lcol = rng.standard_normal(pl) + (1j * rng.standard_normal(pl) if cplx else 0.0)
+    lrow = rng.standard_normal(n) + (1j * rng.standard_normal(n) if cplx else 0.0)
+    lrow[0] = lcol[0]
+    y = rng.standard_normal(n) + (1j * rng.standard_normal(n) if cplx else 0.0)
+    return g, lcol, lrow, y
+
+
+@pytest.mark.parametrize("n,pl,cplx", [(7, 3, False), (20, 20, False), (31, 29, True), (40, 38, False),
+                                       (64, 80, True), (50, 10, True), (100, 98, False)])
+def test_gramian_matches_dense_solve(n, pl, cplx):
+    g, lcol, lrow, y = _gramian_case(n, pl, cplx, seed=n + pl)
+    G = oracle.hermitian_toeplitz_dense(g)
+    assert np.allclose(G, G.conj().T)
+    L = oracle.toeplitz_dense(lcol, lrow)
+    A = G + L.conj().T @ L
+    xd = np.linalg.solve(A, y)
+    x, st = oracle.solve_gramian(g, lcol, lrow, y, nlim=16)
+    assert relerr(x, xd) <= 1e-13 * np.linalg.cond(A) + 1e-12, relerr(x, xd)
+    assert sorted(st["delta"]) == [0, 1, 1, 1, 1]
+    assert st["N"] >= max(n, pl) + n - 1 and st["k"] == st["N"] - (pl + n - 1)
+
+
+def test_gramian_with_scaled_identity_regulariser_is_a_shifted_toeplitz_solve():
+    # L = beta I (pl = n): (G + |beta|^2 I) x = y
+    n, beta = 45, 0.7 - 0.2j
+    g, _, _, y = _gramian_case(n, n, True, seed=3)
+    lcol = np.zeros(n, complex)
+    lcol[0] = beta
+    lrow = np.zeros(n, complex)
+    x, _ = oracle.solve_gramian(g, lcol, lrow, y, nlim=16)
+    xd = np.linalg.solve(oracle.hermitian_toeplitz_dense(g) + abs(beta) ** 2 * np.eye(n), y)
+    assert relerr(x, xd) <= 1e-12
+
+
+def test_gramian_with_scaled_identity_gram_is_the_l2_normal_equation():
+    # G = lam I: (lam I + L^H L) x = y, the l2 system with T = L (its own pinned solver and dense LAPACK)
+    P = W.random_problem(60, 44, 0.3, seed=8)
+    y = oracle.apply_th(P["col"], P["row"], P["b"])
+    g = np.zeros(44, complex)
+    g[0] = 0.3
+    x, _ = oracle.solve_gramian(g, P["col"], P["row"], y, nlim=16)
+    xn, _ = oracle.solve_normal(P["col"], P["row"], y, 0.3, nlim=16)
+    xd = oracle.dense_solve_normal(P["col"], P["row"], y, 0.3)
+    assert relerr(x, xd) <= 1e-12 and relerr(xn, xd) <= 1e-12
+
+
+def test_gramian_solution_independent_of_fill_and_extension():
+    g, lcol, lrow, y = _gramian_case(70, 68, False, seed=12)
+    xd = oracle.dense_solve_gramian(g, lcol, lrow, y)
+    for fill in (0, 1):
+        for m_min in (0, 12, 20):
+            x, st = oracle.solve_gramian(g, lcol, lrow, y, nlim=16, m_min=m_min, fill=fill)
+            assert relerr(x, xd) <= 1e-11, (fill, m_min, st["k"], relerr(x, xd))
