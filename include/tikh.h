@@ -44,9 +44,23 @@ extern "C" {
 #define TIKH_EDEGREE (-8)       /* a basis degree exceeded its planned transform length (retried internally) */
 
 typedef enum { TIKH_R64 = 0, TIKH_C128 = 1 } tikh_dtype;
-typedef enum { TIKH_PREC_FP64 = 0 } tikh_prec;
+/* Precision of the solve (the pattern of Sec. 7.2's refinement remark, made concrete):
+ *  TIKH_PREC_FP64         every step in FP64 (the plain method).
+ *  TIKH_PREC_FP32         the O(N log^2 N) part of the recursion -- the FFT-form evaluations of B_L at the
+ *                         right child's nodes with their residual updates, and the FFT-form basis products
+ *                         (Alg. 1 steps 2 and 4) -- runs in FP32 (complex64 transforms, FP32 pointwise
+ *                         products and accumulation).  FP64 stays for the leaves (the serial single-point
+ *                         construction, its pivot and deferral decisions), the tau-degree bookkeeping, the
+ *                         small-node direct forms, the stored basis and residual rows, the length-N transforms
+ *                         of the extension and the refinement residual.  Less accurate (the error of one
+ *                         solve is far above the FP64 method's); opts.refine_steps corrections as in FP64.
+ *  TIKH_PREC_FP32_REFINE  TIKH_PREC_FP32 solves plus iterative refinement with the FP64 residual
+ *                         r = y - (T^H T + lambda I) x computed by FP64 FFT matrix-vector products (Sec. 7.3);
+ *                         opts.refine_steps corrections (0 -> 2), each an FP32-stage solve. */
+typedef enum { TIKH_PREC_FP64 = 0, TIKH_PREC_FP32_REFINE = 1, TIKH_PREC_FP32 = 2 } tikh_prec;
 
 typedef struct tikh_plan_s* tikh_plan;
+typedef struct tikh_batch_plan_s* tikh_batch_plan;
 
 /* Planner options (NULL -> defaults).
  *  n_lim     leaf cutoff N_lim (Sec. 6.2): leaves hold at most 2M <= n_lim (+ rounding) conditions.
@@ -61,11 +75,12 @@ typedef struct tikh_plan_s* tikh_plan;
  *            method; 0..8).  Each correction recomputes r = y - (T^H T + lambda I) x by FFT matrix-
  *            vector products (Sec. 7.3) and solves for the correction with the same algorithm
  *            (Sec. 7.2: the result "can be further improved with iterative refinement").
- *  batch     largest number of same-shape problems per tikh_solve_batched call (default 1); the
+ *  batch     largest number of same-shape problems per tikh_solve_strided call (default 1); the
  *            plan's workspace scales with it.
- *  graph     1: tikh_solve / tikh_solve_async / tikh_solve_batched capture the whole solve (every
- *            kernel of every recursion node) into one CUDA graph on the first call and replay it while
- *            the pointer and stride arguments stay the same (lambda may change); 0 (default): stream
+ *  graph     1: tikh_solve / tikh_solve_async / tikh_solve_strided capture the whole solve (every
+ *            kernel of every recursion node) into one CUDA graph on the first call with a given number of
+ *            problems and replay it for every later such call (the kernels read each call's pointers,
+ *            sizes and lambdas from device tables written before the replay); 0 (default): stream
  *            launches.  Not used with profiling on.
  *  prod_direct_max  step-4 products (Alg. 1) of planned length P <= this are computed directly
  *            (schoolbook, one warp per output coefficient), longer ones by FFT; 0 (default): automatic
@@ -73,6 +88,9 @@ typedef struct tikh_plan_s* tikh_plan;
  *            O(P^2) direct product is FP64-throughput-bound).  0..4096.
  *  eval_direct_max  step-2 evaluations of B_L at <= this many nodes per coset are computed directly
  *            (chunked Horner), larger ones by FFT; 0 (default): automatic (80 for batch = 1).  0..4096.
+ *  refine_tol  with refine_steps > 0: after the last correction, a relative residual
+ *            ||y - (T^H T + lambda I) x|| / ||y|| above refine_tol makes the call return TIKH_ENOTCONVERGED
+ *            (x is still written).  0 (default): no check.
  *  wait_polls  bound on the one in-kernel wait (the leaf's basis-rebuild warps polling for the next
  *            pivot step): after this many polls the wait gives up and the call returns TIKH_ETIMEOUT.
  *            0 (default): 2^24 polls.  0..2^30.  A small value exists to exercise the failure path.
@@ -89,6 +107,7 @@ typedef struct {
   int prod_direct_max;
   int eval_direct_max;
   int wait_polls;
+  double refine_tol;
 } tikh_opts;
 
 typedef struct {
@@ -113,7 +132,36 @@ typedef struct {
    * extraction, refinement, output) */
   double prof_kind_ms[4];
   int64_t prof_kind_count[4];
+  /* algorithmic FLOPs of one problem's core solve by the same kinds (a model of the arithmetic the
+   * method needs: 5 L log2 L per complex FFT of length L, 8 per complex multiply-add; see the plan's
+   * documentation), and the part of them the FFT stages run in FP32 (0 for TIKH_PREC_FP64).  A refined
+   * solve runs the core solve 1 + refine_steps times. */
+  double model_flops[4];
+  double model_flops_fp32[4];
+  double last_correction;  /* largest ||dx|| / ||x|| of the last refinement correction over the call (-1 if none):
+                            * an estimate of the error of the solution before that correction */
 } tikh_stats;
+
+typedef struct {
+  int ngroups;             /* groups of problems sharing N (and the m < n form): one schedule each */
+  int max_waves;           /* most sequential waves of any group (items beyond the workspace budget) */
+  int64_t items;           /* (problem, lambda) pairs per call = nprob * nlambda */
+  int64_t kernel_launches; /* kernels enqueued per call (all groups) */
+  int64_t workspace_bytes; /* device bytes owned by the batch plan */
+  int graph;               /* 1 if the last call ran as one captured CUDA graph */
+  int retries;             /* re-runs after TIKH_EDEGREE in the last call */
+  int64_t n_difficult;     /* deferred conditions in the last wave of every group, summed */
+  double rel_residual;     /* largest refinement residual over the last wave of every group (-1: none) */
+  double last_correction;  /* largest ||dx|| / ||x|| of the last correction, same items (-1: none) */
+  /* algorithmic FLOPs of one core solve of every item of a call, by kind (leaf, evaluation, product,
+   * other) as in tikh_stats, and their FP32-stage part */
+  double model_flops[4];
+  double model_flops_fp32[4];
+  /* with profiling on (tikh_batch_set_profiling): event-timed durations and counts of the launch groups
+   * by kind, summed over the groups of every call since profiling was switched on */
+  double prof_kind_ms[4];
+  int64_t prof_kind_count[4];
+} tikh_batch_stats;
 
 /* Build a plan for an m x n problem: sizing by Algorithm 2 (Sec. 6.2), the recursion schedule of
  * Algorithm 1 (Sec. 4.3, 6.1), transform lengths and all device workspace.  stream is a
@@ -151,14 +199,23 @@ int tikh_solve_normal(tikh_plan plan, const void* col, const void* row, const vo
 int tikh_solve_grad(tikh_plan plan, const void* col, const void* row, const void* b, double lambda, const void* x,
                     const void* dLdx, void* dLdcol, void* dLdrow, void* dLdb, double* dLdlambda);
 
+/* tikh_solve_grad for `batch` problems of the plan's shape in one pass (each its own col, row, b, lambda,
+ * x and dL/dx; element strides as for tikh_solve_strided, each >= the vector's length: gradients of shared
+ * inputs are not summed here).  Outputs are dense: dLdcol [batch][m], dLdrow [batch][n], dLdb [batch][m]
+ * (device), dLdlambda [batch] (host).  1 <= batch <= opts.batch.  Synchronises. */
+int tikh_solve_grad_strided(tikh_plan plan, int batch, const void* col, int64_t col_stride, const void* row,
+                            int64_t row_stride, const void* b, int64_t b_stride, const double* lambdas, const void* x,
+                            int64_t x_stride, const void* dLdx, int64_t dLdx_stride, void* dLdcol, void* dLdrow,
+                            void* dLdb, double* dLdlambda);
+
 /* `batch` problems of the plan's shape in one pass: every step of the method is one launch for all of
  * them (a batch shares the recursion schedule; each problem keeps its own tau-degrees, pivots and
  * basis).  Problem i reads col + i*col_stride, row + i*row_stride, b + i*b_stride and lambdas[i]
  * (HOST array of batch doubles) and writes x + i*x_stride; strides count elements of the plan's
  * dtype, and a stride of 0 shares one array across the batch (e.g. a regularisation path: one T and
  * b, many lambdas).  1 <= batch <= opts.batch; x_stride >= n when batch > 1.  Synchronises like
- * tikh_solve; the status is the OR over the batch. */
-int tikh_solve_batched(tikh_plan plan, int batch, const void* col, int64_t col_stride, const void* row,
+ * tikh_solve; the status is the worst over the batch. */
+int tikh_solve_strided(tikh_plan plan, int batch, const void* col, int64_t col_stride, const void* row,
                        int64_t row_stride, const void* b, int64_t b_stride, const double* lambdas, void* x,
                        int64_t x_stride);
 
@@ -196,12 +253,87 @@ void tikh_plan_destroy(tikh_plan plan);
 /* Static description of a status code. */
 const char* tikh_strerror(int status);
 
+/* ---- the Toeplitz-Gramian problem (Sec. 3.4) ---- */
+
+/* Plan for x = (G + L^H L)^{-1} y, the Tikhonov system of min ||T x - b||^2 + ||L x||^2 when the Gramian
+ * G = T^H T is an n x n Toeplitz matrix (so y = T^H b), with a p x n Toeplitz regulariser L (Sec. 3.4,
+ * Eq. (gramblk), (ex7)).  The extended system has the l2 problem's two block rows and five components,
+ * with L in the role of T and G's circulant extension in place of lambda I: N = 2^p M >= max(n, p) + n - 1
+ * by Algorithm 2, L's extension k = N - (p + n - 1).  dtype, prec, opts and stream as for
+ * tikh_plan_create (refinement residual: y - (G + L^H L) x).  TIKH_EINVAL for n < 1, p < 1 or invalid
+ * options.  Such a plan serves only tikh_solve_gramian. */
+int tikh_plan_create_gramian(tikh_plan* out, int64_t n, int64_t p, int dtype, int prec, const tikh_opts* opts,
+                             void* stream);
+
+/* x (n) = (G + L^H L)^{-1} y for DEVICE arrays: g = first column of the Hermitian Toeplitz G (n entries;
+ * G[i][j] = g_{i-j}, g_{-d} = conj(g_d); for real data g is real and G symmetric), lcol (p) and lrow (n) =
+ * first column and first row of L (lrow[0] ignored), y (n).  Synchronises like tikh_solve.  TIKH_EINVAL
+ * for a NULL pointer or a plan not made by tikh_plan_create_gramian. */
+int tikh_solve_gramian(tikh_plan plan, const void* g, const void* lcol, const void* lrow, const void* y, void* x);
+
+/* Weighted Gramian of non-uniform Fourier samples (Sec. 7.4): K samples X_k = sum_s x_s exp(-2 pi i f_k s)
+ * of a length-n signal at frequencies f_k in [-1/2, 1/2) with density weights w_k give the Toeplitz-Gramian
+ * system (A^H W A + L^H L) x = A^H W X.  Writes its Hermitian Toeplitz Gramian's first column
+ * g_d = sum_k w_k exp(+2 pi i f_k d) and the right-hand side y_s = sum_k w_k X_k exp(+2 pi i f_k s),
+ * d, s = 0..n-1, by direct FP64 sums (phases reduced to [-1/2, 1/2] before sincospi).  DEVICE arrays:
+ * f, w (K doubles), X (K complex128), g, y (n complex128).  Synchronises the stream.  TIKH_EINVAL for
+ * K < 1, n < 1 or a NULL pointer. */
+int tikh_nufft_gramian(int64_t K, const double* f, const double* w, const void* X, int64_t n, void* g, void* y,
+                       void* stream);
+
+/* ---- batches of problems of different shapes (Sec. 6.2 sizing per problem) ---- */
+
+/* Plan for nprob problems of shapes m[i] x n[i] (HOST arrays), each solved for the same nlambda
+ * regularisation weights: nprob * nlambda items (problem, lambda).  Problems whose core problems get the
+ * same N = 2^p M from Algorithm 2 (Sec. 6.2) -- and the same m < n form -- form one group and share one
+ * recursion schedule (each product transform as long as its longest member needs); every launch of a
+ * group serves all its items at once, each with its own sizes m, n, k, tau-degrees and basis.  Groups run
+ * concurrently on streams of their own, forked from and joined to `stream`.  A group whose items do not
+ * fit the workspace budget runs in sequential waves: max_workspace_bytes bounds the plan's device
+ * memory (0: 60 % of the free memory at creation).  opts as for tikh_plan_create (opts.batch ignored;
+ * opts.graph = 1 captures the whole batch -- every wave of every group -- as one CUDA graph on the first
+ * call and replays it).  TIKH_EINVAL for nprob < 1, nlambda < 1, a size < 1 or invalid options. */
+int tikh_batch_plan_create(tikh_batch_plan* out, int nprob, const int64_t* m, const int64_t* n, int nlambda, int dtype,
+                           int prec, const tikh_opts* opts, int64_t max_workspace_bytes, void* stream);
+
+/* x[i * nlambda + l] = argmin ||T_i x - b_i||^2 + lambdas[l] ||x||^2 for every problem i and weight l.
+ * m, n: the plan's shapes (checked); col, row, b: HOST arrays of nprob DEVICE pointers (problem i's first
+ * column, first row and right-hand side, the plan's dtype); lambdas: HOST array of nlambda weights;
+ * x: HOST array of nprob * nlambda DEVICE pointers to n[i] entries each.  Synchronises the plan's stream;
+ * returns the worst status over all items (TIKH_EDEGREE is retried internally with more degree slack). */
+int tikh_solve_batched(tikh_batch_plan plan, int nprob, const int64_t* m, const int64_t* n, const void* const* col,
+                       const void* const* row, const void* const* b, int nlambda, const double* lambdas,
+                       void* const* x);
+
+/* Profiling of a batch plan: flags as for tikh_set_profiling (bit 1: every launch group timed by kind),
+ * applied to every group; while it is on, calls run the groups one after another on the plan's stream
+ * (no concurrency between groups, no graph), so the per-kind times do not overlap.  Resets the sums.
+ * TIKH_EINVAL for a NULL plan or flags outside 0..3. */
+int tikh_batch_set_profiling(tikh_batch_plan plan, int flags);
+
+/* Statistics of the batch plan and its last call.  TIKH_EINVAL for a NULL plan or out. */
+int tikh_batch_get_stats(tikh_batch_plan plan, tikh_batch_stats* out);
+
+/* Release the batch plan's streams, graphs and device memory.  NULL is ignored. */
+void tikh_batch_plan_destroy(tikh_batch_plan plan);
+
 /* ---- test hooks: one building block on caller data (device pointers), for stage-wise parity ---- */
 
 /* In-place DFT of n complex128 values (device): X_k = sum_j x_j exp(sign 2 pi i jk / n), sign = +1
  * evaluates the coefficient vector at the n-th roots of unity (Sec. 4.1, Eq. (vandprod)); unnormalised.
  * n must factor into 2, 3, 5, 7 and be at most 4096^2.  Synchronises the stream; TIKH_EINVAL otherwise. */
 int tikh_test_fft(int64_t n, void* data, int sign, void* stream);
+
+/* tikh_test_fft in FP32: n complex64 values (interleaved float re, im) transformed in place by the same
+ * engine instantiated for complex64 (FP32 butterflies and twiddles rounded from the FP64 tables), as used
+ * by the recursion's FFT stages under TIKH_PREC_FP32 / TIKH_PREC_FP32_REFINE. */
+int tikh_test_fft32(int64_t n, void* data, int sign, void* stream);
+
+/* The leaf's reciprocal of a pivot magnitude on n positive normal doubles (device arrays d, out; biased
+ * exponent of each d in (2, 2044)): an FP32 approximate-reciprocal seed of d's 23 leading mantissa bits
+ * refined by one third-order step of the series 1/d = y0 (1 + e + e^2 + ...), e = 1 - d y0, which is
+ * within FP64 rounding of 1/d.  Synchronises the stream.  TIKH_EINVAL for n < 1 or a NULL pointer. */
+int tikh_test_rcp(int64_t n, const double* d, double* out, void* stream);
 
 /* One leaf of Algorithm 1: the serial single-point construction of Eq. (spbasis) (Sec. 4.3) with
  * condition pivoting and difficult-point deferral (Sec. 5) over K <= 64 conditions.

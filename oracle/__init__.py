@@ -214,6 +214,14 @@ def solve_gramian(g, lcol, lrow, y, nlim=32, eps_diff=1e-8, mode=AUTO, m_min=0, 
     return x, st.as_dict()
 
 
+def nufft_gramian(f, w, X, n):
+    """Sec. 7.4: first column g_d = sum_k w_k exp(+2 pi i f_k d) of the weighted Gramian A^H W A and the
+    right-hand side y_s = sum_k w_k X_k exp(+2 pi i f_k s), d, s < n, by the plain direct sums."""
+    E = np.exp(2j * np.pi * np.outer(np.arange(n), np.asarray(f, dtype=np.float64)))
+    w = np.asarray(w, dtype=np.float64)
+    return E @ w, E @ (w * _c128(X))
+
+
 def hermitian_toeplitz_dense(g):
     """G[i, j] = g_{i-j} with g_{-d} = conj(g_d)."""
     g = _c128(g)

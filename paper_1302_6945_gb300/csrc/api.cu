@@ -65,6 +65,17 @@ cd* twiddle(Plan& P, int64_t L, int& err) {
   return t;
 }
 
+cf* twiddle32(Plan& P, int64_t L, int& err) {
+  auto it = P.twiddle32_of_len.find(L);
+  if (it != P.twiddle32_of_len.end()) return it->second;
+  cd* src = twiddle(P, L, err);
+  cf* t = (cf*)dalloc(P, sizeof(cf) * (size_t)L, err);
+  if (err) return nullptr;
+  if (launch_to_cf(src, t, L, P.stream) < 0) { err = TIKH_ECUDA; return nullptr; }
+  P.twiddle32_of_len[L] = t;
+  return t;
+}
+
 int fft_index(Plan& P, int64_t L, int& err) {
   auto it = P.fft_of_len.find(L);
   if (it != P.fft_of_len.end()) return it->second;
@@ -84,6 +95,15 @@ int fft_index(Plan& P, int64_t L, int& err) {
     f.d1.tw = twiddle(P, L1, err);
     f.d2.tw = twiddle(P, L2, err);
     f.twL = twiddle(P, L, err);
+  }
+  if (P.stage32 && !err) {  // complex64 tables for the FP32 stages
+    if (!f.four) {
+      f.d1.tw32 = twiddle32(P, L, err);
+    } else {
+      f.d1.tw32 = twiddle32(P, f.L1, err);
+      f.d2.tw32 = twiddle32(P, f.L2, err);
+      f.twL32 = twiddle32(P, L, err);
+    }
   }
   if (err) return -1;
   P.ffts.push_back(f);
@@ -112,24 +132,24 @@ void waterfill(int* d, int64_t C) {
   }
 }
 
-void build_steps(Plan& P, int depth, int64_t a, int64_t s, int64_t L, int side, int* sd, uint64_t& pending,
-                 int64_t slack, int& err) {
-  if (err) return;
+// The DFS of Algorithm 1 for one shape: leaves, evaluations and products in execution order, with the
+// product transform length predicted from the shape's tau-degrees (water-filling) plus slack.
+void build_steps(Plan& P, std::vector<Step>& out, int depth, int64_t a, int64_t s, int64_t L, int side, int* sd,
+                 uint64_t& pending, int64_t slack) {
   if (depth == P.p) {
     Step st{STEP_LEAF, depth, side, a, s, L, -1, 0, pending};
     pending = 0;
     waterfill(sd, 4 * L);
-    P.sched.push_back(st);
+    out.push_back(st);
     return;
   }
   int din[5];
   memcpy(din, sd, sizeof(din));
   pending |= (1ULL << depth);
-  build_steps(P, depth + 1, a, 2 * s, L / 2, 0, sd, pending, slack, err);
-  Step ev{STEP_EVAL, depth, side, a, s, L, fft_index(P, L / 2, err), 0, 0};
-  P.sched.push_back(ev);
-  P.Lrmax = std::max(P.Lrmax, L / 2);
-  build_steps(P, depth + 1, a + s, 2 * s, L / 2, 1, sd, pending, slack, err);
+  build_steps(P, out, depth + 1, a, 2 * s, L / 2, 0, sd, pending, slack);
+  Step ev{STEP_EVAL, depth, side, a, s, L, -1, 0, 0};
+  out.push_back(ev);
+  build_steps(P, out, depth + 1, a + s, 2 * s, L / 2, 1, sd, pending, slack);
   int D = -1;
   for (int i = 0; i < 5; ++i)
     for (int j = 0; j < 5; ++j) D = std::max(D, entry_bound_host(din, sd, i, j));
@@ -137,22 +157,82 @@ void build_steps(Plan& P, int depth, int64_t a, int64_t s, int64_t L, int side, 
   // slack say, and each child's stored entries are at most 2L + 1 long (they are trimmed to the same
   // kind of bound), which the transform must hold
   int64_t Pn = smooth_at_least(std::max<int64_t>(2 * L + 1, std::min<int64_t>((int64_t)D + 1 + slack, 4 * L + 1)));
-  Step pr{STEP_PROD, depth, side, a, s, L, fft_index(P, Pn, err), Pn, 0};
-  P.sched.push_back(pr);
-  P.Pmax = std::max(P.Pmax, Pn);
+  Step pr{STEP_PROD, depth, side, a, s, L, -1, Pn, 0};
+  out.push_back(pr);
 }
 
-// (re)build the schedule, the product scratch and the basis buffers for the current slack
+// Algorithmic FLOPs of one item's core solve by kind (leaf, evaluation, product, other), the part the FFT
+// stages run in FP32 kept apart: a length-L complex FFT counts 5 L log2 L, a complex multiply-add 8.
+//  leaf of K = 4L conditions: 50 K^2 + 90 K (the pivot chain, sum over steps of 60 per remaining
+//    condition and 60 per step, plus the basis rebuild, about 20 K^2);
+//  evaluation at Lr = L/2 nodes per coset: direct, 2 Lr nodes x 25 entries x len Horner steps; FFT, the
+//    twist-fold (50 x len) and 50 transforms of Lr; both plus the update, 2 Lr nodes x 2 rows x 25 CMACs;
+//    len = 2L/5 + 1 is the mean entry length of the left child (its 2L conditions raise each column by 2L/5);
+//  product of length P: direct, 25 outputs x 5 convolutions of len x len; FFT, 75 transforms of P and
+//    25 x 5 pointwise CMACs per bin;
+//  other: the four length-N transforms of the extension, right-hand side and conditions.
+void model_flops(Plan& P) {
+  auto fft = [](double L) { return L > 1 ? 5.0 * L * std::log2(L) : 0.0; };
+  for (int k = 0; k < 4; ++k) P.last.model_flops[k] = P.last.model_flops_fp32[k] = 0.0;
+  for (const Step& st : P.sched) {
+    const double L = (double)st.L, Lr = L / 2, len = 2.0 * L / 5.0 + 1.0;
+    if (st.kind == STEP_LEAF) {
+      const double K = 4 * L;
+      P.last.model_flops[0] += 50 * K * K + 90 * K;
+    } else if (st.kind == STEP_EVAL) {
+      const double upd = 2 * Lr * 2 * 25 * 8;
+      if (st.L / 2 <= P.eval_direct_max) {
+        P.last.model_flops[1] += 2 * Lr * 25 * len * 8 + upd;
+      } else {
+        const double f = 50 * len * 8 + 50 * fft(Lr) + upd;
+        P.last.model_flops[1] += f;
+        if (P.stage32) P.last.model_flops_fp32[1] += f;
+      }
+    } else {
+      const double Pl = (double)st.P;
+      if (st.P <= P.prod_direct_max) {
+        P.last.model_flops[2] += 25 * 5 * len * len * 8;
+      } else {
+        const double f = 75 * fft(Pl) + 25 * 5 * Pl * 8;
+        P.last.model_flops[2] += f;
+        if (P.stage32) P.last.model_flops_fp32[2] += f;
+      }
+    }
+  }
+  P.last.model_flops[3] = 4 * fft((double)P.N);
+}
+
+// (re)build the schedule for every shape the plan serves (the step list is the same for all of them --
+// it depends on N, p, M only -- and each product takes the largest length any shape predicts), then
+// the FFT plans, the product scratch and the basis buffers
 int make_schedule(Plan& P) {
   int err = 0;
   const size_t nb = (size_t)P.batch_max;
   P.sched.clear();
-  int sd[5] = {-(int)(P.cn - 1), -(int)(P.cm - 1), -(int)(P.cm + P.k - 2), -(int)(P.cn + P.k - 2), 0};
-  uint64_t pending = 0;
+  for (const Shape& sh : P.shapes) {
+    std::vector<Step> st;
+    int sd[5] = {-(int)(sh.cn - 1), -(int)(sh.cm - 1), -(int)(sh.cm + sh.k - 2), -(int)(sh.cn + sh.k - 2), 0};
+    uint64_t pending = 0;
+    const int64_t slack = (int64_t)P.slack_mult * (sh.k + 2 * P.M + 4);
+    build_steps(P, st, 0, 0, 2, P.N / 2, 0, sd, pending, slack);
+    if (P.sched.empty()) {
+      P.sched = st;
+    } else {
+      for (size_t i = 0; i < st.size(); ++i) P.sched[i].P = std::max(P.sched[i].P, st[i].P);
+    }
+  }
   int64_t oldP = P.Pmax;
-  int64_t slack = (int64_t)P.slack_mult * (P.k + 2 * P.M + 4);
-  build_steps(P, 0, 0, 2, P.N / 2, 0, sd, pending, slack, err);
+  for (Step& st : P.sched) {
+    if (st.kind == STEP_PROD) P.Pmax = std::max(P.Pmax, st.P);
+    if (st.kind == STEP_EVAL) {
+      st.fft = fft_index(P, st.L / 2, err);
+      P.Lrmax = std::max(P.Lrmax, st.L / 2);
+    } else if (st.kind == STEP_PROD) {
+      st.fft = fft_index(P, st.P, err);
+    }
+  }
   if (err) return err;
+  model_flops(P);
   if (P.Pmax > oldP || !P.FA) {
     size_t n25 = 25 * (size_t)std::max<int64_t>(P.Pmax, 1) * nb;
     P.FA = (cd*)dalloc(P, sizeof(cd) * n25, err);
@@ -184,9 +264,6 @@ int make_schedule(Plan& P) {
   return err;
 }
 
-// the root cause first: a wait that gave up or a non-finite input invalidates everything after it; a
-// full deferred list cannot be fixed by re-planning; a degree overflow (retried with more slack) can
-// itself cause the final degree pattern or extraction to fail
 int status_to_code(int st) {
   if (st & ST_WAIT) return TIKH_ETIMEOUT;
   if (st & ST_INPUT) return TIKH_ENUMERIC;
@@ -277,40 +354,45 @@ int enqueue_core_refined(Plan& P, int64_t& nl) {
   return TIKH_OK;
 }
 
-int enqueue_prologue(Plan& P, const UserArrays& u, int rhs_is_y, const double* lams, int nb, int64_t& nl) {
+// items and lambdas of a call into the device tables at offset `off` (outside any graph: a replay reads
+// whatever the tables hold)
+int stage_items(Plan& P, const ItemDev* items, const double* lams, int nb, int64_t off) {
+  if (nb < 1 || off + nb > P.item_cap) return TIKH_EINVAL;
+  if (cudaMemcpyAsync(P.items_base + off, items, sizeof(ItemDev) * (size_t)nb, cudaMemcpyHostToDevice, P.stream) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(P.lam_base + off, lams, sizeof(double) * (size_t)nb, cudaMemcpyHostToDevice, P.stream) !=
+          cudaSuccess)
+    return TIKH_ECUDA;
+  return TIKH_OK;
+}
+
+int enqueue_prologue(Plan& P, int rhs_is_y, int nb, int64_t& nl) {
   int r;
   if (nb < 1 || nb > P.batch_max) return TIKH_EINVAL;
   P.nb = nb;
-  if (lams &&
-      cudaMemcpyAsync(P.lam, lams, sizeof(double) * (size_t)nb, cudaMemcpyHostToDevice, P.stream) != cudaSuccess)
-    return TIKH_ECUDA;
-  if (cudaMemsetAsync(P.status, 0, sizeof(int), P.stream) != cudaSuccess) return TIKH_ECUDA;
+  if (!P.keep_status && cudaMemsetAsync(P.status, 0, sizeof(int), P.stream) != cudaSuccess) return TIKH_ECUDA;
   ProfScope ps(P, 3);
-  if ((r = launch_spectrum(P, u, rhs_is_y)) < 0) return r;
+  if ((r = launch_spectrum(P, rhs_is_y)) < 0) return r;
   nl += r;
   // for m < n the core problem (T T^H + lam I) v = b takes b itself as its right-hand side
-  if ((r = launch_rhs(P, u, P.dual ? 1 : rhs_is_y)) < 0) return r;
+  if ((r = launch_rhs(P, P.dual ? 1 : rhs_is_y)) < 0) return r;
   nl += r;
   return TIKH_OK;
 }
 
-int enqueue_solve(Plan& P, const UserArrays& u, int rhs_is_y, const double* lams, int nb) {
+// the whole solve of the nb staged items (P.items, P.lam) on the plan's stream
+int enqueue_solve(Plan& P, int rhs_is_y, int nb) {
   int64_t nl = 0;
   int r;
-  if ((r = enqueue_prologue(P, u, rhs_is_y, lams, nb, nl)) < 0) return r;
+  if ((r = enqueue_prologue(P, rhs_is_y, nb, nl)) < 0) return r;
   if ((r = enqueue_core_refined(P, nl)) < 0) return r;
   {
     ProfScope ps(P, 3);
-    if ((r = launch_output(P, P.xcore, u)) < 0) return r;
+    if ((r = launch_output(P, P.xcore)) < 0) return r;
   }
   nl += r;
   P.launches = nl;
   return TIKH_OK;
-}
-
-bool same_args(const UserArrays& a, const UserArrays& b) {
-  return a.col == b.col && a.row == b.row && a.rhs == b.rhs && a.x == b.x && a.col_stride == b.col_stride &&
-         a.row_stride == b.row_stride && a.rhs_stride == b.rhs_stride && a.x_stride == b.x_stride;
 }
 
 void drop_graph(Plan& P) {
@@ -319,27 +401,26 @@ void drop_graph(Plan& P) {
   P.graph_nb = 0;
 }
 
-// the solve as a CUDA graph: lambda is uploaded outside the graph; the rest (status reset, transform,
-// every node of the recursion, refinement, output) is captured once per argument set and replayed
-int enqueue_solve_graph(Plan& P, const UserArrays& u, int rhs_is_y, const double* lams, int nb) {
+// the solve as a CUDA graph: the item and lambda tables are staged outside the graph; the rest (status
+// reset, transform, every node of the recursion, refinement, output) is captured once per item count
+// and replayed -- it reads the arrays and sizes of each call from the tables
+int enqueue_solve_graph(Plan& P, int rhs_is_y, int nb) {
   if (nb < 1 || nb > P.batch_max) return TIKH_EINVAL;
-  if (cudaMemcpyAsync(P.lam, lams, sizeof(double) * (size_t)nb, cudaMemcpyHostToDevice, P.stream) != cudaSuccess)
-    return TIKH_ECUDA;
-  if (!P.graph_exec || P.graph_nb != nb || P.graph_rhs_is_y != rhs_is_y || !same_args(P.graph_key, u)) {
+  if (!P.graph_exec || P.graph_nb != nb || P.graph_rhs_is_y != rhs_is_y) {
     drop_graph(P);
     cudaGraph_t g = nullptr;
     if (cudaStreamBeginCapture(P.stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
       cudaGetLastError();  // e.g. the legacy default stream, which cannot be captured
       P.opts.graph = 0;
-      return enqueue_solve(P, u, rhs_is_y, nullptr, nb);
+      return enqueue_solve(P, rhs_is_y, nb);
     }
-    int rc = enqueue_solve(P, u, rhs_is_y, nullptr, nb);
+    int rc = enqueue_solve(P, rhs_is_y, nb);
     cudaError_t ce = cudaStreamEndCapture(P.stream, &g);
     if (rc || ce != cudaSuccess || !g) {
       cudaGetLastError();
       if (g) cudaGraphDestroy(g);
       P.opts.graph = 0;  // capture not possible here: plain stream launches from now on
-      return rc ? rc : enqueue_solve(P, u, rhs_is_y, nullptr, nb);
+      return rc ? rc : enqueue_solve(P, rhs_is_y, nb);
     }
     ce = cudaGraphInstantiate(&P.graph_exec, g, 0);
     cudaGraphDestroy(g);
@@ -347,9 +428,8 @@ int enqueue_solve_graph(Plan& P, const UserArrays& u, int rhs_is_y, const double
       cudaGetLastError();
       P.graph_exec = nullptr;
       P.opts.graph = 0;
-      return enqueue_solve(P, u, rhs_is_y, nullptr, nb);
+      return enqueue_solve(P, rhs_is_y, nb);
     }
-    P.graph_key = u;
     P.graph_nb = nb;
     P.graph_rhs_is_y = rhs_is_y;
   }
@@ -357,14 +437,14 @@ int enqueue_solve_graph(Plan& P, const UserArrays& u, int rhs_is_y, const double
   return cudaGraphLaunch(P.graph_exec, P.stream) == cudaSuccess ? TIKH_OK : TIKH_ECUDA;
 }
 
-int enqueue_any(Plan& P, const UserArrays& u, int rhs_is_y, const double* lams, int nb) {
+int enqueue_any(Plan& P, int rhs_is_y, int nb) {
   P.last.graph = 0;
   if (P.opts.graph && !P.prof_leaf) {
-    int rc = enqueue_solve_graph(P, u, rhs_is_y, lams, nb);
+    int rc = enqueue_solve_graph(P, rhs_is_y, nb);
     P.last.graph = P.graph_exec && P.opts.graph ? 1 : 0;
     return rc;
   }
-  return enqueue_solve(P, u, rhs_is_y, lams, nb);
+  return enqueue_solve(P, rhs_is_y, nb);
 }
 
 int sync_status(Plan& P) {
@@ -385,15 +465,18 @@ int sync_status(Plan& P) {
   P.last.refine_steps = P.opts.refine_steps;
   P.last.batch = P.nb;
   P.last.rel_residual = -1.0;
+  P.last.last_correction = -1.0;
   if (P.opts.refine_steps > 0) {  // largest relative residual of the batch
     std::vector<double> nr(4 * (size_t)P.nb);
     cudaMemcpy(nr.data(), P.norms, sizeof(double) * nr.size(), cudaMemcpyDeviceToHost);
-    double worst = 0.0;
+    double worst = 0.0, corr = 0.0;
     for (int b = 0; b < P.nb; ++b) {
       double v = nr[4 * b + 1] > 0.0 ? sqrt(nr[4 * b] / nr[4 * b + 1]) : sqrt(nr[4 * b]);
       worst = std::max(worst, v);
+      corr = std::max(corr, nr[4 * b + 3] > 0.0 ? sqrt(nr[4 * b + 2] / nr[4 * b + 3]) : 0.0);
     }
     P.last.rel_residual = worst;
+    P.last.last_correction = corr;
   }
   if (P.prof_leaf) {  // durations of the event pairs recorded since the last sync, accumulated until
                       // tikh_set_profiling re-arms it
@@ -414,16 +497,28 @@ int sync_status(Plan& P) {
   }
   int zero = 0;
   cudaMemcpy(P.status, &zero, sizeof(int), cudaMemcpyHostToDevice);
-  return status_to_code(st);
+  int code = status_to_code(st);
+  // the refinement's tolerance (opts.refine_tol > 0): a residual still above it is reported
+  if (code == TIKH_OK && P.opts.refine_tol > 0.0 && P.opts.refine_steps > 0 &&
+      !(P.last.rel_residual <= P.opts.refine_tol))
+    code = TIKH_ENOTCONVERGED;
+  return code;
 }
 
-int solve_with_retry(Plan& P, const UserArrays& u, int rhs_is_y, const double* lams, int nb, void* x_host,
-                     size_t xbytes) {
+// stage the items, solve, optionally copy x (device x_dev) back to the host, synchronise; re-plan with
+// more degree slack and re-run after TIKH_EDEGREE
+int solve_with_retry(Plan& P, const std::vector<ItemDev>& items, const double* lams, int rhs_is_y, void* x_host,
+                     const void* x_dev, size_t xbytes) {
   P.last.retries = 0;
+  const int nb = (int)items.size();
+  P.items = P.items_base;
+  P.lam = P.lam_base;
+  P.keep_status = false;
   for (int attempt = 0;; ++attempt) {
-    int rc = enqueue_any(P, u, rhs_is_y, lams, nb);
+    int rc = stage_items(P, items.data(), lams, nb, 0);
     if (rc) return rc;
-    if (x_host && cudaMemcpyAsync(x_host, u.x, xbytes, cudaMemcpyDeviceToHost, P.stream) != cudaSuccess)
+    if ((rc = enqueue_any(P, rhs_is_y, nb))) return rc;
+    if (x_host && cudaMemcpyAsync(x_host, x_dev, xbytes, cudaMemcpyDeviceToHost, P.stream) != cudaSuccess)
       return TIKH_ECUDA;
     rc = sync_status(P);
     if (rc != TIKH_EDEGREE || attempt >= 3) return rc;
@@ -436,72 +531,131 @@ int solve_with_retry(Plan& P, const UserArrays& u, int rhs_is_y, const double* l
 
 bool valid_lambda(double lam) { return lam > 0.0 && lam < 1e300; }
 
-UserArrays single(const Plan& P, const void* col, const void* row, const void* rhs, void* x) {
-  UserArrays u;
-  u.col = col;
-  u.row = row;
-  u.rhs = rhs;
-  u.x = x;
-  return u;
+ItemDev make_item(const Shape& sh, const void* col, const void* row, const void* rhs, void* x) {
+  ItemDev it;
+  memset(&it, 0, sizeof(it));  // gram = null: the l2 problem
+  it.col = col;
+  it.row = row;
+  it.rhs = rhs;
+  it.x = x;
+  it.m = sh.m;
+  it.n = sh.n;
+  it.cm = sh.cm;
+  it.cn = sh.cn;
+  it.k = sh.k;
+  it.dual = sh.dual;
+  return it;
 }
 
-}  // namespace
+std::vector<ItemDev> single(const Plan& P, const void* col, const void* row, const void* rhs, void* x) {
+  return std::vector<ItemDev>(1, make_item(P.shapes[0], col, row, rhs, x));
+}
 
-extern "C" {
-
-int tikh_plan_create(tikh_plan* out, int64_t m, int64_t n, int dtype, int prec, const tikh_opts* opts, void* stream) {
-  if (!out) return TIKH_EINVAL;
-  *out = nullptr;
-  if (m < 1 || n < 1 || (dtype != TIKH_R64 && dtype != TIKH_C128) || prec != TIKH_PREC_FP64) return TIKH_EINVAL;
-  tikh_opts o{32, 0, 0, 1e-8, 4096, 0, 1, 0, 0, 0, 0};
-  if (opts) o = *opts;
-  if (o.n_lim < 4 || o.n_lim > 64 || o.m_min < 0 || o.m_min > 32 || (o.fill != 0 && o.fill != 1) ||
-      !(o.eps_diff >= 0.0) || o.max_difficult < 1 || o.max_difficult > (1 << 20) || o.refine_steps < 0 ||
-      o.refine_steps > 8 || o.batch < 1 || o.batch > 65535 || (o.graph != 0 && o.graph != 1) ||
-      o.prod_direct_max < 0 || o.prod_direct_max > 4096 || o.eval_direct_max < 0 || o.eval_direct_max > 4096 ||
-      o.wait_polls < 0 || o.wait_polls > (1 << 30))
-    return TIKH_EINVAL;
-  tikh_plan h = new (std::nothrow) tikh_plan_s;
-  if (!h) return TIKH_ENOMEM;
-  Plan& P = h->P;
-  P.m = m;
-  P.n = n;
-  P.dtype = dtype;
-  P.opts = o;
-  P.batch_max = o.batch;
-  // direct vs FFT forms of steps 2 and 4: a single problem is latency-bound at small nodes (direct forms
-  // spread over more SMs with short chains); a batch is FP64-throughput-bound, where the O(P^2) direct
-  // product loses to the O(P log P) FFT product at much smaller P (measured on GB300)
-  P.prod_direct_max = o.prod_direct_max > 0 ? o.prod_direct_max : (o.batch == 1 ? 360 : BATCH_PROD_DIRECT_MAX);
-  P.eval_direct_max = o.eval_direct_max > 0 ? o.eval_direct_max : (o.batch == 1 ? 80 : BATCH_EVAL_DIRECT_MAX);
-  P.wait_polls = o.wait_polls > 0 ? o.wait_polls : (1 << 24);
-  P.stream = (cudaStream_t)stream;
-  P.dual = m < n ? 1 : 0;
-  P.cm = P.dual ? n : m;
-  P.cn = P.dual ? m : n;
-  // Algorithm 2 (reading: two condition sets, paired interleaving; M even, 7-smooth)
-  int64_t Nt = P.cm + P.cn - 1, Mv = Nt;
+// Algorithm 2 (reading: two condition sets, paired interleaving; M even, 7-smooth) for the core problem
+// cm x cn: halve M while 2M > N_lim, round up to even and 7-smooth; N = 2^p M, k = N - (cm + cn - 1)
+bool alg2(int64_t cm, int64_t cn, const tikh_opts& o, int64_t& N, int64_t& M, int& p) {
+  int64_t Nt = cm + cn - 1, Mv = Nt;
   int pv = 0;
   while (2 * Mv > o.n_lim) { ++pv; Mv = (Mv + 1) / 2; }
   if (Mv % 2) ++Mv;
   if (Mv < o.m_min) Mv = o.m_min + (o.m_min % 2);
   while (!is_7smooth(Mv)) Mv += 2;
-  P.M = Mv;
-  P.p = pv;
-  P.N = Mv << pv;
-  P.k = P.N - Nt;
-  if (pv >= MAX_DEPTH - 1 || 4 * (Mv / 2) > 64 || P.N > (int64_t)1 << 31) { delete h; return TIKH_EINVAL; }
+  M = Mv;
+  p = pv;
+  N = Mv << pv;
+  return !(pv >= MAX_DEPTH - 1 || 4 * (Mv / 2) > 64 || N > (int64_t)1 << 31);
+}
 
+bool valid_prec(int prec) {
+  return prec == TIKH_PREC_FP64 || prec == TIKH_PREC_FP32_REFINE || prec == TIKH_PREC_FP32;
+}
+
+bool valid_opts(const tikh_opts& o) {
+  return !(o.n_lim < 4 || o.n_lim > 64 || o.m_min < 0 || o.m_min > 32 || (o.fill != 0 && o.fill != 1) ||
+           !(o.eps_diff >= 0.0) || o.max_difficult < 1 || o.max_difficult > (1 << 20) || o.refine_steps < 0 ||
+           o.refine_steps > 8 || o.batch < 1 || o.batch > 65535 || (o.graph != 0 && o.graph != 1) ||
+           o.prod_direct_max < 0 || o.prod_direct_max > 4096 || o.eval_direct_max < 0 || o.eval_direct_max > 4096 ||
+           o.wait_polls < 0 || o.wait_polls > (1 << 30) || !(o.refine_tol >= 0.0));
+}
+
+Shape core_shape(int64_t m, int64_t n, int64_t N) {
+  Shape sh;
+  sh.m = m;
+  sh.n = n;
+  sh.dual = m < n ? 1 : 0;
+  sh.cm = sh.dual ? n : m;
+  sh.cn = sh.dual ? m : n;
+  sh.k = N - (sh.cm + sh.cn - 1);
+  return sh;
+}
+
+void set_profiling(Plan& P, int flags) {
+  P.prof_leaf = flags & 3;
+  P.ev_used = 0;
+  P.last.prof_leaf_ms = 0.0;
+  P.last.prof_leaf_launches = 0;
+  for (int k = 0; k < 4; ++k) {
+    P.last.prof_kind_ms[k] = 0.0;
+    P.last.prof_kind_count[k] = 0;
+  }
+}
+
+void free_plan(Plan& P) {
+  cudaStreamSynchronize(P.stream);
+  drop_graph(P);
+  for (cudaEvent_t e : P.ev_pool) cudaEventDestroy(e);
+  P.ev_pool.clear();
+  for (void* p : P.allocs) cudaFree(p);
+  P.allocs.clear();
+}
+
+// Plan for problems of the given shapes (all sharing N, M, p and the dual flag), up to o.batch items per
+// call: schedule, FFT plans, twiddles and every device buffer.  P.m, P.n, P.cm, P.cn are the largest
+// over the shapes (buffer strides); P.k is that of the first shape.
+int plan_setup(Plan& P, const std::vector<Shape>& shapes, int64_t N, int64_t M, int p, int dtype, int prec,
+               const tikh_opts& o, cudaStream_t stream, int64_t item_cap) {
+  P.dtype = dtype;
+  P.prec = prec;
+  P.stage32 = prec != TIKH_PREC_FP64;
+  P.opts = o;
+  // the FP32 pattern refines in FP64: two corrections unless the caller asks for a number
+  if (prec == TIKH_PREC_FP32_REFINE && P.opts.refine_steps == 0) P.opts.refine_steps = 2;
+  P.batch_max = o.batch;
+  // direct vs FFT forms of steps 2 and 4: a single problem is latency-bound at small nodes (direct forms
+  // spread over more SMs with short chains); a batch is FP64-throughput-bound, where the O(P^2) direct
+  // product loses to the O(P log P) FFT product at much smaller P (measured on GB300)
+  // product; with FP32 stages the small nodes stay on the FP64 direct forms whatever the batch: the FP32 FFT
+  // forms at the many small nodes dominate the error (measured: 1e-4 .. divergence in batches with the batch
+  // thresholds, 3e-5 per solve with these)
+  const bool wide = o.batch == 1 || prec != TIKH_PREC_FP64;
+  P.prod_direct_max = o.prod_direct_max > 0 ? o.prod_direct_max : (wide ? 360 : BATCH_PROD_DIRECT_MAX);
+  P.eval_direct_max = o.eval_direct_max > 0 ? o.eval_direct_max : (wide ? 80 : BATCH_EVAL_DIRECT_MAX);
+  P.wait_polls = o.wait_polls > 0 ? o.wait_polls : (1 << 24);
+  P.stream = stream;
+  P.shapes = shapes;
+  P.dual = shapes[0].dual;
+  P.N = N;
+  P.M = M;
+  P.p = p;
+  P.k = shapes[0].k;
+  P.m = P.n = P.cm = P.cn = 0;
+  for (const Shape& sh : shapes) {
+    P.m = std::max(P.m, sh.m);
+    P.n = std::max(P.n, sh.n);
+    P.cm = std::max(P.cm, sh.cm);
+    P.cn = std::max(P.cn, sh.cn);
+  }
   int err = 0;
-  const size_t N = (size_t)P.N, nb = (size_t)P.batch_max;
+  const size_t nb = (size_t)P.batch_max;
   if (fft_index(P, P.N, err) < 0 && !err) err = TIKH_EINVAL;
-  P.wN = P.twiddle_of_len[P.N];
-  P.specT = (cd*)dalloc(P, sizeof(cd) * N * nb, err);
-  P.work = (cd*)dalloc(P, sizeof(cd) * N * nb, err);
-  P.work2 = (cd*)dalloc(P, sizeof(cd) * N * nb, err);
-  P.ftmpN = (cd*)dalloc(P, sizeof(cd) * N * nb, err);
-  P.R = (cd*)dalloc(P, sizeof(cd) * 10 * N * nb, err);
-  P.Phi = (cd*)dalloc(P, sizeof(cd) * 10 * N * nb, err);
+  P.wN = err ? nullptr : P.twiddle_of_len[P.N];
+  if (P.stage32 && !err) P.wN32 = twiddle32(P, P.N, err);
+  P.specT = (cd*)dalloc(P, sizeof(cd) * (size_t)N * nb, err);
+  P.work = (cd*)dalloc(P, sizeof(cd) * (size_t)N * nb, err);
+  P.work2 = (cd*)dalloc(P, sizeof(cd) * (size_t)N * nb, err);
+  P.ftmpN = (cd*)dalloc(P, sizeof(cd) * (size_t)N * nb, err);
+  P.R = (cd*)dalloc(P, sizeof(cd) * 10 * (size_t)N * nb, err);
+  P.Phi = (cd*)dalloc(P, sizeof(cd) * 10 * (size_t)N * nb, err);
   P.delta = (int*)dalloc(P, sizeof(int) * 8 * nb, err);
   P.dstack = (int*)dalloc(P, sizeof(int) * 5 * MAX_DEPTH * nb, err);
   P.status = (int*)dalloc(P, sizeof(int) * 4, err);
@@ -511,7 +665,11 @@ int tikh_plan_create(tikh_plan* out, int64_t m, int64_t n, int dtype, int prec, 
   P.diffr = (cd*)dalloc(P, sizeof(cd) * 5 * (size_t)o.max_difficult * nb, err);
   P.dvals = (cd*)dalloc(P, sizeof(cd) * 25 * (size_t)o.max_difficult * nb, err);
   P.peak = (unsigned long long*)dalloc(P, sizeof(unsigned long long) * nb, err);
-  P.lam = (double*)dalloc(P, sizeof(double) * nb, err);
+  P.item_cap = std::max<int64_t>(item_cap, (int64_t)nb);
+  P.items_base = (ItemDev*)dalloc(P, sizeof(ItemDev) * (size_t)P.item_cap, err);
+  P.lam_base = (double*)dalloc(P, sizeof(double) * (size_t)P.item_cap, err);
+  P.items = P.items_base;
+  P.lam = P.lam_base;
   if (!err) err = make_schedule(P);
   if (!err) {
     size_t nl = 50 * (size_t)std::max<int64_t>(P.Lrmax, 1) * nb;
@@ -522,14 +680,16 @@ int tikh_plan_create(tikh_plan* out, int64_t m, int64_t n, int dtype, int prec, 
     P.xcore = (cd*)dalloc(P, sizeof(cd) * (size_t)P.cn * nb, err);
     P.dx = (cd*)dalloc(P, sizeof(cd) * (size_t)P.cn * nb, err);
     P.norms = (double*)dalloc(P, sizeof(double) * 4 * nb, err);
-    size_t es = dtype == TIKH_C128 ? 16 : 8;
-    P.d_in = dalloc(P, es * (size_t)(2 * m + 2 * n) + 64, err);
+    if (P.gram) {
+      P.specG = (cd*)dalloc(P, sizeof(cd) * (size_t)N * nb, err);
+      P.gX = (cd*)dalloc(P, sizeof(cd) * (size_t)N * nb, err);
+      P.peakG = (unsigned long long*)dalloc(P, sizeof(unsigned long long) * nb, err);
+    }
   }
   if (!err && cudaStreamSynchronize(P.stream) != cudaSuccess) err = TIKH_ECUDA;
   if (err) {
     cudaGetLastError();
-    for (void* p : P.allocs) cudaFree(p);
-    delete h;
+    free_plan(P);
     return err;
   }
   P.last.N = P.N;
@@ -538,71 +698,344 @@ int tikh_plan_create(tikh_plan* out, int64_t m, int64_t n, int dtype, int prec, 
   P.last.p = P.p;
   P.last.dual = P.dual;
   P.last.batch = 1;
+  return TIKH_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------------------
+// batch plans: problems of different shapes and a regularisation path, in one call
+// ---------------------------------------------------------------------------------------------------
+
+// One group of a batch plan: the problems whose core problems share N (and the m < n form), solved
+// with one schedule in waves of up to W items (problem, lambda) on the group's own stream.
+struct BatchGroup {
+  Plan P;
+  std::vector<int64_t> items;  // item ids prob * nlambda + l, in wave order
+  int W = 0, waves = 0;
+  cudaEvent_t done = nullptr;
+  std::vector<cudaGraphExec_t> graphs;  // opts.graph: one captured graph per wave
+};
+
+struct tikh_batch_plan_s {
+  int nprob = 0, nlambda = 0, dtype = 0;
+  std::vector<int64_t> m, n;
+  std::vector<int> group_of;  // problem -> group
+  tikh_opts opts{};
+  cudaStream_t stream = nullptr;
+  std::vector<BatchGroup*> groups;
+  cudaEvent_t fork = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  int64_t launches = 0;
+  int prof = 0;  // profiling flags of every group; groups then run one after another on `stream`
+  tikh_batch_stats last{};
+};
+
+namespace {
+
+void drop_wave_graphs(BatchGroup* g) {
+  for (cudaGraphExec_t e : g->graphs)
+    if (e) cudaGraphExecDestroy(e);
+  g->graphs.clear();
+}
+
+void batch_free(tikh_batch_plan h) {
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  for (BatchGroup* g : h->groups) {
+    drop_wave_graphs(g);
+    free_plan(g->P);
+    if (g->done) cudaEventDestroy(g->done);
+    if (g->P.stream) cudaStreamDestroy(g->P.stream);
+    delete g;
+  }
+  if (h->fork) cudaEventDestroy(h->fork);
+  delete h;
+}
+
+// every wave of every group, each group on its own stream forked from and joined to the plan's stream
+int batch_enqueue(tikh_batch_plan h) {
+  int64_t nl = 0;
+  if (cudaEventRecord(h->fork, h->stream) != cudaSuccess) return TIKH_ECUDA;
+  for (BatchGroup* g : h->groups) {
+    Plan& P = g->P;
+    if (h->prof) {  // profiled: every group in turn on the plan's stream
+      cudaStream_t own = P.stream;
+      P.stream = h->stream;
+      int rc = TIKH_OK;
+      for (int w = 0; w < g->waves && !rc; ++w) {
+        const int64_t off = (int64_t)w * g->W;
+        const int nb = (int)std::min<int64_t>(g->W, (int64_t)g->items.size() - off);
+        P.items = P.items_base + off;
+        P.lam = P.lam_base + off;
+        P.keep_status = w > 0;
+        rc = enqueue_solve(P, 0, nb);
+        nl += P.launches;
+      }
+      P.stream = own;
+      if (rc) return rc;
+      continue;
+    }
+    if (cudaStreamWaitEvent(P.stream, h->fork, 0) != cudaSuccess) return TIKH_ECUDA;
+    for (int w = 0; w < g->waves; ++w) {
+      const int64_t off = (int64_t)w * g->W;
+      const int nb = (int)std::min<int64_t>(g->W, (int64_t)g->items.size() - off);
+      P.items = P.items_base + off;
+      P.lam = P.lam_base + off;
+      P.keep_status = w > 0;  // the status word collects every wave's failures
+      int rc = enqueue_solve(P, 0, nb);
+      if (rc) return rc;
+      nl += P.launches;
+    }
+    if (cudaEventRecord(g->done, P.stream) != cudaSuccess || cudaStreamWaitEvent(h->stream, g->done, 0) != cudaSuccess)
+      return TIKH_ECUDA;
+  }
+  h->launches = nl;
+  return TIKH_OK;
+}
+
+void batch_drop_graph(tikh_batch_plan h) {
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  h->graph = nullptr;
+}
+
+// wave w of group g on the group's stream: its solve, or the replay of its captured graph
+int wave_capture(BatchGroup* g, int w) {
+  Plan& P = g->P;
+  const int64_t off = (int64_t)w * g->W;
+  const int nb = (int)std::min<int64_t>(g->W, (int64_t)g->items.size() - off);
+  P.items = P.items_base + off;
+  P.lam = P.lam_base + off;
+  P.keep_status = w > 0;
+  cudaGraph_t gr = nullptr;
+  if (cudaStreamBeginCapture(P.stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return TIKH_ECUDA;
+  }
+  int rc = enqueue_solve(P, 0, nb);
+  cudaError_t ce = cudaStreamEndCapture(P.stream, &gr);
+  cudaGraphExec_t ex = nullptr;
+  if (!rc && ce == cudaSuccess && gr && cudaGraphInstantiate(&ex, gr, 0) != cudaSuccess) ex = nullptr;
+  if (gr) cudaGraphDestroy(gr);
+  cudaGetLastError();
+  if (rc) return rc;
+  if (!ex) return TIKH_ECUDA;
+  g->graphs[(size_t)w] = ex;
+  return TIKH_OK;
+}
+
+// With opts.graph every wave of every group is one captured graph (each about the size of one solve's
+// schedule), replayed in order on the group's stream between the fork and join events; the first call
+// captures them.  Without it (or while profiling) the waves are stream launches.
+int batch_run(tikh_batch_plan h) {
+  h->last.graph = 0;
+  if (!h->opts.graph || h->prof) return batch_enqueue(h);
+  int64_t nl = 0;
+  for (BatchGroup* g : h->groups) {
+    if ((int)g->graphs.size() != g->waves) {
+      g->graphs.assign((size_t)g->waves, nullptr);
+      for (int w = 0; w < g->waves; ++w) {
+        int rc = wave_capture(g, w);
+        if (rc) {  // capture not possible here: plain stream launches from now on
+          drop_wave_graphs(g);
+          for (BatchGroup* q : h->groups) drop_wave_graphs(q);
+          h->opts.graph = 0;
+          return batch_enqueue(h);
+        }
+      }
+    }
+  }
+  if (cudaEventRecord(h->fork, h->stream) != cudaSuccess) return TIKH_ECUDA;
+  for (BatchGroup* g : h->groups) {
+    Plan& P = g->P;
+    if (cudaStreamWaitEvent(P.stream, h->fork, 0) != cudaSuccess) return TIKH_ECUDA;
+    for (int w = 0; w < g->waves; ++w) {
+      if (cudaGraphLaunch(g->graphs[(size_t)w], P.stream) != cudaSuccess) return TIKH_ECUDA;
+      nl += P.launches;
+    }
+    // the group's last-wave size for the status read
+    P.nb = (int)std::min<int64_t>(g->W, (int64_t)g->items.size() - (int64_t)(g->waves - 1) * g->W);
+    if (cudaEventRecord(g->done, P.stream) != cudaSuccess || cudaStreamWaitEvent(h->stream, g->done, 0) != cudaSuccess)
+      return TIKH_ECUDA;
+  }
+  h->launches = nl;
+  h->last.graph = 1;
+  return TIKH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tikh_plan_create(tikh_plan* out, int64_t m, int64_t n, int dtype, int prec, const tikh_opts* opts, void* stream) {
+  if (!out) return TIKH_EINVAL;
+  *out = nullptr;
+  if (m < 1 || n < 1 || (dtype != TIKH_R64 && dtype != TIKH_C128) || !valid_prec(prec)) return TIKH_EINVAL;
+  tikh_opts o{32, 0, 0, 1e-8, 4096, 0, 1, 0, 0, 0, 0, 0.0};
+  if (opts) o = *opts;
+  if (!valid_opts(o)) return TIKH_EINVAL;
+  const int64_t cm = std::max(m, n), cn = std::min(m, n);
+  int64_t N, M;
+  int p;
+  if (!alg2(cm, cn, o, N, M, p)) return TIKH_EINVAL;
+  tikh_plan h = new (std::nothrow) tikh_plan_s;
+  if (!h) return TIKH_ENOMEM;
+  int err = plan_setup(h->P, std::vector<Shape>(1, core_shape(m, n, N)), N, M, p, dtype, prec, o,
+                       (cudaStream_t)stream, o.batch);
+  if (err) {
+    delete h;
+    return err;
+  }
+  size_t es = dtype == TIKH_C128 ? 16 : 8;
+  h->P.d_in = dalloc(h->P, es * (size_t)(2 * m + 2 * n) + 64, err);
+  if (err) {
+    free_plan(h->P);
+    delete h;
+    return err;
+  }
   *out = h;
   return TIKH_OK;
 }
 
+int tikh_plan_create_gramian(tikh_plan* out, int64_t n, int64_t p, int dtype, int prec, const tikh_opts* opts,
+                             void* stream) {
+  if (!out) return TIKH_EINVAL;
+  *out = nullptr;
+  if (n < 1 || p < 1 || (dtype != TIKH_R64 && dtype != TIKH_C128) || !valid_prec(prec)) return TIKH_EINVAL;
+  tikh_opts o{32, 0, 0, 1e-8, 4096, 0, 1, 0, 0, 0, 0, 0.0};
+  if (opts) o = *opts;
+  if (!valid_opts(o)) return TIKH_EINVAL;
+  // Sec. 3.4: the first block row has q = max(n, p) extension rows at k = 1, so N >= q + n - 1; L takes
+  // T's place, with extension k = N - (p + n - 1)
+  int64_t N, M;
+  int pp;
+  if (!alg2(std::max(n, p), n, o, N, M, pp)) return TIKH_EINVAL;
+  Shape sh;
+  sh.m = p;
+  sh.n = n;
+  sh.cm = p;
+  sh.cn = n;
+  sh.k = N - (p + n - 1);
+  sh.dual = 0;
+  tikh_plan h = new (std::nothrow) tikh_plan_s;
+  if (!h) return TIKH_ENOMEM;
+  h->P.gram = 1;
+  int err = plan_setup(h->P, std::vector<Shape>(1, sh), N, M, pp, dtype, prec, o, (cudaStream_t)stream, o.batch);
+  if (err) {
+    delete h;
+    return err;
+  }
+  *out = h;
+  return TIKH_OK;
+}
+
+int tikh_solve_gramian(tikh_plan h, const void* g, const void* lcol, const void* lrow, const void* y, void* x) {
+  if (!h || !g || !lcol || !lrow || !y || !x || !h->P.gram) return TIKH_EINVAL;
+  std::vector<ItemDev> it = single(h->P, lcol, lrow, y, x);
+  it[0].gram = g;
+  const double zero = 0.0;  // the regularisation is in L
+  return solve_with_retry(h->P, it, &zero, 1, nullptr, nullptr, 0);
+}
+
 int tikh_solve(tikh_plan h, const void* col, const void* row, const void* b, double lambda, void* x) {
-  if (!h || !col || !row || !b || !x || !valid_lambda(lambda)) return TIKH_EINVAL;
-  return solve_with_retry(h->P, single(h->P, col, row, b, x), 0, &lambda, 1, nullptr, 0);
+  if (!h || !col || !row || !b || !x || !valid_lambda(lambda) || h->P.gram) return TIKH_EINVAL;
+  return solve_with_retry(h->P, single(h->P, col, row, b, x), &lambda, 0, nullptr, nullptr, 0);
 }
 
 int tikh_solve_async(tikh_plan h, const void* col, const void* row, const void* b, double lambda, void* x) {
-  if (!h || !col || !row || !b || !x || !valid_lambda(lambda)) return TIKH_EINVAL;
-  return enqueue_any(h->P, single(h->P, col, row, b, x), 0, &lambda, 1);
+  if (!h || !col || !row || !b || !x || !valid_lambda(lambda) || h->P.gram) return TIKH_EINVAL;
+  Plan& P = h->P;
+  P.items = P.items_base;
+  P.lam = P.lam_base;
+  P.keep_status = false;
+  std::vector<ItemDev> it = single(P, col, row, b, x);
+  int rc = stage_items(P, it.data(), &lambda, 1, 0);
+  return rc ? rc : enqueue_any(P, 0, 1);
 }
 
 int tikh_solve_normal(tikh_plan h, const void* col, const void* row, const void* y, double lambda, void* x) {
-  if (!h || !col || !row || !y || !x || !valid_lambda(lambda) || h->P.dual) return TIKH_EINVAL;
-  return solve_with_retry(h->P, single(h->P, col, row, y, x), 1, &lambda, 1, nullptr, 0);
+  if (!h || !col || !row || !y || !x || !valid_lambda(lambda) || h->P.gram || h->P.dual) return TIKH_EINVAL;
+  return solve_with_retry(h->P, single(h->P, col, row, y, x), &lambda, 1, nullptr, nullptr, 0);
 }
 
-int tikh_solve_batched(tikh_plan h, int batch, const void* col, int64_t col_stride, const void* row,
+int tikh_solve_strided(tikh_plan h, int batch, const void* col, int64_t col_stride, const void* row,
                        int64_t row_stride, const void* b, int64_t b_stride, const double* lambdas, void* x,
                        int64_t x_stride) {
-  if (!h || !col || !row || !b || !x || !lambdas || batch < 1 || batch > h->P.batch_max) return TIKH_EINVAL;
+  if (!h || !col || !row || !b || !x || !lambdas || batch < 1 || batch > h->P.batch_max || h->P.gram) return TIKH_EINVAL;
   if (col_stride < 0 || row_stride < 0 || b_stride < 0 || (batch > 1 && x_stride < h->P.n)) return TIKH_EINVAL;
   for (int i = 0; i < batch; ++i)
     if (!valid_lambda(lambdas[i])) return TIKH_EINVAL;
-  UserArrays u;
-  u.col = col;
-  u.row = row;
-  u.rhs = b;
-  u.x = x;
-  u.col_stride = col_stride;
-  u.row_stride = row_stride;
-  u.rhs_stride = b_stride;
-  u.x_stride = x_stride;
-  return solve_with_retry(h->P, u, 0, lambdas, batch, nullptr, 0);
+  const size_t es = h->P.dtype == TIKH_C128 ? 16 : 8;
+  std::vector<ItemDev> items;
+  items.reserve((size_t)batch);
+  for (int i = 0; i < batch; ++i)
+    items.push_back(make_item(h->P.shapes[0], (const char*)col + es * (size_t)(i * col_stride),
+                              (const char*)row + es * (size_t)(i * row_stride), (const char*)b + es * (size_t)(i * b_stride),
+                              (char*)x + es * (size_t)(i * x_stride)));
+  return solve_with_retry(h->P, items, lambdas, 0, nullptr, nullptr, 0);
 }
 
-int tikh_solve_grad(tikh_plan h, const void* col, const void* row, const void* b, double lambda, const void* x,
-                    const void* dLdx, void* dLdcol, void* dLdrow, void* dLdb, double* dLdlambda) {
-  if (!h || !col || !row || !b || !x || !dLdx || !dLdcol || !dLdrow || !dLdb || !dLdlambda || !valid_lambda(lambda))
-    return TIKH_EINVAL;
-  Plan& P = h->P;
-  if (P.dual) return TIKH_EINVAL;  // the adjoint is implemented for m >= n
+// the adjoint of `batch` problems: g = A^{-1} dL/dx by the superfast solve (items carry col, row and dL/dx),
+// then the gradient transforms; dL/dlambda of each problem to the host array dlam
+static int grad_run(Plan& P, const std::vector<ItemDev>& items, const double* lams, const void* x, int64_t x_stride,
+                    const void* b, int64_t b_stride, void* dcol, void* drow, void* db, int64_t out_col_stride,
+                    int64_t out_row_stride, int64_t out_b_stride, double* dlam) {
+  if (P.dual || P.gram) return TIKH_EINVAL;  // the adjoint is implemented for the l2 problem with m >= n
+  const int nb = (int)items.size();
   int err = 0;
   if (!P.gbuf) {  // adjoint workspace, allocated by the first gradient call
     P.gbuf = (cd*)dalloc(P, sizeof(cd) * (size_t)(4 * P.N + 2 * P.cm) * (size_t)P.batch_max, err);
     P.gdl = (double*)dalloc(P, sizeof(double) * (size_t)P.batch_max, err);
     if (err) return err;
   }
-  UserArrays u = single(P, col, row, dLdx, nullptr);
+  P.items = P.items_base;
+  P.lam = P.lam_base;
+  P.keep_status = false;
+  int r = stage_items(P, items.data(), lams, nb, 0);
+  if (r) return r;
   int64_t nl = 0;
-  int r;
-  if ((r = enqueue_prologue(P, u, 1, &lambda, 1, nl)) < 0) return r;  // right-hand side y = dL/dx
-  if ((r = enqueue_core_refined(P, nl)) < 0) return r;                // g = A^{-1} dL/dx
-  if ((r = launch_grad(P, x, 0, b, 0, dLdcol, 0, dLdrow, 0, dLdb, 0, P.gdl, P.gbuf)) < 0) return r;
+  if ((r = enqueue_prologue(P, 1, nb, nl)) < 0) return r;  // right-hand side y = dL/dx
+  if ((r = enqueue_core_refined(P, nl)) < 0) return r;     // g = A^{-1} dL/dx
+  if ((r = launch_grad(P, x, x_stride, b, b_stride, dcol, out_col_stride, drow, out_row_stride, db, out_b_stride, P.gdl,
+                       P.gbuf)) < 0)
+    return r;
   nl += r;
   P.launches = nl;
-  if (cudaMemcpyAsync(dLdlambda, P.gdl, sizeof(double), cudaMemcpyDeviceToHost, P.stream) != cudaSuccess)
+  if (cudaMemcpyAsync(dlam, P.gdl, sizeof(double) * (size_t)nb, cudaMemcpyDeviceToHost, P.stream) != cudaSuccess)
     return TIKH_ECUDA;
   return sync_status(P);
 }
 
+int tikh_solve_grad(tikh_plan h, const void* col, const void* row, const void* b, double lambda, const void* x,
+                    const void* dLdx, void* dLdcol, void* dLdrow, void* dLdb, double* dLdlambda) {
+  if (!h || !col || !row || !b || !x || !dLdx || !dLdcol || !dLdrow || !dLdb || !dLdlambda || !valid_lambda(lambda))
+    return TIKH_EINVAL;
+  return grad_run(h->P, single(h->P, col, row, dLdx, nullptr), &lambda, x, 0, b, 0, dLdcol, dLdrow, dLdb, 0, 0, 0,
+                  dLdlambda);
+}
+
+int tikh_solve_grad_strided(tikh_plan h, int batch, const void* col, int64_t col_stride, const void* row,
+                            int64_t row_stride, const void* b, int64_t b_stride, const double* lambdas, const void* x,
+                            int64_t x_stride, const void* dLdx, int64_t dLdx_stride, void* dLdcol, void* dLdrow,
+                            void* dLdb, double* dLdlambda) {
+  if (!h || !col || !row || !b || !x || !dLdx || !dLdcol || !dLdrow || !dLdb || !dLdlambda || !lambdas || batch < 1 ||
+      batch > h->P.batch_max)
+    return TIKH_EINVAL;
+  Plan& P = h->P;
+  if (col_stride < P.m || row_stride < P.n || b_stride < P.m || x_stride < P.n || dLdx_stride < P.n) return TIKH_EINVAL;
+  for (int i = 0; i < batch; ++i)
+    if (!valid_lambda(lambdas[i])) return TIKH_EINVAL;
+  const size_t es = P.dtype == TIKH_C128 ? 16 : 8;
+  std::vector<ItemDev> items;
+  for (int i = 0; i < batch; ++i)
+    items.push_back(make_item(P.shapes[0], (const char*)col + es * (size_t)(i * col_stride),
+                              (const char*)row + es * (size_t)(i * row_stride),
+                              (const char*)dLdx + es * (size_t)(i * dLdx_stride), nullptr));
+  return grad_run(P, items, lambdas, x, x_stride, b, b_stride, dLdcol, dLdrow, dLdb, P.m, P.n, P.m, dLdlambda);
+}
+
 int tikh_solve_host(tikh_plan h, const void* col, const void* row, const void* b, double lambda, void* x) {
-  if (!h || !col || !row || !b || !x || !valid_lambda(lambda)) return TIKH_EINVAL;
+  if (!h || !col || !row || !b || !x || !valid_lambda(lambda) || h->P.gram) return TIKH_EINVAL;
   Plan& P = h->P;
   size_t es = P.dtype == TIKH_C128 ? 16 : 8;
   char* base = (char*)P.d_in;
@@ -614,7 +1047,230 @@ int tikh_solve_host(tikh_plan h, const void* col, const void* row, const void* b
       cudaMemcpyAsync(drow, row, es * P.n, cudaMemcpyHostToDevice, P.stream) != cudaSuccess ||
       cudaMemcpyAsync(db, b, es * P.m, cudaMemcpyHostToDevice, P.stream) != cudaSuccess)
     return TIKH_ECUDA;
-  return solve_with_retry(P, single(P, dcol, drow, db, dx), 0, &lambda, 1, x, es * P.n);
+  return solve_with_retry(P, single(P, dcol, drow, db, dx), &lambda, 0, x, dx, es * P.n);
+}
+
+int tikh_batch_plan_create(tikh_batch_plan* out, int nprob, const int64_t* m, const int64_t* n, int nlambda, int dtype,
+                           int prec, const tikh_opts* opts, int64_t max_workspace_bytes, void* stream) {
+  if (!out) return TIKH_EINVAL;
+  *out = nullptr;
+  if (nprob < 1 || nlambda < 1 || !m || !n || (int64_t)nprob * nlambda > (1LL << 30) ||
+      (dtype != TIKH_R64 && dtype != TIKH_C128) || !valid_prec(prec) || max_workspace_bytes < 0)
+    return TIKH_EINVAL;
+  tikh_opts o{32, 0, 0, 1e-8, 4096, 0, 1, 0, 0, 0, 0, 0.0};
+  if (opts) o = *opts;
+  o.batch = 1;
+  if (!valid_opts(o)) return TIKH_EINVAL;
+  for (int i = 0; i < nprob; ++i)
+    if (m[i] < 1 || n[i] < 1) return TIKH_EINVAL;
+  tikh_batch_plan h = new (std::nothrow) tikh_batch_plan_s;
+  if (!h) return TIKH_ENOMEM;
+  h->nprob = nprob;
+  h->nlambda = nlambda;
+  h->dtype = dtype;
+  h->opts = o;
+  h->stream = (cudaStream_t)stream;
+  h->m.assign(m, m + nprob);
+  h->n.assign(n, n + nprob);
+  h->group_of.assign((size_t)nprob, -1);
+  // groups: problems whose core problems share (N, M, p) and the m < n form
+  struct Key { int64_t N, M; int p, dual; };
+  std::vector<Key> keys;
+  std::vector<std::vector<int>> members;
+  for (int i = 0; i < nprob; ++i) {
+    const int64_t cm = std::max(m[i], n[i]), cn = std::min(m[i], n[i]);
+    int64_t N, M;
+    int p;
+    if (!alg2(cm, cn, o, N, M, p)) { batch_free(h); return TIKH_EINVAL; }
+    const int dual = m[i] < n[i] ? 1 : 0;
+    size_t g = 0;
+    while (g < keys.size() && !(keys[g].N == N && keys[g].M == M && keys[g].p == p && keys[g].dual == dual)) ++g;
+    if (g == keys.size()) { keys.push_back(Key{N, M, p, dual}); members.emplace_back(); }
+    members[g].push_back(i);
+    h->group_of[(size_t)i] = (int)g;
+  }
+  // per-item workspace of each group, from a one-item plan of its shapes; then the wave size W of every
+  // group scaled so that the groups together fit the workspace budget
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) { cudaGetLastError(); batch_free(h); return TIKH_ECUDA; }
+  const double budget = max_workspace_bytes > 0 ? (double)max_workspace_bytes : 0.6 * (double)free_b;
+  std::vector<double> per_item(keys.size());
+  std::vector<std::vector<Shape>> gshapes(keys.size());
+  double need = 0.0;
+  for (size_t g = 0; g < keys.size(); ++g) {
+    for (int i : members[g]) {
+      Shape sh = core_shape(m[i], n[i], keys[g].N);
+      bool seen = false;
+      for (const Shape& q : gshapes[g]) seen = seen || (q.m == sh.m && q.n == sh.n);
+      if (!seen) gshapes[g].push_back(sh);
+    }
+    Plan probe;
+    tikh_opts o1 = o;
+    o1.batch = 1;
+    int err = plan_setup(probe, gshapes[g], keys[g].N, keys[g].M, keys[g].p, dtype, prec, o1, h->stream, 1);
+    if (err) { batch_free(h); return err; }
+    per_item[g] = (double)probe.bytes;
+    free_plan(probe);
+    need += per_item[g] * (double)members[g].size() * nlambda;
+  }
+  const double scale = need > budget ? budget / need : 1.0;
+  int err = 0;
+  if (cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming) != cudaSuccess) err = TIKH_ECUDA;
+  for (size_t g = 0; g < keys.size() && !err; ++g) {
+    BatchGroup* G = new (std::nothrow) BatchGroup;
+    if (!G) { err = TIKH_ENOMEM; break; }
+    h->groups.push_back(G);
+    for (int i : members[g])
+      for (int l = 0; l < nlambda; ++l) G->items.push_back((int64_t)i * nlambda + l);
+    const int64_t cnt = (int64_t)G->items.size();
+    G->W = (int)std::max<int64_t>(1, std::min<int64_t>({cnt, (int64_t)(cnt * scale), 65535}));
+    G->waves = (int)((cnt + G->W - 1) / G->W);
+    cudaStream_t gs = nullptr;
+    if (cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&G->done, cudaEventDisableTiming) != cudaSuccess) {
+      err = TIKH_ECUDA;
+      if (gs) cudaStreamDestroy(gs);
+      break;
+    }
+    G->P.stream = gs;
+    tikh_opts og = o;
+    og.batch = G->W;
+    // the direct/FFT thresholds follow the group's item count, not its wave size, so an item's arithmetic
+    // does not depend on the workspace budget
+    const bool wide = cnt == 1 || prec != TIKH_PREC_FP64;
+    if (og.prod_direct_max == 0) og.prod_direct_max = wide ? 360 : BATCH_PROD_DIRECT_MAX;
+    if (og.eval_direct_max == 0) og.eval_direct_max = wide ? 80 : BATCH_EVAL_DIRECT_MAX;
+    err = plan_setup(G->P, gshapes[g], keys[g].N, keys[g].M, keys[g].p, dtype, prec, og, gs, cnt);
+    if (err) G->P.stream = gs;  // destroyed by batch_free
+  }
+  if (err) {
+    cudaGetLastError();
+    batch_free(h);
+    return err;
+  }
+  h->last.ngroups = (int)h->groups.size();
+  for (BatchGroup* G : h->groups) {
+    h->last.max_waves = std::max(h->last.max_waves, G->waves);
+    h->last.workspace_bytes += G->P.bytes;
+  }
+  h->last.items = (int64_t)nprob * nlambda;
+  h->last.rel_residual = -1.0;
+  *out = h;
+  return TIKH_OK;
+}
+
+int tikh_solve_batched(tikh_batch_plan h, int nprob, const int64_t* m, const int64_t* n, const void* const* col,
+                       const void* const* row, const void* const* b, int nlambda, const double* lambdas,
+                       void* const* x) {
+  if (!h || !m || !n || !col || !row || !b || !lambdas || !x || nprob != h->nprob || nlambda != h->nlambda)
+    return TIKH_EINVAL;
+  for (int i = 0; i < nprob; ++i)
+    if (m[i] != h->m[(size_t)i] || n[i] != h->n[(size_t)i] || !col[i] || !row[i] || !b[i]) return TIKH_EINVAL;
+  for (int l = 0; l < nlambda; ++l)
+    if (!valid_lambda(lambdas[l])) return TIKH_EINVAL;
+  for (int64_t q = 0; q < (int64_t)nprob * nlambda; ++q)
+    if (!x[q]) return TIKH_EINVAL;
+  for (int attempt = 0;; ++attempt) {
+    // item tables of every wave of every group (outside the graph), then the forked solve
+    for (BatchGroup* G : h->groups) {
+      std::vector<ItemDev> items;
+      std::vector<double> lams;
+      items.reserve(G->items.size());
+      lams.reserve(G->items.size());
+      for (int64_t id : G->items) {
+        const int i = (int)(id / nlambda), l = (int)(id % nlambda);
+        const Shape sh = core_shape(m[i], n[i], G->P.N);
+        items.push_back(make_item(sh, col[i], row[i], b[i], x[id]));
+        lams.push_back(lambdas[l]);
+      }
+      // the group's tables are written on the plan's stream, ahead of the fork that starts the group
+      Plan& P = G->P;
+      if (cudaMemcpyAsync(P.items_base, items.data(), sizeof(ItemDev) * items.size(), cudaMemcpyHostToDevice,
+                          h->stream) != cudaSuccess ||
+          cudaMemcpyAsync(P.lam_base, lams.data(), sizeof(double) * lams.size(), cudaMemcpyHostToDevice, h->stream) !=
+              cudaSuccess)
+        return TIKH_ECUDA;
+    }
+    int rc = batch_run(h);
+    if (rc) return rc;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) { cudaGetLastError(); return TIKH_ECUDA; }
+    int worst = TIKH_OK;
+    bool degree = false;
+    h->last.rel_residual = -1.0;
+    h->last.n_difficult = 0;
+    h->last.last_correction = -1.0;
+    for (int k = 0; k < 4; ++k) h->last.model_flops[k] = h->last.model_flops_fp32[k] = 0.0;
+    for (BatchGroup* G : h->groups) {
+      if (h->prof) {  // the profiled group's events were recorded on the plan's stream
+        cudaStream_t own = G->P.stream;
+        G->P.stream = h->stream;
+        int c = sync_status(G->P);
+        G->P.stream = own;
+        if (c == TIKH_EDEGREE) degree = true;
+        else if (c && !worst) worst = c;
+      } else {
+        int c = sync_status(G->P);
+        if (c == TIKH_EDEGREE) degree = true;
+        else if (c && !worst) worst = c;
+      }
+      const tikh_stats& gl = G->P.last;
+      h->last.rel_residual = std::max(h->last.rel_residual, gl.rel_residual);
+      h->last.last_correction = std::max(h->last.last_correction, gl.last_correction);
+      h->last.n_difficult += gl.n_difficult;
+      const double cnt = (double)G->items.size();
+      for (int k = 0; k < 4; ++k) {
+        h->last.model_flops[k] += gl.model_flops[k] * cnt;
+        h->last.model_flops_fp32[k] += gl.model_flops_fp32[k] * cnt;
+      }
+    }
+    if (h->prof) {
+      for (int k = 0; k < 4; ++k) {
+        h->last.prof_kind_ms[k] = 0.0;
+        h->last.prof_kind_count[k] = 0;
+        for (BatchGroup* G : h->groups) {
+          h->last.prof_kind_ms[k] += G->P.last.prof_kind_ms[k];
+          h->last.prof_kind_count[k] += G->P.last.prof_kind_count[k];
+        }
+      }
+    }
+    h->last.kernel_launches = h->launches;
+    if (worst) return worst;
+    if (!degree) return TIKH_OK;
+    if (attempt >= 3) return TIKH_EDEGREE;
+    // a basis outgrew its planned transform: more degree slack for every group, re-plan, re-run
+    batch_drop_graph(h);
+    for (BatchGroup* G : h->groups) {
+      drop_wave_graphs(G);
+      G->P.slack_mult *= 16;
+      drop_graph(G->P);
+      if ((rc = make_schedule(G->P))) return rc;
+    }
+    h->last.retries = attempt + 1;
+  }
+}
+
+int tikh_batch_set_profiling(tikh_batch_plan h, int flags) {
+  if (!h || flags < 0 || flags > 3) return TIKH_EINVAL;
+  h->prof = flags;
+  for (BatchGroup* G : h->groups)
+    set_profiling(G->P, flags);
+  for (int k = 0; k < 4; ++k) {
+    h->last.prof_kind_ms[k] = 0.0;
+    h->last.prof_kind_count[k] = 0;
+  }
+  return TIKH_OK;
+}
+
+int tikh_batch_get_stats(tikh_batch_plan h, tikh_batch_stats* out) {
+  if (!h || !out) return TIKH_EINVAL;
+  *out = h->last;
+  out->workspace_bytes = 0;
+  for (BatchGroup* G : h->groups) out->workspace_bytes += G->P.bytes;
+  return TIKH_OK;
+}
+
+void tikh_batch_plan_destroy(tikh_batch_plan h) {
+  if (h) batch_free(h);
 }
 
 int tikh_sync(tikh_plan h) {
@@ -644,23 +1300,13 @@ int tikh_get_stats(tikh_plan h, tikh_stats* out) {
 
 int tikh_set_profiling(tikh_plan h, int flags) {
   if (!h || flags < 0 || flags > 3) return TIKH_EINVAL;
-  h->P.prof_leaf = flags & 3;
-  h->P.ev_used = 0;
-  h->P.last.prof_leaf_ms = 0.0;
-  h->P.last.prof_leaf_launches = 0;
-  for (int k = 0; k < 4; ++k) {
-    h->P.last.prof_kind_ms[k] = 0.0;
-    h->P.last.prof_kind_count[k] = 0;
-  }
+  set_profiling(h->P, flags);
   return TIKH_OK;
 }
 
 void tikh_plan_destroy(tikh_plan h) {
   if (!h) return;
-  cudaStreamSynchronize(h->P.stream);
-  drop_graph(h->P);
-  for (cudaEvent_t e : h->P.ev_pool) cudaEventDestroy(e);
-  for (void* p : h->P.allocs) cudaFree(p);
+  free_plan(h->P);
   delete h;
 }
 

@@ -2,10 +2,12 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdlib.h>
 
 namespace tikh {
 
 using cd = double2;  // complex128 as (re, im)
+using cf = float2;   // complex64 as (re, im): the recursion's FFT stages in the FP32 precision pattern
 
 __host__ __device__ __forceinline__ cd mkc(double x, double y) { return make_double2(x, y); }
 __device__ __forceinline__ cd cadd(cd a, cd b) { return mkc(a.x + b.x, a.y + b.y); }
@@ -20,6 +22,65 @@ __device__ __forceinline__ cd cscale(cd a, double s) { return mkc(a.x * s, a.y *
 __device__ __forceinline__ double cabs2(cd a) { return fma(a.x, a.x, a.y * a.y); }
 __device__ __forceinline__ bool cnonzero(cd a) { return a.x != 0.0 || a.y != 0.0; }
 
+// the same operations on complex64 (FP32 arithmetic, FP32 accumulation)
+__host__ __device__ __forceinline__ cf mkcf(float x, float y) { return make_float2(x, y); }
+__device__ __forceinline__ cf cadd(cf a, cf b) { return mkcf(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ cf csub(cf a, cf b) { return mkcf(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ cf cmul(cf a, cf b) { return mkcf(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x)); }
+__device__ __forceinline__ cf cfma(cf a, cf b, cf c) {
+  return mkcf(fmaf(a.x, b.x, fmaf(-a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, c.y)));
+}
+__device__ __forceinline__ cf cconj(cf a) { return mkcf(a.x, -a.y); }
+__device__ __forceinline__ cf cscale(cf a, float s) { return mkcf(a.x * s, a.y * s); }
+__device__ __forceinline__ cd to_cd(cf a) { return mkc((double)a.x, (double)a.y); }
+__device__ __forceinline__ cf to_cf(cd a) { return mkcf((float)a.x, (float)a.y); }
+
+// generic construction and zero of either complex type
+template <class C> __device__ __forceinline__ C czero();
+template <> __device__ __forceinline__ cd czero<cd>() { return mkc(0.0, 0.0); }
+template <> __device__ __forceinline__ cf czero<cf>() { return mkcf(0.0f, 0.0f); }
+template <class C> __device__ __forceinline__ C cfrom(cd a);
+template <> __device__ __forceinline__ cd cfrom<cd>(cd a) { return a; }
+template <> __device__ __forceinline__ cf cfrom<cf>(cd a) { return to_cf(a); }
+
+// Programmatic dependent launch.  The kernels of a solve form one long stream-ordered chain (about 65 000
+// small launches for a c2 solve).  Launched with programmatic stream serialisation, a kernel lets its
+// successor be scheduled as soon as all its own CTAs have started, and waits for its predecessor to finish
+// (with its memory visible) before reading anything: the successor's launch latency overlaps the running
+// kernel, while every kernel still sees all of its predecessors' writes (each one waits for its predecessor,
+// which itself waited for its own).  Without the launch attribute both instructions do nothing.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+// whether solves launch their chain kernels with programmatic serialisation: only when the environment
+// variable TIKH_PDL is "1" (read once per process)
+inline bool pdl_enabled() {
+  static const bool on = [] {
+    const char* v = getenv("TIKH_PDL");
+    return v && v[0] == '1';
+  }();
+  return on;
+}
+
+// launch kernel k with or without programmatic stream serialisation
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(bool pdl, void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                            Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = pdl ? at : nullptr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
+}
+
 // device status word bits (plan->d_status)
 enum : int {
   ST_NUMERIC = 1,    // final degree pattern wrong / zero pivot
@@ -33,6 +94,7 @@ __device__ __forceinline__ void set_status(int* st, int bit) { atomicOr(st, bit)
 
 // twiddle exp(+2 pi i t / L) read from a table of length L (t reduced mod L by the caller)
 __device__ __forceinline__ cd tw_at(const cd* __restrict__ tab, int64_t t) { return __ldg(tab + t); }
+__device__ __forceinline__ cf tw_at(const cf* __restrict__ tab, int64_t t) { return __ldg(tab + t); }
 
 // Column scale carried with every basis: the consumer multiplies column j by 2^{-e_j} where
 // colmax_j = f 2^{e_j}, f in [0.5, 1) (exact power-of-two scaling).

@@ -9,24 +9,33 @@ using namespace tikh;
 
 namespace tikh {
 
+template <class C>
 struct HookLoad {
-  const cd* p;
-  __device__ cd operator()(int, int64_t j) const { return p[j]; }
+  const C* p;
+  __device__ C operator()(int, int64_t j) const { return p[j]; }
 };
+template <class C>
 struct HookStore {
-  cd* p;
-  __device__ void operator()(int, int64_t k, cd v) const { p[k] = v; }
+  C* p;
+  __device__ void operator()(int, int64_t k, C v) const { p[k] = v; }
 };
 
-int launch_fft_test(int64_t L, cd* data, int sign, cudaStream_t s, int64_t* bytes_out) {
-  Plan P;  // scratch plan holding only the twiddle tables
-  P.stream = s;
+// one in-place transform of L values of type C (cd: FP64; cf: FP32 with complex64 twiddle tables)
+template <class C>
+int launch_fft_test_t(int64_t L, C* data, int sign, cudaStream_t s) {
   std::vector<void*> tmp;
   auto table = [&](int64_t n) -> cd* {
     cd* t = nullptr;
     if (cudaMalloc(&t, sizeof(cd) * (size_t)n) != cudaSuccess) return nullptr;
     tmp.push_back(t);
     launch_twiddle(t, n, s);
+    return t;
+  };
+  auto table32 = [&](const cd* src, int64_t n) -> cf* {
+    cf* t = nullptr;
+    if (!src || cudaMalloc(&t, sizeof(cf) * (size_t)n) != cudaSuccess) return nullptr;
+    tmp.push_back(t);
+    launch_to_cf(src, t, n, s);
     return t;
   };
   FftPlan f;
@@ -49,14 +58,25 @@ int launch_fft_test(int64_t L, cd* data, int sign, cudaStream_t s, int64_t* byte
       f.twL = table(L);
     }
   }
-  cd* work = nullptr;
-  if (!rc && f.four && cudaMalloc(&work, sizeof(cd) * (size_t)L) != cudaSuccess) rc = TIKH_ENOMEM;
+  if (!rc && sizeof(C) == sizeof(cf)) {
+    f.d1.tw32 = table32(f.d1.tw, f.four ? f.L1 : L);
+    if (f.four) {
+      f.d2.tw32 = table32(f.d2.tw, f.L2);
+      f.twL32 = table32(f.twL, L);
+    }
+  }
+  C* work = nullptr;
+  if (!rc && f.four && cudaMalloc(&work, sizeof(C) * (size_t)L) != cudaSuccess) rc = TIKH_ENOMEM;
   if (work) tmp.push_back(work);
-  if (!rc && fft_run(f, 1, sign, HookLoad{data}, HookStore{data}, work, s) < 0) rc = TIKH_ECUDA;
+  if (!rc && fft_run(f, 1, sign, HookLoad<C>{data}, HookStore<C>{data}, work, s) < 0) rc = TIKH_ECUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) rc = TIKH_ECUDA;
   for (void* p : tmp) cudaFree(p);
-  if (bytes_out) *bytes_out = 0;
   return rc;
+}
+
+int launch_fft_test(int64_t L, cd* data, int sign, cudaStream_t s, int64_t* bytes_out) {
+  if (bytes_out) *bytes_out = 0;
+  return launch_fft_test_t<cd>(L, data, sign, s);
 }
 
 // Peak FMA rate: every thread runs 8 independent FMA chains of `iters` steps (no memory traffic), on
@@ -119,6 +139,18 @@ int tikh_test_peak(int kind, double* gflops, void* stream) {
 int tikh_test_fft(int64_t n, void* data, int sign, void* stream) {
   if (n < 1 || !data || (sign != 1 && sign != -1)) return TIKH_EINVAL;
   return launch_fft_test(n, (cd*)data, sign, (cudaStream_t)stream, nullptr);
+}
+
+int tikh_test_rcp(int64_t n, const double* d, double* out, void* stream) {
+  if (n < 1 || !d || !out) return TIKH_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (launch_rcp_test(d, out, n, s) < 0) return TIKH_ECUDA;
+  return cudaStreamSynchronize(s) == cudaSuccess ? TIKH_OK : TIKH_ECUDA;
+}
+
+int tikh_test_fft32(int64_t n, void* data, int sign, void* stream) {
+  if (n < 1 || !data || (sign != 1 && sign != -1)) return TIKH_EINVAL;
+  return launch_fft_test_t<cf>(n, (cf*)data, sign, (cudaStream_t)stream);
 }
 
 int tikh_test_leaf(int K, const void* sigma, const void* r, const int* delta_in, double eps, void* B, int* len,

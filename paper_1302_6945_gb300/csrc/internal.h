@@ -47,13 +47,25 @@ struct Step {
   uint64_t save_mask;  // STEP_LEAF: depths whose delta_in is this leaf's delta_in
 };
 
-// per-problem user arrays of a call: element i of problem pb at base + pb * stride + i
-struct UserArrays {
-  const void* col = nullptr;
-  const void* row = nullptr;
-  const void* rhs = nullptr;
-  void* x = nullptr;
-  int64_t col_stride = 0, row_stride = 0, rhs_stride = 0, x_stride = 0;
+// Shape of one problem: user m x n, the core (tall) problem cm x cn (cm >= cn; T^H for m < n) and the
+// extension k = N - (cm + cn - 1) for the plan's N.
+struct Shape {
+  int64_t m = 0, n = 0, cm = 0, cn = 0, k = 0;
+  int dual = 0;
+};
+
+// One item of a call -- a (problem, lambda) pair -- as the kernels see it: its user arrays and shape.
+// Every kernel that depends on the problem's sizes reads them here (item index = problem index pb of
+// the launch), so the items of one launch may have different m, n, k as long as they share N.
+struct ItemDev {
+  const void* col;
+  const void* row;
+  const void* rhs;
+  void* x;
+  const void* gram;  // Toeplitz-Gramian plans: first column of the Hermitian Toeplitz G (n entries)
+  int64_t m, n, cm, cn, k;
+  int dual;
+  int pad_;
 };
 
 struct Plan {
@@ -63,8 +75,9 @@ struct Plan {
   tikh_opts opts{};
   cudaStream_t stream = nullptr;
   int dual = 0;
-  int64_t cm = 0, cn = 0;  // core (tall) problem: cm >= cn
+  int64_t cm = 0, cn = 0;  // core (tall) problem: cm >= cn (the largest over `shapes`)
   int64_t N = 0, M = 0, k = 0;
+  std::vector<Shape> shapes;  // the shapes this plan serves (one for a single-shape plan)
   int p = 0;
   int batch_max = 1;
   int nb = 1;          // problems in the current call
@@ -77,6 +90,14 @@ struct Plan {
   std::map<int64_t, int> fft_of_len;
   std::vector<FftPlan> ffts;
   std::map<int64_t, cd*> twiddle_of_len;
+  std::map<int64_t, cf*> twiddle32_of_len;  // complex64 copies (FP32 stages)
+  int prec = TIKH_PREC_FP64;
+  int gram = 0;          // 1: the Toeplitz-Gramian problem (G + L^H L) x = y (Sec. 3.4); L plays T's part
+  cd* specG = nullptr;   // [nb][N] DFT of G's circulant generator (Gramian plans)
+  cd* gX = nullptr;      // [nb][N] refinement scratch: DFT of [x; 0] (Gramian plans)
+  unsigned long long* peakG = nullptr;  // [nb] fill magnitude of G's extension
+  bool stage32 = false;  // the recursion's FFT stages in FP32 (TIKH_PREC_FP32, TIKH_PREC_FP32_REFINE)
+  cf* wN32 = nullptr;    // omega^e, e < N, complex64 (FP32 evaluation folds)
   int64_t Pmax = 0, Lrmax = 0;
 
   // device memory (per-problem arrays: leading problem index)
@@ -105,7 +126,12 @@ struct Plan {
   cd* FC = nullptr;     // [nb][25][Pmax] products
   cd* ptmp = nullptr;   // [nb][50][Pmax] (four-step temp)
   unsigned long long* peak = nullptr;  // [nb] fill magnitude (bit pattern of a non-negative double)
-  double* lam = nullptr;  // [nb] regularisation weights of the current call
+  double* lam = nullptr;  // [nb] regularisation weights of the current call (points into lam_base)
+  ItemDev* items = nullptr;  // [nb] items of the current call (points into items_base)
+  double* lam_base = nullptr;
+  ItemDev* items_base = nullptr;  // [item_cap] device item tables (several waves for a batch plan)
+  int64_t item_cap = 0;
+  bool keep_status = false;  // true: the prologue does not clear the status word (later waves of a batch)
   cd* ybuf = nullptr;    // [nb][cn] core right-hand side
   cd* rbuf = nullptr;    // [nb][cn] refinement residual
   cd* xcore = nullptr;   // [nb][cn] core solution
@@ -118,9 +144,9 @@ struct Plan {
   double* gdl = nullptr; // [nb] dL/dlambda
   int64_t launches = 0;
 
-  // optional CUDA graph of the whole solve, replayed while the call's arguments stay the same
+  // optional CUDA graph of the whole solve, replayed for every call with the same item count (the
+  // kernels read each call's arrays and sizes from the item table)
   cudaGraphExec_t graph_exec = nullptr;
-  UserArrays graph_key{};
   int graph_nb = 0, graph_rhs_is_y = -1;
 
   // optional timing of every leaf launch with a CUDA event pair on the plan's stream
@@ -134,13 +160,15 @@ struct Plan {
 
 // launchers (return the number of kernels enqueued, or a negative TIKH_E* code)
 int launch_twiddle(cd* tab, int64_t L, cudaStream_t s);
-int launch_spectrum(Plan& P, const UserArrays& u, int rhs_is_y);
-int launch_rhs(Plan& P, const UserArrays& u, int rhs_is_y);
+int launch_to_cf(const cd* in, cf* out, int64_t n, cudaStream_t s);
+int launch_rcp_test(const double* d, double* out, int64_t n, cudaStream_t s);
+int launch_spectrum(Plan& P, int rhs_is_y);
+int launch_rhs(Plan& P, int rhs_is_y);
 int launch_conditions(Plan& P, const cd* y);
 int launch_extract(Plan& P, cd* out);
 int launch_residual(Plan& P, const cd* y, const cd* x, cd* r);
 int launch_axpy(Plan& P, cd* x, const cd* dx);
-int launch_output(Plan& P, const cd* v, const UserArrays& u);
+int launch_output(Plan& P, const cd* v);
 int launch_leaf(Plan& P, const Step& st);
 int launch_eval(Plan& P, const Step& st);
 int launch_prod(Plan& P, const Step& st);

@@ -196,6 +196,17 @@ __device__ __forceinline__ double rcp_series(double d) {
   return fma(y, fma(e, e, e), y);
 }
 
+// test hook: rcp_series on an array of positive normal doubles (biased exponent in (2, 2044))
+__global__ void k_test_rcp(const double* __restrict__ d, double* out, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = rcp_series(d[i]);
+}
+
+int launch_rcp_test(const double* d, double* out, int64_t n, cudaStream_t s) {
+  const int blocks = (int)std::min<int64_t>((n + 255) / 256, 1024);
+  k_test_rcp<<<blocks, 256, 0, s>>>(d, out, n);
+  return cudaGetLastError() == cudaSuccess ? 1 : TIKH_ECUDA;
+}
 
 constexpr int L4_ROWS = 6;
 constexpr int L4_NREC = 128;
@@ -224,6 +235,7 @@ __global__ void __launch_bounds__(32 * CWN + L4_NREC, CWN <= 4 ? 4 : (CWN <= 8 ?
   __shared__ int din[5], dl_out[5];
   __shared__ int chain_state;  // steps recorded so far, | CHAIN_DONE once the chain has stopped
   __shared__ int rb_cmd;
+  pdl_enter();
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, pb = blockIdx.x;
   int* dlt = delta + 8 * pb;
 
@@ -481,14 +493,11 @@ static int launch_leaf_t(const Src& src, int K, int nb, int* delta, int* dstack,
                          const BasisBuf& out, int* ndiff, int64_t* diff, int maxdiff, int* status, int* order,
                          int* pivot, const int* bad, int spin_limit, cudaStream_t s) {
   if (K <= 4 * L4_ROWS)
-    k_leaf<4, Src><<<nb, 32 * 4 + L4_NREC, 0, s>>>(src, K, delta, dstack, mask, eps, out, ndiff, diff, maxdiff,
-                                                   status, order, pivot, bad, spin_limit);
+    launch_k(pdl_enabled(), k_leaf<4, Src>, dim3(nb), dim3(32 * 4 + L4_NREC), 0, s, src, K, delta, dstack, mask, eps, out, ndiff, diff, maxdiff, status, order, pivot, bad, spin_limit);
   else if (K <= 8 * L4_ROWS)
-    k_leaf<8, Src><<<nb, 32 * 8 + L4_NREC, 0, s>>>(src, K, delta, dstack, mask, eps, out, ndiff, diff, maxdiff,
-                                                   status, order, pivot, bad, spin_limit);
+    launch_k(pdl_enabled(), k_leaf<8, Src>, dim3(nb), dim3(32 * 8 + L4_NREC), 0, s, src, K, delta, dstack, mask, eps, out, ndiff, diff, maxdiff, status, order, pivot, bad, spin_limit);
   else
-    k_leaf<11, Src><<<nb, 32 * 11 + L4_NREC, 0, s>>>(src, K, delta, dstack, mask, eps, out, ndiff, diff, maxdiff,
-                                                     status, order, pivot, bad, spin_limit);
+    launch_k(pdl_enabled(), k_leaf<11, Src>, dim3(nb), dim3(32 * 11 + L4_NREC), 0, s, src, K, delta, dstack, mask, eps, out, ndiff, diff, maxdiff, status, order, pivot, bad, spin_limit);
   return cudaGetLastError() == cudaSuccess ? 1 : TIKH_ECUDA;
 }
 

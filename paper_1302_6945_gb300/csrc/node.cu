@@ -7,6 +7,8 @@
 // phi <- phi B_L(sigma).
 // Step 4: B = B_L B_R by length-P DFTs, P > the largest entry degree allowed by the tau-degrees,
 // trimmed to entry (i,j) degree bounds and carried with power-of-two column scales.
+// In the FP32 precision pattern the FFT forms of both steps run in FP32 (complex64 spectra, FP32
+// pointwise products and updates); the direct small-node forms, the leaves and the basis stay FP64.
 // All problems of a batch are processed by the same launches: transform index = problem * 50 (or 25)
 // + entry, grid.y / grid.z = problem for the element-wise kernels.
 #include "internal.h"
@@ -27,12 +29,24 @@ __device__ __forceinline__ int entry_bound_dev(const int* din, const int* dout, 
 // ------------------------------------------------------------------------------------------------
 // step 2
 // ------------------------------------------------------------------------------------------------
+// The FFT path of steps 2 and 4 runs in the plan's stage precision C: complex128 (cd), or complex64 (cf)
+// in the FP32 precision pattern (FP32 arithmetic and accumulation; the basis stays FP64 and so do the
+// residual rows, which the FP64 leaves read).
+template <class C>
+__device__ __forceinline__ C twiddle_of(const cd* wN, const cf* wN32, int64_t i);
+template <>
+__device__ __forceinline__ cd twiddle_of<cd>(const cd* wN, const cf*, int64_t i) { return tw_at(wN, i); }
+template <>
+__device__ __forceinline__ cf twiddle_of<cf>(const cd*, const cf* wN32, int64_t i) { return tw_at(wN32, i); }
+
+template <class C>
 struct LoadTwistFold {  // transform t = 50 pb + 2E + c
   BasisBuf B;
   BasisBuf OUT;  // this node's output slot: its column maxima are reset here, before the product
   const cd* wN;
+  const cf* wN32;
   int64_t N, Lr, beta0;
-  __device__ cd operator()(int t, int64_t u) const {
+  __device__ C operator()(int t, int64_t u) const {
     int pb = t / 50, b = t % 50;
     if (b == 0 && u == 0)
       for (int j = 0; j < 5; ++j) OUT.mp(pb)[j] = 0ULL;
@@ -40,46 +54,50 @@ struct LoadTwistFold {  // transform t = 50 pb + 2E + c
     int64_t beta = beta0 + c;
     int64_t len = B.lp(pb)[E];
     const cd* src = B.cp(pb) + E * B.cap;
-    cd acc = mkc(0.0, 0.0);
+    C acc = czero<C>();
     // twiddle index (beta q) mod N advanced by (beta Lr) mod N per fold term (one 64-bit modulo each)
     int64_t ix = (beta * u) % N;
     const int64_t stepx = (beta * Lr) % N;
     for (int64_t q = u; q < len; q += Lr) {
-      acc = cfma(src[q], tw_at(wN, ix), acc);
+      acc = cfma(cfrom<C>(src[q]), twiddle_of<C>(wN, wN32, ix), acc);
       ix += stepx;
       if (ix >= N) ix -= N;
     }
-    return cscale(acc, col_scale_from_bits(B.mp(pb)[E % 5]));
+    return cscale(acc, (decltype(acc.x))col_scale_from_bits(B.mp(pb)[E % 5]));
   }
 };
+template <class C>
 struct StoreEval {
-  cd* out;
+  C* out;
   int64_t Lr;
-  __device__ void operator()(int t, int64_t j, cd v) const { out[(int64_t)t * Lr + j] = v; }
+  __device__ void operator()(int t, int64_t j, C v) const { out[(int64_t)t * Lr + j] = v; }
 };
 
-// phi <- phi B_L(sigma) for both conditions of every right-child node
-__global__ void k_eval_update(cd* R, const cd* __restrict__ vals, int64_t N, int64_t a0, int64_t s2, int64_t Lr) {
+// phi <- phi B_L(sigma) for both conditions of every right-child node (in C's precision; the rows are
+// stored back in FP64)
+template <class C>
+__global__ void k_eval_update(cd* R, const C* __restrict__ vals, int64_t N, int64_t a0, int64_t s2, int64_t Lr) {
+  pdl_enter();
   const int pb = blockIdx.y;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < 2 * Lr; g += (int64_t)gridDim.x * blockDim.x) {
     int c = (int)(g % 2);
     int64_t j = g / 2;
     int64_t e = a0 + c + s2 * j;
-    cd V[25];
+    C V[25];
 #pragma unroll
     for (int E = 0; E < 25; ++E) V[E] = vals[((int64_t)pb * 50 + E * 2 + c) * Lr + j];
 #pragma unroll
     for (int f = 0; f < 2; ++f) {
       cd* r = R + ((int64_t)pb * N + e) * 10 + f * 5;
-      cd in[5];
+      C in[5];
 #pragma unroll
-      for (int i = 0; i < 5; ++i) in[i] = r[i];
+      for (int i = 0; i < 5; ++i) in[i] = cfrom<C>(r[i]);
 #pragma unroll
       for (int col = 0; col < 5; ++col) {
-        cd acc = mkc(0.0, 0.0);
+        C acc = czero<C>();
 #pragma unroll
         for (int i = 0; i < 5; ++i) acc = cfma(in[i], V[i * 5 + col], acc);
-        r[col] = acc;
+        r[col] = mkc((double)acc.x, (double)acc.y);
       }
     }
   }
@@ -94,6 +112,7 @@ __global__ void __launch_bounds__(25 * G) k_eval_direct(BasisBuf BL, BasisBuf OU
                                                         int64_t N, int64_t a0, int64_t s2) {
   __shared__ cd V[25];
   __shared__ cd Rs[10];
+  pdl_enter();
   const int pb = blockIdx.y, tid = threadIdx.x;
   const int64_t g = blockIdx.x;
   const int64_t e = a0 + (g & 1) + s2 * (g >> 1);
@@ -137,20 +156,31 @@ int launch_eval(Plan& P, const Step& st) {
     const dim3 grid((unsigned)(2 * Lr), (unsigned)P.nb);
     const int64_t cap = BL.cap, a0 = st.a + st.s, s2 = 2 * st.s;
     cudaStream_t s = P.stream;
-    if (cap <= 8) k_eval_direct<1><<<grid, 25, 0, s>>>(BL, OUT, P.R, P.wN, P.N, a0, s2);
-    else if (cap <= 24) k_eval_direct<2><<<grid, 50, 0, s>>>(BL, OUT, P.R, P.wN, P.N, a0, s2);
-    else if (cap <= 48) k_eval_direct<4><<<grid, 100, 0, s>>>(BL, OUT, P.R, P.wN, P.N, a0, s2);
-    else if (cap <= 96) k_eval_direct<8><<<grid, 200, 0, s>>>(BL, OUT, P.R, P.wN, P.N, a0, s2);
-    else if (cap <= 192) k_eval_direct<16><<<grid, 400, 0, s>>>(BL, OUT, P.R, P.wN, P.N, a0, s2);
-    else k_eval_direct<32><<<grid, 800, 0, s>>>(BL, OUT, P.R, P.wN, P.N, a0, s2);
+    if (cap <= 8) launch_k(pdl_enabled(), k_eval_direct<1>, grid, dim3(25), 0, s, BL, OUT, P.R, P.wN, P.N, a0, s2);
+    else if (cap <= 24) launch_k(pdl_enabled(), k_eval_direct<2>, grid, dim3(50), 0, s, BL, OUT, P.R, P.wN, P.N, a0, s2);
+    else if (cap <= 48) launch_k(pdl_enabled(), k_eval_direct<4>, grid, dim3(100), 0, s, BL, OUT, P.R, P.wN, P.N, a0, s2);
+    else if (cap <= 96) launch_k(pdl_enabled(), k_eval_direct<8>, grid, dim3(200), 0, s, BL, OUT, P.R, P.wN, P.N, a0, s2);
+    else if (cap <= 192) launch_k(pdl_enabled(), k_eval_direct<16>, grid, dim3(400), 0, s, BL, OUT, P.R, P.wN, P.N, a0, s2);
+    else launch_k(pdl_enabled(), k_eval_direct<32>, grid, dim3(800), 0, s, BL, OUT, P.R, P.wN, P.N, a0, s2);
     return cudaGetLastError() == cudaSuccess ? 1 : TIKH_ECUDA;
   }
   const FftPlan& F = P.ffts[st.fft];
-  int r = fft_run(F, 50 * P.nb, +1, LoadTwistFold{BL, OUT, P.wN, P.N, Lr, st.a + st.s}, StoreEval{P.evalv, Lr}, P.etmp,
-                  P.stream);
-  if (r < 0) return TIKH_ECUDA;
   dim3 grid((unsigned)std::min<int64_t>((2 * Lr + 127) / 128, 4096), (unsigned)P.nb);
-  k_eval_update<<<grid, 128, 0, P.stream>>>(P.R, P.evalv, P.N, st.a + st.s, 2 * st.s, Lr);
+  int r;
+  if (P.stage32) {
+    cf* ev = reinterpret_cast<cf*>(P.evalv);
+    r = fft_run(F, 50 * P.nb, +1, LoadTwistFold<cf>{BL, OUT, P.wN, P.wN32, P.N, Lr, st.a + st.s},
+                StoreEval<cf>{ev, Lr}, reinterpret_cast<cf*>(P.etmp), P.stream);
+    if (r < 0) return TIKH_ECUDA;
+    launch_k(pdl_enabled(), k_eval_update<cf>, grid, dim3(128), 0, P.stream, P.R, (const cf*)ev, P.N, st.a + st.s,
+             2 * st.s, Lr);
+  } else {
+    r = fft_run(F, 50 * P.nb, +1, LoadTwistFold<cd>{BL, OUT, P.wN, P.wN32, P.N, Lr, st.a + st.s},
+                StoreEval<cd>{P.evalv, Lr}, P.etmp, P.stream);
+    if (r < 0) return TIKH_ECUDA;
+    launch_k(pdl_enabled(), k_eval_update<cd>, grid, dim3(128), 0, P.stream, P.R, (const cd*)P.evalv, P.N, st.a + st.s,
+             2 * st.s, Lr);
+  }
   if (cudaGetLastError() != cudaSuccess) return TIKH_ECUDA;
   return r + 1;
 }
@@ -169,6 +199,7 @@ __device__ __forceinline__ int prod_len_bound(const BasisBuf& BL, const BasisBuf
   return L;
 }
 
+template <class C>
 struct LoadPad {  // transform t = 50 pb + b; b < 25: B_L entry b; b >= 25: B_R entry b - 25; zero-padded to P
   BasisBuf BL, BR, OUT;
   const int* dstack;  // + pb * MAX_DEPTH * 5 + depth * 5: delta_in of the node
@@ -176,7 +207,7 @@ struct LoadPad {  // transform t = 50 pb + b; b < 25: B_L entry b; b >= 25: B_R 
   int depth;
   int* status;
   int64_t P;
-  __device__ cd operator()(int t, int64_t q) const {
+  __device__ C operator()(int t, int64_t q) const {
     int pb = t / 50, b = t % 50;
     if (b == 0 && q == 0) {
       // guard: the transform length must exceed every entry degree of the product (no wrap-around)
@@ -191,46 +222,59 @@ struct LoadPad {  // transform t = 50 pb + b; b < 25: B_L entry b; b >= 25: B_R 
     }
     const BasisBuf& B = b < 25 ? BL : BR;
     int E = b < 25 ? b : b - 25;
-    if (q >= B.lp(pb)[E]) return mkc(0.0, 0.0);
-    return cscale(B.cp(pb)[E * B.cap + q], col_scale_from_bits(B.mp(pb)[E % 5]));
+    if (q >= B.lp(pb)[E]) return czero<C>();
+    return cfrom<C>(cscale(B.cp(pb)[E * B.cap + q], col_scale_from_bits(B.mp(pb)[E % 5])));
   }
 };
+template <class C>
 struct StoreSpec {
-  cd* FA;
-  cd* FB;
+  C* FA;
+  C* FB;
   int64_t P;
-  __device__ void operator()(int t, int64_t k, cd v) const {
+  __device__ void operator()(int t, int64_t k, C v) const {
     int pb = t / 50, b = t % 50;
     if (b < 25) FA[((int64_t)pb * 25 + b) * P + k] = v;
     else FB[((int64_t)pb * 25 + b - 25) * P + k] = v;
   }
 };
+template <class C>
 struct StorePlain2 {
-  cd* out;
+  C* out;
   int64_t P;
-  __device__ void operator()(int t, int64_t k, cd v) const { out[(int64_t)t * P + k] = v; }
+  __device__ void operator()(int t, int64_t k, C v) const { out[(int64_t)t * P + k] = v; }
 };
+template <class C>
 struct LoadProduct {  // transform t = 25 pb + 5i + j: sum_u FA[5i+u] FB[5u+j]
-  const cd* FA;
-  const cd* FB;
+  const C* FA;
+  const C* FB;
   int64_t P;
-  __device__ cd operator()(int t, int64_t q) const {
+  __device__ C operator()(int t, int64_t q) const {
     int pb = t / 25, e = t % 25, i = e / 5, j = e % 5;
-    const cd* a = FA + (int64_t)pb * 25 * P;
-    const cd* b = FB + (int64_t)pb * 25 * P;
-    cd acc = mkc(0.0, 0.0);
+    const C* a = FA + (int64_t)pb * 25 * P;
+    const C* b = FB + (int64_t)pb * 25 * P;
+    C acc = czero<C>();
 #pragma unroll
     for (int u = 0; u < 5; ++u) acc = cfma(a[(int64_t)(5 * i + u) * P + q], b[(int64_t)(5 * u + j) * P + q], acc);
     return acc;
   }
 };
 
-// trim to the degree bounds, scale by 1/P, record column maxima and lengths
-__global__ void k_prod_finish(const cd* __restrict__ FC, int64_t P, BasisBuf BL, BasisBuf BR, BasisBuf OUT,
+// max(|Re|, |Im|) as the bit pattern of a non-negative double, by integer operations (no FP64 instruction:
+// non-negative doubles order like their bit patterns)
+__device__ __forceinline__ unsigned long long absmax_bits(cd v) {
+  const unsigned long long a = (unsigned long long)__double_as_longlong(v.x) & 0x7fffffffffffffffULL;
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v.y) & 0x7fffffffffffffffULL;
+  return a > b ? a : b;
+}
+
+// trim to the degree bounds, scale by 1/P (in FP64), record column maxima and lengths
+template <class C>
+__global__ void k_prod_finish(const C* __restrict__ FC, int64_t P, BasisBuf BL, BasisBuf BR, BasisBuf OUT,
                               const int* dstack, int depth, const int* delta, int* status) {
   const int E = blockIdx.y, i = E / 5, j = E % 5, pb = blockIdx.z;
   __shared__ int want_s;
-  __shared__ double red[32];
+  __shared__ unsigned long long red[32];
+  pdl_enter();
   if (threadIdx.x == 0) {
     int bnd = entry_bound_dev(dstack + (pb * MAX_DEPTH + depth) * 5, delta + 8 * pb, i, j);
     int64_t want = bnd < 0 ? 0 : (int64_t)bnd + 1;
@@ -243,20 +287,25 @@ __global__ void k_prod_finish(const cd* __restrict__ FC, int64_t P, BasisBuf BL,
   __syncthreads();
   const int64_t want = want_s;
   const double inv = 1.0 / (double)P;
-  const cd* src = FC + ((int64_t)pb * 25 + E) * P;
+  const C* src = FC + ((int64_t)pb * 25 + E) * P;
   cd* dst = OUT.cp(pb) + (int64_t)E * OUT.cap;
-  double mx = 0.0;
+  unsigned long long mx = 0ULL;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < want; t += (int64_t)gridDim.x * blockDim.x) {
-    cd v = cscale(src[t], inv);
+    const C w = src[t];
+    cd v = mkc((double)w.x * inv, (double)w.y * inv);
     dst[t] = v;
-    mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+    const unsigned long long m = absmax_bits(v);
+    mx = m > mx ? m : mx;
   }
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long q = __shfl_xor_sync(0xffffffffu, mx, o);
+    mx = q > mx ? q : mx;
+  }
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, red[w]);
-    if (mx > 0.0) atomicMax(OUT.mp(pb) + j, (unsigned long long)__double_as_longlong(mx));
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = red[w] > mx ? red[w] : mx;
+    if (mx > 0ULL) atomicMax(OUT.mp(pb) + j, mx);
   }
 }
 
@@ -274,6 +323,7 @@ __global__ void __launch_bounds__(32 * PD_TC) k_prod_direct(BasisBuf BL, BasisBu
   const int i = E / 5, j = E % 5, pb = blockIdx.y, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   __shared__ int want_s, ll[5], lr[5];
   __shared__ double red[PD_TC];
+  pdl_enter();
   if (tid < 5) {
     ll[tid] = BL.lp(pb)[i * 5 + tid];
     lr[tid] = BR.lp(pb)[tid * 5 + j];
@@ -342,6 +392,29 @@ __global__ void __launch_bounds__(32 * PD_TC) k_prod_direct(BasisBuf BL, BasisBu
   }
 }
 
+// step 4 by length-P transforms in precision C: the 50 operand spectra, 25 pointwise products of 5 terms,
+// 25 inverse transforms, then the FP64 trim / scale / column maxima
+template <class C>
+static int launch_prod_fft(Plan& P, const Step& st, const BasisBuf& BL, const BasisBuf& BR, const BasisBuf& OUT) {
+  const FftPlan& F = P.ffts[st.fft];
+  C* FA = reinterpret_cast<C*>(P.FA);
+  C* FB = reinterpret_cast<C*>(P.FB);
+  C* FC = reinterpret_cast<C*>(P.FC);
+  C* tmp = reinterpret_cast<C*>(P.ptmp);
+  int nl = 0, r;
+  LoadPad<C> lp{BL, BR, OUT, P.dstack, P.delta, st.depth, P.status, st.P};
+  if ((r = fft_run(F, 50 * P.nb, +1, lp, StoreSpec<C>{FA, FB, st.P}, tmp, P.stream)) < 0) return TIKH_ECUDA;
+  nl += r;
+  if ((r = fft_run(F, 25 * P.nb, -1, LoadProduct<C>{FA, FB, st.P}, StorePlain2<C>{FC, st.P}, tmp, P.stream)) < 0)
+    return TIKH_ECUDA;
+  nl += r;
+  int bx = (int)std::min<int64_t>((st.P + 255) / 256, 64);
+  launch_k(pdl_enabled(), k_prod_finish<C>, dim3(bx, 25, P.nb), dim3(256), 0, P.stream, (const C*)FC, st.P, BL, BR, OUT,
+           (const int*)P.dstack, st.depth, (const int*)P.delta, P.status);
+  if (cudaGetLastError() != cudaSuccess) return TIKH_ECUDA;
+  return nl + 1;
+}
+
 int launch_prod(Plan& P, const Step& st) {
   const BasisBuf& BL = P.buf[st.depth + 1][0];
   const BasisBuf& BR = P.buf[st.depth + 1][1];
@@ -349,23 +422,11 @@ int launch_prod(Plan& P, const Step& st) {
   const size_t smem = sizeof(cd) * 5 * (size_t)(BL.cap + BR.cap);
   if (st.P <= P.prod_direct_max && smem <= 48 * 1024) {
     const int ntile = (int)((st.P + PD_TC - 1) / PD_TC);
-    k_prod_direct<<<dim3(25 * ntile, P.nb), 32 * PD_TC, smem, P.stream>>>(BL, BR, OUT, P.dstack, st.depth, P.delta,
-                                                                          P.status, ntile);
+    launch_k(pdl_enabled(), k_prod_direct, dim3(25 * ntile, P.nb), dim3(32 * PD_TC), smem, P.stream, BL, BR, OUT,
+             (const int*)P.dstack, st.depth, (const int*)P.delta, P.status, ntile);
     return cudaGetLastError() == cudaSuccess ? 1 : TIKH_ECUDA;
   }
-  const FftPlan& F = P.ffts[st.fft];
-  int nl = 0, r;
-  LoadPad lp{BL, BR, OUT, P.dstack, P.delta, st.depth, P.status, st.P};
-  if ((r = fft_run(F, 50 * P.nb, +1, lp, StoreSpec{P.FA, P.FB, st.P}, P.ptmp, P.stream)) < 0) return TIKH_ECUDA;
-  nl += r;
-  if ((r = fft_run(F, 25 * P.nb, -1, LoadProduct{P.FA, P.FB, st.P}, StorePlain2{P.FC, st.P}, P.ptmp, P.stream)) < 0)
-    return TIKH_ECUDA;
-  nl += r;
-  int bx = (int)std::min<int64_t>((st.P + 255) / 256, 64);
-  k_prod_finish<<<dim3(bx, 25, P.nb), 256, 0, P.stream>>>(P.FC, st.P, BL, BR, OUT, P.dstack, st.depth, P.delta,
-                                                          P.status);
-  if (cudaGetLastError() != cudaSuccess) return TIKH_ECUDA;
-  return nl + 1;
+  return P.stage32 ? launch_prod_fft<cf>(P, st, BL, BR, OUT) : launch_prod_fft<cd>(P, st, BL, BR, OUT);
 }
 
 }  // namespace tikh

@@ -10,7 +10,10 @@
 // lamH_e = omega^{e(k-1)} conj(that_e) (the T^H generator's DFT, obtained in O(N) as in Sec. 7.3),
 // yhat = DFT of -y placed after cm+k-1 zeros.
 //
-// Length-N transforms run one transform per problem (transform index = problem index).
+// Length-N transforms run one transform per item (transform index = item index pb).  Every size that
+// belongs to a problem (m, n, cm, cn, k) and its user arrays are read from the item table
+// (ItemDev[pb]), so one launch serves items of different shapes that share N; per-item buffers of
+// length cn (y, x, residual, correction) use the plan's largest cn as their stride.
 #include "internal.h"
 
 namespace tikh {
@@ -30,6 +33,18 @@ int launch_twiddle(cd* tab, int64_t L, cudaStream_t s) {
   return cudaGetLastError() == cudaSuccess ? 1 : TIKH_ECUDA;
 }
 
+__global__ void k_to_cf(const cd* __restrict__ in, cf* out, int64_t n) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+    out[t] = to_cf(in[t]);
+}
+
+// complex64 copy of a complex128 table (each entry rounded to nearest)
+int launch_to_cf(const cd* in, cf* out, int64_t n, cudaStream_t s) {
+  int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
+  k_to_cf<<<blocks, 256, 0, s>>>(in, out, n);
+  return cudaGetLastError() == cudaSuccess ? 1 : TIKH_ECUDA;
+}
+
 // ------------------------------------------------------------------------------------------------
 // user data access
 // ------------------------------------------------------------------------------------------------
@@ -42,20 +57,13 @@ __device__ __forceinline__ void store_user(void* p, int64_t i, int dtype, cd v) 
   else ((double*)p)[i] = v.x;
 }
 
-// diagonal d of problem pb's core matrix (d in [-(cn-1), cm-1])
-struct CoreDiag {
-  const void* col;
-  const void* row;
-  int64_t col_stride, row_stride;
-  int dtype, dual;
-  __device__ cd operator()(int pb, int64_t d) const {
-    int64_t oc = pb * col_stride, orow = pb * row_stride;
-    if (!dual) return d >= 0 ? load_user(col, oc + d, dtype) : load_user(row, orow - d, dtype);
-    // a'_d = conj(a_{-d})
-    cd v = d <= 0 ? load_user(col, oc - d, dtype) : load_user(row, orow + d, dtype);
-    return cconj(v);
-  }
-};
+// diagonal d of an item's core matrix (d in [-(cn-1), cm-1])
+__device__ __forceinline__ cd core_diag(const ItemDev& it, int64_t d, int dtype) {
+  if (!it.dual) return d >= 0 ? load_user(it.col, d, dtype) : load_user(it.row, -d, dtype);
+  // a'_d = conj(a_{-d})
+  cd v = d <= 0 ? load_user(it.col, -d, dtype) : load_user(it.row, d, dtype);
+  return cconj(v);
+}
 
 // SplitMix64 (Steele, Lea, Flood 2014) as a counter-based hash, mapped to [-1, 1)
 __device__ __forceinline__ double splitmix_uniform(unsigned long long c) {
@@ -67,25 +75,38 @@ __device__ __forceinline__ double splitmix_uniform(unsigned long long c) {
 }
 
 // peak = max over the known diagonals of max(|Re|, |Im|)  (exact, order independent); and the input
-// check: a non-finite diagonal or right-hand-side entry marks the problem (bad[pb] = 1, whose leaves
-// then process no condition) and the call (ST_INPUT), so no kernel iterates on NaN or Inf
-__global__ void k_peak(CoreDiag a, int64_t cm, int64_t cn, unsigned long long* peak, const void* rhs,
-                       int64_t rhs_stride, int64_t rhs_len, int dtype, int* bad, int* status) {
+// check: a non-finite diagonal or right-hand-side entry marks the item (bad[pb] = 1, whose leaves then
+// process no condition) and the call (ST_INPUT), so no kernel iterates on NaN or Inf
+__global__ void k_peak(const ItemDev* __restrict__ items, int dtype, int rhs_is_y, unsigned long long* peak, int* bad,
+                       int* status, unsigned long long* peakG) {
   const int pb = blockIdx.y;
+  const ItemDev it = items[pb];
   double mx = 0.0;
   bool fin = true;
-  int64_t total = cm + cn - 1;
+  const int64_t total = it.cm + it.cn - 1;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    cd v = a(pb, i - (cn - 1));
+    cd v = core_diag(it, i - (it.cn - 1), dtype);
     fin = fin && isfinite(v.x) && isfinite(v.y);
     mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
   }
+  // the user right-hand side: y (n entries) for the normal-equation form, else b (m entries)
+  const int64_t rhs_len = rhs_is_y ? it.n : it.m;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rhs_len; i += (int64_t)gridDim.x * blockDim.x) {
-    cd v = load_user(rhs, pb * rhs_stride + i, dtype);
+    cd v = load_user(it.rhs, i, dtype);
     fin = fin && isfinite(v.x) && isfinite(v.y);
   }
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if ((threadIdx.x & 31) == 0 && mx > 0.0) atomicMax(peak + pb, (unsigned long long)__double_as_longlong(mx));
+  if (it.gram) {  // Toeplitz-Gramian: G's first column (n entries), its own fill magnitude
+    double mg = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < it.cn; i += (int64_t)gridDim.x * blockDim.x) {
+      cd v = load_user(it.gram, i, dtype);
+      fin = fin && isfinite(v.x) && isfinite(v.y);
+      mg = fmax(mg, fmax(fabs(v.x), fabs(v.y)));
+    }
+    for (int o = 16; o > 0; o >>= 1) mg = fmax(mg, __shfl_xor_sync(0xffffffffu, mg, o));
+    if ((threadIdx.x & 31) == 0 && mg > 0.0) atomicMax(peakG + pb, (unsigned long long)__double_as_longlong(mg));
+  }
   if (!fin) {
     bad[pb] = 1;
     set_status(status, ST_INPUT);
@@ -94,27 +115,57 @@ __global__ void k_peak(CoreDiag a, int64_t cm, int64_t cn, unsigned long long* p
 
 // c_T[j] = a_{j-(cn+k-1)} over the periodic sequence; entries a_{cm-1+i}, i = 1..k, are the fill
 struct LoadGenerator {
-  CoreDiag a;
-  int64_t cm, cn, N, k;
-  int fill, is_complex;
+  const ItemDev* items;
+  int64_t N;
+  int fill, dtype;
   const unsigned long long* peak;
   __device__ cd operator()(int pb, int64_t j) const {
+    const ItemDev& it = items[pb];
+    const int64_t cm = it.cm, cn = it.cn, k = it.k;
     int64_t d = ((j - (cn + k - 1)) % N + N) % N;
-    if (d <= cm - 1) return a(pb, d);
-    if (d >= N - (cn - 1)) return a(pb, d - N);
+    if (d <= cm - 1) return core_diag(it, d, dtype);
+    if (d >= N - (cn - 1)) return core_diag(it, d - N, dtype);
     int64_t i = d - (cm - 1);  // 1..k
     if (fill == 1) {
-      cd lo = a(pb, -(cn - 1)), hi = a(pb, cm - 1);
+      cd lo = core_diag(it, -(cn - 1), dtype), hi = core_diag(it, cm - 1, dtype);
       double f = (double)i / (double)(k + 1);
       return mkc(hi.x + (lo.x - hi.x) * f, hi.y + (lo.y - hi.y) * f);
     }
     double pk = __longlong_as_double((long long)peak[pb]);
     double re = pk * splitmix_uniform((unsigned long long)(2 * i));
-    double im = is_complex ? pk * splitmix_uniform((unsigned long long)(2 * i + 1)) : 0.0;
+    double im = dtype == TIKH_C128 ? pk * splitmix_uniform((unsigned long long)(2 * i + 1)) : 0.0;
     return mkc(re, im);
   }
 };
-// plain per-problem vectors: element j of problem pb at base + pb * stride + j
+// Toeplitz-Gramian (Sec. 3.4, Eq. (gramblk)): the x-column of the first block row is the n x n Hermitian
+// Toeplitz G below N - n extension rows, whose circulant generator is c11[(N - n + d) mod N] = g_d for
+// |d| <= n - 1 (g_{-d} = conj(g_d)); the N - 2n + 1 other entries are the extension's arbitrary entries,
+// filled like L's (R5) with counters offset by 2^40 (fill = 1: a linear ramp from g_{n-1} to conj(g_{n-1}))
+struct LoadGramGenerator {
+  const ItemDev* items;
+  int64_t N;
+  int fill, dtype;
+  const unsigned long long* peakG;
+  __device__ cd operator()(int pb, int64_t j) const {
+    const ItemDev& it = items[pb];
+    const int64_t n = it.cn;
+    const int64_t d = ((j - (N - n)) % N + N) % N;
+    if (d <= n - 1) return load_user(it.gram, d, dtype);
+    if (d >= N - (n - 1)) return cconj(load_user(it.gram, N - d, dtype));
+    const int64_t i = d - (n - 1), nfill = N - 2 * n + 1;  // 1 .. nfill
+    if (fill == 1) {
+      const cd hi = load_user(it.gram, n - 1, dtype), lo = cconj(hi);
+      const double f = (double)i / (double)(nfill + 1);
+      return mkc(hi.x + (lo.x - hi.x) * f, hi.y + (lo.y - hi.y) * f);
+    }
+    const double pk = __longlong_as_double((long long)peakG[pb]);
+    const unsigned long long off = 1ULL << 40;
+    const double re = pk * splitmix_uniform((unsigned long long)(2 * i) + off);
+    const double im = dtype == TIKH_C128 ? pk * splitmix_uniform((unsigned long long)(2 * i + 1) + off) : 0.0;
+    return mkc(re, im);
+  }
+};
+// plain per-item vectors: element j of item pb at base + pb * stride + j
 struct StoreVec {
   cd* out;
   int64_t stride;
@@ -125,28 +176,31 @@ struct LoadVec {
   int64_t stride;
   __device__ cd operator()(int pb, int64_t j) const { return in[pb * stride + j]; }
 };
-// [v; 0]: user vector of length len, zero beyond
-struct LoadPadUser {
-  const void* v;
-  int64_t stride, len;
+// [b; 0]: the item's user right-hand side b (cm entries), zero beyond
+struct LoadPadUserRhs {
+  const ItemDev* items;
   int dtype;
   __device__ cd operator()(int pb, int64_t j) const {
-    return j < len ? load_user(v, pb * stride + j, dtype) : mkc(0.0, 0.0);
+    const ItemDev& it = items[pb];
+    return j < it.cm ? load_user(it.rhs, j, dtype) : mkc(0.0, 0.0);
   }
 };
-// [v; 0]: complex vector of length len, zero beyond
-struct LoadPadC {
+// [v; 0]: the item's complex vector of length cn (stride = the plan's largest cn), zero beyond
+struct LoadPadCn {
   const cd* v;
-  int64_t stride, len;
-  __device__ cd operator()(int pb, int64_t j) const { return j < len ? v[pb * stride + j] : mkc(0.0, 0.0); }
+  const ItemDev* items;
+  int64_t stride;
+  __device__ cd operator()(int pb, int64_t j) const { return j < items[pb].cn ? v[pb * stride + j] : mkc(0.0, 0.0); }
 };
 // spectrum times lamH_e = omega^{e(k-1)} conj(that_e)  (adjoint generator, Sec. 7.3)
 struct StoreMulLamH {
   cd* out;
   const cd* that;
   const cd* wN;
-  int64_t N, k;
+  const ItemDev* items;
+  int64_t N;
   __device__ void operator()(int pb, int64_t e, cd v) const {
+    const int64_t k = items[pb].k;
     int64_t t = ((e * (k - 1)) % N + N) % N;
     out[pb * N + e] = cmul(v, cmul(tw_at(wN, t), cconj(that[pb * N + e])));
   }
@@ -157,31 +211,38 @@ struct StoreMulT {
   int64_t N;
   __device__ void operator()(int pb, int64_t e, cd v) const { out[pb * N + e] = cmul(v, that[pb * N + e]); }
 };
-// window [off, off + len) of an inverse transform, scaled, into a compact vector
-struct StoreWindowC {
+// window [cm + k - 1, cm + k - 1 + cn) of an inverse transform, scaled, into the item's y
+struct StoreWindowY {
   cd* out;
-  int64_t stride, off, len;
+  const ItemDev* items;
+  int64_t stride;
   double scale;
   __device__ void operator()(int pb, int64_t j, cd v) const {
-    if (j >= off && j < off + len) out[pb * stride + j - off] = cscale(v, scale);
+    const ItemDev& it = items[pb];
+    const int64_t off = it.cm + it.k - 1;
+    if (j >= off && j < off + it.cn) out[pb * stride + j - off] = cscale(v, scale);
   }
 };
-// window of the inverse transform [off, off+len) scaled by 1/N into the user output
-struct StoreWindowUser {
-  void* out;
-  int64_t stride, off, len;
+// window [cn + k - 1, cn + k - 1 + cm) of the inverse transform, scaled by 1/N, into the user x (m < n)
+struct StoreWindowUserX {
+  const ItemDev* items;
   int dtype;
   double scale;
   __device__ void operator()(int pb, int64_t j, cd v) const {
-    if (j >= off && j < off + len) store_user(out, pb * stride + j - off, dtype, cscale(v, scale));
+    const ItemDev& it = items[pb];
+    const int64_t off = it.cn + it.k - 1;
+    if (j >= off && j < off + it.cm) store_user(it.x, j - off, dtype, cscale(v, scale));
   }
 };
-// -y (complex, length len) placed at offset off
-struct LoadPlaceNegC {
+// -y (the item's cn entries) placed at offset cm + k - 1
+struct LoadPlaceNegY {
   const cd* y;
-  int64_t stride, off, len;
+  const ItemDev* items;
+  int64_t stride;
   __device__ cd operator()(int pb, int64_t j) const {
-    if (j < off || j >= off + len) return mkc(0.0, 0.0);
+    const ItemDev& it = items[pb];
+    const int64_t off = it.cm + it.k - 1;
+    if (j < off || j >= off + it.cn) return mkc(0.0, 0.0);
     cd v = y[pb * stride + j - off];
     return mkc(-v.x, -v.y);
   }
@@ -193,13 +254,18 @@ struct StoreConditions {
   const cd* that;
   const cd* wN;
   const double* lam;
-  int64_t N, cm, cn, k;
+  const ItemDev* items;
+  const cd* specG;  // Toeplitz-Gramian plans: DFT of G's generator (F's x component); null for l2
+  int64_t N;
   __device__ void operator()(int pb, int64_t e, cd yh) const {
+    const ItemDev& it = items[pb];
+    const int64_t cm = it.cm, cn = it.cn, k = it.k;
     cd th = that[pb * N + e];
     cd wF = tw_at(wN, (e * (cm + k - 1)) % N);
     cd wG = tw_at(wN, (e * (cn + k - 1)) % N);
     cd lh = cmul(tw_at(wN, ((e * (k - 1)) % N + N) % N), cconj(th));
-    cd row[10] = {cscale(wF, lam[pb]), lh, mkc(1.0, 0.0), mkc(0.0, 0.0), yh,
+    const cd f0 = specG ? specG[pb * N + e] : cscale(wF, lam[pb]);
+    cd row[10] = {f0, lh, mkc(1.0, 0.0), mkc(0.0, 0.0), yh,
                   mkc(-th.x, -th.y), wG, mkc(0.0, 0.0), mkc(1.0, 0.0), mkc(0.0, 0.0)};
     int64_t base = (pb * N + e) * 10;
 #pragma unroll
@@ -210,16 +276,24 @@ struct StoreConditions {
   }
 };
 
-__global__ void k_reset_peak(unsigned long long* peak, int* bad, int nb) {
+__global__ void k_reset_peak(unsigned long long* peak, int* bad, unsigned long long* peakG, int nb) {
   for (int i = threadIdx.x; i < nb; i += blockDim.x) {
     peak[i] = 0ULL;
     bad[i] = 0;
+    if (peakG) peakG[i] = 0ULL;
   }
 }
-__global__ void k_reset_tree(int* delta, int d0, int d1, int d2, int d3, int* ndiff, int nb) {
+// Eq. (taudef) with tau = [cn-1, cm-1, cm+k-2, cn+k-2, 0] (reading R3); the starting basis I has
+// tau-degrees delta = -tau
+__global__ void k_reset_tree(const ItemDev* __restrict__ items, int* delta, int* ndiff, int nb) {
   for (int pb = threadIdx.x; pb < nb; pb += blockDim.x) {
+    const ItemDev& it = items[pb];
     int* d = delta + 8 * pb;
-    d[0] = d0; d[1] = d1; d[2] = d2; d[3] = d3; d[4] = 0;
+    d[0] = -(int)(it.cn - 1);
+    d[1] = -(int)(it.cm - 1);
+    d[2] = -(int)(it.cm + it.k - 2);
+    d[3] = -(int)(it.cn + it.k - 2);
+    d[4] = 0;
     ndiff[4 * pb] = 0;
   }
 }
@@ -228,48 +302,53 @@ static inline dim3 grid2(int64_t n, int nb, int threads = 256, int cap = 4096) {
   return dim3((unsigned)std::max<int64_t>(1, std::min<int64_t>((n + threads - 1) / threads, cap)), (unsigned)nb);
 }
 
-// that = DFT(c_T) of each problem's core matrix (Sec. 3.1, Eq. (circdiag))
-int launch_spectrum(Plan& P, const UserArrays& u, int rhs_is_y) {
+// that = DFT(c_T) of each item's core matrix (Sec. 3.1, Eq. (circdiag)), after the input check
+int launch_spectrum(Plan& P, int rhs_is_y) {
   cudaStream_t s = P.stream;
   int nl = 0, r;
-  k_reset_peak<<<1, 256, 0, s>>>(P.peak, P.bad, P.nb);
+  k_reset_peak<<<1, 256, 0, s>>>(P.peak, P.bad, P.peakG, P.nb);
   ++nl;
-  CoreDiag a{u.col, u.row, u.col_stride, u.row_stride, P.dtype, P.dual};
-  // the user right-hand side: y (n entries) for the normal-equation form, else b (m entries)
-  const int64_t rhs_len = rhs_is_y ? P.n : P.m;
-  k_peak<<<grid2(P.cm + P.cn, P.nb, 256, 1024), 256, 0, s>>>(a, P.cm, P.cn, P.peak, u.rhs, u.rhs_stride, rhs_len,
-                                                              P.dtype, P.bad, P.status);
+  k_peak<<<grid2(std::max(P.cm + P.cn, P.m), P.nb, 256, 1024), 256, 0, s>>>(P.items, P.dtype, rhs_is_y, P.peak, P.bad,
+                                                                            P.status, P.peakG);
   ++nl;
   if (cudaGetLastError() != cudaSuccess) return TIKH_ECUDA;
   const FftPlan& FN = P.ffts[P.fft_of_len.at(P.N)];
-  LoadGenerator lg{a, P.cm, P.cn, P.N, P.k, P.opts.fill, P.dtype == TIKH_C128 ? 1 : 0, P.peak};
+  LoadGenerator lg{P.items, P.N, P.opts.fill, P.dtype, P.peak};
   if ((r = fft_run(FN, P.nb, +1, lg, StoreVec{P.specT, P.N}, P.ftmpN, s)) < 0) return TIKH_ECUDA;
-  return nl + r;
+  nl += r;
+  if (P.gram) {  // DFT of G's circulant generator (F's x component, Sec. 3.4)
+    LoadGramGenerator lgg{P.items, P.N, P.opts.fill, P.dtype, P.peakG};
+    if ((r = fft_run(FN, P.nb, +1, lgg, StoreVec{P.specG, P.N}, P.ftmpN, s)) < 0) return TIKH_ECUDA;
+    nl += r;
+  }
+  return nl;
 }
 
-__global__ void k_to_complex(const void* in, int64_t stride, int dtype, int64_t n, cd* out) {
+// the item's user vector (cn entries: y, or b for m < n) as complex, stride = the plan's largest cn
+__global__ void k_rhs_to_complex(const ItemDev* __restrict__ items, int dtype, int64_t stride, cd* out) {
   const int pb = blockIdx.y;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    out[pb * n + i] = load_user(in, pb * stride + i, dtype);
+  const ItemDev it = items[pb];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < it.cn; i += (int64_t)gridDim.x * blockDim.x)
+    out[pb * stride + i] = load_user(it.rhs, i, dtype);
 }
 
-// core right-hand side y (complex, cn per problem): T^H b, or the given vector (user y, or b for m < n)
-int launch_rhs(Plan& P, const UserArrays& u, int rhs_is_y) {
+// core right-hand side y (complex, cn per item): T^H b, or the given vector (user y, or b for m < n)
+int launch_rhs(Plan& P, int rhs_is_y) {
   cudaStream_t s = P.stream;
   int nl = 0, r;
-  const int64_t N = P.N, k = P.k, cm = P.cm, cn = P.cn;
+  const int64_t N = P.N;
   if (rhs_is_y) {
-    k_to_complex<<<grid2(cn, P.nb), 256, 0, s>>>(u.rhs, u.rhs_stride, P.dtype, cn, P.ybuf);
+    k_rhs_to_complex<<<grid2(P.cn, P.nb), 256, 0, s>>>(P.items, P.dtype, P.cn, P.ybuf);
     return cudaGetLastError() == cudaSuccess ? 1 : TIKH_ECUDA;
   }
   // y = T^H b: rows cm+k-1.. of circ(c_H) [b; 0] (Sec. 3.1), DFT(c_H) = lamH
   const FftPlan& FN = P.ffts[P.fft_of_len.at(N)];
-  if ((r = fft_run(FN, P.nb, +1, LoadPadUser{u.rhs, u.rhs_stride, cm, P.dtype},
-                   StoreMulLamH{P.work, P.specT, P.wN, N, k}, P.ftmpN, s)) < 0)
+  if ((r = fft_run(FN, P.nb, +1, LoadPadUserRhs{P.items, P.dtype}, StoreMulLamH{P.work, P.specT, P.wN, P.items, N},
+                   P.ftmpN, s)) < 0)
     return TIKH_ECUDA;
   nl += r;
-  if ((r = fft_run(FN, P.nb, -1, LoadVec{P.work, N}, StoreWindowC{P.ybuf, cn, cm + k - 1, cn, 1.0 / (double)N},
-                   P.ftmpN, s)) < 0)
+  if ((r = fft_run(FN, P.nb, -1, LoadVec{P.work, N}, StoreWindowY{P.ybuf, P.items, P.cn, 1.0 / (double)N}, P.ftmpN,
+                   s)) < 0)
     return TIKH_ECUDA;
   return nl + r;
 }
@@ -277,13 +356,11 @@ int launch_rhs(Plan& P, const UserArrays& u, int rhs_is_y) {
 // conditions F, G of the core system with right-hand side y (Sec. 3.3, 4.1); resets the degrees
 int launch_conditions(Plan& P, const cd* y) {
   cudaStream_t s = P.stream;
-  const int64_t N = P.N, k = P.k, cm = P.cm, cn = P.cn;
-  // Eq. (taudef) with tau = [cn-1, cm-1, cm+k-2, cn+k-2, 0]; the starting basis has delta = -tau
-  k_reset_tree<<<1, 256, 0, s>>>(P.delta, -(int)(cn - 1), -(int)(cm - 1), -(int)(cm + k - 2), -(int)(cn + k - 2),
-                                 P.ndiff, P.nb);
+  const int64_t N = P.N;
+  k_reset_tree<<<1, 256, 0, s>>>(P.items, P.delta, P.ndiff, P.nb);
   const FftPlan& FN = P.ffts[P.fft_of_len.at(N)];
-  StoreConditions sc{P.R, P.Phi, P.specT, P.wN, P.lam, N, cm, cn, k};
-  int r = fft_run(FN, P.nb, +1, LoadPlaceNegC{y, cn, cm + k - 1, cn}, sc, P.ftmpN, s);
+  StoreConditions sc{P.R, P.Phi, P.specT, P.wN, P.lam, P.items, P.gram ? P.specG : nullptr, N};
+  int r = fft_run(FN, P.nb, +1, LoadPlaceNegY{y, P.items, P.cn}, sc, P.ftmpN, s);
   if (r < 0) return TIKH_ECUDA;
   return r + 1;
 }
@@ -291,8 +368,10 @@ int launch_conditions(Plan& P, const cd* y) {
 // ------------------------------------------------------------------------------------------------
 // extraction: x(z) = B*_1^{(j)}(z) / B*_5^{(j)}, j the column of tau-degree 0 (Sec. 4.3 end, 5)
 // ------------------------------------------------------------------------------------------------
-__global__ void k_extract(BasisBuf B, const int* delta, int* status, int64_t cn, cd* out) {
+__global__ void k_extract(BasisBuf B, const int* delta, int* status, const ItemDev* __restrict__ items, int64_t stride,
+                          cd* out) {
   const int pb = blockIdx.y;
+  const int64_t cn = items[pb].cn;
   const int* dl = delta + 8 * pb;
   int js = -1, nz = 0, no = 0;
   for (int j = 0; j < 5; ++j) {
@@ -318,44 +397,53 @@ __global__ void k_extract(BasisBuf B, const int* delta, int* status, int64_t cn,
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cn; i += (int64_t)gridDim.x * blockDim.x) {
     cd v = i < l1 ? cmul(b1[i], inv) : mkc(0.0, 0.0);
     if (!isfinite(v.x) || !isfinite(v.y)) set_status(status, ST_NUMERIC);
-    out[pb * cn + i] = v;
+    out[pb * stride + i] = v;
   }
 }
 
 int launch_extract(Plan& P, cd* out) {
-  k_extract<<<grid2(P.cn, P.nb, 256, 2048), 256, 0, P.stream>>>(P.buf[0][0], P.delta, P.status, P.cn, out);
+  k_extract<<<grid2(P.cn, P.nb, 256, 2048), 256, 0, P.stream>>>(P.buf[0][0], P.delta, P.status, P.items, P.cn, out);
   return cudaGetLastError() == cudaSuccess ? 1 : TIKH_ECUDA;
 }
 
 // ------------------------------------------------------------------------------------------------
 // refinement pieces: r = y - (T_c^H T_c x + lam x) by FFT matvecs (cf. Sec. 7.3), x += dx
 // ------------------------------------------------------------------------------------------------
-// keep the inverse-transform window [off, N) scaled at its own index, zero before
+// keep the inverse-transform window [cn + k - 1, N) scaled at its own index, zero before
 struct StoreKeepFrom {
   cd* out;
-  int64_t N, off;
+  const ItemDev* items;
+  int64_t N;
   double scale;
   __device__ void operator()(int pb, int64_t j, cd v) const {
+    const int64_t off = items[pb].cn + items[pb].k - 1;
     out[pb * N + j] = j >= off ? cscale(v, scale) : mkc(0.0, 0.0);
   }
 };
-// [u; 0] with u = in[off .. off + len)
+// [u; 0] with u = in[cn + k - 1 .. cn + k - 1 + cm)
 struct LoadShift {
   const cd* in;
-  int64_t N, off, len;
-  __device__ cd operator()(int pb, int64_t j) const { return j < len ? in[pb * N + off + j] : mkc(0.0, 0.0); }
+  const ItemDev* items;
+  int64_t N;
+  __device__ cd operator()(int pb, int64_t j) const {
+    const ItemDev& it = items[pb];
+    return j < it.cm ? in[pb * N + it.cn + it.k - 1 + j] : mkc(0.0, 0.0);
+  }
 };
 struct StoreResidual {
   cd* r;
   const cd* y;
   const cd* x;
   const double* lam;
-  int64_t cn, off;
+  const ItemDev* items;
+  int64_t stride;
   double scale;
   double* norms;
   __device__ void operator()(int pb, int64_t j, cd v) const {
-    if (j < off || j >= off + cn) return;
-    int64_t i = pb * cn + j - off;
+    const ItemDev& it = items[pb];
+    const int64_t off = it.cm + it.k - 1;
+    if (j < off || j >= off + it.cn) return;
+    int64_t i = pb * stride + j - off;
     double l = lam[pb];
     cd ax = mkc(v.x * scale + l * x[i].x, v.y * scale + l * x[i].y);
     cd ri = csub(y[i], ax);
@@ -365,67 +453,129 @@ struct StoreResidual {
   }
 };
 
-__global__ void k_zero_norms(double* p, int nb) {
-  for (int i = threadIdx.x; i < 4 * nb; i += blockDim.x) p[i] = 0.0;
+// norms[4 pb + 0, 1]: ||r||^2, ||y||^2 of the last residual; [4 pb + 2, 3]: ||dx||^2, ||x + dx||^2 of the
+// last correction.  k_zero_norms clears the pair starting at `first` (0 or 2) of every item.
+__global__ void k_zero_norms(double* p, int nb, int first) {
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+    p[4 * i + first] = 0.0;
+    p[4 * i + first + 1] = 0.0;
+  }
 }
+
+// T_c^H u spectrum (lamH U) plus, for Toeplitz-Gramian plans, G's spectrum times X = DFT([x; 0]): the inverse
+// transform's window [N - n, N) is then L^H L x + G x
+struct StoreMulLamHPlusG {
+  cd* out;
+  const cd* that;
+  const cd* wN;
+  const ItemDev* items;
+  const cd* specG;
+  const cd* X;
+  int64_t N;
+  __device__ void operator()(int pb, int64_t e, cd v) const {
+    const int64_t k = items[pb].k;
+    int64_t t = ((e * (k - 1)) % N + N) % N;
+    const int64_t i = pb * N + e;
+    out[i] = cfma(specG[i], X[i], cmul(v, cmul(tw_at(wN, t), cconj(that[i]))));
+  }
+};
+// stores t_hat X and X itself (the refinement of a Toeplitz-Gramian plan needs both)
+struct StoreMulTKeep {
+  cd* out;
+  cd* keep;
+  const cd* that;
+  int64_t N;
+  __device__ void operator()(int pb, int64_t e, cd v) const {
+    out[pb * N + e] = cmul(v, that[pb * N + e]);
+    keep[pb * N + e] = v;
+  }
+};
 
 int launch_residual(Plan& P, const cd* y, const cd* x, cd* r) {
   cudaStream_t s = P.stream;
-  const int64_t N = P.N, k = P.k, cm = P.cm, cn = P.cn;
+  const int64_t N = P.N;
   const FftPlan& FN = P.ffts[P.fft_of_len.at(N)];
   int nl = 0, q;
-  k_zero_norms<<<1, 256, 0, s>>>(P.norms, P.nb);
+  k_zero_norms<<<1, 256, 0, s>>>(P.norms, P.nb, 0);
   ++nl;
   // u = T_c x: rows cn+k-1.. of circ(c_T) [x; 0]
-  if ((q = fft_run(FN, P.nb, +1, LoadPadC{x, cn, cn}, StoreMulT{P.work, P.specT, N}, P.ftmpN, s)) < 0)
-    return TIKH_ECUDA;
+  if (P.gram)
+    q = fft_run(FN, P.nb, +1, LoadPadCn{x, P.items, P.cn}, StoreMulTKeep{P.work, P.gX, P.specT, N}, P.ftmpN, s);
+  else
+    q = fft_run(FN, P.nb, +1, LoadPadCn{x, P.items, P.cn}, StoreMulT{P.work, P.specT, N}, P.ftmpN, s);
+  if (q < 0) return TIKH_ECUDA;
   nl += q;
-  if ((q = fft_run(FN, P.nb, -1, LoadVec{P.work, N}, StoreKeepFrom{P.work2, N, cn + k - 1, 1.0 / (double)N}, P.ftmpN,
+  if ((q = fft_run(FN, P.nb, -1, LoadVec{P.work, N}, StoreKeepFrom{P.work2, P.items, N, 1.0 / (double)N}, P.ftmpN,
                    s)) < 0)
     return TIKH_ECUDA;
   nl += q;
-  // T_c^H u: rows cm+k-1.. of circ(c_H) [u; 0]
-  if ((q = fft_run(FN, P.nb, +1, LoadShift{P.work2, N, cn + k - 1, cm}, StoreMulLamH{P.work, P.specT, P.wN, N, k},
-                   P.ftmpN, s)) < 0)
-    return TIKH_ECUDA;
+  // T_c^H u: rows cm+k-1.. of circ(c_H) [u; 0] (plus G x for Toeplitz-Gramian plans, same rows)
+  if (P.gram)
+    q = fft_run(FN, P.nb, +1, LoadShift{P.work2, P.items, N},
+                StoreMulLamHPlusG{P.work, P.specT, P.wN, P.items, P.specG, P.gX, N}, P.ftmpN, s);
+  else
+    q = fft_run(FN, P.nb, +1, LoadShift{P.work2, P.items, N}, StoreMulLamH{P.work, P.specT, P.wN, P.items, N},
+                P.ftmpN, s);
+  if (q < 0) return TIKH_ECUDA;
   nl += q;
-  StoreResidual sr{r, y, x, P.lam, cn, cm + k - 1, 1.0 / (double)N, P.norms};
+  StoreResidual sr{r, y, x, P.lam, P.items, P.cn, 1.0 / (double)N, P.norms};
   if ((q = fft_run(FN, P.nb, -1, LoadVec{P.work, N}, sr, P.ftmpN, s)) < 0) return TIKH_ECUDA;
   return nl + q;
 }
 
-__global__ void k_axpy(cd* x, const cd* dx, int64_t n) {
-  const int64_t off = (int64_t)blockIdx.y * n;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    x[off + i] = cadd(x[off + i], dx[off + i]);
+__global__ void k_axpy(cd* x, const cd* dx, const ItemDev* __restrict__ items, int64_t stride, double* norms) {
+  __shared__ double red[2][8];
+  const int64_t off = (int64_t)blockIdx.y * stride, n = items[blockIdx.y].cn;
+  double sd = 0.0, sx = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const cd d = dx[off + i], v = cadd(x[off + i], d);
+    x[off + i] = v;
+    sd += cabs2(d);
+    sx += cabs2(v);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    sd += __shfl_xor_sync(0xffffffffu, sd, o);
+    sx += __shfl_xor_sync(0xffffffffu, sx, o);
+  }
+  if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = sd; red[1][threadIdx.x >> 5] = sx; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) { sd += red[0][w]; sx += red[1][w]; }
+    atomicAdd(norms + 4 * blockIdx.y + 2, sd);
+    atomicAdd(norms + 4 * blockIdx.y + 3, sx);
+  }
 }
 
+// x += dx, accumulating ||dx||^2 and ||x + dx||^2 (the relative size of the last correction)
 int launch_axpy(Plan& P, cd* x, const cd* dx) {
-  k_axpy<<<grid2(P.cn, P.nb), 256, 0, P.stream>>>(x, dx, P.cn);
-  return cudaGetLastError() == cudaSuccess ? 1 : TIKH_ECUDA;
+  k_zero_norms<<<1, 256, 0, P.stream>>>(P.norms, P.nb, 2);
+  k_axpy<<<grid2(P.cn, P.nb), 256, 0, P.stream>>>(x, dx, P.items, P.cn, P.norms);
+  return cudaGetLastError() == cudaSuccess ? 2 : TIKH_ECUDA;
 }
 
-__global__ void k_from_complex(const cd* in, int64_t n, void* out, int64_t stride, int dtype) {
+__global__ void k_output_direct(const cd* in, int64_t stride, const ItemDev* __restrict__ items, int dtype) {
   const int pb = blockIdx.y;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    store_user(out, pb * stride + i, dtype, in[pb * n + i]);
+  const ItemDev it = items[pb];
+  if (it.dual) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < it.cn; i += (int64_t)gridDim.x * blockDim.x)
+    store_user(it.x, i, dtype, in[pb * stride + i]);
 }
 
-// user x from the core solution: x itself, or x = T^H v = T_c v for m < n
-int launch_output(Plan& P, const cd* v, const UserArrays& u) {
+// user x from the core solution: x itself, or x = T^H v = T_c v for m < n (the plan's items are
+// either all direct or all dual: the two forms have different core shapes)
+int launch_output(Plan& P, const cd* v) {
   cudaStream_t s = P.stream;
   if (!P.dual) {
-    k_from_complex<<<grid2(P.cn, P.nb), 256, 0, s>>>(v, P.cn, u.x, u.x_stride, P.dtype);
+    k_output_direct<<<grid2(P.cn, P.nb), 256, 0, s>>>(v, P.cn, P.items, P.dtype);
     return cudaGetLastError() == cudaSuccess ? 1 : TIKH_ECUDA;
   }
   const FftPlan& FN = P.ffts[P.fft_of_len.at(P.N)];
   int nl = 0, r;
-  if ((r = fft_run(FN, P.nb, +1, LoadPadC{v, P.cn, P.cn}, StoreMulT{P.work, P.specT, P.N}, P.ftmpN, s)) < 0)
+  if ((r = fft_run(FN, P.nb, +1, LoadPadCn{v, P.items, P.cn}, StoreMulT{P.work, P.specT, P.N}, P.ftmpN, s)) < 0)
     return TIKH_ECUDA;
   nl += r;
-  if ((r = fft_run(FN, P.nb, -1, LoadVec{P.work, P.N},
-                   StoreWindowUser{u.x, u.x_stride, P.cn + P.k - 1, P.cm, P.dtype, 1.0 / (double)P.N}, P.ftmpN, s)) <
-      0)
+  if ((r = fft_run(FN, P.nb, -1, LoadVec{P.work, P.N}, StoreWindowUserX{P.items, P.dtype, 1.0 / (double)P.N},
+                   P.ftmpN, s)) < 0)
     return TIKH_ECUDA;
   return nl + r;
 }

@@ -15,14 +15,16 @@ LIB_PATH = os.path.join(_HERE, "_build", "libtikh.so")
 TIKH_OK, TIKH_EINVAL, TIKH_ENOMEM, TIKH_ECUDA, TIKH_ENUMERIC, TIKH_EDIFFICULT, TIKH_ENOTCONVERGED, \
     TIKH_ETIMEOUT, TIKH_EDEGREE = 0, -1, -2, -3, -4, -5, -6, -7, -8
 TIKH_R64, TIKH_C128 = 0, 1
-TIKH_PREC_FP64 = 0
+TIKH_PREC_FP64, TIKH_PREC_FP32_REFINE, TIKH_PREC_FP32 = 0, 1, 2
+PRECISIONS = {"fp64": TIKH_PREC_FP64, "fp32_refine": TIKH_PREC_FP32_REFINE, "fp32": TIKH_PREC_FP32}
 
 
 class tikh_opts(ctypes.Structure):
     _fields_ = [("n_lim", ctypes.c_int), ("m_min", ctypes.c_int), ("fill", ctypes.c_int),
                 ("eps_diff", ctypes.c_double), ("max_difficult", ctypes.c_int), ("refine_steps", ctypes.c_int),
                 ("batch", ctypes.c_int), ("graph", ctypes.c_int),
-                ("prod_direct_max", ctypes.c_int), ("eval_direct_max", ctypes.c_int), ("wait_polls", ctypes.c_int)]
+                ("prod_direct_max", ctypes.c_int), ("eval_direct_max", ctypes.c_int), ("wait_polls", ctypes.c_int),
+                ("refine_tol", ctypes.c_double)]
 
 
 class tikh_stats(ctypes.Structure):
@@ -31,11 +33,28 @@ class tikh_stats(ctypes.Structure):
                 ("jstar", ctypes.c_int), ("retries", ctypes.c_int), ("kernel_launches", ctypes.c_int64),
                 ("workspace_bytes", ctypes.c_int64), ("refine_steps", ctypes.c_int), ("rel_residual", ctypes.c_double),
                 ("batch", ctypes.c_int), ("prof_leaf_ms", ctypes.c_double), ("prof_leaf_launches", ctypes.c_int64),
-                ("graph", ctypes.c_int), ("prof_kind_ms", ctypes.c_double * 4), ("prof_kind_count", ctypes.c_int64 * 4)]
+                ("graph", ctypes.c_int), ("prof_kind_ms", ctypes.c_double * 4), ("prof_kind_count", ctypes.c_int64 * 4),
+                ("model_flops", ctypes.c_double * 4), ("model_flops_fp32", ctypes.c_double * 4),
+                ("last_correction", ctypes.c_double)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}
-        for f in ("delta", "prof_kind_ms", "prof_kind_count"):
+        for f in ("delta", "prof_kind_ms", "prof_kind_count", "model_flops", "model_flops_fp32"):
+            d[f] = list(getattr(self, f))
+        return d
+
+
+class tikh_batch_stats(ctypes.Structure):
+    _fields_ = [("ngroups", ctypes.c_int), ("max_waves", ctypes.c_int), ("items", ctypes.c_int64),
+                ("kernel_launches", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64), ("graph", ctypes.c_int),
+                ("retries", ctypes.c_int), ("n_difficult", ctypes.c_int64), ("rel_residual", ctypes.c_double),
+                ("last_correction", ctypes.c_double), ("model_flops", ctypes.c_double * 4),
+                ("model_flops_fp32", ctypes.c_double * 4), ("prof_kind_ms", ctypes.c_double * 4),
+                ("prof_kind_count", ctypes.c_int64 * 4)]
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_}
+        for f in ("model_flops", "model_flops_fp32", "prof_kind_ms", "prof_kind_count"):
             d[f] = list(getattr(self, f))
         return d
 
@@ -49,7 +68,9 @@ class TikhError(RuntimeError):
 _lib = None
 
 EXPORTED = ["tikh_plan_create", "tikh_solve", "tikh_solve_async", "tikh_solve_normal", "tikh_solve_host",
-            "tikh_solve_batched",
+            "tikh_solve_strided", "tikh_batch_plan_create", "tikh_solve_batched", "tikh_batch_get_stats",
+            "tikh_batch_plan_destroy", "tikh_test_fft32", "tikh_batch_set_profiling", "tikh_plan_create_gramian",
+            "tikh_solve_gramian", "tikh_nufft_gramian", "tikh_test_rcp", "tikh_solve_grad_strided",
             "tikh_sync", "tikh_get_stats", "tikh_plan_destroy", "tikh_strerror", "tikh_test_fft", "tikh_test_leaf",
             "tikh_fft_noalloc", "tikh_set_profiling", "tikh_solve_grad", "tikh_get_difficult", "tikh_test_peak"]
 
@@ -66,10 +87,21 @@ def lib():
         L.tikh_plan_create.argtypes = [ctypes.POINTER(vp), i64, i64, ci, ci, ctypes.POINTER(tikh_opts), vp]
         for f in ("tikh_solve", "tikh_solve_async", "tikh_solve_normal", "tikh_solve_host"):
             getattr(L, f).argtypes = [vp, vp, vp, vp, dbl, vp]
-        L.tikh_solve_batched.argtypes = [vp, ci, vp, i64, vp, i64, vp, i64, vp, vp, i64]
+        L.tikh_solve_strided.argtypes = [vp, ci, vp, i64, vp, i64, vp, i64, vp, vp, i64]
+        L.tikh_batch_plan_create.argtypes = [ctypes.POINTER(vp), ci, vp, vp, ci, ci, ci, ctypes.POINTER(tikh_opts),
+                                             i64, vp]
+        L.tikh_solve_batched.argtypes = [vp, ci, vp, vp, vp, vp, vp, ci, vp, vp]
+        L.tikh_batch_get_stats.argtypes = [vp, ctypes.POINTER(tikh_batch_stats)]
+        L.tikh_plan_create_gramian.argtypes = [ctypes.POINTER(vp), i64, i64, ci, ci, ctypes.POINTER(tikh_opts), vp]
+        L.tikh_solve_gramian.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.tikh_nufft_gramian.argtypes = [i64, vp, vp, vp, i64, vp, vp, vp]
+        L.tikh_batch_set_profiling.argtypes = [vp, ci]
+        L.tikh_batch_plan_destroy.argtypes = [vp]
+        L.tikh_batch_plan_destroy.restype = None
         L.tikh_sync.argtypes = [vp]
         L.tikh_set_profiling.argtypes = [vp, ci]
         L.tikh_solve_grad.argtypes = [vp, vp, vp, vp, dbl, vp, vp, vp, vp, vp, ctypes.POINTER(dbl)]
+        L.tikh_solve_grad_strided.argtypes = [vp, ci, vp, i64, vp, i64, vp, i64, vp, vp, i64, vp, i64, vp, vp, vp, vp]
         L.tikh_get_stats.argtypes = [vp, ctypes.POINTER(tikh_stats)]
         L.tikh_get_difficult.argtypes = [vp, vp, i64, ctypes.POINTER(i64)]
         L.tikh_plan_destroy.argtypes = [vp]
@@ -77,6 +109,8 @@ def lib():
         L.tikh_strerror.argtypes = [ci]
         L.tikh_strerror.restype = ctypes.c_char_p
         L.tikh_test_fft.argtypes = [i64, vp, ci, vp]
+        L.tikh_test_fft32.argtypes = [i64, vp, ci, vp]
+        L.tikh_test_rcp.argtypes = [i64, vp, vp, vp]
         L.tikh_fft_noalloc.argtypes = [i64, vp, ci, vp]
         L.tikh_test_peak.argtypes = [ci, ctypes.POINTER(dbl), vp]
         L.tikh_test_leaf.argtypes = [ci, vp, vp, vp, dbl, vp, vp, vp, vp, vp, vp, vp, vp]
@@ -105,6 +139,33 @@ def tikh_plan_create(m, n, dtype=TIKH_R64, prec=TIKH_PREC_FP64, opts=None, strea
     return h
 
 
+def tikh_plan_create_gramian(n, p, dtype=TIKH_R64, prec=TIKH_PREC_FP64, opts=None, stream=0):
+    h = ctypes.c_void_p()
+    o = ctypes.byref(opts) if opts is not None else None
+    _check(lib().tikh_plan_create_gramian(ctypes.byref(h), int(n), int(p), int(dtype), int(prec), o,
+                                          ctypes.c_void_p(int(stream))), "tikh_plan_create_gramian")
+    return h
+
+
+def tikh_solve_gramian(plan, g, lcol, lrow, y, x):
+    _check(lib().tikh_solve_gramian(plan, g, lcol, lrow, y, x), "tikh_solve_gramian")
+
+
+def tikh_nufft_gramian(K, f, w, X, n, g, y, stream=0):
+    _check(lib().tikh_nufft_gramian(int(K), f, w, X, int(n), g, y, ctypes.c_void_p(int(stream))),
+           "tikh_nufft_gramian")
+
+
+def nufft_gramian(f, w, X, n):
+    """(g, y) of the weighted non-uniform Fourier Gramian from CUDA tensors f, w (float64) and X (complex128)."""
+    import torch
+    g = torch.empty(int(n), dtype=torch.complex128, device=f.device)
+    y = torch.empty(int(n), dtype=torch.complex128, device=f.device)
+    p = lambda t: ctypes.c_void_p(t.data_ptr())
+    tikh_nufft_gramian(f.numel(), p(f), p(w), p(X), n, p(g), p(y), torch.cuda.current_stream().cuda_stream)
+    return g, y
+
+
 def tikh_solve(plan, col, row, b, lam, x):
     _check(lib().tikh_solve(plan, col, row, b, float(lam), x), "tikh_solve")
 
@@ -117,10 +178,59 @@ def tikh_solve_normal(plan, col, row, y, lam, x):
     _check(lib().tikh_solve_normal(plan, col, row, y, float(lam), x), "tikh_solve_normal")
 
 
-def tikh_solve_batched(plan, batch, col, col_stride, row, row_stride, b, b_stride, lambdas, x, x_stride):
+def tikh_solve_strided(plan, batch, col, col_stride, row, row_stride, b, b_stride, lambdas, x, x_stride):
     lam = np.ascontiguousarray(lambdas, dtype=np.float64)
-    _check(lib().tikh_solve_batched(plan, int(batch), col, int(col_stride), row, int(row_stride), b, int(b_stride),
-                                    lam.ctypes.data_as(ctypes.c_void_p), x, int(x_stride)), "tikh_solve_batched")
+    _check(lib().tikh_solve_strided(plan, int(batch), col, int(col_stride), row, int(row_stride), b, int(b_stride),
+                                    lam.ctypes.data_as(ctypes.c_void_p), x, int(x_stride)), "tikh_solve_strided")
+
+
+def _i64s(v):
+    a = np.ascontiguousarray(np.asarray(v, dtype=np.int64).reshape(-1))
+    return a, a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _ptrs(v):
+    a = (ctypes.c_void_p * len(v))(*[int(p) for p in v])
+    return a, ctypes.cast(a, ctypes.c_void_p)
+
+
+def tikh_batch_plan_create(m, n, nlambda, dtype=TIKH_R64, prec=TIKH_PREC_FP64, opts=None, max_workspace_bytes=0,
+                           stream=0):
+    h = ctypes.c_void_p()
+    ma, mp = _i64s(m)
+    na, npt = _i64s(n)
+    o = ctypes.byref(opts) if opts is not None else None
+    _check(lib().tikh_batch_plan_create(ctypes.byref(h), int(ma.size), mp, npt, int(nlambda), int(dtype), int(prec), o,
+                                        int(max_workspace_bytes), ctypes.c_void_p(int(stream))),
+           "tikh_batch_plan_create")
+    return h
+
+
+def tikh_solve_batched(plan, m, n, col_ptrs, row_ptrs, b_ptrs, lambdas, x_ptrs):
+    """Pointer lists are device addresses (ints); lambdas a host sequence."""
+    ma, mp = _i64s(m)
+    na, npt = _i64s(n)
+    ca, cp = _ptrs(col_ptrs)
+    ra, rp = _ptrs(row_ptrs)
+    ba, bp = _ptrs(b_ptrs)
+    xa, xp = _ptrs(x_ptrs)
+    lam = np.ascontiguousarray(lambdas, dtype=np.float64)
+    _check(lib().tikh_solve_batched(plan, int(ma.size), mp, npt, cp, rp, bp, int(lam.size),
+                                    lam.ctypes.data_as(ctypes.c_void_p), xp), "tikh_solve_batched")
+
+
+def tikh_batch_get_stats(plan):
+    st = tikh_batch_stats()
+    _check(lib().tikh_batch_get_stats(plan, ctypes.byref(st)), "tikh_batch_get_stats")
+    return st.as_dict()
+
+
+def tikh_batch_set_profiling(plan, flags):
+    _check(lib().tikh_batch_set_profiling(plan, int(flags)), "tikh_batch_set_profiling")
+
+
+def tikh_batch_plan_destroy(plan):
+    lib().tikh_batch_plan_destroy(plan)
 
 
 def tikh_solve_grad(plan, col, row, b, lam, x, dldx, dcol, drow, db):
@@ -163,6 +273,14 @@ def tikh_set_profiling(plan, flags):
 
 def tikh_test_fft(n, data, sign, stream=0):
     _check(lib().tikh_test_fft(int(n), data, int(sign), ctypes.c_void_p(int(stream))), "tikh_test_fft")
+
+
+def tikh_test_fft32(n, data, sign, stream=0):
+    _check(lib().tikh_test_fft32(int(n), data, int(sign), ctypes.c_void_p(int(stream))), "tikh_test_fft32")
+
+
+def tikh_test_rcp(n, d, out, stream=0):
+    _check(lib().tikh_test_rcp(int(n), d, out, ctypes.c_void_p(int(stream))), "tikh_test_rcp")
 
 
 def tikh_test_peak(kind, stream=0):
@@ -230,19 +348,20 @@ class Plan:
 
     def __init__(self, m, n, dtype="r64", n_lim=32, m_min=0, fill=0, eps_diff=1e-8, max_difficult=4096,
                  refine_steps=0, batch=1, graph=False, prod_direct_max=0, eval_direct_max=0, wait_polls=0,
-                 stream=None):
+                 refine_tol=0.0, precision="fp64", stream=None):
         import torch
         self.m, self.n = int(m), int(n)
         self.dtype = TIKH_C128 if dtype in ("c128", TIKH_C128, torch.complex128) else TIKH_R64
         self.batch = int(batch)
         self.opts = tikh_opts(int(n_lim), int(m_min), int(fill), float(eps_diff), int(max_difficult),
                               int(refine_steps), self.batch, 1 if graph else 0, int(prod_direct_max),
-                              int(eval_direct_max), int(wait_polls))
+                              int(eval_direct_max), int(wait_polls), float(refine_tol))
+        self.prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
         handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
-        self.h = tikh_plan_create(self.m, self.n, self.dtype, TIKH_PREC_FP64, self.opts, handle)
+        self.h = tikh_plan_create(self.m, self.n, self.dtype, self.prec, self.opts, handle)
 
     def _args(self, col, row, v, vlen):
         import torch
@@ -267,7 +386,7 @@ class Plan:
         f(self.h, c, r, bb, lam, ctypes.c_void_p(x.data_ptr()))
         return x
 
-    def solve_batched(self, col, row, b, lams, x=None):
+    def solve_strided(self, col, row, b, lams, x=None):
         """Solve a batch: col (B, m) or (m,), row (B, n) or (n,), b (B, m) or (m,), lams (B,) on the host.
         A 1-D argument is shared by every problem of the batch (stride 0)."""
         import torch
@@ -286,17 +405,34 @@ class Plan:
         bb, bs = arg(b, self.m)
         if x is None:
             x = torch.empty((B, self.n), dtype=b.dtype, device=b.device)
-        tikh_solve_batched(self.h, B, c, cs, r, rs, bb, bs, lams, ctypes.c_void_p(x.data_ptr()), self.n)
+        tikh_solve_strided(self.h, B, c, cs, r, rs, bb, bs, lams, ctypes.c_void_p(x.data_ptr()), self.n)
         return x
 
     def grad(self, col, row, b, lam, x, dldx):
         """Adjoint: returns (dL/dcol, dL/drow, dL/db, dL/dlambda) for dL/dx = dldx (m >= n)."""
         c, r, bb = self._args(col, row, b, self.m)
         _, _, xx = self._args(col, row, x, self.n)
-        _, _, gg = self._args(col, row, dldx.contiguous(), self.n)
+        dl = dldx.contiguous()  # kept alive for the call
+        _, _, gg = self._args(col, row, dl, self.n)
         dcol, drow, db = torch_empty_like(col), torch_empty_like(row), torch_empty_like(b)
         dlam = tikh_solve_grad(self.h, c, r, bb, lam, xx, gg, ctypes.c_void_p(dcol.data_ptr()),
                                ctypes.c_void_p(drow.data_ptr()), ctypes.c_void_p(db.data_ptr()))
+        return dcol, drow, db, dlam
+
+    def grad_strided(self, col, row, b, lams, x, dldx):
+        """Adjoint of a batch: col (B, m), row (B, n), b (B, m), x and dldx (B, n) contiguous CUDA tensors, lams (B,)
+        on the host.  Returns (dL/dcol (B, m), dL/drow (B, n), dL/db (B, m), dL/dlambda (B,) numpy)."""
+        import torch
+        B = col.shape[0]
+        lam = np.ascontiguousarray(np.asarray(lams, dtype=np.float64).reshape(-1))
+        dcol, drow, db = torch.empty_like(col), torch.empty_like(row), torch.empty_like(b)
+        dlam = np.zeros(B, np.float64)
+        dl = dldx.contiguous()  # kept alive for the call
+        p = lambda t: ctypes.c_void_p(t.data_ptr())
+        _check(lib().tikh_solve_grad_strided(self.h, int(B), p(col), self.m, p(row), self.n, p(b), self.m,
+                                             lam.ctypes.data_as(ctypes.c_void_p), p(x), self.n, p(dl),
+                                             self.n, p(dcol), p(drow), p(db),
+                                             dlam.ctypes.data_as(ctypes.c_void_p)), "tikh_solve_grad_strided")
         return dcol, drow, db, dlam
 
     def solve_normal(self, col, row, y, lam, x=None):
@@ -334,6 +470,104 @@ class Plan:
     def close(self):
         if getattr(self, "h", None):
             tikh_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class GramianPlan(Plan):
+    """A plan for the Toeplitz-Gramian problem x = (G + L^H L)^{-1} y (G n x n Hermitian Toeplitz, L p x n)."""
+
+    def __init__(self, n, p, dtype="r64", n_lim=32, m_min=0, fill=0, eps_diff=1e-8, max_difficult=4096,
+                 refine_steps=0, graph=False, prod_direct_max=0, eval_direct_max=0, wait_polls=0, refine_tol=0.0,
+                 precision="fp64", stream=None):
+        import torch
+        self.m, self.n = int(p), int(n)
+        self.dtype = TIKH_C128 if dtype in ("c128", TIKH_C128, torch.complex128) else TIKH_R64
+        self.batch = 1
+        self.opts = tikh_opts(int(n_lim), int(m_min), int(fill), float(eps_diff), int(max_difficult),
+                              int(refine_steps), 1, 1 if graph else 0, int(prod_direct_max), int(eval_direct_max),
+                              int(wait_polls), float(refine_tol))
+        self.prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        self.h = tikh_plan_create_gramian(self.n, self.m, self.dtype, self.prec, self.opts, handle)
+
+    def solve(self, g, lcol, lrow, y, x=None):
+        """x = (G + L^H L)^{-1} y from contiguous CUDA tensors g (n), lcol (p), lrow (n), y (n)."""
+        import torch
+        for t, ln in ((g, self.n), (lcol, self.m), (lrow, self.n), (y, self.n)):
+            if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
+                raise TypeError("expected contiguous CUDA tensors")
+            if _dtype_code(t) != self.dtype or t.numel() != ln:
+                raise ValueError("tensor dtype/size does not match the plan")
+        if x is None:
+            x = torch.empty(self.n, dtype=y.dtype, device=y.device)
+        p = lambda t: ctypes.c_void_p(t.data_ptr())
+        tikh_solve_gramian(self.h, p(g), p(lcol), p(lrow), p(y), p(x))
+        return x
+
+
+class BatchPlan:
+    """A plan for problems of different shapes m[i] x n[i], each solved for the same nlambda weights."""
+
+    def __init__(self, m, n, nlambda, dtype="r64", n_lim=32, m_min=0, fill=0, eps_diff=1e-8, max_difficult=4096,
+                 refine_steps=0, graph=False, prod_direct_max=0, eval_direct_max=0, wait_polls=0,
+                 refine_tol=0.0, precision="fp64", max_workspace_bytes=0, stream=None):
+        import torch
+        self.m = [int(v) for v in m]
+        self.n = [int(v) for v in n]
+        self.nlambda = int(nlambda)
+        self.dtype = TIKH_C128 if dtype in ("c128", TIKH_C128, torch.complex128) else TIKH_R64
+        self.opts = tikh_opts(int(n_lim), int(m_min), int(fill), float(eps_diff), int(max_difficult),
+                              int(refine_steps), 1, 1 if graph else 0, int(prod_direct_max), int(eval_direct_max),
+                              int(wait_polls), float(refine_tol))
+        self.prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        self.h = tikh_batch_plan_create(self.m, self.n, self.nlambda, self.dtype, self.prec, self.opts,
+                                        int(max_workspace_bytes), handle)
+
+    def solve(self, cols, rows, bs, lams, xs=None):
+        """cols[i], rows[i], bs[i]: contiguous CUDA tensors of problem i; lams: nlambda weights.  Returns xs,
+        a list of nprob * nlambda tensors, xs[i * nlambda + l] for problem i and weight l."""
+        import torch
+        npb = len(self.m)
+        if not (len(cols) == len(rows) == len(bs) == npb):
+            raise ValueError("one col, row and b per problem")
+        for i in range(npb):
+            for t, ln in ((cols[i], self.m[i]), (rows[i], self.n[i]), (bs[i], self.m[i])):
+                if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
+                    raise TypeError("expected contiguous CUDA tensors")
+                if _dtype_code(t) != self.dtype or t.numel() != ln:
+                    raise ValueError("tensor dtype/size does not match the plan")
+        lams = np.ascontiguousarray(np.asarray(lams, dtype=np.float64).reshape(-1))
+        if lams.size != self.nlambda:
+            raise ValueError("expected %d lambdas" % self.nlambda)
+        if xs is None:
+            xs = [torch.empty(self.n[i], dtype=cols[i].dtype, device=cols[i].device)
+                  for i in range(npb) for _ in range(self.nlambda)]
+        tikh_solve_batched(self.h, self.m, self.n, [t.data_ptr() for t in cols], [t.data_ptr() for t in rows],
+                           [t.data_ptr() for t in bs], lams, [t.data_ptr() for t in xs])
+        return xs
+
+    def stats(self):
+        return tikh_batch_get_stats(self.h)
+
+    def set_profiling(self, flags):
+        tikh_batch_set_profiling(self.h, flags)
+
+    def close(self):
+        if getattr(self, "h", None):
+            tikh_batch_plan_destroy(self.h)
             self.h = None
 
     def __del__(self):
@@ -448,12 +682,12 @@ def autotune(m, n, dtype="c128", batch=1, refine_steps=0, reps=2, seed=0, time_f
                 p = Plan(m, n, dtype, refine_steps=refine_steps, batch=B, graph=True, stream=stream, **o)
                 try:
                     x = torch.empty((B, n), dtype=tdt, device="cuda")
-                    p.solve_batched(col, row, b, lams, x)
+                    p.solve_strided(col, row, b, lams, x)
                     best = float("inf")
                     for _ in range(max(1, int(reps))):
                         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                         e0.record(stream)
-                        p.solve_batched(col, row, b, lams, x)
+                        p.solve_strided(col, row, b, lams, x)
                         e1.record(stream)
                         e1.synchronize()
                         best = min(best, e0.elapsed_time(e1) * 1e-3)

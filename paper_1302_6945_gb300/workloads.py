@@ -145,3 +145,25 @@ def random_problem(m, n, lam, seed, complex_data=True):
         b = rng.standard_normal(m)
     row[0] = col[0]
     return dict(col=col, row=row, b=b, lam=lam, m=m, n=n)
+
+
+def nufft_problem(n=4096, K=4096, seed=6, l_scale=1e-2):
+    """Sec. 7.4's reconstruction workload: a length-n signal of three sinusoids with random frequencies in
+    [0, 0.02]; K spectral samples X_k = sum_s x_s exp(-2 pi i f_k s) at frequencies drawn from the triangular
+    distribution on [-1/2, 1/2); Voronoi-cell density weights w_k (half the distance between the neighbours
+    on the unit circle of frequencies, summing to 1); L = l_scale x [-1, 2, -1], a square second difference.
+    Returns dict(f, w, X, x_true, lcol, lrow)."""
+    rng = np.random.default_rng(seed)
+    s = np.arange(n)
+    fr = rng.uniform(0.0, 0.02, 3)
+    amp = rng.standard_normal(3)
+    ph = rng.uniform(0.0, 2 * np.pi, 3)
+    x_true = sum(a * np.cos(2 * np.pi * fq * s + p) for a, fq, p in zip(amp, fr, ph))
+    f = np.sort(rng.triangular(-0.5, 0.0, 0.5, K))
+    fp = np.concatenate([[f[-1] - 1.0], f, [f[0] + 1.0]])
+    w = (fp[2:] - fp[:-2]) / 2
+    X = np.exp(-2j * np.pi * np.outer(f, s)) @ x_true
+    lcol = np.zeros(n)
+    lcol[:2] = [2 * l_scale, -l_scale]
+    return dict(f=f, w=w, X=X, x_true=x_true, lcol=lcol, lrow=lcol.copy(), n=n, K=K)
+

@@ -36,11 +36,11 @@ def test_strerror_and_invalid_plan_without_gpu():
                                          ("max_difficult", 0), ("refine_steps", 9), ("batch", 0), ("graph", 2),
                                          ("prod_direct_max", -1), ("prod_direct_max", 4097),
                                          ("eval_direct_max", -1), ("eval_direct_max", 4097), ("wait_polls", -1),
-                                         ("wait_polls", (1 << 30) + 1)])
+                                         ("wait_polls", (1 << 30) + 1), ("refine_tol", -1.0)])
 def test_invalid_options_are_rejected_before_any_device_work(field, value):
     # argument checks come first, so they hold on a machine without a GPU
     from paper_1302_6945_gb300 import tikh
-    o = tikh.tikh_opts(32, 0, 0, 1e-8, 4096, 0, 1, 0, 0, 0, 0)
+    o = tikh.tikh_opts(32, 0, 0, 1e-8, 4096, 0, 1, 0, 0, 0, 0, 0.0)
     setattr(o, field, value)
     with pytest.raises(tikh.TikhError) as e:
         tikh.tikh_plan_create(64, 64, tikh.TIKH_R64, tikh.TIKH_PREC_FP64, o)

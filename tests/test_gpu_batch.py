@@ -1,4 +1,4 @@
-"""Batched solves (tikh_solve_batched) against one-at-a-time solves and the oracle."""
+"""Batched solves (tikh_solve_strided) against one-at-a-time solves and the oracle."""
 import numpy as np
 import pytest
 import torch
@@ -37,13 +37,13 @@ def test_batch_of_problems_matches_single_solves(m, n, cplx):
     # same direct/FFT thresholds on both sides: identical arithmetic per problem
     same = dict(prod_direct_max=36, eval_direct_max=10)
     plan = tikh.Plan(m, n, "c128" if cplx else "r64", batch=B, **same)
-    x = plan.solve_batched(col, row, b, lams).cpu().numpy()
+    x = plan.solve_strided(col, row, b, lams).cpu().numpy()
     st = plan.stats()
     plan.close()
     # automatic thresholds (a batch plan takes FFT products where a single plan multiplies directly):
     # the same results up to rounding
     plan = tikh.Plan(m, n, "c128" if cplx else "r64", batch=B)
-    xa = plan.solve_batched(col, row, b, lams).cpu().numpy()
+    xa = plan.solve_strided(col, row, b, lams).cpu().numpy()
     plan.close()
     assert st["batch"] == B
     for i, p in enumerate(probs):
@@ -65,7 +65,7 @@ def test_regularisation_path_shares_generator_and_data():
     lams = np.logspace(-6, 0, 16)
     plan = tikh.Plan(1024, 1024, "r64", batch=16, refine_steps=1)
     t = lambda a: torch.tensor(a, dtype=torch.float64, device=DEV)
-    x = plan.solve_batched(t(P["col"]), t(P["row"]), t(P["b"]), lams).cpu().numpy()
+    x = plan.solve_strided(t(P["col"]), t(P["row"]), t(P["b"]), lams).cpu().numpy()
     st = plan.stats()
     plan.close()
     assert st["rel_residual"] < 1e-13
@@ -81,7 +81,7 @@ def test_batch_dual_and_refinement():
     row = torch.tensor(np.stack([p["row"] for p in probs]), device=DEV)
     b = torch.tensor(np.stack([p["b"] for p in probs]), device=DEV)
     plan = tikh.Plan(400, 600, "r64", batch=4, refine_steps=1)
-    x = plan.solve_batched(col, row, b, [p["lam"] for p in probs]).cpu().numpy()
+    x = plan.solve_strided(col, row, b, [p["lam"] for p in probs]).cpu().numpy()
     assert plan.stats()["dual"] == 1
     plan.close()
     for i, p in enumerate(probs):
@@ -93,5 +93,5 @@ def test_batch_size_validation():
     plan = tikh.Plan(64, 64, "r64", batch=2)
     z = torch.zeros((3, 64), dtype=torch.float64, device=DEV)
     with pytest.raises(tikh.TikhError):
-        plan.solve_batched(z, z, z, [1.0, 1.0, 1.0])
+        plan.solve_strided(z, z, z, [1.0, 1.0, 1.0])
     plan.close()

@@ -71,7 +71,7 @@ def test_non_finite_entry_of_one_problem_in_a_batch_is_reported():
     cb[1, 7] = complex(float("nan"), 0.0)
     plan = tikh.Plan(64, 48, "c128", n_lim=16, batch=B)
     with pytest.raises(tikh.TikhError) as e:
-        plan.solve_batched(cb, row, b, [P["lam"]] * B)
+        plan.solve_strided(cb, row, b, [P["lam"]] * B)
     assert e.value.status == tikh.TIKH_ENUMERIC
     plan.close()
 

@@ -76,3 +76,28 @@ def test_lambda_gradient_matches_central_difference_on_gpu():
     fd = (loss(P["lam"] + h) - loss(P["lam"] - h)) / (2 * h)
     plan.close()
     assert abs(fd - dlam) <= 1e-5 * abs(dlam)
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_strided_batch_adjoint_matches_oracle(cplx):
+    B, m, n = 4, 300, 200
+    probs = [W.deconvolution_problem(m, n, 3.0 + i, 12, 1e-6, 1e-6, 1e-3 * (i + 1), seed=90 + i, complex_data=cplx,
+                                     signal="smooth" if cplx else "piecewise") for i in range(B)]
+    dt = torch.complex128 if cplx else torch.float64
+    t = lambda a: torch.tensor(np.stack(a), dtype=dt, device=DEV)
+    col, row, b = t([p["col"] for p in probs]), t([p["row"] for p in probs]), t([p["b"] for p in probs])
+    lams = [p["lam"] for p in probs]
+    plan = tikh.Plan(m, n, "c128" if cplx else "r64", refine_steps=1, batch=B)
+    x = plan.solve_strided(col, row, b, lams)
+    rng = np.random.default_rng(5)
+    G = rng.standard_normal((B, n)) + (1j * rng.standard_normal((B, n)) if cplx else 0)
+    dcol, drow, db, dlam = plan.grad_strided(col, row, b, lams, x, torch.tensor(G, dtype=dt, device=DEV))
+    plan.close()
+    for i, P in enumerate(probs):
+        ocol, orow, ob, olam = oracle.adjoint(P["col"], P["row"], P["b"], P["lam"], x[i].cpu().numpy(), G[i])
+        if not cplx:
+            ocol, orow, ob = ocol.real, orow.real, ob.real
+        assert relerr(dcol[i].cpu().numpy(), ocol) <= 1e-9
+        assert relerr(drow[i].cpu().numpy(), orow) <= 1e-9
+        assert relerr(db[i].cpu().numpy(), ob) <= 1e-9
+        assert abs(dlam[i] - olam) <= 1e-9 * max(1.0, abs(olam))

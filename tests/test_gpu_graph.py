@@ -58,10 +58,10 @@ def test_graph_batched_and_default_stream_fallback():
     with torch.cuda.stream(s):
         ref = tikh.Plan(m, n, "r64", batch=B, stream=s)
         gp = tikh.Plan(m, n, "r64", batch=B, graph=True, stream=s)
-        xr = ref.solve_batched(col, row, b, lams).cpu().numpy()
+        xr = ref.solve_strided(col, row, b, lams).cpu().numpy()
         xg = torch.empty((B, n), dtype=torch.float64, device=DEV)
         for _ in range(2):
-            gp.solve_batched(col, row, b, lams, x=xg)
+            gp.solve_strided(col, row, b, lams, x=xg)
             assert gp.stats()["graph"] == 1
             assert relerr(xg.cpu().numpy(), xr) <= 1e-14
         ref.close()

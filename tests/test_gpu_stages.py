@@ -60,3 +60,23 @@ def test_leaf_deferral_matches_oracle():
         o = oracle.leaf(sigma, r.copy(), [-3, -3, -3, -3, 0], eps=eps)
         assert g["deferred"] == sorted(o["deferred"]), eps
         assert list(g["order"]) == list(o["order"])
+
+
+def test_leaf_series_reciprocal_is_within_fp64_rounding():
+    # the leaf's 1/|r_pi|^2: FP32 seed + one third-order series step; over the whole exponent range it
+    # admits (biased exponent 3 .. 2043) and random mantissas it must be within 1 ulp of the correctly
+    # rounded 1/d (the series' truncation e^3 < 2^-63 leaves only the final roundings)
+    import ctypes
+    rng = np.random.default_rng(17)
+    mant = 1.0 + rng.random(200000)
+    expo = rng.integers(-1018, 1018, 200000)
+    d = np.ldexp(mant, expo)
+    d = np.concatenate([d, [1.0, 2.0, 1.5, np.nextafter(2.0, 0.0), np.ldexp(1.0, -1018), np.ldexp(1.0, 1017)]])
+    x = torch.tensor(d, dtype=torch.float64, device=DEV)
+    out = torch.empty_like(x)
+    tikh.tikh_test_rcp(x.numel(), ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                       torch.cuda.current_stream().cuda_stream)
+    got = out.cpu().numpy()
+    ref = 1.0 / d
+    ulp = np.abs(np.spacing(ref))
+    assert (np.abs(got - ref) <= ulp).all(), np.max(np.abs(got - ref) / ulp)

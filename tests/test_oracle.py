@@ -427,3 +427,25 @@ def test_gramian_solution_independent_of_fill_and_extension():
         for m_min in (0, 12, 20):
             x, st = oracle.solve_gramian(g, lcol, lrow, y, nlim=16, m_min=m_min, fill=fill)
             assert relerr(x, xd) <= 1e-11, (fill, m_min, st["k"], relerr(x, xd))
+
+
+def test_nufft_gramian_direct_sums_match_the_matrix_definition():
+    # Sec. 7.4: (A^H W A)_{rs} = sum_k w_k exp(2 pi i f_k (r - s)) is Hermitian Toeplitz; g is its first
+    # column and y = A^H W X, with A_{ks} = exp(-2 pi i f_k s)
+    P = W.nufft_problem(n=48, K=60, seed=2)
+    A = np.exp(-2j * np.pi * np.outer(P["f"], np.arange(48)))
+    GA = A.conj().T @ np.diag(P["w"]) @ A
+    g, y = oracle.nufft_gramian(P["f"], P["w"], P["X"], 48)
+    np.testing.assert_allclose(oracle.hermitian_toeplitz_dense(g), GA, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(y, A.conj().T @ (P["w"] * P["X"]), rtol=0, atol=1e-12)
+    assert abs(P["w"].sum() - 1.0) < 1e-14 and (P["w"] > 0).all()
+
+
+def test_nufft_reconstruction_small_matches_dense():
+    P = W.nufft_problem(n=512, K=512, seed=3)
+    g, y = oracle.nufft_gramian(P["f"], P["w"], P["X"], 512)
+    xd = oracle.dense_solve_gramian(g, P["lcol"], P["lrow"], y)
+    x, _ = oracle.solve_gramian(g, P["lcol"], P["lrow"], y)
+    A = oracle.hermitian_toeplitz_dense(g) + oracle.toeplitz_dense(P["lcol"], P["lrow"]).T @ \
+        oracle.toeplitz_dense(P["lcol"], P["lrow"])
+    assert relerr(x, xd) <= 1e-13 * np.linalg.cond(A) + 1e-12
