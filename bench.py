@@ -1,12 +1,16 @@
 """Benchmark: superfast Tikhonov solves of the deconvolution workload on GB300.
 
-Workload (one step = one full solve: extension, transformation, recursive basis construction,
+Default workload (one step = one full solve: extension, transformation, recursive basis construction,
 difficult points, extraction, optional refinement): complex128, m = 98304, n = 65536, Gaussian PSF
-(sigma 8) with random phases, lambda = 1e-4.  value = solves/s over all ranks (weak scaling: every
-rank solves its own problem).  Inputs are resident in HBM when the timed region starts; the working
+(sigma 8) with random phases, lambda = 1e-4 (plain FP64).  value = solves/s over all ranks (weak scaling:
+every rank solves its own problem).  Inputs are resident in HBM when the timed region starts; the working
 set (~1 GB) exceeds L2 and L2 is also flushed between steps.  e2e repeats the measurement through
-tikh_solve_host with host buffers (copies inside the timed region).
+tikh_solve_host with host buffers (copies inside the timed region).  The default run also reports the
+metric's n sweep (n = 2^17 .. 2^20, m = 1.5 n, one FP64 refinement correction) under "sweep".
 
+--config c3 runs the batching configuration instead: 512 real problems of uneven shape, each with a
+16-value regularisation path, as one ragged batch (tikh_solve_batched, one captured graph per call).
+--precision selects FP64, FP32 stages, or FP32 stages with FP64 refinement.
 --impl reference times the CPU oracle (the paper's algorithm in plain C, FP64) on the host cores.
 """
 import argparse
@@ -23,34 +27,20 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "solves/s and n*solves/s at n=2^16..2^20 vs plain FP64 GPU at rel err<=1e-8; HBM %"
+KINDS = ("leaf", "evaluation", "product", "other")
 
-# FP64 peak of GB300 from its unit counts: 152 SMs x 4 sub-partitions x 0.5 DFMA/clk x 2 flop x clock
-# (the sub-partition rate was measured: one FP64 warp instruction per 64 cycles).
-FP64_PEAK_GFLOPS = 152 * 4 * 0.5 * 2 * 2.070
-
-
-def leaf_model_flops(K):
-    """Algorithmic FP64 flops of one leaf of K conditions (serial single-point construction):
-    pivot chain sum_s [60 (K - s) + 60] (score 20 + update 40 per remaining condition, mu 60 per step)
-    plus the basis rebuild ~20 K^2 (5 rows x ~K/10 coefficients x 40 flops per step)."""
-    return 30 * K * K + 90 * K + 20 * K * K
+# dram__bytes_read.sum + dram__bytes_write.sum of one leaf launch (K = 20, one problem): the mean of two
+# launches of an ncu capture with warm caches (--cache-control none) of the current leaf kernel at n = 4096
+# (the same K = 20 kernel as the c2 workload); None whenever the kernel changes until it is recaptured
+LEAF_TRAFFIC_BYTES = 640
+LEAF_TRAFFIC_NOTE = "ncu, warm caches, c2 recipe at n = 4096 (same K = 20 kernel), mean of 2 launches"
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum of one k_leaf launch (K = 20, one problem), from
-# profiles/k_leaf_c2recipe_n4096.md; None once the kernel changes after that capture
-# dram__bytes_read.sum + dram__bytes_write.sum of one leaf launch (K = 20) from an ncu capture of the
-# current kernel (profiles/k_leaf_c2recipe_n4096.md); None whenever the kernel changes until recaptured
-LEAF_TRAFFIC_BYTES = 45056
-# sm__inst_executed_pipe_fp64 (fraction of the SM's peak while the leaf runs) from the same capture
-LEAF_FP64_PIPE_ACTIVE = 0.376
-
-
-def model_bytes_per_solve(N, p):
-    """Algorithmic HBM words of one solve (c128, 16 B each): per split level the left basis read
-    for the evaluation (~5N), the right residuals read and written (~10N), both bases into the product
-    (~10N) and the product out (~10N), about 35N; the leaves read their conditions and write their
-    bases (~10N)."""
-    return 16 * (35 * N * p + 10 * N)
+def model_bytes_per_solve(N, p, word=16):
+    """Algorithmic HBM bytes of one core solve: per split level the left basis read for the evaluation
+    (~5N words), the right residuals read and written (~10N), both bases into the product (~10N) and the
+    product out (~10N), about 35N; the leaves read their conditions and write their bases (~10N)."""
+    return word * (35 * N * p + 10 * N)
 
 
 def peaks():
@@ -59,6 +49,30 @@ def peaks():
             return json.load(f), "measured"
     except Exception:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def fma_peaks(tikh, stream):
+    """Measured FP64 and FP32 FMA rates of this GPU (GFLOP/s), by the library's peak-rate kernel."""
+    return tikh.tikh_test_peak(0, stream), tikh.tikh_test_peak(1, stream)
+
+
+def kind_rooflines(st, pst, steps, items, solves_per_item, p64, p32):
+    """Per kind of launch group (leaf, evaluation, product, other): model FLOPs of the groups (the library's
+    algorithmic count per core solve x items x core solves per item) over their event-timed duration, as a
+    fraction of the measured FMA peak of the precision they run in (FP32 for the FP32-stage share)."""
+    out = {}
+    for i, k in enumerate(KINDS):
+        t = pst["prof_kind_ms"][i] / steps * 1e-3
+        f = st["model_flops"][i] * items * solves_per_item
+        f32 = st["model_flops_fp32"][i] * items * solves_per_item
+        if t <= 0:
+            continue
+        # the time the kind's flops need at the two peaks, over the time it took
+        t_peak = (f - f32) / (p64 * 1e9) + f32 / (p32 * 1e9)
+        out[k] = {"ms_per_step": t * 1e3, "model_gflop_per_step": f / 1e9, "fp32_share_of_flops": f32 / f if f else 0.0,
+                  "achieved_gflops": f / t / 1e9, "frac_of_peak": t_peak / t,
+                  "groups_per_step": pst["prof_kind_count"][i] / steps}
+    return out
 
 
 class ClockSampler:
@@ -148,13 +162,46 @@ def workload(seed_offset=0, n=None):
     return W.config_c2(seed=1 + seed_offset, m=3 * n // 2, n=n)
 
 
+def c3_reference_sample(count=8, seed=11):
+    """A bounded, seeded sample of the batching configuration's items (problem, lambda): `count` items drawn
+    uniformly from the 512 x 16, so the mean time per item estimates the whole workload's."""
+    import numpy as np
+    from paper_1302_6945_gb300 import workloads as W
+    probs, lams = W.batch_c3()
+    rng = np.random.default_rng(seed)
+    ids = rng.choice(len(probs) * len(lams), size=count, replace=False)
+    return [(probs[i // len(lams)], float(lams[i % len(lams)])) for i in sorted(ids)], len(probs) * len(lams)
+
+
 def run_reference(args, world, rank):
     """The CPU oracle on the host cores, on this arm's workload and metric."""
     if rank != 0:
         return
-    import numpy as np
     import oracle
     oracle.build()
+    if args.config == "c3":
+        sample, total = c3_reference_sample()
+        times = []
+        for s in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            for P, lam in sample:
+                oracle.solve(P["col"], P["row"], P["b"], lam, nlim=args.n_lim, is_complex=0)
+            dt = time.perf_counter() - t0
+            if s >= args.warmup:
+                times.append(dt)
+        t = sum(times) / len(times)
+        v = len(sample) / t
+        cfg = {"workload": "c3: 512 real deconvolution problems, n log-uniform in [256, 65536], m = n + U[0, n/2], "
+                           "16-value lambda path 1e-6..1 (8192 solves)", "n_lim": args.n_lim}
+        out = {"metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference", "config": cfg,
+               "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                                "sample": "%d items (problem, lambda) drawn uniformly from the %d, single thread, "
+                                          "each solved plainly" % (len(sample), total)},
+               "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(out))
+        return
     P = workload(n=args.n)
     times = []
     for s in range(args.warmup + args.steps):
@@ -168,12 +215,190 @@ def run_reference(args, world, rank):
     out = {"metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "c128", "data": "synthetic", "impl": "reference",
-           "config": {"workload": "deconvolution m=%d n=%d complex128 lambda=1e-4 (c2 recipe)" % (P["m"], P["n"]), "m": P["m"],
-                      "n": P["n"], "n_lim": args.n_lim, "l2": "working set > L2"},
+           "config": {"workload": "deconvolution m=%d n=%d complex128 lambda=1e-4 (c2 recipe)" % (P["m"], P["n"]),
+                      "m": P["m"], "n": P["n"], "n_lim": args.n_lim, "l2": "working set > L2"},
            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
                             "sample": "full c2 solve per step, single thread"},
            "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
+
+
+def normal_residual_t(torch, col, row, b, xv, lam):
+    """||T^H (b - T x) - lam x|| / ||T^H b|| by FFT convolutions in torch (outside any timed region)."""
+    col, row, b, xv = (v.to(torch.complex128) for v in (col, row, b, xv))
+    m, n = col.numel(), row.numel()
+    L = 1 << int(math.ceil(math.log2(m + 2 * n)))
+    a = torch.cat([row[1:].flip(0), col])  # a_{-(n-1)} .. a_{m-1}
+    A = torch.fft.fft(a, L)
+    Ah = torch.fft.fft(a.conj().flip(0), L)
+    Tx = torch.fft.ifft(A * torch.fft.fft(xv, L))[n - 1:n - 1 + m]
+    Thr = torch.fft.ifft(Ah * torch.fft.fft(b - Tx, L))[m - 1:m - 1 + n]
+    Thb = torch.fft.ifft(Ah * torch.fft.fft(b, L))[m - 1:m - 1 + n]
+    return float(torch.linalg.norm(Thr - lam * xv) / torch.linalg.norm(Thb))
+
+
+def run_c3(args, world, rank, local):
+    """The batching configuration as one ragged batch per step (weak scaling: rank r solves its own
+    512-problem set, seed 2 + r)."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1302_6945_gb300 import tikh
+    from paper_1302_6945_gb300 import workloads as W
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    probs, lams = W.batch_c3(seed=2 + rank)
+    L = len(lams)
+    ms, ns = [p["m"] for p in probs], [p["n"] for p in probs]
+    t = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)
+    cols, rows, bs = [t(p["col"]) for p in probs], [t(p["row"]) for p in probs], [t(p["b"]) for p in probs]
+    xs = [torch.empty(n, dtype=torch.float64, device=dev) for n in ns for _ in range(L)]
+    stream = torch.cuda.Stream(device=dev)
+    t0 = time.perf_counter()
+    bp = tikh.BatchPlan(ms, ns, L, "r64", n_lim=args.n_lim, refine_steps=args.refine, graph=bool(args.graph),
+                        precision=args.precision, stream=stream)
+    t_plan = time.perf_counter() - t0
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            bp.solve(cols, rows, bs, lams, xs)
+    st = bp.stats()
+    # accuracy on a sample of items against single FP64 solves with two refinement corrections
+    rng = np.random.default_rng(7)
+    pick = sorted(rng.choice(len(probs), size=6, replace=False).tolist()) + [int(np.argmax(ns))]
+    errs = []
+    with torch.cuda.stream(stream):
+        for i in pick:
+            l = int(rng.integers(L))
+            ref = tikh.Plan(ms[i], ns[i], "r64", n_lim=args.n_lim, refine_steps=2, stream=stream)
+            xr = ref.solve(cols[i], rows[i], bs[i], float(lams[l]))
+            ref.close()
+            x = xs[i * L + l]
+            errs.append(float(torch.linalg.norm(x - xr) / torch.linalg.norm(xr)))
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with torch.cuda.stream(stream):
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            bp.solve(cols, rows, bs, lams, xs)
+            ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_step = sum(step_ms) / len(step_ms)
+    t_max = max_over_ranks(t_step, dev)
+    items = len(probs) * L
+    value = whole_job_rate(world, items, t_max / 1e3)
+    # profiled pass (groups one after another, every launch group timed by kind)
+    bp.set_profiling(2)
+    with torch.cuda.stream(stream):
+        bp.solve(cols, rows, bs, lams, xs)
+    torch.cuda.synchronize()
+    pst = bp.stats()
+    bp.set_profiling(0)
+    # e2e: the same call with the problems in pinned host memory, copies inside the timed region
+    hc = [torch.tensor(p["col"], dtype=torch.float64).pin_memory() for p in probs]
+    hr = [torch.tensor(p["row"], dtype=torch.float64).pin_memory() for p in probs]
+    hb = [torch.tensor(p["b"], dtype=torch.float64).pin_memory() for p in probs]
+    hx = [torch.empty(n, dtype=torch.float64).pin_memory() for n in ns for _ in range(L)]
+    h2d = sum(8 * (a.numel() + b.numel() + c.numel()) for a, b, c in zip(hc, hr, hb))
+    d2h = sum(8 * x.numel() for x in hx)
+    e2e_times = []
+    with torch.cuda.stream(stream):
+        for _ in range(max(1, min(args.steps, 3))):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for dst, src in zip(cols + rows + bs, hc + hr + hb):
+                dst.copy_(src, non_blocking=True)
+            bp.solve(cols, rows, bs, lams, xs)
+            for dst, src in zip(hx, xs):
+                dst.copy_(src, non_blocking=True)
+            stream.synchronize()
+            e2e_times.append(time.perf_counter() - t0)
+    e2e_t = sum(e2e_times) / len(e2e_times)
+    e2e_v = whole_job_rate(world, items, max_over_ranks(e2e_t, dev))
+    p64, p32 = fma_peaks(tikh, stream.cuda_stream)
+    nref = args.refine if args.refine > 0 else (2 if args.precision == "fp32_refine" else 0)
+    solves = 1 + nref
+    pst_one = dict(pst)
+    kr = kind_rooflines({"model_flops": [f / items for f in pst["model_flops"]],
+                         "model_flops_fp32": [f / items for f in pst["model_flops_fp32"]]},
+                        pst_one, 1, items, solves, p64, p32)
+    dom = max(kr, key=lambda k: kr[k]["ms_per_step"]) if kr else None
+    roof = None
+    if dom:
+        d = kr[dom]
+        f32 = d["fp32_share_of_flops"]
+        roof = {"bound": "alu", "kernel": "%s launch groups of the ragged batch (profiled pass, groups serialised)" % dom,
+                "achieved": d["achieved_gflops"], "unit": "GFLOP/s",
+                "peak": p64 if f32 < 0.5 else p32, "peak_kind": "measured FMA rate (tikh_test_peak), %s"
+                % ("FP64" if f32 < 0.5 else "FP32"), "frac": d["frac_of_peak"],
+                "frac_note": "time the group's model FLOPs need at the measured FP64/FP32 peaks over its time",
+                "traffic": None}
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": t_max, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32 stages + f64",
+               "data": "synthetic",
+               "config": {"workload": "c3: 512 real deconvolution problems, n log-uniform in [256, 65536], "
+                                      "m = n + U[0, n/2], sigma ~ U[2, 16], 16-value lambda path 1e-6..1 "
+                                      "(8192 solves per step, one ragged batch)",
+                          "items": items, "precision": args.precision, "refine_steps": solves - 1,
+                          "groups": st["ngroups"], "max_waves": st["max_waves"], "cuda_graph": bool(st["graph"]),
+                          "workspace_bytes": st["workspace_bytes"], "plan_s": t_plan,
+                          "l2": "256 MB flush between steps; working set > L2"},
+               "accuracy": {"sampled_items": len(errs), "max_rel_err_vs_fp64_refined": max(errs),
+                            "reference": "single FP64 solves with 2 refinement corrections",
+                            "max_rel_residual": st["rel_residual"]},
+               "e2e": {"value": e2e_v, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+               "gpu_launches": int(st["kernel_launches"]) * args.steps, "clocks": clocks,
+               "fma_peaks_gflops": {"fp64": p64, "fp32": p32}, "roofline": roof, "kinds": kr,
+               "cpu_baseline": None}
+        print(json.dumps(out))
+    bp.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def sweep_point(tikh, torch, n, refine, args, stream, dev):
+    """One point of the metric's sweep: the c2 recipe at n, m = 1.5 n, `refine` FP64 corrections; one warm-up
+    (graph capture) and args.sweep_steps timed solves."""
+    P = workload(n=n)
+    m = P["m"]
+    t = lambda a: torch.tensor(a, dtype=torch.complex128, device=dev)
+    col, row, b = t(P["col"]), t(P["row"]), t(P["b"])
+    x = torch.empty(n, dtype=torch.complex128, device=dev)
+    plan = tikh.Plan(m, n, "c128", n_lim=args.n_lim, refine_steps=refine, graph=True, stream=stream)
+    with torch.cuda.stream(stream):
+        plan.solve(col, row, b, P["lam"], x)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.sweep_steps):
+            plan.solve(col, row, b, P["lam"], x, sync=False)
+        e1.record(stream)
+        e1.synchronize()
+        plan.sync()
+    st = plan.stats()
+    ms = e0.elapsed_time(e1) / args.sweep_steps
+    res = normal_residual_t(torch, col, row, b, x, P["lam"])
+    plan.close()
+    return {"n": n, "m": m, "N": st["N"], "refine_steps": refine, "ms_per_solve": ms, "solves_per_s": 1e3 / ms,
+            "n_solves_per_s": n * 1e3 / ms, "normal_eq_rel_residual": res,
+            "library_rel_residual": st["rel_residual"],
+            "last_correction_rel": st["last_correction"],
+            "accuracy_note": "last_correction_rel = ||dx||/||x|| of the last correction, the error of the solution "
+                             "before it; each FP64 correction contracts the error (DESIGN: <= 1.4e-11 after one "
+                             "correction at n = 2^20 against two)"}
 
 
 def main():
@@ -182,12 +407,17 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="c2", choices=["c2", "c3"],
+                    help="c2 (default): the complex deconvolution solve; c3: the ragged batch of 512 problems x 16 lambdas")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "fp32_refine"])
     ap.add_argument("--n-lim", type=int, default=32)
     ap.add_argument("--refine", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=None, help="sweep point: n unknowns, m = 1.5 n (default: c2)")
-    ap.add_argument("--batch", type=int, default=1, help="independent problems per step (tikh_solve_batched)")
+    ap.add_argument("--batch", type=int, default=1, help="independent problems per step (tikh_solve_strided)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the n = 2^17 .. 2^20 sweep of the default run")
+    ap.add_argument("--sweep-steps", type=int, default=1)
     ap.add_argument("--prod-direct-max", type=int, default=0, help="direct products up to this P (0: automatic)")
     ap.add_argument("--eval-direct-max", type=int, default=0, help="direct evaluations up to this size (0: automatic)")
     ap.add_argument("--graph", type=int, default=1, help="1 (default): replay each solve as one captured CUDA graph; 0: stream launches")
@@ -197,6 +427,8 @@ def main():
     world, rank, local = dist_setup()
     if args.impl == "reference":
         return run_reference(args, world, rank)
+    if args.config == "c3":
+        return run_c3(args, world, rank, local)
 
     import numpy as np
     import torch
@@ -221,13 +453,14 @@ def main():
     x = xb[0]
     stream = torch.cuda.Stream(device=dev)
     plan = tikh.Plan(m, n, "c128", n_lim=args.n_lim, refine_steps=args.refine, batch=B, graph=bool(args.graph),
-                     prod_direct_max=args.prod_direct_max, eval_direct_max=args.eval_direct_max, stream=stream)
+                     prod_direct_max=args.prod_direct_max, eval_direct_max=args.eval_direct_max,
+                     precision=args.precision, stream=stream)
 
     def step(sync=True):
         if B == 1:
             plan.solve(col[0], row[0], bb[0], lams[0], x, sync=sync)
         else:
-            plan.solve_batched(col, row, bb, lams, xb)
+            plan.solve_strided(col, row, bb, lams, xb)
     if args.single:
         with torch.cuda.stream(stream):
             step()
@@ -243,29 +476,15 @@ def main():
         for _ in range(args.warmup):
             step()
     st = plan.stats()
-
-    # accuracy of the benchmarked solution: relative residual of the normal equations (FFT matvec in
-    # torch, outside the timed region)
-    def normal_residual(xv):
-        L = 1 << int(math.ceil(math.log2(m + 2 * n)))
-        a = torch.cat([row[0, 1:].flip(0), col[0]])  # a_{-(n-1)} .. a_{m-1}
-        A = torch.fft.fft(a, L)
-        Tx = torch.fft.ifft(A * torch.fft.fft(xv, L))[n - 1:n - 1 + m]
-        r = b - Tx
-        # T^H r: correlate with conj(a)
-        Ah = torch.fft.fft(a.conj().flip(0), L)
-        Thr = torch.fft.ifft(Ah * torch.fft.fft(r, L))[m - 1:m - 1 + n]
-        Thb = torch.fft.ifft(Ah * torch.fft.fft(b, L))[m - 1:m - 1 + n]
-        return float(torch.linalg.norm(Thr - P["lam"] * xv) / torch.linalg.norm(Thb))
-
-    res = normal_residual(x)
+    res = normal_residual_t(torch, col[0], row[0], b, x, P["lam"])
 
     # forward error of the benchmarked solution against a solve of the same problem with two FP64
     # refinement corrections (outside the timed region)
-    ref_plan = tikh.Plan(m, n, "c128", n_lim=args.n_lim, refine_steps=max(2, args.refine + 1), stream=stream)
+    nref = max(2, args.refine + 1)
+    ref_plan = tikh.Plan(m, n, "c128", n_lim=args.n_lim, refine_steps=nref, stream=stream)
     with torch.cuda.stream(stream):
         x_ref = ref_plan.solve(col[0], row[0], bb[0], lams[0])
-    ref_res = normal_residual(x_ref)
+    ref_res = normal_residual_t(torch, col[0], row[0], b, x_ref, P["lam"])
     rel_err_ref = float(torch.linalg.norm(x - x_ref) / torch.linalg.norm(x_ref))
     ref_plan.close()
 
@@ -286,8 +505,8 @@ def main():
     clocks = clk.stop()
     step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
 
-    # dominant kernel (the leaf): every launch timed with a CUDA event pair on the plan's stream, over
-    # the same number of steps right after the timed region (events are not in the timed steps)
+    # every launch group timed with a CUDA event pair on the plan's stream, over the same number of
+    # steps right after the timed region (events are not in the timed steps)
     plan.set_profiling(3)
     with torch.cuda.stream(stream):
         for i in range(args.steps):
@@ -296,9 +515,8 @@ def main():
     plan.sync()
     pst = plan.stats()
     plan.set_profiling(0)
-    kinds = ("leaf", "evaluation", "product", "other")
     breakdown = {k: {"ms_per_step": pst["prof_kind_ms"][i] / args.steps,
-                     "groups_per_step": pst["prof_kind_count"][i] / args.steps} for i, k in enumerate(kinds)}
+                     "groups_per_step": pst["prof_kind_count"][i] / args.steps} for i, k in enumerate(KINDS)}
     t_step = sum(step_ms) / len(step_ms)
     t_max = max_over_ranks(t_step, dev)
     if world > 1:
@@ -322,20 +540,35 @@ def main():
         e2e_v = whole_job_rate(world, 1, max_over_ranks(e2e_t, dev))
 
     pk, pk_kind = peaks()
-    K_leaf = 2 * int(st["M"])
-    leaf_launches = max(1, int(pst["prof_leaf_launches"]))
-    leaf_ms = max(pst["prof_leaf_ms"] / leaf_launches, 1e-9)
-    leaf_gflops = leaf_model_flops(K_leaf) * B / (leaf_ms * 1e-3) / 1e9
-    roofline = {"bound": "alu", "kernel": "k_leaf (FP64 serial single-point construction)",
-                "achieved": leaf_gflops, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                "frac": leaf_gflops / FP64_PEAK_GFLOPS, "peak_kind": "derived from unit counts and max clock",
-                "traffic": LEAF_TRAFFIC_BYTES, "avg_launch_ms": leaf_ms,
-                # a leaf is one CTA: a single solve can use one SM's FP64 units at most
-                "peak_one_sm": FP64_PEAK_GFLOPS / 152, "frac_of_one_sm": leaf_gflops / B / (FP64_PEAK_GFLOPS / 152),
-                "fp64_pipe_active_ncu": LEAF_FP64_PIPE_ACTIVE,
-                "launches_per_step": leaf_launches / args.steps,
-                "share_of_step": (pst["prof_leaf_ms"] / args.steps) / t_step,
-                "flops_per_launch": leaf_model_flops(K_leaf) * B}
+    p64, p32 = fma_peaks(tikh, stream.cuda_stream)
+    solves_per_item = 1 + int(st["refine_steps"])
+    kr = kind_rooflines(st, pst, args.steps, B, solves_per_item, p64, p32)
+    dom = max(kr, key=lambda k: kr[k]["ms_per_step"])
+    if dom == "leaf":
+        # the leaf as one kernel: model FLOPs per launch over its event-timed average launch duration
+        leaf_launches = max(1, int(pst["prof_leaf_launches"]))
+        leaf_ms = max(pst["prof_leaf_ms"] / leaf_launches, 1e-9)
+        leaves = 1 << int(st["p"])
+        flops_launch = st["model_flops"][0] / leaves * B
+        ach = flops_launch / (leaf_ms * 1e-3) / 1e9
+        roofline = {"bound": "alu", "kernel": "k_leaf (FP64 serial single-point construction)",
+                    "achieved": ach, "peak": p64, "unit": "GFLOP/s", "frac": ach / p64,
+                    "peak_kind": "measured FP64 FMA rate of this GPU (tikh_test_peak)",
+                    "traffic": LEAF_TRAFFIC_BYTES if B == 1 else None, "traffic_note": LEAF_TRAFFIC_NOTE,
+                    "avg_launch_ms": leaf_ms, "flops_per_launch": flops_launch,
+                    # a leaf is one CTA: a single solve can use one SM's FP64 units at most
+                    "peak_one_sm": p64 / 152, "frac_of_one_sm": ach / B / (p64 / 152),
+                    "launches_per_step": leaf_launches / args.steps,
+                    "share_of_step": (pst["prof_leaf_ms"] / args.steps) / t_step}
+    else:
+        d = kr[dom]
+        f32 = d["fp32_share_of_flops"]
+        roofline = {"bound": "alu", "kernel": "%s launch groups (FFT tiles and their pointwise kernels)" % dom,
+                    "achieved": d["achieved_gflops"], "unit": "GFLOP/s", "peak": p64 if f32 < 0.5 else p32,
+                    "peak_kind": "measured %s FMA rate of this GPU (tikh_test_peak)" % ("FP64" if f32 < 0.5 else "FP32"),
+                    "frac": d["frac_of_peak"],
+                    "frac_note": "time the groups' model FLOPs need at the measured FP64/FP32 peaks over their time",
+                    "traffic": None, "share_of_step": d["ms_per_step"] / t_step}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
@@ -343,37 +576,51 @@ def main():
         t0 = time.perf_counter()
         xo, _ = oracle.solve(P["col"], P["row"], P["b"], P["lam"], nlim=args.n_lim)
         tc = time.perf_counter() - t0
+        xr = x_ref.cpu().numpy()
         err = float(np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo))
         cpu = {"value": 1.0 / tc, "unit": "solves/s", "cores": 1, "kind": "oracle",
-               "sample": "one full solve of the same problem (m=%d, n=%d), single thread" % (m, n), "gpu_vs_oracle_rel_err": err}
+               "sample": "one full solve of the same problem (m=%d, n=%d), single thread" % (m, n),
+               "gpu_vs_oracle_rel_err": err,
+               "oracle_vs_refined_rel_err": float(np.linalg.norm(xo - xr) / np.linalg.norm(xr)),
+               "gpu_vs_refined_rel_err": rel_err_ref}
+
+    sweep = None
+    if rank == 0 and world == 1 and not args.no_sweep and args.n is None and B == 1 and args.precision == "fp64":
+        sweep = []
+        for e in range(17, 21):
+            sweep.append(sweep_point(tikh, torch, 1 << e, 1, args, stream, dev))
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": t_max, "higher_is_better": True, "scaling": "weak",
-               "vs_baseline": None, "dtype": "c128", "data": "synthetic",
-               "config": {"workload": "deconvolution m=%d n=%d complex128 lambda=1e-4 (c2 recipe)" % (m, n), "m": m, "n": n,
-                          "N": st["N"], "p": st["p"], "M": st["M"], "n_lim": args.n_lim,
-                          "refine_steps": args.refine, "precision": "fp64", "batch": B,
+               "vs_baseline": None, "dtype": "c128" if args.precision == "fp64" else "c64 stages + c128",
+               "data": "synthetic",
+               "config": {"workload": "deconvolution m=%d n=%d complex128 lambda=1e-4 (c2 recipe)" % (m, n),
+                          "m": m, "n": n, "N": st["N"], "p": st["p"], "M": st["M"], "n_lim": args.n_lim,
+                          "refine_steps": st["refine_steps"], "precision": args.precision, "batch": B,
                           "cuda_graph": bool(st["graph"]),
-                          "prod_direct_max": args.prod_direct_max or "auto", "eval_direct_max": args.eval_direct_max or "auto",
+                          "prod_direct_max": args.prod_direct_max or "auto",
+                          "eval_direct_max": args.eval_direct_max or "auto",
                           "l2": "256 MB flush between steps; working set > L2"},
                "n_solves_per_s": value * n,
                "solves_per_s_per_problem_stream": value / B,
                "normal_eq_rel_residual": res,
                "rel_err_vs_refined": {"value": rel_err_ref, "reference": "same problem, %d FP64 refinement "
-                                      "corrections" % max(2, args.refine + 1), "reference_normal_eq_rel_residual":
-                                      ref_res},
+                                      "corrections" % nref, "reference_normal_eq_rel_residual": ref_res},
                "e2e": {"value": e2e_v, "unit": "solves/s", "h2d_bytes_per_step": 16 * (2 * m + n),
                        "d2h_bytes_per_step": 16 * n},
                "gpu_launches": int(st["kernel_launches"]) * args.steps,
                "clocks": clocks,
-               "peaks": {"hbm_gbs": pk.get("hbm_gbs"), "kind": pk_kind},
+               "peaks": {"hbm_gbs": pk.get("hbm_gbs"), "kind": pk_kind, "fma_fp64_gflops": p64,
+                         "fma_fp32_gflops": p32},
                "roofline": roofline,
+               "kinds": kr,
                "hbm": {"model_bytes_per_solve": model_bytes_per_solve(st["N"], st["p"]),
-                       "achieved_gbs": model_bytes_per_solve(st["N"], st["p"]) * B / (t_max / 1e3) / 1e9,
-                       "pct_of_measured": 100.0 * model_bytes_per_solve(st["N"], st["p"]) * B / (t_max / 1e3) / 1e9
-                       / pk.get("hbm_gbs", 6788.3)},
+                       "achieved_gbs": model_bytes_per_solve(st["N"], st["p"]) * solves_per_item * B / (t_max / 1e3) / 1e9,
+                       "pct_of_measured": 100.0 * model_bytes_per_solve(st["N"], st["p"]) * solves_per_item * B
+                       / (t_max / 1e3) / 1e9 / pk.get("hbm_gbs", 6788.3)},
                "step_breakdown": breakdown,
+               "sweep": sweep,
                "cpu_baseline": cpu}
         print(json.dumps(out))
     plan.close()
