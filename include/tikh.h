@@ -91,6 +91,9 @@ typedef struct tikh_batch_plan_s* tikh_batch_plan;
  *  refine_tol  with refine_steps > 0: after the last correction, a relative residual
  *            ||y - (T^H T + lambda I) x|| / ||y|| above refine_tol makes the call return TIKH_ENOTCONVERGED
  *            (x is still written).  0 (default): no check.
+ *  fft_radix  largest power-of-two radix of the FFT stages: 8 (default, 0) or 4 (more, lighter stages).
+ *  fft_tile   elements per CTA for transforms shorter than it (several transforms share a CTA): a power
+ *            of two up to 4096; 0 = 256.  Both are tuning knobs (tikh.autotune); the results agree to rounding.
  *  wait_polls  bound on the one in-kernel wait (the leaf's basis-rebuild warps polling for the next
  *            pivot step): after this many polls the wait gives up and the call returns TIKH_ETIMEOUT.
  *            0 (default): 2^24 polls.  0..2^30.  A small value exists to exercise the failure path.
@@ -108,6 +111,8 @@ typedef struct {
   int eval_direct_max;
   int wait_polls;
   double refine_tol;
+  int fft_radix;
+  int fft_tile;
 } tikh_opts;
 
 typedef struct {

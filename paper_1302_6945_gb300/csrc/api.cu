@@ -81,8 +81,10 @@ int fft_index(Plan& P, int64_t L, int& err) {
   if (it != P.fft_of_len.end()) return it->second;
   FftPlan f;
   f.L = L;
+  f.tile = P.opts.fft_tile > 0 ? P.opts.fft_tile : 256;
+  const int rmax = P.opts.fft_radix > 0 ? P.opts.fft_radix : 8;
   if (L <= FFT_TILE_MAX) {
-    if (!fft_factor((int)L, f.d1)) { err = TIKH_EINVAL; return -1; }
+    if (!fft_factor((int)L, f.d1, rmax)) { err = TIKH_EINVAL; return -1; }
     f.d1.tw = twiddle(P, L, err);
   } else {
     int64_t L1, L2;
@@ -90,8 +92,8 @@ int fft_index(Plan& P, int64_t L, int& err) {
     f.four = true;
     f.L1 = L1;
     f.L2 = L2;
-    fft_factor((int)L1, f.d1);
-    fft_factor((int)L2, f.d2);
+    fft_factor((int)L1, f.d1, rmax);
+    fft_factor((int)L2, f.d2, rmax);
     f.d1.tw = twiddle(P, L1, err);
     f.d2.tw = twiddle(P, L2, err);
     f.twL = twiddle(P, L, err);
@@ -575,7 +577,9 @@ bool valid_opts(const tikh_opts& o) {
            !(o.eps_diff >= 0.0) || o.max_difficult < 1 || o.max_difficult > (1 << 20) || o.refine_steps < 0 ||
            o.refine_steps > 8 || o.batch < 1 || o.batch > 65535 || (o.graph != 0 && o.graph != 1) ||
            o.prod_direct_max < 0 || o.prod_direct_max > 4096 || o.eval_direct_max < 0 || o.eval_direct_max > 4096 ||
-           o.wait_polls < 0 || o.wait_polls > (1 << 30) || !(o.refine_tol >= 0.0));
+           o.wait_polls < 0 || o.wait_polls > (1 << 30) || !(o.refine_tol >= 0.0) ||
+           (o.fft_radix != 0 && o.fft_radix != 4 && o.fft_radix != 8) || o.fft_tile < 0 || o.fft_tile > 4096 ||
+           (o.fft_tile & (o.fft_tile - 1)) != 0);
 }
 
 Shape core_shape(int64_t m, int64_t n, int64_t N) {
@@ -871,7 +875,7 @@ int tikh_plan_create(tikh_plan* out, int64_t m, int64_t n, int dtype, int prec, 
   if (!out) return TIKH_EINVAL;
   *out = nullptr;
   if (m < 1 || n < 1 || (dtype != TIKH_R64 && dtype != TIKH_C128) || !valid_prec(prec)) return TIKH_EINVAL;
-  tikh_opts o{32, 0, 0, 1e-8, 4096, 0, 1, 0, 0, 0, 0, 0.0};
+  tikh_opts o{32, 0, 0, 1e-8, 4096, 0, 1, 0, 0, 0, 0, 0.0, 0, 0};
   if (opts) o = *opts;
   if (!valid_opts(o)) return TIKH_EINVAL;
   const int64_t cm = std::max(m, n), cn = std::min(m, n);
@@ -902,7 +906,7 @@ int tikh_plan_create_gramian(tikh_plan* out, int64_t n, int64_t p, int dtype, in
   if (!out) return TIKH_EINVAL;
   *out = nullptr;
   if (n < 1 || p < 1 || (dtype != TIKH_R64 && dtype != TIKH_C128) || !valid_prec(prec)) return TIKH_EINVAL;
-  tikh_opts o{32, 0, 0, 1e-8, 4096, 0, 1, 0, 0, 0, 0, 0.0};
+  tikh_opts o{32, 0, 0, 1e-8, 4096, 0, 1, 0, 0, 0, 0, 0.0, 0, 0};
   if (opts) o = *opts;
   if (!valid_opts(o)) return TIKH_EINVAL;
   // Sec. 3.4: the first block row has q = max(n, p) extension rows at k = 1, so N >= q + n - 1; L takes
@@ -1057,7 +1061,7 @@ int tikh_batch_plan_create(tikh_batch_plan* out, int nprob, const int64_t* m, co
   if (nprob < 1 || nlambda < 1 || !m || !n || (int64_t)nprob * nlambda > (1LL << 30) ||
       (dtype != TIKH_R64 && dtype != TIKH_C128) || !valid_prec(prec) || max_workspace_bytes < 0)
     return TIKH_EINVAL;
-  tikh_opts o{32, 0, 0, 1e-8, 4096, 0, 1, 0, 0, 0, 0, 0.0};
+  tikh_opts o{32, 0, 0, 1e-8, 4096, 0, 1, 0, 0, 0, 0, 0.0, 0, 0};
   if (opts) o = *opts;
   o.batch = 1;
   if (!valid_opts(o)) return TIKH_EINVAL;

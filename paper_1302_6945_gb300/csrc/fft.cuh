@@ -35,6 +35,7 @@ struct FftDesc {
 
 struct FftPlan {
   int64_t L = 0;
+  int tile = 256;  // elements per CTA for transforms shorter than this (several transforms per CTA)
   bool four = false;
   int64_t L1 = 0, L2 = 0;
   FftDesc d1{}, d2{};
@@ -347,7 +348,7 @@ template <class LD, class ST>
 inline int fft_run(const FftPlan& p, int batch, int sign, LD ld, ST st, ElemOf<LD>* tmp, cudaStream_t s) {
   using C = ElemOf<LD>;
   if (!p.four) {
-    int want = p.L >= 256 ? 1 : (int)(256 / p.L);
+    int want = p.L >= p.tile ? 1 : (int)(p.tile / p.L);
     return launch_tile(p.d1, want, batch, sign, /*ljf*/ 1, /*sjf*/ 1, ld, st, s) == cudaSuccess ? 1 : -1;
   }
   ColLoad<LD> cl{ld, p.L2};
@@ -359,12 +360,12 @@ inline int fft_run(const FftPlan& p, int batch, int sign, LD ld, ST st, ElemOf<L
   return 2;
 }
 
-// radix schedule for a 7-smooth length (8s first, then 4 / 2, then 7s, 5s and 3s)
-inline bool fft_factor(int L, FftDesc& d) {
+// radix schedule for a 7-smooth length (8s first unless radix_max is 4, then 4 / 2, then 7s, 5s and 3s)
+inline bool fft_factor(int L, FftDesc& d, int radix_max = 8) {
   d.L = L;
   d.nst = 0;
   int v = L;
-  while (v % 8 == 0 && d.nst < FFT_MAX_STAGES) { d.rad[d.nst++] = 8; v /= 8; }
+  while (radix_max >= 8 && v % 8 == 0 && d.nst < FFT_MAX_STAGES) { d.rad[d.nst++] = 8; v /= 8; }
   while (v % 4 == 0 && d.nst < FFT_MAX_STAGES) { d.rad[d.nst++] = 4; v /= 4; }
   while (v % 2 == 0 && d.nst < FFT_MAX_STAGES) { d.rad[d.nst++] = 2; v /= 2; }
   while (v % 7 == 0 && d.nst < FFT_MAX_STAGES) { d.rad[d.nst++] = 7; v /= 7; }

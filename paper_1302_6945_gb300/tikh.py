@@ -24,7 +24,7 @@ class tikh_opts(ctypes.Structure):
                 ("eps_diff", ctypes.c_double), ("max_difficult", ctypes.c_int), ("refine_steps", ctypes.c_int),
                 ("batch", ctypes.c_int), ("graph", ctypes.c_int),
                 ("prod_direct_max", ctypes.c_int), ("eval_direct_max", ctypes.c_int), ("wait_polls", ctypes.c_int),
-                ("refine_tol", ctypes.c_double)]
+                ("refine_tol", ctypes.c_double), ("fft_radix", ctypes.c_int), ("fft_tile", ctypes.c_int)]
 
 
 class tikh_stats(ctypes.Structure):
@@ -348,14 +348,15 @@ class Plan:
 
     def __init__(self, m, n, dtype="r64", n_lim=32, m_min=0, fill=0, eps_diff=1e-8, max_difficult=4096,
                  refine_steps=0, batch=1, graph=False, prod_direct_max=0, eval_direct_max=0, wait_polls=0,
-                 refine_tol=0.0, precision="fp64", stream=None):
+                 refine_tol=0.0, precision="fp64", fft_radix=0, fft_tile=0, stream=None):
         import torch
         self.m, self.n = int(m), int(n)
         self.dtype = TIKH_C128 if dtype in ("c128", TIKH_C128, torch.complex128) else TIKH_R64
         self.batch = int(batch)
         self.opts = tikh_opts(int(n_lim), int(m_min), int(fill), float(eps_diff), int(max_difficult),
                               int(refine_steps), self.batch, 1 if graph else 0, int(prod_direct_max),
-                              int(eval_direct_max), int(wait_polls), float(refine_tol))
+                              int(eval_direct_max), int(wait_polls), float(refine_tol),
+                              int(fft_radix), int(fft_tile))
         self.prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         if stream is None:
             stream = torch.cuda.current_stream()
@@ -484,14 +485,14 @@ class GramianPlan(Plan):
 
     def __init__(self, n, p, dtype="r64", n_lim=32, m_min=0, fill=0, eps_diff=1e-8, max_difficult=4096,
                  refine_steps=0, graph=False, prod_direct_max=0, eval_direct_max=0, wait_polls=0, refine_tol=0.0,
-                 precision="fp64", stream=None):
+                 precision="fp64", fft_radix=0, fft_tile=0, stream=None):
         import torch
         self.m, self.n = int(p), int(n)
         self.dtype = TIKH_C128 if dtype in ("c128", TIKH_C128, torch.complex128) else TIKH_R64
         self.batch = 1
         self.opts = tikh_opts(int(n_lim), int(m_min), int(fill), float(eps_diff), int(max_difficult),
                               int(refine_steps), 1, 1 if graph else 0, int(prod_direct_max), int(eval_direct_max),
-                              int(wait_polls), float(refine_tol))
+                              int(wait_polls), float(refine_tol), int(fft_radix), int(fft_tile))
         self.prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         if stream is None:
             stream = torch.cuda.current_stream()
@@ -519,7 +520,7 @@ class BatchPlan:
 
     def __init__(self, m, n, nlambda, dtype="r64", n_lim=32, m_min=0, fill=0, eps_diff=1e-8, max_difficult=4096,
                  refine_steps=0, graph=False, prod_direct_max=0, eval_direct_max=0, wait_polls=0,
-                 refine_tol=0.0, precision="fp64", max_workspace_bytes=0, stream=None):
+                 refine_tol=0.0, precision="fp64", fft_radix=0, fft_tile=0, max_workspace_bytes=0, stream=None):
         import torch
         self.m = [int(v) for v in m]
         self.n = [int(v) for v in n]
@@ -527,7 +528,7 @@ class BatchPlan:
         self.dtype = TIKH_C128 if dtype in ("c128", TIKH_C128, torch.complex128) else TIKH_R64
         self.opts = tikh_opts(int(n_lim), int(m_min), int(fill), float(eps_diff), int(max_difficult),
                               int(refine_steps), 1, 1 if graph else 0, int(prod_direct_max), int(eval_direct_max),
-                              int(wait_polls), float(refine_tol))
+                              int(wait_polls), float(refine_tol), int(fft_radix), int(fft_tile))
         self.prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         if stream is None:
             stream = torch.cuda.current_stream()
@@ -634,6 +635,8 @@ TUNE_SPACE = {
     "n_lim": (24, 32, 40),
     "prod_direct_max": (36, 72, 192, 360),
     "eval_direct_max": (10, 20, 40, 80),
+    "fft_radix": (8, 4),
+    "fft_tile": (256, 512, 1024),
 }
 
 
@@ -651,7 +654,9 @@ def coordinate_search(time_fn, start, space=None):
         return seen[k]
 
     best_t = t(best)
-    for key in ("n_lim", "prod_direct_max", "eval_direct_max"):
+    for key in ("n_lim", "prod_direct_max", "eval_direct_max", "fft_radix", "fft_tile"):
+        if key not in space:
+            continue
         for v in space[key]:
             cand = dict(best)
             cand[key] = v
@@ -695,5 +700,5 @@ def autotune(m, n, dtype="c128", batch=1, refine_steps=0, reps=2, seed=0, time_f
                 finally:
                     p.close()
 
-    start = {"n_lim": 32, "prod_direct_max": 0, "eval_direct_max": 0}
+    start = {"n_lim": 32, "prod_direct_max": 0, "eval_direct_max": 0, "fft_radix": 0, "fft_tile": 0}
     return coordinate_search(time_fn, start)

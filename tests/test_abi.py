@@ -36,7 +36,8 @@ def test_strerror_and_invalid_plan_without_gpu():
                                          ("max_difficult", 0), ("refine_steps", 9), ("batch", 0), ("graph", 2),
                                          ("prod_direct_max", -1), ("prod_direct_max", 4097),
                                          ("eval_direct_max", -1), ("eval_direct_max", 4097), ("wait_polls", -1),
-                                         ("wait_polls", (1 << 30) + 1), ("refine_tol", -1.0)])
+                                         ("wait_polls", (1 << 30) + 1), ("refine_tol", -1.0),
+                                         ("fft_radix", 2), ("fft_tile", 300), ("fft_tile", 8192)])
 def test_invalid_options_are_rejected_before_any_device_work(field, value):
     # argument checks come first, so they hold on a machine without a GPU
     from paper_1302_6945_gb300 import tikh

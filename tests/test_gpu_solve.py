@@ -116,6 +116,15 @@ def test_c1_config_vs_oracle_and_dense():
     assert relerr(x, xd) <= 1e-9
 
 
+@pytest.mark.parametrize("radix,tile", [(4, 0), (8, 1024), (4, 2048)])
+def test_fft_radix_and_tile_options_keep_parity(radix, tile):
+    # the tuner's FFT knobs change only the transforms' schedule: same solution as the oracle
+    P = W.config_c1()
+    x, st = gpu_solve(P, False, fft_radix=radix, fft_tile=tile, prod_direct_max=36, eval_direct_max=10)
+    xo, _ = oracle.solve(P["col"], P["row"], P["b"], P["lam"], is_complex=0)
+    assert relerr(x, xo.real) <= TOL
+
+
 def test_solve_normal_paper_workload():
     # Sec. 7.1: known x, y = (T^H T + lam I) x
     P = W.paper_problem(512, seed=3)

@@ -20,3 +20,14 @@ def test_coordinate_search_keeps_the_start_when_nothing_is_faster():
     start = {"n_lim": 32, "prod_direct_max": 0, "eval_direct_max": 0}
     best, _ = tikh.coordinate_search(lambda o: 0.0 if o == start else 1.0, start)
     assert best == start
+
+
+def test_coordinate_search_tunes_the_fft_radix_and_tile():
+    want = {"n_lim": 32, "prod_direct_max": 0, "eval_direct_max": 0, "fft_radix": 4, "fft_tile": 1024}
+
+    def cost(o):
+        return sum(abs((o.get(k) or 0) - want[k]) for k in want)
+
+    best, _ = tikh.coordinate_search(cost, {"n_lim": 32, "prod_direct_max": 0, "eval_direct_max": 0, "fft_radix": 0,
+                                            "fft_tile": 0})
+    assert best["fft_radix"] == 4 and best["fft_tile"] == 1024
