@@ -116,12 +116,13 @@ static int is_7smooth(int64_t v) {
   return is_5smooth(v);
 }
 
-int tikh_oracle_plan(int64_t m, int64_t n, const tikh_oracle_opts* opts, int64_t* N, int64_t* M, int64_t* k,
-                     int* p) {
-  if (m < 1 || n < 1 || !opts || opts->nlim < 2) return TIKH_ORACLE_EINVAL;
-  int64_t Nt = m + n - 1, Mv = Nt;
+/* Algorithm 2 for ns condition sets per node over a circulant of at least Nt points: halve M while
+ * ns M > N_lim, then M even and 7-smooth (R6); N = 2^p M. */
+static int plan_sets(int64_t Nt, int ns, const tikh_oracle_opts* opts, int64_t* N, int64_t* M, int* p) {
+  if (Nt < 1 || !opts || opts->nlim < ns) return TIKH_ORACLE_EINVAL;
+  int64_t Mv = Nt;
   int pv = 0;
-  while (2 * Mv > opts->nlim) { /* two condition sets per node: s*M with s = 2 */
+  while (ns * Mv > opts->nlim) {
     ++pv;
     Mv = (Mv + 1) / 2;
   }
@@ -130,8 +131,16 @@ int tikh_oracle_plan(int64_t m, int64_t n, const tikh_oracle_opts* opts, int64_t
   while (!is_7smooth(Mv)) Mv += 2;
   *N = Mv << pv;
   *M = Mv;
-  *k = *N - Nt;
   *p = pv;
+  return 0;
+}
+
+int tikh_oracle_plan(int64_t m, int64_t n, const tikh_oracle_opts* opts, int64_t* N, int64_t* M, int64_t* k,
+                     int* p) {
+  if (m < 1 || n < 1 || !opts || opts->nlim < 2) return TIKH_ORACLE_EINVAL;
+  int rc = plan_sets(m + n - 1, 2, opts, N, M, p); /* two condition sets per node: s*M with s = 2 */
+  if (rc) return rc;
+  *k = *N - (m + n - 1);
   return 0;
 }
 
@@ -148,9 +157,10 @@ static double splitmix_uniform(uint64_t c) {
   return (double)(z >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
 }
 
-/* periodic sequence at[d mod N] = a_d on d in [-(n-1), m-1]; k arbitrary entries filled by R5 */
+/* periodic sequence at[d mod N] = a_d on d in [-(n-1), m-1]; k arbitrary entries filled by R5 (SplitMix64
+ * counters from ctr0: 0 for T, 2^41 for a general regulariser L) */
 static void periodic_generator(int64_t m, int64_t n, int64_t N, int64_t k, const cx* col, const cx* row,
-                               int fill, int is_complex, cx* at) {
+                               int fill, int is_complex, uint64_t ctr0, cx* at) {
   for (int64_t d = 0; d < N; ++d) at[d] = 0;
   for (int64_t d = 0; d < m; ++d) at[d % N] = col[d];
   for (int64_t d = 1; d < n; ++d) at[(N - d) % N] = row[d];
@@ -170,8 +180,8 @@ static void periodic_generator(int64_t m, int64_t n, int64_t N, int64_t k, const
     if (fabs(cimag(row[d])) > peak) peak = fabs(cimag(row[d]));
   }
   for (int64_t i = 1; i <= k; ++i) {
-    double re = peak * splitmix_uniform((uint64_t)(2 * i));
-    double im = is_complex ? peak * splitmix_uniform((uint64_t)(2 * i + 1)) : 0.0;
+    double re = peak * splitmix_uniform((uint64_t)(2 * i) + ctr0);
+    double im = is_complex ? peak * splitmix_uniform((uint64_t)(2 * i + 1) + ctr0) : 0.0;
     at[(m - 1 + i) % N] = re + im * I;
   }
 }
@@ -198,7 +208,7 @@ static int build_conditions(int64_t m, int64_t n, int64_t N, int64_t k, const cx
   cx* cy = (cx*)malloc(sizeof(cx) * (size_t)N);
   int rc = TIKH_ORACLE_ENOMEM;
   if (!at || !cT || !cH || !cy) goto done;
-  periodic_generator(m, n, N, k, col, row, fill, is_complex, at);
+  periodic_generator(m, n, N, k, col, row, fill, is_complex, 0, at);
   for (int64_t j = 0; j < N; ++j) {
     int64_t dT = ((j - (n + k - 1)) % N + N) % N; /* c_T[j]  = a_{j-(n+k-1)}         (R2) */
     int64_t dH = ((m + k - 1 - j) % N + N) % N;   /* c_H[j]  = conj(a_{(m+k-1)-j})   (T^H) */
@@ -230,25 +240,30 @@ done:
 }
 
 /* ------------------------------------------------------------------------------------------ */
-/* Polynomial 5x5 matrices.                                                                   */
+/* Polynomial w x w matrices (w = 5 for the l2 and Toeplitz-Gramian systems, 7 for the general   */
+/* problem of Sec. 3.2).                                                                      */
 /* ------------------------------------------------------------------------------------------ */
 
+#define WMAX 7
+
 typedef struct {
-  cx* c[25];
-  int64_t len[25]; /* number of stored coefficients; 0 = the zero polynomial */
+  int w;                 /* matrix size */
+  cx* c[WMAX * WMAX];    /* entry (i, j) at c[w i + j] */
+  int64_t len[WMAX * WMAX]; /* number of stored coefficients; 0 = the zero polynomial */
 } pmat;
 
 static void pm_free(pmat* B) {
-  for (int e = 0; e < 25; ++e) { free(B->c[e]); B->c[e] = NULL; B->len[e] = 0; }
+  for (int e = 0; e < WMAX * WMAX; ++e) { free(B->c[e]); B->c[e] = NULL; B->len[e] = 0; }
 }
 
-static int pm_identity(pmat* B) {
+static int pm_identity(pmat* B, int w) {
   memset(B, 0, sizeof(*B));
-  for (int i = 0; i < 5; ++i) {
-    B->c[6 * i] = (cx*)malloc(sizeof(cx));
-    if (!B->c[6 * i]) return TIKH_ORACLE_ENOMEM;
-    B->c[6 * i][0] = 1.0;
-    B->len[6 * i] = 1;
+  B->w = w;
+  for (int i = 0; i < w; ++i) {
+    B->c[(w + 1) * i] = (cx*)malloc(sizeof(cx));
+    if (!B->c[(w + 1) * i]) return TIKH_ORACLE_ENOMEM;
+    B->c[(w + 1) * i][0] = 1.0;
+    B->len[(w + 1) * i] = 1;
   }
   return 0;
 }
@@ -274,28 +289,28 @@ static cx horner(const cx* c, int64_t len, cx z) {
 /* Serial single-point construction (Eq. (spbasis), Sec. 4.3) with pivoting (R1, R7, R8).       */
 /* ------------------------------------------------------------------------------------------ */
 
-/* Processes the conditions (sigma[q], r[q]) q < K against basis B (updated in place, B <- B E_q).
- * active[q] != 0 marks the conditions still to process.  eps < 0 disables deferral.
+/* Processes the conditions (sigma[q], r[q]) q < K (rows of B->w entries) against basis B (updated in place,
+ * B <- B E_q).  active[q] != 0 marks the conditions still to process.  eps < 0 disables deferral.
  * order/pivot (may be null) record the processing; deferred (may be null) collects deferred
  * positions; n_drop counts conditions whose residual is exactly zero. */
 static int serial_construct(int K, const cx* sigma, cx* r, char* active, int* delta, double eps, pmat* B,
                             int* order, int* pivot, int* deferred, int* n_def, int64_t* n_drop) {
+  const int w = B->w;
   int step = 0;
   if (n_def) *n_def = 0;
   for (;;) {
     int best = -1, bpi = -1;
     double bscore = -1.0;
-    int remaining = 0;
     for (int q = 0; q < K; ++q) {
       if (!active[q]) continue;
-      const cx* rq = r + 5 * q;
-      double mag[5], tot = 0.0;
+      const cx* rq = r + w * q;
+      double mag[WMAX], tot = 0.0;
       int pi = -1;
-      for (int i = 0; i < 5; ++i) {
+      for (int i = 0; i < w; ++i) {
         mag[i] = creal(rq[i]) * creal(rq[i]) + cimag(rq[i]) * cimag(rq[i]);
         tot += mag[i];
       }
-      for (int i = 0; i < 5; ++i) {
+      for (int i = 0; i < w; ++i) {
         if (creal(rq[i]) == 0.0 && cimag(rq[i]) == 0.0) continue; /* R1: non-zero entries only */
         if (pi < 0 || delta[i] < delta[pi] || (delta[i] == delta[pi] && mag[i] > mag[pi])) pi = i;
       }
@@ -304,7 +319,6 @@ static int serial_construct(int K, const cx* sigma, cx* r, char* active, int* de
         if (n_drop) ++*n_drop;
         continue;
       }
-      ++remaining;
       double score = mag[pi] / tot; /* R8 */
       if (score > bscore) { bscore = score; best = q; bpi = pi; }
     }
@@ -317,15 +331,14 @@ static int serial_construct(int K, const cx* sigma, cx* r, char* active, int* de
         }
       break;
     }
-    (void)remaining;
     const int pi = bpi;
     const cx sg = sigma[best];
-    const cx* rs = r + 5 * best;
+    const cx* rs = r + w * best;
     /* mu_i = -r_i / r_pi, division as r_i * conj(r_pi) / |r_pi|^2 */
     double den = creal(rs[pi]) * creal(rs[pi]) + cimag(rs[pi]) * cimag(rs[pi]);
     cx inv = creal(rs[pi]) / den - (cimag(rs[pi]) / den) * I;
-    cx mu[5];
-    for (int i = 0; i < 5; ++i) mu[i] = (i == pi) ? 0.0 : -(rs[i] * inv);
+    cx mu[WMAX];
+    for (int i = 0; i < w; ++i) mu[i] = (i == pi) ? 0.0 : -(rs[i] * inv);
     active[best] = 0;
     if (order) order[step] = best;
     if (pivot) pivot[step] = pi;
@@ -333,23 +346,23 @@ static int serial_construct(int K, const cx* sigma, cx* r, char* active, int* de
     /* residual update r_q <- r_q E(sigma_q): E = I except column pi = (z - sg) e_pi + sum mu_i e_i */
     for (int q = 0; q < K; ++q) {
       if (!active[q]) continue;
-      cx* rq = r + 5 * q;
+      cx* rq = r + w * q;
       cx rp = rq[pi];
-      for (int i = 0; i < 5; ++i)
+      for (int i = 0; i < w; ++i)
         if (i != pi) rq[i] = rq[i] + mu[i] * rp;
       rq[pi] = rp * (sigma[q] - sg);
     }
     /* basis update B <- B E: column pi <- (z - sg) column pi; column i += mu_i * old column pi */
-    for (int row = 0; row < 5; ++row) {
-      int ep = 5 * row + pi;
+    for (int row = 0; row < w; ++row) {
+      int ep = w * row + pi;
       int64_t L = B->len[ep];
       if (L == 0) continue;
       cx* old = (cx*)malloc(sizeof(cx) * (size_t)L);
       if (!old) return TIKH_ORACLE_ENOMEM;
       memcpy(old, B->c[ep], sizeof(cx) * (size_t)L);
-      for (int i = 0; i < 5; ++i) {
+      for (int i = 0; i < w; ++i) {
         if (i == pi) continue;
-        int ei = 5 * row + i;
+        int ei = w * row + i;
         if (pm_reserve(B, ei, L)) { free(old); return TIKH_ORACLE_ENOMEM; }
         for (int64_t t = 0; t < L; ++t) B->c[ei][t] = B->c[ei][t] + mu[i] * old[t];
       }
@@ -372,7 +385,7 @@ int tikh_oracle_leaf(int K, const double* sigma, double* r, int* delta, double e
                      int64_t* len, int* order, int* pivot, int* deferred, int* n_def) {
   if (K < 0 || !sigma || !r || !delta || !B || !len) return TIKH_ORACLE_EINVAL;
   pmat P;
-  int rc = pm_identity(&P);
+  int rc = pm_identity(&P, 5);
   char* active = (char*)malloc((size_t)K + 1);
   if (rc || !active) { pm_free(&P); free(active); return TIKH_ORACLE_ENOMEM; }
   memset(active, 1, (size_t)K);
@@ -399,15 +412,15 @@ int tikh_oracle_leaf(int K, const double* sigma, double* r, int* delta, double e
 /* Degree bounds (R10) and column scaling (R9).                                               */
 /* ------------------------------------------------------------------------------------------ */
 
-static void degree_bounds(const int* din, const int* dout, int64_t* bound /* 25 */) {
+static void degree_bounds(int w, const int* din, const int* dout, int64_t* bound /* w * w */) {
   int have_active = 0, amax = 0;
-  for (int j = 0; j < 5; ++j)
+  for (int j = 0; j < w; ++j)
     if (dout[j] > din[j]) {
       if (!have_active || dout[j] > amax) amax = dout[j];
       have_active = 1;
     }
-  for (int i = 0; i < 5; ++i)
-    for (int j = 0; j < 5; ++j) {
+  for (int i = 0; i < w; ++i)
+    for (int j = 0; j < w; ++j) {
       int64_t b;
       if (dout[j] > din[j]) {
         b = (int64_t)dout[j] - din[i];
@@ -417,12 +430,12 @@ static void degree_bounds(const int* din, const int* dout, int64_t* bound /* 25 
         int64_t tau_b = (int64_t)dout[j] - din[i];
         b = acc < tau_b ? acc : tau_b;
       }
-      bound[5 * i + j] = b;
+      bound[w * i + j] = b;
     }
 }
 
 static int trim_to_bounds(pmat* B, const int64_t* bound) {
-  for (int e = 0; e < 25; ++e) {
+  for (int e = 0; e < B->w * B->w; ++e) {
     int64_t want = bound[e] < 0 ? 0 : bound[e] + 1;
     if (B->len[e] > want) {
       B->len[e] = want;
@@ -433,10 +446,11 @@ static int trim_to_bounds(pmat* B, const int64_t* bound) {
 }
 
 static void scale_columns(pmat* B) {
-  for (int j = 0; j < 5; ++j) {
+  const int w = B->w;
+  for (int j = 0; j < w; ++j) {
     double mx = 0.0;
-    for (int i = 0; i < 5; ++i) {
-      int e = 5 * i + j;
+    for (int i = 0; i < w; ++i) {
+      int e = w * i + j;
       for (int64_t t = 0; t < B->len[e]; ++t) {
         double a = fabs(creal(B->c[e][t])), b = fabs(cimag(B->c[e][t]));
         if (a > mx) mx = a;
@@ -446,8 +460,8 @@ static void scale_columns(pmat* B) {
     if (mx == 0.0) continue;
     int ex;
     frexp(mx, &ex); /* mx = f 2^ex, f in [0.5, 1) */
-    for (int i = 0; i < 5; ++i) {
-      int e = 5 * i + j;
+    for (int i = 0; i < w; ++i) {
+      int e = w * i + j;
       for (int64_t t = 0; t < B->len[e]; ++t)
         B->c[e][t] = ldexp(creal(B->c[e][t]), -ex) + ldexp(cimag(B->c[e][t]), -ex) * I;
     }
@@ -457,47 +471,49 @@ static void scale_columns(pmat* B) {
 /* ------------------------------------------------------------------------------------------ */
 /* The recursion (Algorithm 1 with paired interleaving, Sec. 6.1).                             */
 /* A node is (a, s, L): its nodes are omega^{a + c + s j}, c in {0,1}, j < L; s L = N.         */
-/* Its conditions, in list order, are position 4j + 2c + f (f = 0: F, f = 1: G).              */
+/* Its conditions, in list order, are position 2 ns j + ns c + f (f < ns: the condition set).  */
 /* ------------------------------------------------------------------------------------------ */
 
 typedef struct {
   int64_t N, M;
   double eps;
   int mode;
-  cx* R; /* residual rows [N][2][5] */
-  int64_t* deferred; /* deferred condition ids 2e + f */
+  int w, ns;  /* basis size and condition sets per node */
+  cx* R; /* residual rows [N][ns][w] */
+  int64_t* deferred; /* deferred condition ids ns e + f */
   int64_t n_def, n_drop;
 } rstate;
 
 static int leaf_node(rstate* st, int64_t a, int64_t s, int64_t L, int* delta, pmat* out) {
-  int K = (int)(4 * L);
+  const int w = st->w, ns = st->ns;
+  int K = (int)(2 * ns * L);
   cx* sig = (cx*)malloc(sizeof(cx) * (size_t)K);
-  cx* r = (cx*)malloc(sizeof(cx) * 5 * (size_t)K);
+  cx* r = (cx*)malloc(sizeof(cx) * (size_t)w * (size_t)K);
   char* act = (char*)malloc((size_t)K);
   int* dq = (int*)malloc(sizeof(int) * (size_t)K);
   int rc = TIKH_ORACLE_ENOMEM, nd = 0;
   if (!sig || !r || !act || !dq) goto done;
   for (int64_t j = 0; j < L; ++j)
     for (int c = 0; c < 2; ++c)
-      for (int f = 0; f < 2; ++f) {
-        int q = (int)(4 * j + 2 * c + f);
+      for (int f = 0; f < ns; ++f) {
+        int q = (int)(2 * ns * j + ns * c + f);
         int64_t e = a + c + s * j;
         sig[q] = node(e, st->N);
-        memcpy(r + 5 * q, st->R + 10 * e + 5 * f, sizeof(cx) * 5);
+        memcpy(r + (size_t)w * q, st->R + ((size_t)ns * e + f) * w, sizeof(cx) * (size_t)w);
         act[q] = 1;
       }
-  int din[5];
-  memcpy(din, delta, sizeof(din));
-  if ((rc = pm_identity(out))) goto done;
+  int din[WMAX];
+  memcpy(din, delta, sizeof(int) * (size_t)w);
+  if ((rc = pm_identity(out, w))) goto done;
   rc = serial_construct(K, sig, r, act, delta, st->eps, out, NULL, NULL, dq, &nd, &st->n_drop);
   if (rc) goto done;
   for (int i = 0; i < nd; ++i) {
     int q = dq[i];
-    int64_t j = q / 4, c = (q / 2) % 2, f = q % 2;
-    st->deferred[st->n_def++] = 2 * (a + c + s * j) + f;
+    int64_t j = q / (2 * ns), c = (q / ns) % 2, f = q % ns;
+    st->deferred[st->n_def++] = ns * (a + c + s * j) + f;
   }
-  int64_t bound[25];
-  degree_bounds(din, delta, bound);
+  int64_t bound[WMAX * WMAX];
+  degree_bounds(w, din, delta, bound);
   trim_to_bounds(out, bound);
   scale_columns(out);
 done:
@@ -513,11 +529,12 @@ static int64_t smooth_at_least(int64_t v) {
 
 /* step 2 of Algorithm 1: phi <- phi B_L(sigma) for every condition of the right child (aR, 2s, L/2) */
 static int update_right(rstate* st, const pmat* BL, int64_t aR, int64_t sR, int64_t Lr) {
+  const int w = st->w, ns = st->ns;
   int64_t N = st->N;
   int use_fft = st->mode == TIKH_ORACLE_FFT || (st->mode == TIKH_ORACLE_AUTO && Lr > 64);
-  cx* val = (cx*)malloc(sizeof(cx) * 25 * 2 * (size_t)Lr); /* [entry][c][j] */
+  cx* val = (cx*)malloc(sizeof(cx) * (size_t)(w * w) * 2 * (size_t)Lr); /* [entry][c][j] */
   if (!val) return TIKH_ORACLE_ENOMEM;
-  for (int e = 0; e < 25; ++e)
+  for (int e = 0; e < w * w; ++e)
     for (int c = 0; c < 2; ++c) {
       cx* v = val + ((size_t)e * 2 + c) * (size_t)Lr;
       int64_t beta = aR + c;
@@ -534,15 +551,15 @@ static int update_right(rstate* st, const pmat* BL, int64_t aR, int64_t sR, int6
   for (int64_t j = 0; j < Lr; ++j)
     for (int c = 0; c < 2; ++c) {
       int64_t e = aR + c + sR * j;
-      for (int f = 0; f < 2; ++f) {
-        cx* rq = st->R + 10 * e + 5 * f;
-        cx nr[5];
-        for (int col = 0; col < 5; ++col) {
+      for (int f = 0; f < ns; ++f) {
+        cx* rq = st->R + ((size_t)ns * e + f) * w;
+        cx nr[WMAX];
+        for (int col = 0; col < w; ++col) {
           cx acc = 0;
-          for (int i = 0; i < 5; ++i) acc += rq[i] * val[((size_t)(5 * i + col) * 2 + c) * (size_t)Lr + j];
+          for (int i = 0; i < w; ++i) acc += rq[i] * val[((size_t)(w * i + col) * 2 + c) * (size_t)Lr + j];
           nr[col] = acc;
         }
-        memcpy(rq, nr, sizeof(nr));
+        memcpy(rq, nr, sizeof(cx) * (size_t)w);
       }
     }
   free(val);
@@ -551,27 +568,29 @@ static int update_right(rstate* st, const pmat* BL, int64_t aR, int64_t sR, int6
 
 /* step 4 of Algorithm 1: B = B_L B_R, trimmed to the node's degree bounds */
 static int multiply(const rstate* st, const pmat* BL, const pmat* BR, const int64_t* bound, pmat* out) {
+  const int w = BL->w;
   memset(out, 0, sizeof(*out));
+  out->w = w;
   int64_t D = -1;
-  for (int e = 0; e < 25; ++e)
+  for (int e = 0; e < w * w; ++e)
     if (bound[e] > D) D = bound[e];
   int64_t maxlen = 0;
-  for (int e = 0; e < 25; ++e) {
+  for (int e = 0; e < w * w; ++e) {
     if (BL->len[e] > maxlen) maxlen = BL->len[e];
     if (BR->len[e] > maxlen) maxlen = BR->len[e];
   }
   int use_fft = st->mode == TIKH_ORACLE_FFT || (st->mode == TIKH_ORACLE_AUTO && maxlen > 64);
   if (!use_fft) {
-    for (int i = 0; i < 5; ++i)
-      for (int j = 0; j < 5; ++j) {
-        int eo = 5 * i + j;
+    for (int i = 0; i < w; ++i)
+      for (int j = 0; j < w; ++j) {
+        int eo = w * i + j;
         int64_t want = bound[eo] < 0 ? 0 : bound[eo] + 1;
         if (want == 0) continue;
         if (pm_reserve(out, eo, want)) return TIKH_ORACLE_ENOMEM;
-        for (int t = 0; t < 5; ++t) {
-          const cx* x = BL->c[5 * i + t];
-          const cx* y = BR->c[5 * t + j];
-          int64_t lx = BL->len[5 * i + t], ly = BR->len[5 * t + j];
+        for (int t = 0; t < w; ++t) {
+          const cx* x = BL->c[w * i + t];
+          const cx* y = BR->c[w * t + j];
+          int64_t lx = BL->len[w * i + t], ly = BR->len[w * t + j];
           for (int64_t u = 0; u < lx; ++u)
             for (int64_t v = 0; v < ly; ++v)
               if (u + v < want) out->c[eo][u + v] += x[u] * y[v];
@@ -582,12 +601,12 @@ static int multiply(const rstate* st, const pmat* BL, const pmat* BR, const int6
   /* FFT products of length P > D: a linear convolution of polynomials whose product has degree
    * <= D equals the cyclic one */
   int64_t P = smooth_at_least(D + 1);
-  cx* fl = (cx*)calloc(25 * (size_t)P, sizeof(cx));
-  cx* fr = (cx*)calloc(25 * (size_t)P, sizeof(cx));
+  cx* fl = (cx*)calloc((size_t)(w * w) * (size_t)P, sizeof(cx));
+  cx* fr = (cx*)calloc((size_t)(w * w) * (size_t)P, sizeof(cx));
   cx* acc = (cx*)malloc(sizeof(cx) * (size_t)P);
   int rc = TIKH_ORACLE_ENOMEM;
   if (!fl || !fr || !acc) goto done;
-  for (int e = 0; e < 25; ++e) {
+  for (int e = 0; e < w * w; ++e) {
     /* entries longer than P would wrap; their high coefficients multiply into terms above D
      * only if the bound is violated, which trim_to_bounds would have removed anyway */
     int64_t lx = BL->len[e] < P ? BL->len[e] : P, ly = BR->len[e] < P ? BR->len[e] : P;
@@ -596,14 +615,14 @@ static int multiply(const rstate* st, const pmat* BL, const pmat* BR, const int6
     if (lx && (rc = dft(fl + (size_t)e * P, P, +1))) goto done;
     if (ly && (rc = dft(fr + (size_t)e * P, P, +1))) goto done;
   }
-  for (int i = 0; i < 5; ++i)
-    for (int j = 0; j < 5; ++j) {
-      int eo = 5 * i + j;
+  for (int i = 0; i < w; ++i)
+    for (int j = 0; j < w; ++j) {
+      int eo = w * i + j;
       int64_t want = bound[eo] < 0 ? 0 : bound[eo] + 1;
       if (want == 0) continue;
       for (int64_t u = 0; u < P; ++u) {
         cx s = 0;
-        for (int t = 0; t < 5; ++t) s += fl[(size_t)(5 * i + t) * P + u] * fr[(size_t)(5 * t + j) * P + u];
+        for (int t = 0; t < w; ++t) s += fl[(size_t)(w * i + t) * P + u] * fr[(size_t)(w * t + j) * P + u];
         acc[u] = s;
       }
       if ((rc = dft(acc, P, -1))) goto done;
@@ -618,8 +637,9 @@ done:
 
 static int rec_tanint(rstate* st, int64_t a, int64_t s, int64_t L, int* delta, pmat* out) {
   if (2 * L == st->M) return leaf_node(st, a, s, L, delta, out);
-  int din[5];
-  memcpy(din, delta, sizeof(din));
+  const int w = st->w;
+  int din[WMAX];
+  memcpy(din, delta, sizeof(int) * (size_t)w);
   pmat BL, BR;
   memset(&BR, 0, sizeof(BR));
   int rc = rec_tanint(st, a, 2 * s, L / 2, delta, &BL); /* step 1: {t mod 4 in {0,1}} */
@@ -627,8 +647,8 @@ static int rec_tanint(rstate* st, int64_t a, int64_t s, int64_t L, int* delta, p
   rc = update_right(st, &BL, a + s, 2 * s, L / 2); /* step 2 */
   if (!rc) rc = rec_tanint(st, a + s, 2 * s, L / 2, delta, &BR); /* step 3: {t mod 4 in {2,3}} */
   if (!rc) {
-    int64_t bound[25];
-    degree_bounds(din, delta, bound);
+    int64_t bound[WMAX * WMAX];
+    degree_bounds(w, din, delta, bound);
     rc = multiply(st, &BL, &BR, bound, out); /* step 4 */
     if (!rc) scale_columns(out);
   }
@@ -693,27 +713,96 @@ static int gram_column(int64_t n, int64_t N, const cx* g, int fill, int is_compl
   return dft(out, N, +1);
 }
 
-/* The superfast solve from the plan (N, M, k, p) on: conditions, Algorithm 1, difficult points,
- * extraction.  gram == NULL: the l2 system (Eq. (ex6)) for (T^H T + lam I) x = y; otherwise the
- * Toeplitz-Gramian system (Eq. (ex7)) for (G + L^H L) x = y with L = [col, row] (m x n) in the role of T
- * and G (first column gram) in place of lam I. */
+/* The superfast solve from given conditions: cond[N][ns][w] (row f of node e: the condition of set f at
+ * omega^e), tau[w] (Eq. (taudef); the starting basis I has tau-degrees -tau), the plan (N, M).  Algorithm 1
+ * over all N nodes, the difficult points at the end (Sec. 5), extraction x(z) = B*_{1,j}(z) / B*_{w,j}
+ * for the column j of tau-degree 0 (Sec. 4.3 end, Sec. 5): nx coefficients of x. */
+static int solve_conditions(int64_t N, int64_t M, int w, int ns, const cx* cond, const int* tau, int64_t nx,
+                            const tikh_oracle_opts* opts, cx* x, int* delta_out, int64_t* n_def, int64_t* n_drop,
+                            double* Bout, int64_t cap, int64_t* lenout, int64_t* deferred_out,
+                            int64_t deferred_cap) {
+  rstate st;
+  memset(&st, 0, sizeof(st));
+  st.N = N; st.M = M; st.eps = opts->eps_diff; st.mode = opts->mode; st.w = w; st.ns = ns;
+  const size_t rows = (size_t)ns * (size_t)N;
+  st.R = (cx*)malloc(sizeof(cx) * rows * (size_t)w);
+  st.deferred = (int64_t*)malloc(sizeof(int64_t) * rows);
+  pmat B;
+  memset(&B, 0, sizeof(B));
+  int rc = TIKH_ORACLE_ENOMEM;
+  if (!st.R || !st.deferred) goto done;
+  memcpy(st.R, cond, sizeof(cx) * rows * (size_t)w);
+  int delta[WMAX];
+  for (int i = 0; i < w; ++i) delta[i] = -tau[i];
+  /* root node: all N nodes = omega^{0 + c + 2 j}, j < N/2 */
+  if ((rc = rec_tanint(&st, 0, 2, N / 2, delta, &B))) goto done;
+  if (deferred_out)
+    for (int64_t q = 0; q < st.n_def && q < deferred_cap; ++q) deferred_out[q] = st.deferred[q];
+  if (st.n_def > 0) {
+    /* difficult points (Sec. 5): residual against the final basis, then serial processing */
+    int K = (int)st.n_def;
+    cx* sig = (cx*)malloc(sizeof(cx) * (size_t)K);
+    cx* r = (cx*)malloc(sizeof(cx) * (size_t)w * (size_t)K);
+    char* act = (char*)malloc((size_t)K);
+    if (!sig || !r || !act) { free(sig); free(r); free(act); rc = TIKH_ORACLE_ENOMEM; goto done; }
+    for (int q = 0; q < K; ++q) {
+      int64_t id = st.deferred[q], e = id / ns;
+      const cx* ph = cond + ((size_t)ns * e + (size_t)(id % ns)) * w;
+      sig[q] = node(e, N);
+      for (int j = 0; j < w; ++j) {
+        cx acc = 0;
+        for (int i = 0; i < w; ++i) acc += ph[i] * horner(B.c[w * i + j], B.len[w * i + j], sig[q]);
+        r[w * q + j] = acc;
+      }
+      act[q] = 1;
+    }
+    rc = serial_construct(K, sig, r, act, delta, -1.0, &B, NULL, NULL, NULL, NULL, &st.n_drop);
+    free(sig); free(r); free(act);
+    if (rc) goto done;
+  }
+  /* Sec. 4.3 end: one column has tau-degree 0, the other w - 1 have 1 */
+  int jstar = -1, nzero = 0, none = 0;
+  for (int j = 0; j < w; ++j) {
+    if (delta[j] == 0) { jstar = j; ++nzero; }
+    else if (delta[j] == 1) ++none;
+  }
+  memcpy(delta_out, delta, sizeof(int) * (size_t)w);
+  *n_def = st.n_def;
+  *n_drop = st.n_drop;
+  if (nzero != 1 || none != w - 1 || B.len[w * (w - 1) + jstar] < 1) { rc = TIKH_ORACLE_ENUMERIC; goto done; }
+  {
+    cx cw = B.c[w * (w - 1) + jstar][0];
+    const cx* b1 = B.c[jstar];
+    int64_t l1 = B.len[jstar];
+    for (int64_t i = 0; i < nx; ++i) x[i] = (i < l1 ? b1[i] : 0.0) / cw;
+  }
+  if (Bout && lenout) {
+    for (int e = 0; e < w * w; ++e) {
+      int64_t L = B.len[e] < cap ? B.len[e] : cap;
+      lenout[e] = B.len[e];
+      cx* dst = (cx*)Bout + (size_t)e * (size_t)cap;
+      for (int64_t t = 0; t < cap; ++t) dst[t] = (t < L) ? B.c[e][t] : 0.0;
+    }
+  }
+  rc = 0;
+done:
+  pm_free(&B);
+  free(st.R); free(st.deferred);
+  return rc;
+}
+
+/* The l2 system (Eq. (ex6)) for (T^H T + lam I) x = y, or with gram != NULL the Toeplitz-Gramian system
+ * (Eq. (ex7)) for (G + L^H L) x = y with L = [col, row] (m x n) in the role of T and G (first column gram)
+ * in place of lam I: conditions F, G (two sets), tau = [n-1, m-1, m+k-2, n+k-2, 0], then the solve. */
 static int solve_core(int64_t m, int64_t n, const double* col, const double* row, const double* y, double lam,
                       const double* gram, int64_t N, int64_t M, int64_t k, int p, const tikh_oracle_opts* opts,
                       double* x, tikh_oracle_stats* stats, double* Bout, int64_t cap, int64_t* lenout,
                       int64_t* deferred_out, int64_t deferred_cap) {
-  int rc;
-  rstate st;
-  memset(&st, 0, sizeof(st));
-  st.N = N; st.M = M; st.eps = opts->eps_diff; st.mode = opts->mode;
   cx* F = (cx*)malloc(sizeof(cx) * 5 * (size_t)N);
   cx* G = (cx*)malloc(sizeof(cx) * 5 * (size_t)N);
-  cx* Phi = (cx*)malloc(sizeof(cx) * 10 * (size_t)N);
-  st.R = (cx*)malloc(sizeof(cx) * 10 * (size_t)N);
-  st.deferred = (int64_t*)malloc(sizeof(int64_t) * 2 * (size_t)N);
-  pmat B;
-  memset(&B, 0, sizeof(B));
-  rc = TIKH_ORACLE_ENOMEM;
-  if (!F || !G || !Phi || !st.R || !st.deferred) goto done;
+  cx* cond = (cx*)malloc(sizeof(cx) * 10 * (size_t)N);
+  int rc = TIKH_ORACLE_ENOMEM;
+  if (!F || !G || !cond) goto done;
   if ((rc = build_conditions(m, n, N, k, (const cx*)col, (const cx*)row, (const cx*)y, lam, opts->fill,
                              opts->is_complex, F, G)))
     goto done;
@@ -726,70 +815,28 @@ static int solve_core(int64_t m, int64_t n, const double* col, const double* row
     if (rc) goto done;
   }
   for (int64_t e = 0; e < N; ++e) {
-    memcpy(st.R + 10 * e, F + 5 * e, sizeof(cx) * 5);
-    memcpy(st.R + 10 * e + 5, G + 5 * e, sizeof(cx) * 5);
+    memcpy(cond + 10 * e, F + 5 * e, sizeof(cx) * 5);
+    memcpy(cond + 10 * e + 5, G + 5 * e, sizeof(cx) * 5);
   }
-  memcpy(Phi, st.R, sizeof(cx) * 10 * (size_t)N);
-  /* Eq. (taudef) with reading R3; the starting basis I has tau-degrees -tau (Sec. 4.3) */
-  int delta[5] = {-(int)(n - 1), -(int)(m - 1), -(int)(m + k - 2), -(int)(n + k - 2), 0};
-  /* root node: all N nodes = omega^{0 + c + 2 j}, j < N/2 */
-  if ((rc = rec_tanint(&st, 0, 2, N / 2, delta, &B))) goto done;
-  if (deferred_out)
-    for (int64_t q = 0; q < st.n_def && q < deferred_cap; ++q) deferred_out[q] = st.deferred[q];
-  if (st.n_def > 0) {
-    /* difficult points (Sec. 5): residual against the final basis, then serial processing */
-    int K = (int)st.n_def;
-    cx* sig = (cx*)malloc(sizeof(cx) * (size_t)K);
-    cx* r = (cx*)malloc(sizeof(cx) * 5 * (size_t)K);
-    char* act = (char*)malloc((size_t)K);
-    if (!sig || !r || !act) { free(sig); free(r); free(act); rc = TIKH_ORACLE_ENOMEM; goto done; }
-    for (int q = 0; q < K; ++q) {
-      int64_t id = st.deferred[q], e = id / 2;
-      const cx* ph = Phi + 10 * e + 5 * (id % 2);
-      sig[q] = node(e, N);
-      for (int j = 0; j < 5; ++j) {
-        cx acc = 0;
-        for (int i = 0; i < 5; ++i) acc += ph[i] * horner(B.c[5 * i + j], B.len[5 * i + j], sig[q]);
-        r[5 * q + j] = acc;
-      }
-      act[q] = 1;
-    }
-    rc = serial_construct(K, sig, r, act, delta, -1.0, &B, NULL, NULL, NULL, NULL, &st.n_drop);
-    free(sig); free(r); free(act);
-    if (rc) goto done;
-  }
-  /* Sec. 4.3 end: one column has tau-degree 0, the other four 1 */
-  int jstar = -1, nzero = 0, none = 0;
-  for (int j = 0; j < 5; ++j) {
-    if (delta[j] == 0) { jstar = j; ++nzero; }
-    else if (delta[j] == 1) ++none;
-  }
-  if (stats) {
-    stats->N = N; stats->M = M; stats->k = k; stats->p = p;
-    stats->n_difficult = st.n_def; stats->n_dropped = st.n_drop;
-    memcpy(stats->delta, delta, sizeof(delta));
-    stats->jstar = jstar; stats->dual = 0;
-  }
-  if (nzero != 1 || none != 4 || B.len[5 * 4 + jstar] < 1) { rc = TIKH_ORACLE_ENUMERIC; goto done; }
-  /* Sec. 5: x(z) = B*_1^{(j)}(z) / B*_5^{(j)} (the constant last component) */
   {
-    cx c5 = B.c[5 * 4 + jstar][0];
-    const cx* b1 = B.c[jstar];
-    int64_t l1 = B.len[jstar];
-    for (int64_t i = 0; i < n; ++i) ((cx*)x)[i] = (i < l1 ? b1[i] : 0.0) / c5;
-  }
-  if (Bout && lenout) {
-    for (int e = 0; e < 25; ++e) {
-      int64_t L = B.len[e] < cap ? B.len[e] : cap;
-      lenout[e] = B.len[e];
-      cx* dst = (cx*)Bout + (size_t)e * (size_t)cap;
-      for (int64_t t = 0; t < cap; ++t) dst[t] = (t < L) ? B.c[e][t] : 0.0;
+    /* Eq. (taudef) with reading R3 */
+    int tau[5] = {(int)(n - 1), (int)(m - 1), (int)(m + k - 2), (int)(n + k - 2), 0};
+    int delta[5];
+    int64_t nd = 0, ndrop = 0;
+    rc = solve_conditions(N, M, 5, 2, cond, tau, n, opts, (cx*)x, delta, &nd, &ndrop, Bout, cap, lenout, deferred_out,
+                          deferred_cap);
+    if (stats) {
+      stats->N = N; stats->M = M; stats->k = k; stats->p = p;
+      stats->n_difficult = nd; stats->n_dropped = ndrop;
+      memcpy(stats->delta, delta, sizeof(delta));
+      stats->jstar = -1;
+      for (int j = 0; j < 5; ++j)
+        if (delta[j] == 0) stats->jstar = j;
+      stats->dual = 0;
     }
   }
-  rc = 0;
 done:
-  pm_free(&B);
-  free(F); free(G); free(Phi); free(st.R); free(st.deferred);
+  free(F); free(G); free(cond);
   return rc;
 }
 
