@@ -47,12 +47,12 @@ class Opts(ctypes.Structure):
 
 class Stats(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int64), ("M", ctypes.c_int64), ("k", ctypes.c_int64), ("p", ctypes.c_int),
-                ("n_difficult", ctypes.c_int64), ("n_dropped", ctypes.c_int64), ("delta", ctypes.c_int * 5),
+                ("n_difficult", ctypes.c_int64), ("n_dropped", ctypes.c_int64), ("delta", ctypes.c_int * 7),
                 ("jstar", ctypes.c_int), ("dual", ctypes.c_int)]
 
-    def as_dict(self):
+    def as_dict(self, w=5):
         return dict(N=self.N, M=self.M, k=self.k, p=self.p, n_difficult=self.n_difficult,
-                    n_dropped=self.n_dropped, delta=list(self.delta), jstar=self.jstar, dual=self.dual)
+                    n_dropped=self.n_dropped, delta=list(self.delta)[:w], jstar=self.jstar, dual=self.dual)
 
 
 def _lib():
@@ -212,6 +212,54 @@ def solve_gramian(g, lcol, lrow, y, nlim=32, eps_diff=1e-8, mode=AUTO, m_min=0, 
     _check(_lib().tikh_oracle_solve_gramian(ctypes.c_int64(n), ctypes.c_int64(pl), _ptr(g), _ptr(lcol), _ptr(lrow),
                                             _ptr(y), ctypes.byref(o), _ptr(x), ctypes.byref(st)), "solve_gramian")
     return x, st.as_dict()
+
+
+def plan_general(m, n, p, nlim=48, m_min=0):
+    """Algorithm 2 with three condition sets per node (Sec. 3.2, 6.2): (N, M, p')."""
+    N, M, pp = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int()
+    o = opts(nlim=nlim, m_min=m_min)
+    _check(_lib().tikh_oracle_plan_general(ctypes.c_int64(m), ctypes.c_int64(n), ctypes.c_int64(p), ctypes.byref(o),
+                                           ctypes.byref(N), ctypes.byref(M), ctypes.byref(pp)), "plan_general")
+    return N.value, M.value, pp.value
+
+
+def conditions_general(col, row, lcol, lrow, y, nlim=48, m_min=0, fill=0, is_complex=None):
+    """The general problem's interpolation conditions (Eq. (interp)): (cond [N, 3, 7], tau [7])."""
+    if is_complex is None:
+        is_complex = _is_complex(col, row, lcol, lrow)
+    col, row, lcol, lrow, y = _c128(col), _c128(row), _c128(lcol), _c128(lrow), _c128(y)
+    m, n, p = col.size, row.size, lcol.size
+    N = plan_general(m, n, p, nlim, m_min)[0]
+    cond = np.zeros((N, 3, 7), np.complex128)
+    tau = (ctypes.c_int * 7)()
+    o = opts(nlim=nlim, m_min=m_min, fill=fill, is_complex=is_complex)
+    _check(_lib().tikh_oracle_conditions_general(ctypes.c_int64(m), ctypes.c_int64(n), ctypes.c_int64(p), _ptr(col),
+                                                 _ptr(row), _ptr(lcol), _ptr(lrow), _ptr(y), ctypes.byref(o),
+                                                 _ptr(cond), tau), "conditions_general")
+    return cond, list(tau)
+
+
+def solve_general(col, row, lcol, lrow, y, nlim=48, eps_diff=1e-8, mode=AUTO, m_min=0, fill=0, is_complex=None):
+    """General problem (Sec. 3.2): x = (T^H T + L^H L)^{-1} y with T = [col, row] (m x n) and
+    L = [lcol, lrow] (p x n) Toeplitz.  Returns (x, stats)."""
+    if is_complex is None:
+        is_complex = _is_complex(col, row, lcol, lrow)
+    col, row, lcol, lrow, y = _c128(col), _c128(row), _c128(lcol), _c128(lrow), _c128(y)
+    m, n, p = col.size, row.size, lcol.size
+    x = np.zeros(n, np.complex128)
+    st = Stats()
+    o = opts(nlim=nlim, eps_diff=eps_diff, mode=mode, m_min=m_min, fill=fill, is_complex=is_complex)
+    _check(_lib().tikh_oracle_solve_general(ctypes.c_int64(m), ctypes.c_int64(n), ctypes.c_int64(p), _ptr(col),
+                                            _ptr(row), _ptr(lcol), _ptr(lrow), _ptr(y), ctypes.byref(o), _ptr(x),
+                                            ctypes.byref(st)), "solve_general")
+    return x, st.as_dict(w=7)
+
+
+def dense_solve_general(col, row, lcol, lrow, y):
+    """(T^H T + L^H L)^{-1} y by a dense LU solve (numpy)."""
+    T = toeplitz_dense(_c128(col), _c128(row))
+    L = toeplitz_dense(_c128(lcol), _c128(lrow))
+    return np.linalg.solve(T.conj().T @ T + L.conj().T @ L, _c128(y))
 
 
 def nufft_gramian(f, w, X, n):

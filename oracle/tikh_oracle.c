@@ -1,6 +1,6 @@
 /*
- * tikh_oracle.c -- plain CPU FP64 oracle for the l2-penalised superfast Tikhonov solver of
- * Turnes, Balcan & Romberg (arXiv 1302.6945).
+ * tikh_oracle.c -- plain CPU FP64 oracle for the superfast Tikhonov solver of Turnes, Balcan & Romberg
+ * (arXiv 1302.6945): the l2-penalised problem, the Toeplitz-Gramian problem and the general problem.
  *
  * TEST INFRASTRUCTURE ONLY: used by the tests, the smoke check and the benchmark's CPU baseline,
  * never by the product path.  It shares nothing with the CUDA library.
@@ -37,6 +37,11 @@
  *     trimmed to these bounds (what is cut is round-off).
  *  R11 m < n is solved as x = T^H (T T^H + lam I)^{-1} b with the same algorithm on T^H, whose
  *     right-hand-side term is b itself (Sec. 7.1 solves (G_T + G_L) x = y with y given).
+ *  R12 general problem (Sec. 3.2): the three block rows of Eq. (ex3) are printed with q+n, m+n and p+n
+ *     rows; the interpolation needs one node set, so all three are extended to the same N >= q + n - 1
+ *     (q = max(m, p)) with N - n, N - m and N - p extension rows, and tau_i + 1 is the length of each
+ *     unknown: tau = [n-1, m-1, p-1, N-n-1, N-m-1, N-p-1, 0] (Eq. (taudef) is printed for m = p = q and
+ *     a 1-circulant extension).  L's arbitrary entries use SplitMix64 counters offset by 2^41.
  */
 #include "tikh_oracle.h"
 
@@ -864,6 +869,120 @@ int tikh_oracle_solve_gramian(int64_t n, int64_t pl, const double* g, const doub
   if (rc) return rc;
   const int64_t k = N - (pl + n - 1);
   return solve_core(pl, n, lcol, lrow, y, 0.0, g, N, M, k, p, opts, x, stats, NULL, 0, NULL, NULL, 0);
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* The general problem (Sec. 3.2, Eq. (ex1)-(ex3)): (T^H T + L^H L) x = y with T (m x n) and     */
+/* L (p x n) generic Toeplitz.  Reading R12: all three block rows are extended to the same N     */
+/* points (the nodes are shared), N >= max(m, p) + n - 1, so block row 1 has N - n extension rows, */
+/* block row 2 N - m and block row 3 N - p; gamma_1, gamma_2, gamma_3 have those lengths.         */
+/* ------------------------------------------------------------------------------------------ */
+
+/* Conditions F, G, H per node (Eq. (interp)), rows cond[N][3][7] over the unknowns
+ *   [x (n), sigma_1 (m), sigma_2 (p), gamma_1 (N-n), gamma_2 (N-m), gamma_3 (N-p), 1]:
+ *   block row 1: T^H sigma_1 + L^H sigma_2 - y = 0 below N-n rows defining gamma_1
+ *   block row 2: -T x + sigma_1 = 0 below N-m rows defining gamma_2
+ *   block row 3: -L x + sigma_2 = 0 below N-p rows defining gamma_3
+ * each partial circulant turned into the DFT of its generator (Eq. (circdiag)). */
+static int build_conditions_general(int64_t m, int64_t n, int64_t p, int64_t N, const cx* col, const cx* row,
+                                    const cx* lcol, const cx* lrow, const cx* y, int fill, int is_complex,
+                                    cx* cond) {
+  const int64_t kT = N - (m + n - 1), kL = N - (p + n - 1);
+  cx* aT = (cx*)malloc(sizeof(cx) * (size_t)N);
+  cx* aL = (cx*)malloc(sizeof(cx) * (size_t)N);
+  cx* cT = (cx*)malloc(sizeof(cx) * (size_t)N);
+  cx* cH = (cx*)malloc(sizeof(cx) * (size_t)N);
+  cx* cL = (cx*)malloc(sizeof(cx) * (size_t)N);
+  cx* cLH = (cx*)malloc(sizeof(cx) * (size_t)N);
+  cx* cy = (cx*)malloc(sizeof(cx) * (size_t)N);
+  int rc = TIKH_ORACLE_ENOMEM;
+  if (!aT || !aL || !cT || !cH || !cL || !cLH || !cy) goto done;
+  periodic_generator(m, n, N, kT, col, row, fill, is_complex, 0, aT);
+  periodic_generator(p, n, N, kL, lcol, lrow, fill, is_complex, 1ULL << 41, aL);
+  for (int64_t j = 0; j < N; ++j) {
+    cT[j] = aT[((j - (N - m)) % N + N) % N];        /* C(T): rows N-m .. N-1 hold T       (R2) */
+    cL[j] = aL[((j - (N - p)) % N + N) % N];        /* C(L): rows N-p .. N-1 hold L            */
+    cH[j] = conj(aT[((N - n - j) % N + N) % N]);    /* C(T^H): rows N-n .. N-1 hold T^H        */
+    cLH[j] = conj(aL[((N - n - j) % N + N) % N]);   /* C(L^H): rows N-n .. N-1 hold L^H        */
+    cy[j] = 0;
+  }
+  for (int64_t i = 0; i < n; ++i) cy[N - n + i] = -y[i];
+  if ((rc = dft(cT, N, +1)) || (rc = dft(cL, N, +1)) || (rc = dft(cH, N, +1)) || (rc = dft(cLH, N, +1)) ||
+      (rc = dft(cy, N, +1)))
+    goto done;
+  for (int64_t e = 0; e < N; ++e) {
+    cx* f = cond + 21 * e;
+    cx* g = f + 7;
+    cx* h = f + 14;
+    for (int i = 0; i < 21; ++i) f[i] = 0.0;
+    f[1] = cH[e];               /* C_12 */
+    f[2] = cLH[e];              /* C_13 */
+    f[3] = 1.0;                 /* C_14 = [I_{N-n}; 0]: generator e_0 */
+    f[6] = cy[e];               /* C_17 */
+    g[0] = -cT[e];              /* C_21 */
+    g[1] = node(e * (N - m), N); /* C_22 = [0; I_m] below N-m rows: generator e_{N-m} */
+    g[4] = 1.0;                 /* C_25 */
+    h[0] = -cL[e];              /* C_31 */
+    h[2] = node(e * (N - p), N); /* C_33 */
+    h[5] = 1.0;                 /* C_36 */
+  }
+  rc = 0;
+done:
+  free(aT); free(aL); free(cT); free(cH); free(cL); free(cLH); free(cy);
+  return rc;
+}
+
+/* Algorithm 2 with three condition sets per node over N >= max(m, p) + n - 1 */
+int tikh_oracle_plan_general(int64_t m, int64_t n, int64_t p, const tikh_oracle_opts* opts, int64_t* N, int64_t* M,
+                             int* pp) {
+  if (m < 1 || n < 1 || p < 1 || !opts) return TIKH_ORACLE_EINVAL;
+  const int64_t q = m > p ? m : p;
+  return plan_sets(q + n - 1, 3, opts, N, M, pp);
+}
+
+int tikh_oracle_conditions_general(int64_t m, int64_t n, int64_t p, const double* col, const double* row,
+                                   const double* lcol, const double* lrow, const double* y,
+                                   const tikh_oracle_opts* opts, double* cond, int* tau) {
+  int64_t N, M;
+  int pp;
+  int rc = tikh_oracle_plan_general(m, n, p, opts, &N, &M, &pp);
+  if (rc) return rc;
+  rc = build_conditions_general(m, n, p, N, (const cx*)col, (const cx*)row, (const cx*)lcol, (const cx*)lrow,
+                                (const cx*)y, opts->fill, opts->is_complex, (cx*)cond);
+  if (rc) return rc;
+  /* Eq. (taudef) for unequal sizes: tau_i + 1 = the length of unknown i */
+  tau[0] = (int)(n - 1); tau[1] = (int)(m - 1); tau[2] = (int)(p - 1);
+  tau[3] = (int)(N - n - 1); tau[4] = (int)(N - m - 1); tau[5] = (int)(N - p - 1); tau[6] = 0;
+  return 0;
+}
+
+int tikh_oracle_solve_general(int64_t m, int64_t n, int64_t p, const double* col, const double* row,
+                              const double* lcol, const double* lrow, const double* y, const tikh_oracle_opts* opts,
+                              double* x, tikh_oracle_stats* stats) {
+  int64_t N, M;
+  int pp;
+  int rc = tikh_oracle_plan_general(m, n, p, opts, &N, &M, &pp);
+  if (rc) return rc;
+  cx* cond = (cx*)malloc(sizeof(cx) * 21 * (size_t)N);
+  if (!cond) return TIKH_ORACLE_ENOMEM;
+  int tau[7];
+  rc = tikh_oracle_conditions_general(m, n, p, col, row, lcol, lrow, y, opts, (double*)cond, tau);
+  if (!rc) {
+    int delta[7];
+    int64_t nd = 0, ndrop = 0;
+    rc = solve_conditions(N, M, 7, 3, cond, tau, n, opts, (cx*)x, delta, &nd, &ndrop, NULL, 0, NULL, NULL, 0);
+    if (stats) {
+      stats->N = N; stats->M = M; stats->k = N - (m + n - 1); stats->p = pp;
+      stats->n_difficult = nd; stats->n_dropped = ndrop;
+      memcpy(stats->delta, delta, sizeof(delta));
+      stats->jstar = -1;
+      for (int j = 0; j < 7; ++j)
+        if (delta[j] == 0) stats->jstar = j;
+      stats->dual = 0;
+    }
+  }
+  free(cond);
+  return rc;
 }
 
 /* y = T^H v and u = T x through the circulant embedding of length >= m+n-1 (a plain DFT identity) */

@@ -47,7 +47,7 @@ typedef struct {
   int p;           /* number of paired-interleaving splits */
   int64_t n_difficult; /* conditions deferred to the end (Sec. 5, difficult points) */
   int64_t n_dropped;   /* conditions whose residual was exactly zero (already satisfied) */
-  int delta[5];        /* final tau-degrees of the basis columns */
+  int delta[7];        /* final tau-degrees of the basis columns (5 used by the l2 and Gramian solves) */
   int jstar;           /* the column with tau-degree 0 */
   int dual;            /* 1 when m < n was solved through T^H (T T^H + lam I)^{-1} b */
 } tikh_oracle_stats;
@@ -96,6 +96,21 @@ int tikh_oracle_solve_normal_ex(int64_t m, int64_t n, const double* col, const d
  * and G in place of lam I; N = 2^p M >= max(n, pl) + n - 1.  x: n complex. */
 int tikh_oracle_solve_gramian(int64_t n, int64_t pl, const double* g, const double* lcol, const double* lrow,
                               const double* y, const tikh_oracle_opts* opts, double* x, tikh_oracle_stats* stats);
+
+/* The general problem (Sec. 3.2, Eq. (ex1)-(ex3)): x = (T^H T + L^H L)^{-1} y with T an m x n and L a p x n
+ * Toeplitz matrix (first columns col, lcol; first rows row, lrow, whose [0] entries are ignored).  Three
+ * condition sets F, G, H per node (Eq. (interp)), a 7 x 7 basis, tau = [n-1, m-1, p-1, N-n-1, N-m-1,
+ * N-p-1, 0] (Eq. (taudef) for unequal sizes); N = 2^p' M >= max(m, p) + n - 1 by Algorithm 2 with three
+ * sets per node.  x: n complex. */
+int tikh_oracle_plan_general(int64_t m, int64_t n, int64_t p, const tikh_oracle_opts* opts, int64_t* N,
+                             int64_t* M, int* pp);
+int tikh_oracle_solve_general(int64_t m, int64_t n, int64_t p, const double* col, const double* row,
+                              const double* lcol, const double* lrow, const double* y, const tikh_oracle_opts* opts,
+                              double* x, tikh_oracle_stats* stats);
+/* The general problem's conditions: cond[N][3][7] complex (rows F, G, H of node e), tau: 7 ints. */
+int tikh_oracle_conditions_general(int64_t m, int64_t n, int64_t p, const double* col, const double* row,
+                                   const double* lcol, const double* lrow, const double* y,
+                                   const tikh_oracle_opts* opts, double* cond, int* tau);
 
 /* Tikhonov solution x = argmin ||T x - b||^2 + lam ||x||^2  (Eq. (tik), (tiksol)).
  * m >= n: y = T^H b then solve_normal.  m < n: x = T^H v with (T T^H + lam I) v = b, solved by the

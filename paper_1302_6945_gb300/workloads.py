@@ -147,6 +147,19 @@ def random_problem(m, n, lam, seed, complex_data=True):
     return dict(col=col, row=row, b=b, lam=lam, m=m, n=n)
 
 
+def general_problem(m, n, p, seed, complex_data=False):
+    """Sec. 7.1's general problem: T (m x n) and L (p x n) Toeplitz with standard-normal generators, x_true
+    standard normal, b = T x_true; the system is (T^H T + L^H L) x = T^H b.  Returns dict(col, row, lcol,
+    lrow, b, x_true, m, n, p)."""
+    rng = np.random.default_rng(seed)
+    draw = (lambda k: rng.standard_normal(k) + 1j * rng.standard_normal(k)) if complex_data else rng.standard_normal
+    col, row, lcol, lrow, x_true = draw(m), draw(n), draw(p), draw(n), draw(n)
+    row[0] = col[0]
+    lrow[0] = lcol[0]
+    b = toeplitz_matvec(col, row, x_true)
+    return dict(col=col, row=row, lcol=lcol, lrow=lrow, b=b, x_true=x_true, m=m, n=n, p=p)
+
+
 def nufft_problem(n=4096, K=4096, seed=6, l_scale=1e-2):
     """Sec. 7.4's reconstruction workload: a length-n signal of three sinusoids with random frequencies in
     [0, 0.02]; K spectral samples X_k = sum_s x_s exp(-2 pi i f_k s) at frequencies drawn from the triangular

@@ -449,3 +449,103 @@ def test_nufft_reconstruction_small_matches_dense():
     A = oracle.hermitian_toeplitz_dense(g) + oracle.toeplitz_dense(P["lcol"], P["lrow"]).T @ \
         oracle.toeplitz_dense(P["lcol"], P["lrow"])
     assert relerr(x, xd) <= 1e-13 * np.linalg.cond(A) + 1e-12
+
+
+# ---- the general problem (Sec. 3.2): (T^H T + L^H L) x = y, 7 x 7 basis, conditions F, G, H ----
+
+def _general_case(m, n, p, cplx, seed):
+    P = W.general_problem(m, n, p, seed, complex_data=cplx)
+    T = oracle.toeplitz_dense(P["col"], P["row"])
+    return P, T.conj().T @ P["b"]
+
+
+@pytest.mark.parametrize("m,n,p,cplx", [(12, 8, 8, False), (30, 20, 20, True), (40, 30, 25, False),
+                                        (25, 30, 40, True), (9, 16, 20, False), (100, 64, 64, False),
+                                        (301, 200, 150, True), (64, 1, 3, False)])
+def test_general_matches_dense_solve(m, n, p, cplx):
+    P, y = _general_case(m, n, p, cplx, seed=m + 3 * n + 7 * p)
+    T = oracle.toeplitz_dense(P["col"], P["row"])
+    L = oracle.toeplitz_dense(P["lcol"], P["lrow"])
+    A = T.conj().T @ T + L.conj().T @ L
+    xd = np.linalg.solve(A, y)
+    x, st = oracle.solve_general(P["col"], P["row"], P["lcol"], P["lrow"], y, nlim=24)
+    assert relerr(x, xd) <= 1e-13 * np.linalg.cond(A) + 1e-12, relerr(x, xd)
+    assert st["N"] >= max(m, p) + n - 1 and st["N"] == st["M"] << st["p"]
+
+
+def test_general_final_degrees_are_six_ones_and_one_zero():
+    # Sec. 5: tau sums to 3N - 6, so the final tau-degrees sum to 6 with spread <= 1: six 1s and one 0
+    P, y = _general_case(70, 50, 45, True, seed=4)
+    cond, tau = oracle.conditions_general(P["col"], P["row"], P["lcol"], P["lrow"], y, nlim=24)
+    N = cond.shape[0]
+    assert sum(tau) == 3 * N - 6
+    x, st = oracle.solve_general(P["col"], P["row"], P["lcol"], P["lrow"], y, nlim=24)
+    assert sorted(st["delta"]) == [0, 1, 1, 1, 1, 1, 1] and st["delta"][st["jstar"]] == 0
+
+
+@pytest.mark.parametrize("m,n,p", [(7, 5, 6), (10, 8, 12), (14, 9, 9)])
+def test_general_conditions_have_the_solution_as_their_only_null_vector(m, n, p):
+    # Eq. (ex2)-(interp): the 3N conditions on the 3N + 1 coefficients of p*(z) (component lengths
+    # n, m, p, N-n, N-m, N-p, 1) have a one-dimensional null space, spanned by the extended solution;
+    # its x part over its constant part is the dense solution
+    P, y = _general_case(m, n, p, False, seed=m * n * p)
+    cond, tau = oracle.conditions_general(P["col"], P["row"], P["lcol"], P["lrow"], y, nlim=6)
+    N = cond.shape[0]
+    lens = [t + 1 for t in tau]
+    assert lens == [n, m, p, N - n, N - m, N - p, 1]
+    w = np.exp(2j * np.pi * np.arange(N) / N)
+    cols = []
+    for i, L in enumerate(lens):
+        V = w[:, None] ** np.arange(L)[None, :]            # N x L monomials at the nodes
+        cols.append((cond[:, :, i][:, :, None] * V[:, None, :]).reshape(3 * N, L))
+    A = np.concatenate(cols, axis=1)
+    assert A.shape == (3 * N, 3 * N + 1)
+    s, vh = np.linalg.svd(A)[1:]
+    assert s[-1] > 1e-8 * s[0]                             # rank 3N: the null space is one-dimensional
+    v = vh[-1].conj()
+    xd = oracle.dense_solve_general(P["col"], P["row"], P["lcol"], P["lrow"], y)
+    assert relerr(v[:n] / v[-1], xd) <= 1e-10
+    assert np.abs(A @ v).max() <= 1e-12 * np.abs(A).max()
+
+
+def test_general_with_scaled_identity_regulariser_is_the_l2_solve():
+    # L = beta I (p = n): T^H T + |beta|^2 I, the l2 system of Sec. 3.3 (its own pinned solver)
+    P, y = _general_case(60, 44, 44, True, seed=8)
+    beta = 0.6 + 0.3j
+    lcol = np.zeros(44, complex)
+    lcol[0] = beta
+    x, _ = oracle.solve_general(P["col"], P["row"], lcol, np.zeros(44, complex), y, nlim=24)
+    xn, _ = oracle.solve_normal(P["col"], P["row"], y, abs(beta) ** 2, nlim=16)
+    xd = oracle.dense_solve_normal(P["col"], P["row"], y, abs(beta) ** 2)
+    assert relerr(x, xd) <= 1e-12 and relerr(xn, xd) <= 1e-12
+
+
+def test_general_second_difference_regulariser():
+    # the scaled second-order difference L of Sec. 7.4 (p = n, stencil [-1, 2, -1])
+    P, y = _general_case(90, 64, 64, False, seed=11)
+    lcol = np.zeros(64)
+    lcol[:2] = [2.0, -1.0]
+    x, _ = oracle.solve_general(P["col"], P["row"], lcol, lcol.copy(), y, nlim=24)
+    xd = oracle.dense_solve_general(P["col"], P["row"], lcol, lcol, y)
+    assert relerr(x, xd) <= 1e-11
+
+
+def test_general_solution_independent_of_fill_extension_and_mode():
+    P, y = _general_case(80, 56, 50, False, seed=13)
+    xd = oracle.dense_solve_general(P["col"], P["row"], P["lcol"], P["lrow"], y)
+    for fill in (0, 1):
+        for m_min in (0, 14, 24):
+            for mode in (oracle.AUTO, oracle.DIRECT, oracle.FFT):
+                x, st = oracle.solve_general(P["col"], P["row"], P["lcol"], P["lrow"], y, nlim=24, m_min=m_min,
+                                             fill=fill, mode=mode)
+                assert relerr(x, xd) <= 1e-11, (fill, m_min, mode, st["N"], relerr(x, xd))
+
+
+@pytest.mark.parametrize("m,n,p,eps", [(30, 20, 25, 0.2), (17, 11, 11, 0.3), (40, 27, 30, 0.25)])
+def test_general_difficult_points_processed_at_the_end_match_dense(m, n, p, eps):
+    # Sec. 5 with a large threshold: many conditions deferred, the result still the exact solution
+    P, y = _general_case(m, n, p, True, seed=m + n + p)
+    xd = oracle.dense_solve_general(P["col"], P["row"], P["lcol"], P["lrow"], y)
+    x, st = oracle.solve_general(P["col"], P["row"], P["lcol"], P["lrow"], y, nlim=24, eps_diff=eps)
+    assert st["n_difficult"] > 0
+    assert relerr(x, xd) <= 1e-10, (st, relerr(x, xd))
