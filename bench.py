@@ -237,6 +237,137 @@ def normal_residual_t(torch, col, row, b, xv, lam):
     return float(torch.linalg.norm(Thr - lam * xv) / torch.linalg.norm(Thb))
 
 
+def toeplitz_mv_t(torch, col, row, v, adjoint=False):
+    """T v (or T^H v) for the Toeplitz T = [col, row] by one FFT convolution in torch."""
+    m, n = col.numel(), row.numel()
+    L = 1 << int(math.ceil(math.log2(m + n)))
+    a = torch.cat([row[1:].flip(0), col])  # a_{-(n-1)} .. a_{m-1}
+    if not adjoint:
+        return torch.fft.ifft(torch.fft.fft(a, L) * torch.fft.fft(v, L))[n - 1:n - 1 + m]
+    return torch.fft.ifft(torch.fft.fft(a.conj().flip(0), L) * torch.fft.fft(v, L))[m - 1:m - 1 + n]
+
+
+def general_residual_t(torch, col, row, lcol, lrow, b, xv):
+    """||T^H b - (T^H T + L^H L) x|| / ||T^H b|| (outside any timed region)."""
+    col, row, lcol, lrow, b, xv = (v.to(torch.complex128) for v in (col, row, lcol, lrow, b, xv))
+    y = toeplitz_mv_t(torch, col, row, b, True)
+    ax = toeplitz_mv_t(torch, col, row, toeplitz_mv_t(torch, col, row, xv), True) + \
+        toeplitz_mv_t(torch, lcol, lrow, toeplitz_mv_t(torch, lcol, lrow, xv), True)
+    return float(torch.linalg.norm(y - ax) / torch.linalg.norm(y))
+
+
+def run_general(args, world, rank, local):
+    """The general problem (Sec. 3.2) on its own line: square T and L (m = p = n, the paper's Sec. 7.1 case)
+    with standard-normal generators, one solve per step (weak scaling: rank r solves its own problem,
+    seed 20 + r)."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1302_6945_gb300 import tikh
+    from paper_1302_6945_gb300 import workloads as W
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    n = args.n or 65536
+    P = W.general_problem(n, n, n, seed=20 + rank)
+    t = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)
+    col, row, lcol, lrow, b = t(P["col"]), t(P["row"]), t(P["lcol"]), t(P["lrow"]), t(P["b"])
+    x = torch.empty(n, dtype=torch.float64, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    plan = tikh.GeneralPlan(n, n, n, "r64", refine_steps=args.refine, graph=bool(args.graph), stream=stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            plan.solve(col, row, lcol, lrow, b, x)
+    st = plan.stats()
+    rel_res = general_residual_t(torch, col, row, lcol, lrow, b, x)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with torch.cuda.stream(stream):
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            plan.solve(col, row, lcol, lrow, b, x)
+            ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    t_step = sum(a.elapsed_time(c) for a, c in ev) / args.steps
+    t_max = max_over_ranks(t_step, dev)
+    value = whole_job_rate(world, 1, t_max / 1e3)
+    # profiled pass: every launch group timed by kind (stream launches)
+    plan.set_profiling(3)
+    with torch.cuda.stream(stream):
+        plan.solve(col, row, lcol, lrow, b, x)
+    torch.cuda.synchronize()
+    pst = plan.stats()
+    plan.set_profiling(0)
+    # e2e: the problem in pinned host memory, copies in and the solution out inside the timed region
+    host = [torch.tensor(P[k], dtype=torch.float64).pin_memory() for k in ("col", "row", "lcol", "lrow", "b")]
+    hx = torch.empty(n, dtype=torch.float64).pin_memory()
+    e2e_times = []
+    with torch.cuda.stream(stream):
+        for _ in range(max(1, min(args.steps, 3))):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for dst, src in zip((col, row, lcol, lrow, b), host):
+                dst.copy_(src, non_blocking=True)
+            plan.solve(col, row, lcol, lrow, b, x)
+            hx.copy_(x, non_blocking=True)
+            stream.synchronize()
+            e2e_times.append(time.perf_counter() - t0)
+    e2e_v = whole_job_rate(world, 1, max_over_ranks(sum(e2e_times) / len(e2e_times), dev))
+    h2d = sum(8 * h.numel() for h in host)
+    p64, p32 = fma_peaks(tikh, stream.cuda_stream)
+    solves = 1 + args.refine
+    kr = kind_rooflines(st, pst, 1, 1, solves, p64, p32)
+    dom = max(kr, key=lambda k: kr[k]["ms_per_step"]) if kr else None
+    roof = None
+    if dom:
+        d = kr[dom]
+        roof = {"bound": "alu", "kernel": "%s launch groups (profiled pass)" % dom, "achieved": d["achieved_gflops"],
+                "unit": "GFLOP/s", "peak": p64, "peak_kind": "measured FP64 FMA rate (tikh_test_peak)",
+                "frac": d["frac_of_peak"],
+                "frac_note": "time the group's model FLOPs need at the measured FP64 peak over its time",
+                "traffic": None}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        y = toeplitz_mv_t(torch, col.cpu().to(torch.complex128), row.cpu().to(torch.complex128),
+                          b.cpu().to(torch.complex128), True).numpy()
+        t0 = time.perf_counter()
+        xo, _ = oracle.solve_general(P["col"], P["row"], P["lcol"], P["lrow"], y, nlim=30, is_complex=0)
+        dt = time.perf_counter() - t0
+        xg = x.cpu().numpy()
+        cpu = {"value": 1.0 / dt, "unit": "solves/s", "cores": 1, "kind": "oracle",
+               "sample": "one full solve of the same problem, single thread",
+               "rel_diff_gpu_vs_oracle": float(np.linalg.norm(xg - xo.real) / np.linalg.norm(xo.real))}
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": t_max, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+               "config": {"workload": "general problem (Sec. 3.2): min ||T x - b||^2 + ||L x||^2, T and L %d x %d "
+                                      "real Toeplitz with standard-normal generators, b = T x_true" % (n, n),
+                          "m": n, "n": n, "pl": n, "N": st["N"], "p": st["p"], "M": st["M"],
+                          "refine_steps": args.refine, "cuda_graph": bool(st["graph"]),
+                          "l2": "256 MB flush between steps"},
+               "accuracy": {"rel_residual": rel_res, "n_difficult": st["n_difficult"]},
+               "e2e": {"value": e2e_v, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8 * n},
+               "gpu_launches": int(st["kernel_launches"]) * args.steps, "clocks": clocks,
+               "fma_peaks_gflops": {"fp64": p64, "fp32": p32}, "roofline": roof, "kinds": kr, "cpu_baseline": cpu}
+        print(json.dumps(out))
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def run_c3(args, world, rank, local):
     """The batching configuration as one ragged batch per step (weak scaling: rank r solves its own
     512-problem set, seed 2 + r)."""
@@ -407,8 +538,9 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c2", choices=["c2", "c3"],
-                    help="c2 (default): the complex deconvolution solve; c3: the ragged batch of 512 problems x 16 lambdas")
+    ap.add_argument("--config", default="c2", choices=["c2", "c3", "general"],
+                    help="c2 (default): the complex deconvolution solve; c3: the ragged batch of 512 problems x 16 "
+                         "lambdas; general: the general problem (Sec. 3.2) with square T and L (--n, default 65536)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "fp32_refine"])
     ap.add_argument("--n-lim", type=int, default=32)
     ap.add_argument("--refine", type=int, default=0)
@@ -429,6 +561,8 @@ def main():
         return run_reference(args, world, rank)
     if args.config == "c3":
         return run_c3(args, world, rank, local)
+    if args.config == "general":
+        return run_general(args, world, rank, local)
 
     import numpy as np
     import torch

@@ -120,7 +120,8 @@ typedef struct {
   int p;           /* paired-interleaving splits; 2^p leaves */
   int dual;        /* 1: m < n solved through T^H */
   int64_t n_difficult; /* conditions deferred to the end in the last solve */
-  int delta[5];        /* final tau-degrees of the basis columns in the last solve */
+  int delta[7];        /* final tau-degrees of the basis columns in the last solve (5 used; 7 for the general
+                        * problem) */
   int jstar;           /* column holding the solution */
   int retries;         /* internal re-runs after TIKH_EDEGREE */
   int64_t kernel_launches; /* kernels enqueued by the last solve */
@@ -275,6 +276,39 @@ int tikh_plan_create_gramian(tikh_plan* out, int64_t n, int64_t p, int dtype, in
  * first column and first row of L (lrow[0] ignored), y (n).  Synchronises like tikh_solve.  TIKH_EINVAL
  * for a NULL pointer or a plan not made by tikh_plan_create_gramian. */
 int tikh_solve_gramian(tikh_plan plan, const void* g, const void* lcol, const void* lrow, const void* y, void* x);
+
+/* ---- the general problem (Sec. 3.2) ---- */
+
+/* Plan for min ||T x - b||^2 + ||L x||^2, i.e. x = (T^H T + L^H L)^{-1} T^H b, with T an m x n and L a pl x n
+ * Toeplitz matrix (Sec. 3.2, Eq. (ex1)-(ex3)).  The extended system has three block rows, so three
+ * interpolation conditions F, G, H per node (Eq. (interp)) and a 7 x 7 polynomial basis with
+ * tau = [n-1, m-1, pl-1, N-n-1, N-m-1, N-pl-1, 0] (Eq. (taudef) for unequal sizes, all three block rows
+ * extended to the same N); N = 2^p M >= max(m, pl) + n - 1 by Algorithm 2 with three condition sets per
+ * node (a leaf holds 3 M <= opts.n_lim conditions, at most 42).  Any m, n, pl >= 1 with T^H T + L^H L
+ * non-singular (m < n needs no separate form).  dtype, opts and stream as for tikh_plan_create (opts NULL:
+ * n_lim 30 and eps_diff 1e-12, the measured threshold below which deferring a condition to the end stops
+ * costing accuracy for this problem); the stages
+ * run in FP64 (refinement residual: y - (T^H T + L^H L) x).  TIKH_EINVAL for m, n or pl < 1, invalid
+ * options or a leaf size above 42 conditions.  Such a plan serves only the tikh_solve_general* calls. */
+int tikh_plan_create_general(tikh_plan* out, int64_t m, int64_t n, int64_t pl, int dtype, const tikh_opts* opts,
+                             void* stream);
+
+/* x (n) = (T^H T + L^H L)^{-1} T^H b for DEVICE arrays col (m) / row (n) = first column / first row of T
+ * (row[0] ignored), lcol (pl) / lrow (n) = those of L (lrow[0] ignored), b (m).  Synchronises like
+ * tikh_solve.  TIKH_EINVAL for a NULL pointer or a plan not made by tikh_plan_create_general. */
+int tikh_solve_general(tikh_plan plan, const void* col, const void* row, const void* lcol, const void* lrow,
+                       const void* b, void* x);
+
+/* The same with the right-hand side y (n) of the normal equations given: x = (T^H T + L^H L)^{-1} y. */
+int tikh_solve_general_normal(tikh_plan plan, const void* col, const void* row, const void* lcol, const void* lrow,
+                              const void* y, void* x);
+
+/* batch (<= opts.batch) problems of the plan's shape in one call, problem i's arrays at base + i * stride
+ * elements (when batch > 1: an input stride is 0, one array shared by all, or >= the array's length;
+ * x_stride >= n): every launch serves all of them. */
+int tikh_solve_general_strided(tikh_plan plan, int batch, const void* col, int64_t col_stride, const void* row,
+                               int64_t row_stride, const void* lcol, int64_t lcol_stride, const void* lrow,
+                               int64_t lrow_stride, const void* b, int64_t b_stride, void* x, int64_t x_stride);
 
 /* Weighted Gramian of non-uniform Fourier samples (Sec. 7.4): K samples X_k = sum_s x_s exp(-2 pi i f_k s)
  * of a length-n signal at frequencies f_k in [-1/2, 1/2) with density weights w_k give the Toeplitz-Gramian

@@ -37,7 +37,7 @@
  *     trimmed to these bounds (what is cut is round-off).
  *  R11 m < n is solved as x = T^H (T T^H + lam I)^{-1} b with the same algorithm on T^H, whose
  *     right-hand-side term is b itself (Sec. 7.1 solves (G_T + G_L) x = y with y given).
- *  R12 general problem (Sec. 3.2): the three block rows of Eq. (ex3) are printed with q+n, m+n and p+n
+ *  R22 general problem (Sec. 3.2): the three block rows of Eq. (ex3) are printed with q+n, m+n and p+n
  *     rows; the interpolation needs one node set, so all three are extended to the same N >= q + n - 1
  *     (q = max(m, p)) with N - n, N - m and N - p extension rows, and tau_i + 1 is the length of each
  *     unknown: tau = [n-1, m-1, p-1, N-n-1, N-m-1, N-p-1, 0] (Eq. (taudef) is printed for m = p = q and
@@ -873,7 +873,7 @@ int tikh_oracle_solve_gramian(int64_t n, int64_t pl, const double* g, const doub
 
 /* ------------------------------------------------------------------------------------------ */
 /* The general problem (Sec. 3.2, Eq. (ex1)-(ex3)): (T^H T + L^H L) x = y with T (m x n) and     */
-/* L (p x n) generic Toeplitz.  Reading R12: all three block rows are extended to the same N     */
+/* L (p x n) generic Toeplitz.  Reading R22: all three block rows are extended to the same N     */
 /* points (the nodes are shared), N >= max(m, p) + n - 1, so block row 1 has N - n extension rows, */
 /* block row 2 N - m and block row 3 N - p; gamma_1, gamma_2, gamma_3 have those lengths.         */
 /* ------------------------------------------------------------------------------------------ */

@@ -114,10 +114,10 @@ int fft_index(Plan& P, int64_t L, int& err) {
 }
 
 // same bound as the device: tau-degree bound for pivoted columns, accumulation bound otherwise
-int entry_bound_host(const int* din, const int* dout, int i, int j) {
+int entry_bound_host(int W, const int* din, const int* dout, int i, int j) {
   int amax = 0;
   bool have = false;
-  for (int c = 0; c < 5; ++c)
+  for (int c = 0; c < W; ++c)
     if (dout[c] > din[c]) { amax = have ? std::max(amax, dout[c]) : dout[c]; have = true; }
   if (dout[j] > din[j]) return dout[j] - din[i];
   int acc = have ? amax - din[i] : -1;
@@ -125,10 +125,10 @@ int entry_bound_host(const int* din, const int* dout, int i, int j) {
   return std::min(acc, dout[j] - din[i]);
 }
 
-void waterfill(int* d, int64_t C) {
+void waterfill(int W, int* d, int64_t C) {
   for (int64_t c = 0; c < C; ++c) {
     int j = 0;
-    for (int i = 1; i < 5; ++i)
+    for (int i = 1; i < W; ++i)
       if (d[i] < d[j]) j = i;
     d[j] += 1;
   }
@@ -138,70 +138,76 @@ void waterfill(int* d, int64_t C) {
 // product transform length predicted from the shape's tau-degrees (water-filling) plus slack.
 void build_steps(Plan& P, std::vector<Step>& out, int depth, int64_t a, int64_t s, int64_t L, int side, int* sd,
                  uint64_t& pending, int64_t slack) {
+  const int W = P.w, NS = P.ns;
   if (depth == P.p) {
     Step st{STEP_LEAF, depth, side, a, s, L, -1, 0, pending};
     pending = 0;
-    waterfill(sd, 4 * L);
+    waterfill(W, sd, 2 * NS * L);
     out.push_back(st);
     return;
   }
-  int din[5];
-  memcpy(din, sd, sizeof(din));
+  int din[WMAX];
+  memcpy(din, sd, sizeof(int) * W);
   pending |= (1ULL << depth);
   build_steps(P, out, depth + 1, a, 2 * s, L / 2, 0, sd, pending, slack);
   Step ev{STEP_EVAL, depth, side, a, s, L, -1, 0, 0};
   out.push_back(ev);
   build_steps(P, out, depth + 1, a + s, 2 * s, L / 2, 1, sd, pending, slack);
   int D = -1;
-  for (int i = 0; i < 5; ++i)
-    for (int j = 0; j < 5; ++j) D = std::max(D, entry_bound_host(din, sd, i, j));
-  // the product of the bases of 4L conditions has degree <= 4L whatever the tau-degree bound and the
-  // slack say, and each child's stored entries are at most 2L + 1 long (they are trimmed to the same
-  // kind of bound), which the transform must hold
-  int64_t Pn = smooth_at_least(std::max<int64_t>(2 * L + 1, std::min<int64_t>((int64_t)D + 1 + slack, 4 * L + 1)));
+  for (int i = 0; i < W; ++i)
+    for (int j = 0; j < W; ++j) D = std::max(D, entry_bound_host(W, din, sd, i, j));
+  // the product of the bases of 2 NS L conditions has degree <= 2 NS L whatever the tau-degree bound and
+  // the slack say, and each child's stored entries are at most NS L + 1 long (they are trimmed to the
+  // same kind of bound), which the transform must hold
+  int64_t Pn = smooth_at_least(
+      std::max<int64_t>(NS * L + 1, std::min<int64_t>((int64_t)D + 1 + slack, 2 * NS * L + 1)));
   Step pr{STEP_PROD, depth, side, a, s, L, -1, Pn, 0};
   out.push_back(pr);
 }
 
 // Algorithmic FLOPs of one item's core solve by kind (leaf, evaluation, product, other), the part the FFT
 // stages run in FP32 kept apart: a length-L complex FFT counts 5 L log2 L, a complex multiply-add 8.
-//  leaf of K = 4L conditions: 50 K^2 + 90 K (the pivot chain, sum over steps of 60 per remaining
-//    condition and 60 per step, plus the basis rebuild, about 20 K^2);
-//  evaluation at Lr = L/2 nodes per coset: direct, 2 Lr nodes x 25 entries x len Horner steps; FFT, the
-//    twist-fold (50 x len) and 50 transforms of Lr; both plus the update, 2 Lr nodes x 2 rows x 25 CMACs;
-//    len = 2L/5 + 1 is the mean entry length of the left child (its 2L conditions raise each column by 2L/5);
-//  product of length P: direct, 25 outputs x 5 convolutions of len x len; FFT, 75 transforms of P and
-//    25 x 5 pointwise CMACs per bin;
-//  other: the four length-N transforms of the extension, right-hand side and conditions.
+// W = basis size (5, or 7 for the general problem), NS = condition sets per node (2, or 3).
+//  leaf of K = 2 NS L conditions: (W/5)(30 K^2 + 90 K) for the pivot chain (a sum over steps of 60 per
+//    remaining condition and 90 per step at W = 5, both proportional to the row length W) plus
+//    (W^2/25) 20 K^2 for the basis rebuild (W^2 entries); 50 K^2 + 90 K at W = 5;
+//  evaluation at Lr = L/2 nodes per coset: direct, 2 Lr nodes x W^2 entries x len Horner steps; FFT, the
+//    twist-fold (2 W^2 x len) and 2 W^2 transforms of Lr; both plus the update, 2 Lr nodes x NS rows x
+//    W^2 CMACs; len = NS L / W + 1 is the mean entry length of the left child (its NS L conditions raise
+//    each of the W columns by NS L / W);
+//  product of length P: direct, W^2 outputs x W convolutions of len x len; FFT, 3 W^2 transforms of P
+//    and W^2 x W pointwise CMACs per bin;
+//  other: the length-N transforms of the extension (one more for L or G), right-hand side and conditions.
 void model_flops(Plan& P) {
   auto fft = [](double L) { return L > 1 ? 5.0 * L * std::log2(L) : 0.0; };
+  const double W = P.w, WW = W * W, NS = P.ns;
   for (int k = 0; k < 4; ++k) P.last.model_flops[k] = P.last.model_flops_fp32[k] = 0.0;
   for (const Step& st : P.sched) {
-    const double L = (double)st.L, Lr = L / 2, len = 2.0 * L / 5.0 + 1.0;
+    const double L = (double)st.L, Lr = L / 2, len = NS * L / W + 1.0;
     if (st.kind == STEP_LEAF) {
-      const double K = 4 * L;
-      P.last.model_flops[0] += 50 * K * K + 90 * K;
+      const double K = 2 * NS * L;
+      P.last.model_flops[0] += (W / 5) * (30 * K * K + 90 * K) + (WW / 25) * 20 * K * K;
     } else if (st.kind == STEP_EVAL) {
-      const double upd = 2 * Lr * 2 * 25 * 8;
+      const double upd = 2 * Lr * NS * WW * 8;
       if (st.L / 2 <= P.eval_direct_max) {
-        P.last.model_flops[1] += 2 * Lr * 25 * len * 8 + upd;
+        P.last.model_flops[1] += 2 * Lr * WW * len * 8 + upd;
       } else {
-        const double f = 50 * len * 8 + 50 * fft(Lr) + upd;
+        const double f = 2 * WW * len * 8 + 2 * WW * fft(Lr) + upd;
         P.last.model_flops[1] += f;
         if (P.stage32) P.last.model_flops_fp32[1] += f;
       }
     } else {
       const double Pl = (double)st.P;
       if (st.P <= P.prod_direct_max) {
-        P.last.model_flops[2] += 25 * 5 * len * len * 8;
+        P.last.model_flops[2] += WW * W * len * len * 8;
       } else {
-        const double f = 75 * fft(Pl) + 25 * 5 * Pl * 8;
+        const double f = 3 * WW * fft(Pl) + WW * W * Pl * 8;
         P.last.model_flops[2] += f;
         if (P.stage32) P.last.model_flops_fp32[2] += f;
       }
     }
   }
-  P.last.model_flops[3] = 4 * fft((double)P.N);
+  P.last.model_flops[3] = (P.gram || P.general ? 5 : 4) * fft((double)P.N);
 }
 
 // (re)build the schedule for every shape the plan serves (the step list is the same for all of them --
@@ -213,9 +219,13 @@ int make_schedule(Plan& P) {
   P.sched.clear();
   for (const Shape& sh : P.shapes) {
     std::vector<Step> st;
-    int sd[5] = {-(int)(sh.cn - 1), -(int)(sh.cm - 1), -(int)(sh.cm + sh.k - 2), -(int)(sh.cn + sh.k - 2), 0};
+    int sd[WMAX] = {-(int)(sh.cn - 1), -(int)(sh.cm - 1), -(int)(sh.cm + sh.k - 2), -(int)(sh.cn + sh.k - 2), 0, 0, 0};
+    if (P.general) {  // tau = [n-1, m-1, pl-1, N-n-1, N-m-1, N-pl-1, 0]
+      const int64_t t[WMAX] = {sh.cn - 1, sh.cm - 1, sh.pl - 1, P.N - sh.cn - 1, P.N - sh.cm - 1, P.N - sh.pl - 1, 0};
+      for (int i = 0; i < WMAX; ++i) sd[i] = -(int)t[i];
+    }
     uint64_t pending = 0;
-    const int64_t slack = (int64_t)P.slack_mult * (sh.k + 2 * P.M + 4);
+    const int64_t slack = (int64_t)P.slack_mult * (std::max(sh.k, sh.kl) + P.ns * P.M + 4);
     build_steps(P, st, 0, 0, 2, P.N / 2, 0, sd, pending, slack);
     if (P.sched.empty()) {
       P.sched = st;
@@ -235,18 +245,19 @@ int make_schedule(Plan& P) {
   }
   if (err) return err;
   model_flops(P);
+  const size_t WW = (size_t)P.w * P.w;
   if (P.Pmax > oldP || !P.FA) {
-    size_t n25 = 25 * (size_t)std::max<int64_t>(P.Pmax, 1) * nb;
-    P.FA = (cd*)dalloc(P, sizeof(cd) * n25, err);
-    P.FB = (cd*)dalloc(P, sizeof(cd) * n25, err);
-    P.FC = (cd*)dalloc(P, sizeof(cd) * n25, err);
-    P.ptmp = (cd*)dalloc(P, sizeof(cd) * 2 * n25, err);
+    size_t nww = WW * (size_t)std::max<int64_t>(P.Pmax, 1) * nb;
+    P.FA = (cd*)dalloc(P, sizeof(cd) * nww, err);
+    P.FB = (cd*)dalloc(P, sizeof(cd) * nww, err);
+    P.FC = (cd*)dalloc(P, sizeof(cd) * nww, err);
+    P.ptmp = (cd*)dalloc(P, sizeof(cd) * 2 * nww, err);
   }
   // basis capacity per depth: a product's entries are at most P long (P exceeds every entry degree
   // bound of the node, which can exceed the node's condition count by the spread of delta_in);
-  // leaves hold at most K + 1 coefficients; the root also absorbs the difficult points
+  // leaves hold at most K + 1 = NS M + 1 coefficients; the root also absorbs the difficult points
   int64_t need[MAX_DEPTH] = {0};
-  need[P.p] = 2 * P.M + 1;
+  need[P.p] = P.ns * P.M + 1;
   for (const Step& st : P.sched)
     if (st.kind == STEP_PROD) need[st.depth] = std::max(need[st.depth], st.P);
   need[0] += std::min(P.opts.max_difficult, 4096) + 2;
@@ -255,11 +266,12 @@ int make_schedule(Plan& P) {
       BasisBuf& B = P.buf[d][side];
       if (B.cap >= need[d]) continue;
       B.cap = need[d];
-      B.c = (cd*)dalloc(P, sizeof(cd) * 25 * (size_t)B.cap * nb, err);
-      if (!B.len) B.len = (int*)dalloc(P, sizeof(int) * 32 * nb, err);
+      B.ww = (int)WW;
+      B.c = (cd*)dalloc(P, sizeof(cd) * WW * (size_t)B.cap * nb, err);
+      if (!B.len) B.len = (int*)dalloc(P, sizeof(int) * 64 * nb, err);
       if (!B.colmax) B.colmax = (unsigned long long*)dalloc(P, sizeof(unsigned long long) * 8 * nb, err);
       if (d == 0) {
-        P.dscr_stride = 5 * B.cap + P.opts.max_difficult;
+        P.dscr_stride = P.w * B.cap + P.opts.max_difficult;
         P.dscr = (cd*)dalloc(P, sizeof(cd) * (size_t)P.dscr_stride * nb, err);
       }
     }
@@ -453,15 +465,15 @@ int sync_status(Plan& P) {
   if (cudaStreamSynchronize(P.stream) != cudaSuccess) { cudaGetLastError(); return TIKH_ECUDA; }
   int st = 0;
   if (cudaMemcpy(&st, P.status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return TIKH_ECUDA;
-  std::vector<int> nd(4 * (size_t)P.nb), dl(8 * (size_t)P.nb);
+  std::vector<int> nd(4 * (size_t)P.nb), dl(DSTR * (size_t)P.nb);
   cudaMemcpy(nd.data(), P.ndiff, sizeof(int) * nd.size(), cudaMemcpyDeviceToHost);
   cudaMemcpy(dl.data(), P.delta, sizeof(int) * dl.size(), cudaMemcpyDeviceToHost);
   int64_t total = 0;
   for (int b = 0; b < P.nb; ++b) total += nd[4 * b];
   P.last.n_difficult = total;
-  memcpy(P.last.delta, dl.data(), sizeof(int) * 5);
+  for (int j = 0; j < 7; ++j) P.last.delta[j] = j < P.w ? dl[j] : 0;
   P.last.jstar = -1;
-  for (int j = 0; j < 5; ++j)
+  for (int j = 0; j < P.w; ++j)
     if (dl[j] == 0) P.last.jstar = j;
   P.last.kernel_launches = P.launches;
   P.last.refine_steps = P.opts.refine_steps;
@@ -555,17 +567,23 @@ std::vector<ItemDev> single(const Plan& P, const void* col, const void* row, con
 
 // Algorithm 2 (reading: two condition sets, paired interleaving; M even, 7-smooth) for the core problem
 // cm x cn: halve M while 2M > N_lim, round up to even and 7-smooth; N = 2^p M, k = N - (cm + cn - 1)
-bool alg2(int64_t cm, int64_t cn, const tikh_opts& o, int64_t& N, int64_t& M, int& p) {
-  int64_t Nt = cm + cn - 1, Mv = Nt;
+// Algorithm 2 for ns condition sets per node over a circulant of at least Nt points: halve M while
+// ns M > N_lim; a leaf then holds ns M conditions, at most kmax (64 for the 5 x 5 basis, 42 for 7 x 7)
+bool alg2_sets(int64_t Nt, int ns, int kmax, const tikh_opts& o, int64_t& N, int64_t& M, int& p) {
+  int64_t Mv = Nt;
   int pv = 0;
-  while (2 * Mv > o.n_lim) { ++pv; Mv = (Mv + 1) / 2; }
+  while (ns * Mv > o.n_lim) { ++pv; Mv = (Mv + 1) / 2; }
   if (Mv % 2) ++Mv;
   if (Mv < o.m_min) Mv = o.m_min + (o.m_min % 2);
   while (!is_7smooth(Mv)) Mv += 2;
   M = Mv;
   p = pv;
   N = Mv << pv;
-  return !(pv >= MAX_DEPTH - 1 || 4 * (Mv / 2) > 64 || N > (int64_t)1 << 31);
+  return !(pv >= MAX_DEPTH - 1 || ns * Mv > kmax || N > (int64_t)1 << 31);
+}
+
+bool alg2(int64_t cm, int64_t cn, const tikh_opts& o, int64_t& N, int64_t& M, int& p) {
+  return alg2_sets(cm + cn - 1, 2, 64, o, N, M, p);
 }
 
 bool valid_prec(int prec) {
@@ -642,13 +660,15 @@ int plan_setup(Plan& P, const std::vector<Shape>& shapes, int64_t N, int64_t M, 
   P.M = M;
   P.p = p;
   P.k = shapes[0].k;
-  P.m = P.n = P.cm = P.cn = 0;
+  P.m = P.n = P.cm = P.cn = P.pl = 0;
   for (const Shape& sh : shapes) {
     P.m = std::max(P.m, sh.m);
     P.n = std::max(P.n, sh.n);
     P.cm = std::max(P.cm, sh.cm);
     P.cn = std::max(P.cn, sh.cn);
+    P.pl = std::max(P.pl, sh.pl);
   }
+  const size_t rw = (size_t)P.ns * P.w;  // residual entries per node
   int err = 0;
   const size_t nb = (size_t)P.batch_max;
   if (fft_index(P, P.N, err) < 0 && !err) err = TIKH_EINVAL;
@@ -658,16 +678,16 @@ int plan_setup(Plan& P, const std::vector<Shape>& shapes, int64_t N, int64_t M, 
   P.work = (cd*)dalloc(P, sizeof(cd) * (size_t)N * nb, err);
   P.work2 = (cd*)dalloc(P, sizeof(cd) * (size_t)N * nb, err);
   P.ftmpN = (cd*)dalloc(P, sizeof(cd) * (size_t)N * nb, err);
-  P.R = (cd*)dalloc(P, sizeof(cd) * 10 * (size_t)N * nb, err);
-  P.Phi = (cd*)dalloc(P, sizeof(cd) * 10 * (size_t)N * nb, err);
-  P.delta = (int*)dalloc(P, sizeof(int) * 8 * nb, err);
-  P.dstack = (int*)dalloc(P, sizeof(int) * 5 * MAX_DEPTH * nb, err);
+  P.R = (cd*)dalloc(P, sizeof(cd) * rw * (size_t)N * nb, err);
+  P.Phi = (cd*)dalloc(P, sizeof(cd) * rw * (size_t)N * nb, err);
+  P.delta = (int*)dalloc(P, sizeof(int) * DSTR * nb, err);
+  P.dstack = (int*)dalloc(P, sizeof(int) * DSTR * MAX_DEPTH * nb, err);
   P.status = (int*)dalloc(P, sizeof(int) * 4, err);
   P.ndiff = (int*)dalloc(P, sizeof(int) * 4 * nb, err);
   P.bad = (int*)dalloc(P, sizeof(int) * nb, err);
   P.diff = (int64_t*)dalloc(P, sizeof(int64_t) * (size_t)o.max_difficult * nb, err);
-  P.diffr = (cd*)dalloc(P, sizeof(cd) * 5 * (size_t)o.max_difficult * nb, err);
-  P.dvals = (cd*)dalloc(P, sizeof(cd) * 25 * (size_t)o.max_difficult * nb, err);
+  P.diffr = (cd*)dalloc(P, sizeof(cd) * P.w * (size_t)o.max_difficult * nb, err);
+  P.dvals = (cd*)dalloc(P, sizeof(cd) * P.w * P.w * (size_t)o.max_difficult * nb, err);
   P.peak = (unsigned long long*)dalloc(P, sizeof(unsigned long long) * nb, err);
   P.item_cap = std::max<int64_t>(item_cap, (int64_t)nb);
   P.items_base = (ItemDev*)dalloc(P, sizeof(ItemDev) * (size_t)P.item_cap, err);
@@ -676,7 +696,7 @@ int plan_setup(Plan& P, const std::vector<Shape>& shapes, int64_t N, int64_t M, 
   P.lam = P.lam_base;
   if (!err) err = make_schedule(P);
   if (!err) {
-    size_t nl = 50 * (size_t)std::max<int64_t>(P.Lrmax, 1) * nb;
+    size_t nl = 2 * (size_t)P.w * P.w * (size_t)std::max<int64_t>(P.Lrmax, 1) * nb;
     P.evalv = (cd*)dalloc(P, sizeof(cd) * nl, err);
     P.etmp = (cd*)dalloc(P, sizeof(cd) * nl, err);
     P.ybuf = (cd*)dalloc(P, sizeof(cd) * (size_t)P.cn * nb, err);
@@ -686,9 +706,13 @@ int plan_setup(Plan& P, const std::vector<Shape>& shapes, int64_t N, int64_t M, 
     P.norms = (double*)dalloc(P, sizeof(double) * 4 * nb, err);
     if (P.gram) {
       P.specG = (cd*)dalloc(P, sizeof(cd) * (size_t)N * nb, err);
-      P.gX = (cd*)dalloc(P, sizeof(cd) * (size_t)N * nb, err);
       P.peakG = (unsigned long long*)dalloc(P, sizeof(unsigned long long) * nb, err);
     }
+    if (P.general) {
+      P.specL = (cd*)dalloc(P, sizeof(cd) * (size_t)N * nb, err);
+      P.peakL = (unsigned long long*)dalloc(P, sizeof(unsigned long long) * nb, err);
+    }
+    if (P.gram || P.general) P.gX = (cd*)dalloc(P, sizeof(cd) * (size_t)N * nb, err);
   }
   if (!err && cudaStreamSynchronize(P.stream) != cudaSuccess) err = TIKH_ECUDA;
   if (err) {
@@ -933,6 +957,91 @@ int tikh_plan_create_gramian(tikh_plan* out, int64_t n, int64_t p, int dtype, in
   return TIKH_OK;
 }
 
+// the general problem (Sec. 3.2): (T^H T + L^H L) x = y with T m x n and L pl x n; three condition sets per
+// node and a 7 x 7 basis; N >= max(m, pl) + n - 1 by Algorithm 2 with three sets; FP64 stages only
+int tikh_plan_create_general(tikh_plan* out, int64_t m, int64_t n, int64_t pl, int dtype, const tikh_opts* opts,
+                             void* stream) {
+  if (!out) return TIKH_EINVAL;
+  *out = nullptr;
+  if (m < 1 || n < 1 || pl < 1 || (dtype != TIKH_R64 && dtype != TIKH_C128)) return TIKH_EINVAL;
+  // defaults: leaves of 3 M <= 30 conditions; difficult-point threshold 1e-12 (deferring the conditions
+  // whose best ratio lies in [1e-12, 1e-8) and processing them against B* costs accuracy here)
+  tikh_opts o{30, 0, 0, 1e-12, 4096, 0, 1, 0, 0, 0, 0, 0.0, 0, 0};
+  if (opts) o = *opts;
+  if (!valid_opts(o)) return TIKH_EINVAL;
+  int64_t N, M;
+  int pp;
+  if (!alg2_sets(std::max(m, pl) + n - 1, 3, 42, o, N, M, pp)) return TIKH_EINVAL;
+  Shape sh;
+  sh.m = m;
+  sh.n = n;
+  sh.cm = m;
+  sh.cn = n;
+  sh.k = N - (m + n - 1);
+  sh.pl = pl;
+  sh.kl = N - (pl + n - 1);
+  sh.dual = 0;
+  tikh_plan h = new (std::nothrow) tikh_plan_s;
+  if (!h) return TIKH_ENOMEM;
+  h->P.general = 1;
+  h->P.w = 7;
+  h->P.ns = 3;
+  int err = plan_setup(h->P, std::vector<Shape>(1, sh), N, M, pp, dtype, TIKH_PREC_FP64, o, (cudaStream_t)stream,
+                       o.batch);
+  if (err) {
+    delete h;
+    return err;
+  }
+  *out = h;
+  return TIKH_OK;
+}
+
+static int general_run(tikh_plan h, int batch, const void* col, int64_t col_stride, const void* row,
+                       int64_t row_stride, const void* lcol, int64_t lcol_stride, const void* lrow,
+                       int64_t lrow_stride, const void* rhs, int64_t rhs_stride, void* x, int64_t x_stride,
+                       int rhs_is_y) {
+  if (!h || !h->P.general || !col || !row || !lcol || !lrow || !rhs || !x || batch < 1 || batch > h->P.batch_max)
+    return TIKH_EINVAL;
+  Plan& P = h->P;
+  // an input stride is 0 (one array shared by the batch) or at least the array's length
+  auto bad_stride = [](int64_t st, int64_t len) { return st < 0 || (st > 0 && st < len); };
+  if (batch > 1 && (bad_stride(col_stride, P.m) || bad_stride(row_stride, P.n) || bad_stride(lcol_stride, P.pl) ||
+                    bad_stride(lrow_stride, P.n) || bad_stride(rhs_stride, rhs_is_y ? P.n : P.m) || x_stride < P.n))
+    return TIKH_EINVAL;
+  const size_t es = P.dtype == TIKH_C128 ? 16 : 8;
+  std::vector<ItemDev> items;
+  items.reserve((size_t)batch);
+  for (int i = 0; i < batch; ++i) {
+    ItemDev it = make_item(P.shapes[0], (const char*)col + es * (size_t)(i * col_stride),
+                           (const char*)row + es * (size_t)(i * row_stride),
+                           (const char*)rhs + es * (size_t)(i * rhs_stride), (char*)x + es * (size_t)(i * x_stride));
+    it.lcol = (const char*)lcol + es * (size_t)(i * lcol_stride);
+    it.lrow = (const char*)lrow + es * (size_t)(i * lrow_stride);
+    it.pl = P.shapes[0].pl;
+    it.kl = P.shapes[0].kl;
+    items.push_back(it);
+  }
+  const std::vector<double> zeros((size_t)batch, 0.0);  // the regularisation is in L
+  return solve_with_retry(P, items, zeros.data(), rhs_is_y, nullptr, nullptr, 0);
+}
+
+int tikh_solve_general(tikh_plan h, const void* col, const void* row, const void* lcol, const void* lrow,
+                       const void* b, void* x) {
+  return general_run(h, 1, col, 0, row, 0, lcol, 0, lrow, 0, b, 0, x, 0, 0);
+}
+
+int tikh_solve_general_normal(tikh_plan h, const void* col, const void* row, const void* lcol, const void* lrow,
+                              const void* y, void* x) {
+  return general_run(h, 1, col, 0, row, 0, lcol, 0, lrow, 0, y, 0, x, 0, 1);
+}
+
+int tikh_solve_general_strided(tikh_plan h, int batch, const void* col, int64_t col_stride, const void* row,
+                               int64_t row_stride, const void* lcol, int64_t lcol_stride, const void* lrow,
+                               int64_t lrow_stride, const void* b, int64_t b_stride, void* x, int64_t x_stride) {
+  return general_run(h, batch, col, col_stride, row, row_stride, lcol, lcol_stride, lrow, lrow_stride, b, b_stride, x,
+                     x_stride, 0);
+}
+
 int tikh_solve_gramian(tikh_plan h, const void* g, const void* lcol, const void* lrow, const void* y, void* x) {
   if (!h || !g || !lcol || !lrow || !y || !x || !h->P.gram) return TIKH_EINVAL;
   std::vector<ItemDev> it = single(h->P, lcol, lrow, y, x);
@@ -942,12 +1051,12 @@ int tikh_solve_gramian(tikh_plan h, const void* g, const void* lcol, const void*
 }
 
 int tikh_solve(tikh_plan h, const void* col, const void* row, const void* b, double lambda, void* x) {
-  if (!h || !col || !row || !b || !x || !valid_lambda(lambda) || h->P.gram) return TIKH_EINVAL;
+  if (!h || !col || !row || !b || !x || !valid_lambda(lambda) || h->P.gram || h->P.general) return TIKH_EINVAL;
   return solve_with_retry(h->P, single(h->P, col, row, b, x), &lambda, 0, nullptr, nullptr, 0);
 }
 
 int tikh_solve_async(tikh_plan h, const void* col, const void* row, const void* b, double lambda, void* x) {
-  if (!h || !col || !row || !b || !x || !valid_lambda(lambda) || h->P.gram) return TIKH_EINVAL;
+  if (!h || !col || !row || !b || !x || !valid_lambda(lambda) || h->P.gram || h->P.general) return TIKH_EINVAL;
   Plan& P = h->P;
   P.items = P.items_base;
   P.lam = P.lam_base;
@@ -958,14 +1067,16 @@ int tikh_solve_async(tikh_plan h, const void* col, const void* row, const void* 
 }
 
 int tikh_solve_normal(tikh_plan h, const void* col, const void* row, const void* y, double lambda, void* x) {
-  if (!h || !col || !row || !y || !x || !valid_lambda(lambda) || h->P.gram || h->P.dual) return TIKH_EINVAL;
+  if (!h || !col || !row || !y || !x || !valid_lambda(lambda) || h->P.gram || h->P.general || h->P.dual)
+    return TIKH_EINVAL;
   return solve_with_retry(h->P, single(h->P, col, row, y, x), &lambda, 1, nullptr, nullptr, 0);
 }
 
 int tikh_solve_strided(tikh_plan h, int batch, const void* col, int64_t col_stride, const void* row,
                        int64_t row_stride, const void* b, int64_t b_stride, const double* lambdas, void* x,
                        int64_t x_stride) {
-  if (!h || !col || !row || !b || !x || !lambdas || batch < 1 || batch > h->P.batch_max || h->P.gram) return TIKH_EINVAL;
+  if (!h || !col || !row || !b || !x || !lambdas || batch < 1 || batch > h->P.batch_max || h->P.gram || h->P.general)
+    return TIKH_EINVAL;
   if (col_stride < 0 || row_stride < 0 || b_stride < 0 || (batch > 1 && x_stride < h->P.n)) return TIKH_EINVAL;
   for (int i = 0; i < batch; ++i)
     if (!valid_lambda(lambdas[i])) return TIKH_EINVAL;
@@ -984,7 +1095,7 @@ int tikh_solve_strided(tikh_plan h, int batch, const void* col, int64_t col_stri
 static int grad_run(Plan& P, const std::vector<ItemDev>& items, const double* lams, const void* x, int64_t x_stride,
                     const void* b, int64_t b_stride, void* dcol, void* drow, void* db, int64_t out_col_stride,
                     int64_t out_row_stride, int64_t out_b_stride, double* dlam) {
-  if (P.dual || P.gram) return TIKH_EINVAL;  // the adjoint is implemented for the l2 problem with m >= n
+  if (P.dual || P.gram || P.general) return TIKH_EINVAL;  // the adjoint is implemented for the l2 problem, m >= n
   const int nb = (int)items.size();
   int err = 0;
   if (!P.gbuf) {  // adjoint workspace, allocated by the first gradient call
@@ -1039,7 +1150,7 @@ int tikh_solve_grad_strided(tikh_plan h, int batch, const void* col, int64_t col
 }
 
 int tikh_solve_host(tikh_plan h, const void* col, const void* row, const void* b, double lambda, void* x) {
-  if (!h || !col || !row || !b || !x || !valid_lambda(lambda) || h->P.gram) return TIKH_EINVAL;
+  if (!h || !col || !row || !b || !x || !valid_lambda(lambda) || h->P.gram || h->P.general) return TIKH_EINVAL;
   Plan& P = h->P;
   size_t es = P.dtype == TIKH_C128 ? 16 : 8;
   char* base = (char*)P.d_in;

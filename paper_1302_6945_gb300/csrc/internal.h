@@ -16,23 +16,26 @@
 namespace tikh {
 
 constexpr int MAX_DEPTH = 40;
+constexpr int WMAX = 7;  // largest basis size: 5 (l2, Toeplitz-Gramian), 7 (general problem, Sec. 3.2)
+constexpr int DSTR = 8;  // stride of per-problem degree vectors (delta, the delta_in stack)
 
-// one basis matrix B(z) per problem: 25 polynomials (entry (i,j) at c + pb*cstride + (5i+j)*cap),
-// device-side lengths (32 per problem) and per-column max |Re|,|Im| bit patterns (8 per problem)
+// one basis matrix B(z) per problem: ww = W^2 polynomials (entry (i,j) at c + pb*cstride + (W i+j)*cap),
+// device-side lengths (64 per problem) and per-column max |Re|,|Im| bit patterns (8 per problem)
 // that fix the lazy power-of-two column scaling
 struct BasisBuf {
   cd* c = nullptr;
   int* len = nullptr;
   unsigned long long* colmax = nullptr;
   int64_t cap = 0;
-  __host__ __device__ int64_t cstride() const { return 25 * cap; }
+  int ww = 25;
+  __host__ __device__ int64_t cstride() const { return ww * cap; }
   __device__ cd* cp(int pb) const { return c + pb * cstride(); }
-  __device__ int* lp(int pb) const { return len + pb * 32; }
+  __device__ int* lp(int pb) const { return len + pb * 64; }
   __device__ unsigned long long* mp(int pb) const { return colmax + pb * 8; }
 };
 
 // DFS schedule of Algorithm 1: a node (a, s, L) at `depth` has nodes omega^{a + c + s j}, c in {0,1},
-// j < L (s L = N) and 4L conditions.
+// j < L (s L = N) and 2 NS L conditions (NS condition sets per node: 2, or 3 for the general problem).
 enum StepKind { STEP_LEAF = 0, STEP_EVAL = 1, STEP_PROD = 2 };
 constexpr int BATCH_PROD_DIRECT_MAX = 36;  // automatic thresholds for plans with batch > 1 (measured)
 constexpr int BATCH_EVAL_DIRECT_MAX = 10;
@@ -51,6 +54,7 @@ struct Step {
 // extension k = N - (cm + cn - 1) for the plan's N.
 struct Shape {
   int64_t m = 0, n = 0, cm = 0, cn = 0, k = 0;
+  int64_t pl = 0, kl = 0;  // general problem: rows of L, its extension N - (pl + n - 1)
   int dual = 0;
 };
 
@@ -63,7 +67,10 @@ struct ItemDev {
   const void* rhs;
   void* x;
   const void* gram;  // Toeplitz-Gramian plans: first column of the Hermitian Toeplitz G (n entries)
+  const void* lcol;  // general plans: the regulariser L (pl x n), first column and first row
+  const void* lrow;
   int64_t m, n, cm, cn, k;
+  int64_t pl, kl;    // general plans: rows of L and its extension kl = N - (pl + n - 1)
   int dual;
   int pad_;
 };
@@ -93,6 +100,11 @@ struct Plan {
   std::map<int64_t, cf*> twiddle32_of_len;  // complex64 copies (FP32 stages)
   int prec = TIKH_PREC_FP64;
   int gram = 0;          // 1: the Toeplitz-Gramian problem (G + L^H L) x = y (Sec. 3.4); L plays T's part
+  int general = 0;       // 1: the general problem (T^H T + L^H L) x = y (Sec. 3.2)
+  int w = 5, ns = 2;     // basis size and condition sets per node (7 and 3 for the general problem)
+  int64_t pl = 0;        // general plans: rows of L (the largest over the shapes)
+  cd* specL = nullptr;   // [nb][N] DFT of L's circulant generator (general plans)
+  unsigned long long* peakL = nullptr;  // [nb] fill magnitude of L's extension
   cd* specG = nullptr;   // [nb][N] DFT of G's circulant generator (Gramian plans)
   cd* gX = nullptr;      // [nb][N] refinement scratch: DFT of [x; 0] (Gramian plans)
   unsigned long long* peakG = nullptr;  // [nb] fill magnitude of G's extension
@@ -108,23 +120,23 @@ struct Plan {
   cd* work = nullptr;   // [nb][N]
   cd* work2 = nullptr;  // [nb][N]
   cd* ftmpN = nullptr;  // [nb][N] four-step temp for length-N transforms
-  cd* R = nullptr;      // [nb][N][2][5] residual rows
-  cd* Phi = nullptr;    // [nb][N][2][5] original condition rows
-  int* delta = nullptr;   // [nb][8]
-  int* dstack = nullptr;  // [nb][MAX_DEPTH][5]
+  cd* R = nullptr;      // [nb][N][ns][w] residual rows
+  cd* Phi = nullptr;    // [nb][N][ns][w] original condition rows
+  int* delta = nullptr;   // [nb][DSTR]
+  int* dstack = nullptr;  // [nb][MAX_DEPTH][DSTR]
   int* status = nullptr;  // 1 (shared by the batch)
   int* ndiff = nullptr;   // [nb][4]
   int* bad = nullptr;     // [nb] 1: non-finite input (set by the prologue's check)
-  int64_t* diff = nullptr;  // [nb][max_difficult] condition ids 2e + f
-  cd* diffr = nullptr;      // [nb][max_difficult][5] residuals
-  cd* dvals = nullptr;      // [nb][max_difficult][25] B*(sigma) of the deferred conditions
+  int64_t* diff = nullptr;  // [nb][max_difficult] condition ids ns e + f
+  cd* diffr = nullptr;      // [nb][max_difficult][w] residuals
+  cd* dvals = nullptr;      // [nb][max_difficult][w^2] B*(sigma) of the deferred conditions
   BasisBuf buf[MAX_DEPTH][2];
-  cd* evalv = nullptr;  // [nb][50][Lrmax]
-  cd* etmp = nullptr;   // [nb][50][Lrmax] (four-step temp)
-  cd* FA = nullptr;     // [nb][25][Pmax] spectra of B_L
-  cd* FB = nullptr;     // [nb][25][Pmax] spectra of B_R
-  cd* FC = nullptr;     // [nb][25][Pmax] products
-  cd* ptmp = nullptr;   // [nb][50][Pmax] (four-step temp)
+  cd* evalv = nullptr;  // [nb][2 w^2][Lrmax]
+  cd* etmp = nullptr;   // [nb][2 w^2][Lrmax] (four-step temp)
+  cd* FA = nullptr;     // [nb][w^2][Pmax] spectra of B_L
+  cd* FB = nullptr;     // [nb][w^2][Pmax] spectra of B_R
+  cd* FC = nullptr;     // [nb][w^2][Pmax] products
+  cd* ptmp = nullptr;   // [nb][2 w^2][Pmax] (four-step temp)
   unsigned long long* peak = nullptr;  // [nb] fill magnitude (bit pattern of a non-negative double)
   double* lam = nullptr;  // [nb] regularisation weights of the current call (points into lam_base)
   ItemDev* items = nullptr;  // [nb] items of the current call (points into items_base)

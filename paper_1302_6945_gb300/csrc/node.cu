@@ -9,16 +9,18 @@
 // trimmed to entry (i,j) degree bounds and carried with power-of-two column scales.
 // In the FP32 precision pattern the FFT forms of both steps run in FP32 (complex64 spectra, FP32
 // pointwise products and updates); the direct small-node forms, the leaves and the basis stay FP64.
-// All problems of a batch are processed by the same launches: transform index = problem * 50 (or 25)
-// + entry, grid.y / grid.z = problem for the element-wise kernels.
+// All problems of a batch are processed by the same launches: transform index = problem * 2 W^2 (or W^2)
+// + entry, grid.y / grid.z = problem for the element-wise kernels.  W = 5 (the l2 and Toeplitz-Gramian
+// problems, two condition sets per node) or 7 (the general problem, three sets per node).
 #include "internal.h"
 
 namespace tikh {
 
+template <int W>
 __device__ __forceinline__ int entry_bound_dev(const int* din, const int* dout, int i, int j) {
   int amax = 0;
   bool have = false;
-  for (int c = 0; c < 5; ++c)
+  for (int c = 0; c < W; ++c)
     if (dout[c] > din[c]) { amax = have ? max(amax, dout[c]) : dout[c]; have = true; }
   if (dout[j] > din[j]) return dout[j] - din[i];
   int acc = have ? amax - din[i] : -1;
@@ -39,17 +41,17 @@ __device__ __forceinline__ cd twiddle_of<cd>(const cd* wN, const cf*, int64_t i)
 template <>
 __device__ __forceinline__ cf twiddle_of<cf>(const cd*, const cf* wN32, int64_t i) { return tw_at(wN32, i); }
 
-template <class C>
-struct LoadTwistFold {  // transform t = 50 pb + 2E + c
+template <class C, int W>
+struct LoadTwistFold {  // transform t = 2 W^2 pb + 2E + c
   BasisBuf B;
   BasisBuf OUT;  // this node's output slot: its column maxima are reset here, before the product
   const cd* wN;
   const cf* wN32;
   int64_t N, Lr, beta0;
   __device__ C operator()(int t, int64_t u) const {
-    int pb = t / 50, b = t % 50;
+    int pb = t / (2 * W * W), b = t % (2 * W * W);
     if (b == 0 && u == 0)
-      for (int j = 0; j < 5; ++j) OUT.mp(pb)[j] = 0ULL;
+      for (int j = 0; j < W; ++j) OUT.mp(pb)[j] = 0ULL;
     int E = b >> 1, c = b & 1;
     int64_t beta = beta0 + c;
     int64_t len = B.lp(pb)[E];
@@ -63,7 +65,7 @@ struct LoadTwistFold {  // transform t = 50 pb + 2E + c
       ix += stepx;
       if (ix >= N) ix -= N;
     }
-    return cscale(acc, (decltype(acc.x))col_scale_from_bits(B.mp(pb)[E % 5]));
+    return cscale(acc, (decltype(acc.x))col_scale_from_bits(B.mp(pb)[E % W]));
   }
 };
 template <class C>
@@ -73,9 +75,9 @@ struct StoreEval {
   __device__ void operator()(int t, int64_t j, C v) const { out[(int64_t)t * Lr + j] = v; }
 };
 
-// phi <- phi B_L(sigma) for both conditions of every right-child node (in C's precision; the rows are
+// phi <- phi B_L(sigma) for the NS conditions of every right-child node (in C's precision; the rows are
 // stored back in FP64)
-template <class C>
+template <class C, int W, int NS>
 __global__ void k_eval_update(cd* R, const C* __restrict__ vals, int64_t N, int64_t a0, int64_t s2, int64_t Lr) {
   pdl_enter();
   const int pb = blockIdx.y;
@@ -83,41 +85,41 @@ __global__ void k_eval_update(cd* R, const C* __restrict__ vals, int64_t N, int6
     int c = (int)(g % 2);
     int64_t j = g / 2;
     int64_t e = a0 + c + s2 * j;
-    C V[25];
+    C V[W * W];
 #pragma unroll
-    for (int E = 0; E < 25; ++E) V[E] = vals[((int64_t)pb * 50 + E * 2 + c) * Lr + j];
+    for (int E = 0; E < W * W; ++E) V[E] = vals[((int64_t)pb * (2 * W * W) + E * 2 + c) * Lr + j];
 #pragma unroll
-    for (int f = 0; f < 2; ++f) {
-      cd* r = R + ((int64_t)pb * N + e) * 10 + f * 5;
-      C in[5];
+    for (int f = 0; f < NS; ++f) {
+      cd* r = R + ((int64_t)pb * N + e) * (NS * W) + f * W;
+      C in[W];
 #pragma unroll
-      for (int i = 0; i < 5; ++i) in[i] = cfrom<C>(r[i]);
+      for (int i = 0; i < W; ++i) in[i] = cfrom<C>(r[i]);
 #pragma unroll
-      for (int col = 0; col < 5; ++col) {
+      for (int col = 0; col < W; ++col) {
         C acc = czero<C>();
 #pragma unroll
-        for (int i = 0; i < 5; ++i) acc = cfma(in[i], V[i * 5 + col], acc);
+        for (int i = 0; i < W; ++i) acc = cfma(in[i], V[i * W + col], acc);
         r[col] = mkc((double)acc.x, (double)acc.y);
       }
     }
   }
 }
 
-// Small nodes: B_L evaluated at each right-child node, then the residual update of that node's two
-// conditions, in one launch.  Block = one node (g = 2j + c), 25 entries x G lanes: lane gl evaluates
+// Small nodes: B_L evaluated at each right-child node, then the residual update of that node's NS
+// conditions, in one launch.  Block = one node (g = 2j + c), W^2 entries x G lanes: lane gl evaluates
 // the coefficient chunk [gl C, gl C + C) of its entry by Horner, multiplies by z^(gl C) (twiddle
-// table) and the G lanes are added by shuffles; then ten threads form phi <- phi B_L(sigma).
-template <int G>
-__global__ void __launch_bounds__(25 * G) k_eval_direct(BasisBuf BL, BasisBuf OUT, cd* R, const cd* __restrict__ wN,
-                                                        int64_t N, int64_t a0, int64_t s2) {
-  __shared__ cd V[25];
-  __shared__ cd Rs[10];
+// table) and the G lanes are added by shuffles; then NS W threads form phi <- phi B_L(sigma).
+template <int G, int W, int NS>
+__global__ void __launch_bounds__(W * W * G) k_eval_direct(BasisBuf BL, BasisBuf OUT, cd* R, const cd* __restrict__ wN,
+                                                           int64_t N, int64_t a0, int64_t s2) {
+  __shared__ cd V[W * W];
+  __shared__ cd Rs[NS * W];
   pdl_enter();
   const int pb = blockIdx.y, tid = threadIdx.x;
   const int64_t g = blockIdx.x;
   const int64_t e = a0 + (g & 1) + s2 * (g >> 1);
-  if (g == 0 && tid < 5) OUT.mp(pb)[tid] = 0ULL;  // the parent's column maxima, rebuilt by its product
-  if (tid < 10) Rs[tid] = R[((int64_t)pb * N + e) * 10 + tid];
+  if (g == 0 && tid < W) OUT.mp(pb)[tid] = 0ULL;  // the parent's column maxima, rebuilt by its product
+  if (tid < NS * W) Rs[tid] = R[((int64_t)pb * N + e) * (NS * W) + tid];
   const int E = tid / G, gl = tid - E * G;
   const int len = BL.lp(pb)[E];
   const int C = (len + G - 1) / G;
@@ -137,104 +139,117 @@ __global__ void __launch_bounds__(25 * G) k_eval_direct(BasisBuf BL, BasisBuf OU
       v.y += __shfl_xor_sync(mask, v.y, o);
     }
   }
-  if (gl == 0) V[E] = cscale(v, col_scale_from_bits(BL.mp(pb)[E % 5]));
+  if (gl == 0) V[E] = cscale(v, col_scale_from_bits(BL.mp(pb)[E % W]));
   __syncthreads();
-  if (tid < 10) {  // (condition f, column): phi <- phi B_L(sigma)
-    const int f = tid / 5, col = tid % 5;
+  if (tid < NS * W) {  // (condition f, column): phi <- phi B_L(sigma)
+    const int f = tid / W, col = tid % W;
     cd acc = mkc(0.0, 0.0);
 #pragma unroll
-    for (int i = 0; i < 5; ++i) acc = cfma(Rs[f * 5 + i], V[i * 5 + col], acc);
-    R[((int64_t)pb * N + e) * 10 + f * 5 + col] = acc;
+    for (int i = 0; i < W; ++i) acc = cfma(Rs[f * W + i], V[i * W + col], acc);
+    R[((int64_t)pb * N + e) * (NS * W) + f * W + col] = acc;
   }
 }
 
-int launch_eval(Plan& P, const Step& st) {
+template <int W, int NS>
+static int launch_eval_t(Plan& P, const Step& st) {
   const int64_t Lr = st.L / 2;
   const BasisBuf& BL = P.buf[st.depth + 1][0];
   const BasisBuf& OUT = P.buf[st.depth][st.side];
+  constexpr int WW = W * W;
   if (Lr <= P.eval_direct_max) {
     const dim3 grid((unsigned)(2 * Lr), (unsigned)P.nb);
     const int64_t cap = BL.cap, a0 = st.a + st.s, s2 = 2 * st.s;
     cudaStream_t s = P.stream;
-    if (cap <= 8) launch_k(pdl_enabled(), k_eval_direct<1>, grid, dim3(25), 0, s, BL, OUT, P.R, P.wN, P.N, a0, s2);
-    else if (cap <= 24) launch_k(pdl_enabled(), k_eval_direct<2>, grid, dim3(50), 0, s, BL, OUT, P.R, P.wN, P.N, a0, s2);
-    else if (cap <= 48) launch_k(pdl_enabled(), k_eval_direct<4>, grid, dim3(100), 0, s, BL, OUT, P.R, P.wN, P.N, a0, s2);
-    else if (cap <= 96) launch_k(pdl_enabled(), k_eval_direct<8>, grid, dim3(200), 0, s, BL, OUT, P.R, P.wN, P.N, a0, s2);
-    else if (cap <= 192) launch_k(pdl_enabled(), k_eval_direct<16>, grid, dim3(400), 0, s, BL, OUT, P.R, P.wN, P.N, a0, s2);
-    else launch_k(pdl_enabled(), k_eval_direct<32>, grid, dim3(800), 0, s, BL, OUT, P.R, P.wN, P.N, a0, s2);
+    const bool pdl = pdl_enabled();
+    if (cap <= 8) launch_k(pdl, k_eval_direct<1, W, NS>, grid, dim3(WW), 0, s, BL, OUT, P.R, P.wN, P.N, a0, s2);
+    else if (cap <= 24) launch_k(pdl, k_eval_direct<2, W, NS>, grid, dim3(2 * WW), 0, s, BL, OUT, P.R, P.wN, P.N, a0, s2);
+    else if (cap <= 48) launch_k(pdl, k_eval_direct<4, W, NS>, grid, dim3(4 * WW), 0, s, BL, OUT, P.R, P.wN, P.N, a0, s2);
+    else if (cap <= 96) launch_k(pdl, k_eval_direct<8, W, NS>, grid, dim3(8 * WW), 0, s, BL, OUT, P.R, P.wN, P.N, a0, s2);
+    else if (cap <= 192 || W > 5)  // 16 lanes per entry at most for the 7 x 7 basis (784 threads)
+      launch_k(pdl, k_eval_direct<16, W, NS>, grid, dim3(16 * WW), 0, s, BL, OUT, P.R, P.wN, P.N, a0, s2);
+    else launch_k(pdl, k_eval_direct<32, W, NS>, grid, dim3(32 * WW), 0, s, BL, OUT, P.R, P.wN, P.N, a0, s2);
     return cudaGetLastError() == cudaSuccess ? 1 : TIKH_ECUDA;
   }
   const FftPlan& F = P.ffts[st.fft];
   dim3 grid((unsigned)std::min<int64_t>((2 * Lr + 127) / 128, 4096), (unsigned)P.nb);
   int r;
-  if (P.stage32) {
-    cf* ev = reinterpret_cast<cf*>(P.evalv);
-    r = fft_run(F, 50 * P.nb, +1, LoadTwistFold<cf>{BL, OUT, P.wN, P.wN32, P.N, Lr, st.a + st.s},
-                StoreEval<cf>{ev, Lr}, reinterpret_cast<cf*>(P.etmp), P.stream);
-    if (r < 0) return TIKH_ECUDA;
-    launch_k(pdl_enabled(), k_eval_update<cf>, grid, dim3(128), 0, P.stream, P.R, (const cf*)ev, P.N, st.a + st.s,
-             2 * st.s, Lr);
-  } else {
-    r = fft_run(F, 50 * P.nb, +1, LoadTwistFold<cd>{BL, OUT, P.wN, P.wN32, P.N, Lr, st.a + st.s},
-                StoreEval<cd>{P.evalv, Lr}, P.etmp, P.stream);
-    if (r < 0) return TIKH_ECUDA;
-    launch_k(pdl_enabled(), k_eval_update<cd>, grid, dim3(128), 0, P.stream, P.R, (const cd*)P.evalv, P.N, st.a + st.s,
-             2 * st.s, Lr);
+  if constexpr (W == 5) {
+    if (P.stage32) {
+      cf* ev = reinterpret_cast<cf*>(P.evalv);
+      r = fft_run(F, 2 * WW * P.nb, +1, LoadTwistFold<cf, W>{BL, OUT, P.wN, P.wN32, P.N, Lr, st.a + st.s},
+                  StoreEval<cf>{ev, Lr}, reinterpret_cast<cf*>(P.etmp), P.stream);
+      if (r < 0) return TIKH_ECUDA;
+      launch_k(pdl_enabled(), k_eval_update<cf, W, NS>, grid, dim3(128), 0, P.stream, P.R, (const cf*)ev, P.N,
+               st.a + st.s, 2 * st.s, Lr);
+      if (cudaGetLastError() != cudaSuccess) return TIKH_ECUDA;
+      return r + 1;
+    }
   }
+  r = fft_run(F, 2 * WW * P.nb, +1, LoadTwistFold<cd, W>{BL, OUT, P.wN, P.wN32, P.N, Lr, st.a + st.s},
+              StoreEval<cd>{P.evalv, Lr}, P.etmp, P.stream);
+  if (r < 0) return TIKH_ECUDA;
+  launch_k(pdl_enabled(), k_eval_update<cd, W, NS>, grid, dim3(128), 0, P.stream, P.R, (const cd*)P.evalv, P.N,
+           st.a + st.s, 2 * st.s, Lr);
   if (cudaGetLastError() != cudaSuccess) return TIKH_ECUDA;
   return r + 1;
 }
+
+int launch_eval(Plan& P, const Step& st) { return P.w == 7 ? launch_eval_t<7, 3>(P, st) : launch_eval_t<5, 2>(P, st); }
 
 // ------------------------------------------------------------------------------------------------
 // step 4
 // ------------------------------------------------------------------------------------------------
 // length bound of entry (i, j) of B_L B_R from the operands' lengths: max_u len(a_iu) + len(b_uj) - 1 (the
 // tau-degree bound can be far looser when the extension k is large)
+template <int W>
 __device__ __forceinline__ int prod_len_bound(const BasisBuf& BL, const BasisBuf& BR, int pb, int i, int j) {
   int L = 0;
-  for (int u = 0; u < 5; ++u) {
-    const int la = BL.lp(pb)[i * 5 + u], lb = BR.lp(pb)[u * 5 + j];
+  for (int u = 0; u < W; ++u) {
+    const int la = BL.lp(pb)[i * W + u], lb = BR.lp(pb)[u * W + j];
     if (la > 0 && lb > 0) L = max(L, la + lb - 1);
   }
   return L;
 }
 
-template <class C>
-struct LoadPad {  // transform t = 50 pb + b; b < 25: B_L entry b; b >= 25: B_R entry b - 25; zero-padded to P
+template <class C, int W>
+struct LoadPad {  // transform t = 2 W^2 pb + b; b < W^2: B_L entry b; else B_R entry b - W^2; zero-padded to P
   BasisBuf BL, BR, OUT;
-  const int* dstack;  // + pb * MAX_DEPTH * 5 + depth * 5: delta_in of the node
-  const int* delta;   // + 8 pb: delta_out
+  const int* dstack;  // + (pb * MAX_DEPTH + depth) * DSTR: delta_in of the node
+  const int* delta;   // + DSTR pb: delta_out
   int depth;
   int* status;
   int64_t P;
   __device__ C operator()(int t, int64_t q) const {
-    int pb = t / 50, b = t % 50;
+    constexpr int WW = W * W;
+    int pb = t / (2 * WW), b = t % (2 * WW);
     if (b == 0 && q == 0) {
       // guard: the transform length must exceed every entry degree of the product (no wrap-around)
-      const int* din = dstack + (pb * MAX_DEPTH + depth) * 5;
-      const int* dout = delta + 8 * pb;
+      const int* din = dstack + (pb * MAX_DEPTH + depth) * DSTR;
+      const int* dout = delta + DSTR * pb;
       int D = -1;
-      for (int i = 0; i < 5; ++i)
-        for (int j = 0; j < 5; ++j) D = max(D, min(entry_bound_dev(din, dout, i, j), prod_len_bound(BL, BR, pb, i, j) - 1));
-      for (int E = 0; E < 25; ++E) D = max(D, max(BL.lp(pb)[E], BR.lp(pb)[E]) - 1);  // operands fit the transform
+      for (int i = 0; i < W; ++i)
+        for (int j = 0; j < W; ++j)
+          D = max(D, min(entry_bound_dev<W>(din, dout, i, j), prod_len_bound<W>(BL, BR, pb, i, j) - 1));
+      for (int E = 0; E < WW; ++E) D = max(D, max(BL.lp(pb)[E], BR.lp(pb)[E]) - 1);  // operands fit the transform
       if (D >= P) set_status(status, ST_DEGREE);
-      for (int j = 0; j < 5; ++j) OUT.mp(pb)[j] = 0ULL;
+      for (int j = 0; j < W; ++j) OUT.mp(pb)[j] = 0ULL;
     }
-    const BasisBuf& B = b < 25 ? BL : BR;
-    int E = b < 25 ? b : b - 25;
+    const BasisBuf& B = b < WW ? BL : BR;
+    int E = b < WW ? b : b - WW;
     if (q >= B.lp(pb)[E]) return czero<C>();
-    return cfrom<C>(cscale(B.cp(pb)[E * B.cap + q], col_scale_from_bits(B.mp(pb)[E % 5])));
+    return cfrom<C>(cscale(B.cp(pb)[E * B.cap + q], col_scale_from_bits(B.mp(pb)[E % W])));
   }
 };
-template <class C>
+template <class C, int W>
 struct StoreSpec {
   C* FA;
   C* FB;
   int64_t P;
   __device__ void operator()(int t, int64_t k, C v) const {
-    int pb = t / 50, b = t % 50;
-    if (b < 25) FA[((int64_t)pb * 25 + b) * P + k] = v;
-    else FB[((int64_t)pb * 25 + b - 25) * P + k] = v;
+    constexpr int WW = W * W;
+    int pb = t / (2 * WW), b = t % (2 * WW);
+    if (b < WW) FA[((int64_t)pb * WW + b) * P + k] = v;
+    else FB[((int64_t)pb * WW + b - WW) * P + k] = v;
   }
 };
 template <class C>
@@ -243,18 +258,19 @@ struct StorePlain2 {
   int64_t P;
   __device__ void operator()(int t, int64_t k, C v) const { out[(int64_t)t * P + k] = v; }
 };
-template <class C>
-struct LoadProduct {  // transform t = 25 pb + 5i + j: sum_u FA[5i+u] FB[5u+j]
+template <class C, int W>
+struct LoadProduct {  // transform t = W^2 pb + W i + j: sum_u FA[W i + u] FB[W u + j]
   const C* FA;
   const C* FB;
   int64_t P;
   __device__ C operator()(int t, int64_t q) const {
-    int pb = t / 25, e = t % 25, i = e / 5, j = e % 5;
-    const C* a = FA + (int64_t)pb * 25 * P;
-    const C* b = FB + (int64_t)pb * 25 * P;
+    constexpr int WW = W * W;
+    int pb = t / WW, e = t % WW, i = e / W, j = e % W;
+    const C* a = FA + (int64_t)pb * WW * P;
+    const C* b = FB + (int64_t)pb * WW * P;
     C acc = czero<C>();
 #pragma unroll
-    for (int u = 0; u < 5; ++u) acc = cfma(a[(int64_t)(5 * i + u) * P + q], b[(int64_t)(5 * u + j) * P + q], acc);
+    for (int u = 0; u < W; ++u) acc = cfma(a[(int64_t)(W * i + u) * P + q], b[(int64_t)(W * u + j) * P + q], acc);
     return acc;
   }
 };
@@ -268,17 +284,17 @@ __device__ __forceinline__ unsigned long long absmax_bits(cd v) {
 }
 
 // trim to the degree bounds, scale by 1/P (in FP64), record column maxima and lengths
-template <class C>
+template <class C, int W>
 __global__ void k_prod_finish(const C* __restrict__ FC, int64_t P, BasisBuf BL, BasisBuf BR, BasisBuf OUT,
                               const int* dstack, int depth, const int* delta, int* status) {
-  const int E = blockIdx.y, i = E / 5, j = E % 5, pb = blockIdx.z;
+  const int E = blockIdx.y, i = E / W, j = E % W, pb = blockIdx.z;
   __shared__ int want_s;
   __shared__ unsigned long long red[32];
   pdl_enter();
   if (threadIdx.x == 0) {
-    int bnd = entry_bound_dev(dstack + (pb * MAX_DEPTH + depth) * 5, delta + 8 * pb, i, j);
+    int bnd = entry_bound_dev<W>(dstack + (pb * MAX_DEPTH + depth) * DSTR, delta + DSTR * pb, i, j);
     int64_t want = bnd < 0 ? 0 : (int64_t)bnd + 1;
-    want = min(want, (int64_t)prod_len_bound(BL, BR, pb, i, j));
+    want = min(want, (int64_t)prod_len_bound<W>(BL, BR, pb, i, j));
     if (want > P) want = P;
     if (want > OUT.cap) { set_status(status, ST_DEGREE); want = OUT.cap; }
     want_s = (int)want;
@@ -287,7 +303,7 @@ __global__ void k_prod_finish(const C* __restrict__ FC, int64_t P, BasisBuf BL, 
   __syncthreads();
   const int64_t want = want_s;
   const double inv = 1.0 / (double)P;
-  const C* src = FC + ((int64_t)pb * 25 + E) * P;
+  const C* src = FC + ((int64_t)pb * (W * W) + E) * P;
   cd* dst = OUT.cp(pb) + (int64_t)E * OUT.cap;
   unsigned long long mx = 0ULL;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < want; t += (int64_t)gridDim.x * blockDim.x) {
@@ -316,22 +332,23 @@ __global__ void k_prod_finish(const C* __restrict__ FC, int64_t P, BasisBuf BL, 
 // column j of B_R are staged in shared memory with their column scales applied.  Output trimmed to
 // the degree bound; column maxima accumulated (reset by this node's evaluation step).
 constexpr int PD_TC = 8;
+template <int W>
 __global__ void __launch_bounds__(32 * PD_TC) k_prod_direct(BasisBuf BL, BasisBuf BR, BasisBuf OUT, const int* dstack,
                                                              int depth, const int* delta, int* status, int ntile) {
-  extern __shared__ cd pd_sh[];  // A: 5 x BL.cap, then B: 5 x BR.cap
+  extern __shared__ cd pd_sh[];  // A: W x BL.cap, then B: W x BR.cap
   const int E = blockIdx.x / ntile, tile = blockIdx.x % ntile;
-  const int i = E / 5, j = E % 5, pb = blockIdx.y, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  __shared__ int want_s, ll[5], lr[5];
+  const int i = E / W, j = E % W, pb = blockIdx.y, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  __shared__ int want_s, ll[W], lr[W];
   __shared__ double red[PD_TC];
   pdl_enter();
-  if (tid < 5) {
-    ll[tid] = BL.lp(pb)[i * 5 + tid];
-    lr[tid] = BR.lp(pb)[tid * 5 + j];
+  if (tid < W) {
+    ll[tid] = BL.lp(pb)[i * W + tid];
+    lr[tid] = BR.lp(pb)[tid * W + j];
   }
   if (tid == 0) {
-    int bnd = entry_bound_dev(dstack + (pb * MAX_DEPTH + depth) * 5, delta + 8 * pb, i, j);
+    int bnd = entry_bound_dev<W>(dstack + (pb * MAX_DEPTH + depth) * DSTR, delta + DSTR * pb, i, j);
     int want = bnd < 0 ? 0 : bnd + 1;
-    want = min(want, prod_len_bound(BL, BR, pb, i, j));
+    want = min(want, prod_len_bound<W>(BL, BR, pb, i, j));
     if (want > OUT.cap) { set_status(status, ST_DEGREE); want = (int)OUT.cap; }
     want_s = want;
     if (tile == 0) OUT.lp(pb)[E] = want;
@@ -342,24 +359,24 @@ __global__ void __launch_bounds__(32 * PD_TC) k_prod_direct(BasisBuf BL, BasisBu
   const int tmax = min(want, t0 + PD_TC);
   const int capL = (int)BL.cap, capR = (int)BR.cap;
   cd* As = pd_sh;
-  cd* Bs = pd_sh + 5 * capL;
-  for (int idx = tid; idx < 5 * capL; idx += blockDim.x) {
+  cd* Bs = pd_sh + W * capL;
+  for (int idx = tid; idx < W * capL; idx += blockDim.x) {
     const int u = idx / capL, q = idx - u * capL;
     if (q < min(ll[u], tmax))
-      As[idx] = cscale(BL.cp(pb)[(int64_t)(i * 5 + u) * capL + q], col_scale_from_bits(BL.mp(pb)[u]));
+      As[idx] = cscale(BL.cp(pb)[(int64_t)(i * W + u) * capL + q], col_scale_from_bits(BL.mp(pb)[u]));
   }
   const double sr = col_scale_from_bits(BR.mp(pb)[j]);
-  for (int idx = tid; idx < 5 * capR; idx += blockDim.x) {
+  for (int idx = tid; idx < W * capR; idx += blockDim.x) {
     const int u = idx / capR, q = idx - u * capR;
-    if (q < min(lr[u], tmax)) Bs[idx] = cscale(BR.cp(pb)[(int64_t)(u * 5 + j) * capR + q], sr);
+    if (q < min(lr[u], tmax)) Bs[idx] = cscale(BR.cp(pb)[(int64_t)(u * W + j) * capR + q], sr);
   }
   __syncthreads();
   double mx = 0.0;
   const int t = t0 + w;
   if (t < tmax) {  // warp-uniform
-    int lo[5], pre[5], tot = 0;
+    int lo[W], pre[W], tot = 0;
 #pragma unroll
-    for (int u = 0; u < 5; ++u) {
+    for (int u = 0; u < W; ++u) {
       lo[u] = max(0, t - lr[u] + 1);
       const int hi = min(t, ll[u] - 1);
       pre[u] = tot;
@@ -369,7 +386,7 @@ __global__ void __launch_bounds__(32 * PD_TC) k_prod_direct(BasisBuf BL, BasisBu
     for (int k = lane; k < tot; k += 32) {
       int u = 0, base = 0, l0 = lo[0];
 #pragma unroll
-      for (int v = 1; v < 5; ++v)
+      for (int v = 1; v < W; ++v)
         if (k >= pre[v]) { u = v; base = pre[v]; l0 = lo[v]; }
       const int q = l0 + (k - base);
       acc = cfma(As[u * capL + q], Bs[u * capR + (t - q)], acc);
@@ -392,41 +409,48 @@ __global__ void __launch_bounds__(32 * PD_TC) k_prod_direct(BasisBuf BL, BasisBu
   }
 }
 
-// step 4 by length-P transforms in precision C: the 50 operand spectra, 25 pointwise products of 5 terms,
-// 25 inverse transforms, then the FP64 trim / scale / column maxima
-template <class C>
+// step 4 by length-P transforms in precision C: the 2 W^2 operand spectra, W^2 pointwise products of W
+// terms, W^2 inverse transforms, then the FP64 trim / scale / column maxima
+template <class C, int W>
 static int launch_prod_fft(Plan& P, const Step& st, const BasisBuf& BL, const BasisBuf& BR, const BasisBuf& OUT) {
+  constexpr int WW = W * W;
   const FftPlan& F = P.ffts[st.fft];
   C* FA = reinterpret_cast<C*>(P.FA);
   C* FB = reinterpret_cast<C*>(P.FB);
   C* FC = reinterpret_cast<C*>(P.FC);
   C* tmp = reinterpret_cast<C*>(P.ptmp);
   int nl = 0, r;
-  LoadPad<C> lp{BL, BR, OUT, P.dstack, P.delta, st.depth, P.status, st.P};
-  if ((r = fft_run(F, 50 * P.nb, +1, lp, StoreSpec<C>{FA, FB, st.P}, tmp, P.stream)) < 0) return TIKH_ECUDA;
+  LoadPad<C, W> lp{BL, BR, OUT, P.dstack, P.delta, st.depth, P.status, st.P};
+  if ((r = fft_run(F, 2 * WW * P.nb, +1, lp, StoreSpec<C, W>{FA, FB, st.P}, tmp, P.stream)) < 0) return TIKH_ECUDA;
   nl += r;
-  if ((r = fft_run(F, 25 * P.nb, -1, LoadProduct<C>{FA, FB, st.P}, StorePlain2<C>{FC, st.P}, tmp, P.stream)) < 0)
+  if ((r = fft_run(F, WW * P.nb, -1, LoadProduct<C, W>{FA, FB, st.P}, StorePlain2<C>{FC, st.P}, tmp, P.stream)) < 0)
     return TIKH_ECUDA;
   nl += r;
   int bx = (int)std::min<int64_t>((st.P + 255) / 256, 64);
-  launch_k(pdl_enabled(), k_prod_finish<C>, dim3(bx, 25, P.nb), dim3(256), 0, P.stream, (const C*)FC, st.P, BL, BR, OUT,
-           (const int*)P.dstack, st.depth, (const int*)P.delta, P.status);
+  launch_k(pdl_enabled(), k_prod_finish<C, W>, dim3(bx, WW, P.nb), dim3(256), 0, P.stream, (const C*)FC, st.P, BL, BR,
+           OUT, (const int*)P.dstack, st.depth, (const int*)P.delta, P.status);
   if (cudaGetLastError() != cudaSuccess) return TIKH_ECUDA;
   return nl + 1;
 }
 
-int launch_prod(Plan& P, const Step& st) {
+template <int W>
+static int launch_prod_t(Plan& P, const Step& st) {
   const BasisBuf& BL = P.buf[st.depth + 1][0];
   const BasisBuf& BR = P.buf[st.depth + 1][1];
   const BasisBuf& OUT = P.buf[st.depth][st.side];
-  const size_t smem = sizeof(cd) * 5 * (size_t)(BL.cap + BR.cap);
+  const size_t smem = sizeof(cd) * W * (size_t)(BL.cap + BR.cap);
   if (st.P <= P.prod_direct_max && smem <= 48 * 1024) {
     const int ntile = (int)((st.P + PD_TC - 1) / PD_TC);
-    launch_k(pdl_enabled(), k_prod_direct, dim3(25 * ntile, P.nb), dim3(32 * PD_TC), smem, P.stream, BL, BR, OUT,
-             (const int*)P.dstack, st.depth, (const int*)P.delta, P.status, ntile);
+    launch_k(pdl_enabled(), k_prod_direct<W>, dim3(W * W * ntile, P.nb), dim3(32 * PD_TC), smem, P.stream, BL, BR,
+             OUT, (const int*)P.dstack, st.depth, (const int*)P.delta, P.status, ntile);
     return cudaGetLastError() == cudaSuccess ? 1 : TIKH_ECUDA;
   }
-  return P.stage32 ? launch_prod_fft<cf>(P, st, BL, BR, OUT) : launch_prod_fft<cd>(P, st, BL, BR, OUT);
+  if constexpr (W == 5) {
+    if (P.stage32) return launch_prod_fft<cf, W>(P, st, BL, BR, OUT);
+  }
+  return launch_prod_fft<cd, W>(P, st, BL, BR, OUT);
 }
+
+int launch_prod(Plan& P, const Step& st) { return P.w == 7 ? launch_prod_t<7>(P, st) : launch_prod_t<5>(P, st); }
 
 }  // namespace tikh

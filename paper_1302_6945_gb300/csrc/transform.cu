@@ -10,6 +10,12 @@
 // lamH_e = omega^{e(k-1)} conj(that_e) (the T^H generator's DFT, obtained in O(N) as in Sec. 7.3),
 // yhat = DFT of -y placed after cm+k-1 zeros.
 //
+// General problem (Sec. 3.2, reading: all three block rows extended to the same N): unknowns
+// [x (n), sigma_1 (m), sigma_2 (pl), gamma_1 (N-n), gamma_2 (N-m), gamma_3 (N-pl), 1] and
+//   F_e = [0, lamH_e, lamLH_e, 1, 0, 0, yhat_e],  G_e = [-that_e, omega^{e(N-m)}, 0, 0, 1, 0, 0],
+//   H_e = [-lhat_e, 0, omega^{e(N-pl)}, 0, 0, 1, 0]
+// with lhat the DFT of L's generator (extension kl = N - (pl + n - 1)) and lamLH_e = omega^{e(kl-1)} conj(lhat_e).
+//
 // Length-N transforms run one transform per item (transform index = item index pb).  Every size that
 // belongs to a problem (m, n, cm, cn, k) and its user arrays are read from the item table
 // (ItemDev[pb]), so one launch serves items of different shapes that share N; per-item buffers of
@@ -77,8 +83,13 @@ __device__ __forceinline__ double splitmix_uniform(unsigned long long c) {
 // peak = max over the known diagonals of max(|Re|, |Im|)  (exact, order independent); and the input
 // check: a non-finite diagonal or right-hand-side entry marks the item (bad[pb] = 1, whose leaves then
 // process no condition) and the call (ST_INPUT), so no kernel iterates on NaN or Inf
+// diagonal d of an item's regulariser L (general plans; d in [-(n-1), pl-1])
+__device__ __forceinline__ cd l_diag(const ItemDev& it, int64_t d, int dtype) {
+  return d >= 0 ? load_user(it.lcol, d, dtype) : load_user(it.lrow, -d, dtype);
+}
+
 __global__ void k_peak(const ItemDev* __restrict__ items, int dtype, int rhs_is_y, unsigned long long* peak, int* bad,
-                       int* status, unsigned long long* peakG) {
+                       int* status, unsigned long long* peakG, unsigned long long* peakL) {
   const int pb = blockIdx.y;
   const ItemDev it = items[pb];
   double mx = 0.0;
@@ -107,6 +118,17 @@ __global__ void k_peak(const ItemDev* __restrict__ items, int dtype, int rhs_is_
     for (int o = 16; o > 0; o >>= 1) mg = fmax(mg, __shfl_xor_sync(0xffffffffu, mg, o));
     if ((threadIdx.x & 31) == 0 && mg > 0.0) atomicMax(peakG + pb, (unsigned long long)__double_as_longlong(mg));
   }
+  if (it.lcol) {  // general problem: L's diagonals, its own fill magnitude
+    double ml = 0.0;
+    const int64_t tl = it.pl + it.cn - 1;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tl; i += (int64_t)gridDim.x * blockDim.x) {
+      cd v = l_diag(it, i - (it.cn - 1), dtype);
+      fin = fin && isfinite(v.x) && isfinite(v.y);
+      ml = fmax(ml, fmax(fabs(v.x), fabs(v.y)));
+    }
+    for (int o = 16; o > 0; o >>= 1) ml = fmax(ml, __shfl_xor_sync(0xffffffffu, ml, o));
+    if ((threadIdx.x & 31) == 0 && ml > 0.0) atomicMax(peakL + pb, (unsigned long long)__double_as_longlong(ml));
+  }
   if (!fin) {
     bad[pb] = 1;
     set_status(status, ST_INPUT);
@@ -134,6 +156,32 @@ struct LoadGenerator {
     double pk = __longlong_as_double((long long)peak[pb]);
     double re = pk * splitmix_uniform((unsigned long long)(2 * i));
     double im = dtype == TIKH_C128 ? pk * splitmix_uniform((unsigned long long)(2 * i + 1)) : 0.0;
+    return mkc(re, im);
+  }
+};
+// general plans: c_L[j] = l_{j-(n+kl-1)} over L's N-periodic sequence; the kl entries l_{pl-1+i} are the
+// fill, as T's (R5) but from L's own peak and with counters offset by 2^41
+struct LoadLGenerator {
+  const ItemDev* items;
+  int64_t N;
+  int fill, dtype;
+  const unsigned long long* peakL;
+  __device__ cd operator()(int pb, int64_t j) const {
+    const ItemDev& it = items[pb];
+    const int64_t pl = it.pl, n = it.cn, kl = it.kl;
+    int64_t d = ((j - (n + kl - 1)) % N + N) % N;
+    if (d <= pl - 1) return l_diag(it, d, dtype);
+    if (d >= N - (n - 1)) return l_diag(it, d - N, dtype);
+    int64_t i = d - (pl - 1);  // 1..kl
+    if (fill == 1) {
+      cd lo = l_diag(it, -(n - 1), dtype), hi = l_diag(it, pl - 1, dtype);
+      double f = (double)i / (double)(kl + 1);
+      return mkc(hi.x + (lo.x - hi.x) * f, hi.y + (lo.y - hi.y) * f);
+    }
+    const double pk = __longlong_as_double((long long)peakL[pb]);
+    const unsigned long long off = 1ULL << 41;
+    const double re = pk * splitmix_uniform((unsigned long long)(2 * i) + off);
+    const double im = dtype == TIKH_C128 ? pk * splitmix_uniform((unsigned long long)(2 * i + 1) + off) : 0.0;
     return mkc(re, im);
   }
 };
@@ -276,24 +324,68 @@ struct StoreConditions {
   }
 };
 
-__global__ void k_reset_peak(unsigned long long* peak, int* bad, unsigned long long* peakG, int nb) {
+// conditions F_e, G_e, H_e of the general problem into R and Phi (21 entries per node)
+struct StoreConditionsGeneral {
+  cd* R;
+  cd* Phi;
+  const cd* that;
+  const cd* lhat;
+  const cd* wN;
+  const ItemDev* items;
+  int64_t N;
+  __device__ void operator()(int pb, int64_t e, cd yh) const {
+    const ItemDev& it = items[pb];
+    const int64_t m = it.cm, n = it.cn, pl = it.pl, k = it.k, kl = it.kl;
+    const cd th = that[pb * N + e], lh = lhat[pb * N + e];
+    const cd tH = cmul(tw_at(wN, ((e * (k - 1)) % N + N) % N), cconj(th));
+    const cd lH = cmul(tw_at(wN, ((e * (kl - 1)) % N + N) % N), cconj(lh));
+    const cd wG = tw_at(wN, (e * (N - m)) % N), wH = tw_at(wN, (e * (N - pl)) % N);
+    const cd z = mkc(0.0, 0.0), one = mkc(1.0, 0.0);
+    (void)n;
+    cd row[21] = {z, tH, lH, one, z, z, yh,
+                  mkc(-th.x, -th.y), wG, z, z, one, z, z,
+                  mkc(-lh.x, -lh.y), z, wH, z, z, one, z};
+    const int64_t base = (pb * N + e) * 21;
+#pragma unroll
+    for (int i = 0; i < 21; ++i) {
+      R[base + i] = row[i];
+      Phi[base + i] = row[i];
+    }
+  }
+};
+
+__global__ void k_reset_peak(unsigned long long* peak, int* bad, unsigned long long* peakG, unsigned long long* peakL,
+                             int nb) {
   for (int i = threadIdx.x; i < nb; i += blockDim.x) {
     peak[i] = 0ULL;
     bad[i] = 0;
     if (peakG) peakG[i] = 0ULL;
+    if (peakL) peakL[i] = 0ULL;
   }
 }
-// Eq. (taudef) with tau = [cn-1, cm-1, cm+k-2, cn+k-2, 0] (reading R3); the starting basis I has
-// tau-degrees delta = -tau
-__global__ void k_reset_tree(const ItemDev* __restrict__ items, int* delta, int* ndiff, int nb) {
+// Eq. (taudef) with tau = [cn-1, cm-1, cm+k-2, cn+k-2, 0] (reading R3), or for the general problem
+// tau = [n-1, m-1, pl-1, N-n-1, N-m-1, N-pl-1, 0] (tau_i + 1 = the length of unknown i); the starting
+// basis I has tau-degrees delta = -tau
+__global__ void k_reset_tree(const ItemDev* __restrict__ items, int* delta, int* ndiff, int nb, int general,
+                             int64_t N) {
   for (int pb = threadIdx.x; pb < nb; pb += blockDim.x) {
     const ItemDev& it = items[pb];
-    int* d = delta + 8 * pb;
-    d[0] = -(int)(it.cn - 1);
-    d[1] = -(int)(it.cm - 1);
-    d[2] = -(int)(it.cm + it.k - 2);
-    d[3] = -(int)(it.cn + it.k - 2);
-    d[4] = 0;
+    int* d = delta + DSTR * pb;
+    if (general) {
+      d[0] = -(int)(it.cn - 1);
+      d[1] = -(int)(it.cm - 1);
+      d[2] = -(int)(it.pl - 1);
+      d[3] = -(int)(N - it.cn - 1);
+      d[4] = -(int)(N - it.cm - 1);
+      d[5] = -(int)(N - it.pl - 1);
+      d[6] = 0;
+    } else {
+      d[0] = -(int)(it.cn - 1);
+      d[1] = -(int)(it.cm - 1);
+      d[2] = -(int)(it.cm + it.k - 2);
+      d[3] = -(int)(it.cn + it.k - 2);
+      d[4] = 0;
+    }
     ndiff[4 * pb] = 0;
   }
 }
@@ -306,10 +398,10 @@ static inline dim3 grid2(int64_t n, int nb, int threads = 256, int cap = 4096) {
 int launch_spectrum(Plan& P, int rhs_is_y) {
   cudaStream_t s = P.stream;
   int nl = 0, r;
-  k_reset_peak<<<1, 256, 0, s>>>(P.peak, P.bad, P.peakG, P.nb);
+  k_reset_peak<<<1, 256, 0, s>>>(P.peak, P.bad, P.peakG, P.peakL, P.nb);
   ++nl;
-  k_peak<<<grid2(std::max(P.cm + P.cn, P.m), P.nb, 256, 1024), 256, 0, s>>>(P.items, P.dtype, rhs_is_y, P.peak, P.bad,
-                                                                            P.status, P.peakG);
+  k_peak<<<grid2(std::max(std::max(P.cm + P.cn, P.m), P.pl + P.cn), P.nb, 256, 1024), 256, 0, s>>>(
+      P.items, P.dtype, rhs_is_y, P.peak, P.bad, P.status, P.peakG, P.peakL);
   ++nl;
   if (cudaGetLastError() != cudaSuccess) return TIKH_ECUDA;
   const FftPlan& FN = P.ffts[P.fft_of_len.at(P.N)];
@@ -319,6 +411,11 @@ int launch_spectrum(Plan& P, int rhs_is_y) {
   if (P.gram) {  // DFT of G's circulant generator (F's x component, Sec. 3.4)
     LoadGramGenerator lgg{P.items, P.N, P.opts.fill, P.dtype, P.peakG};
     if ((r = fft_run(FN, P.nb, +1, lgg, StoreVec{P.specG, P.N}, P.ftmpN, s)) < 0) return TIKH_ECUDA;
+    nl += r;
+  }
+  if (P.general) {  // DFT of L's circulant generator (Sec. 3.2)
+    LoadLGenerator llg{P.items, P.N, P.opts.fill, P.dtype, P.peakL};
+    if ((r = fft_run(FN, P.nb, +1, llg, StoreVec{P.specL, P.N}, P.ftmpN, s)) < 0) return TIKH_ECUDA;
     nl += r;
   }
   return nl;
@@ -353,37 +450,46 @@ int launch_rhs(Plan& P, int rhs_is_y) {
   return nl + r;
 }
 
-// conditions F, G of the core system with right-hand side y (Sec. 3.3, 4.1); resets the degrees
+// conditions F, G (and H for the general problem) of the core system with right-hand side y (Sec. 3.2,
+// 3.3, 4.1); resets the degrees
 int launch_conditions(Plan& P, const cd* y) {
   cudaStream_t s = P.stream;
   const int64_t N = P.N;
-  k_reset_tree<<<1, 256, 0, s>>>(P.items, P.delta, P.ndiff, P.nb);
+  k_reset_tree<<<1, 256, 0, s>>>(P.items, P.delta, P.ndiff, P.nb, P.general, N);
   const FftPlan& FN = P.ffts[P.fft_of_len.at(N)];
-  StoreConditions sc{P.R, P.Phi, P.specT, P.wN, P.lam, P.items, P.gram ? P.specG : nullptr, N};
-  int r = fft_run(FN, P.nb, +1, LoadPlaceNegY{y, P.items, P.cn}, sc, P.ftmpN, s);
+  int r;
+  if (P.general) {
+    StoreConditionsGeneral sc{P.R, P.Phi, P.specT, P.specL, P.wN, P.items, N};
+    r = fft_run(FN, P.nb, +1, LoadPlaceNegY{y, P.items, P.cn}, sc, P.ftmpN, s);
+  } else {
+    StoreConditions sc{P.R, P.Phi, P.specT, P.wN, P.lam, P.items, P.gram ? P.specG : nullptr, N};
+    r = fft_run(FN, P.nb, +1, LoadPlaceNegY{y, P.items, P.cn}, sc, P.ftmpN, s);
+  }
   if (r < 0) return TIKH_ECUDA;
   return r + 1;
 }
 
 // ------------------------------------------------------------------------------------------------
-// extraction: x(z) = B*_1^{(j)}(z) / B*_5^{(j)}, j the column of tau-degree 0 (Sec. 4.3 end, 5)
+// extraction: x(z) = B*_1^{(j)}(z) / B*_W^{(j)}, j the column of tau-degree 0 (Sec. 4.3 end, 5)
 // ------------------------------------------------------------------------------------------------
+template <int W>
 __global__ void k_extract(BasisBuf B, const int* delta, int* status, const ItemDev* __restrict__ items, int64_t stride,
                           cd* out) {
   const int pb = blockIdx.y;
   const int64_t cn = items[pb].cn;
-  const int* dl = delta + 8 * pb;
+  const int* dl = delta + DSTR * pb;
   int js = -1, nz = 0, no = 0;
-  for (int j = 0; j < 5; ++j) {
+  for (int j = 0; j < W; ++j) {
     int d = dl[j];
     if (d == 0) { js = j; ++nz; } else if (d == 1) ++no;
   }
-  bool ok = nz == 1 && no == 4;
+  bool ok = nz == 1 && no == W - 1;
   cd c5 = mkc(0.0, 0.0);
   const cd* c = B.cp(pb);
   const int* len = B.lp(pb);
   if (ok) {
-    if (len[20 + js] >= 1) c5 = c[(int64_t)(20 + js) * B.cap];
+    const int last = W * (W - 1) + js;
+    if (len[last] >= 1) c5 = c[(int64_t)last * B.cap];
     ok = cnonzero(c5);
   }
   if (!ok) {
@@ -402,7 +508,10 @@ __global__ void k_extract(BasisBuf B, const int* delta, int* status, const ItemD
 }
 
 int launch_extract(Plan& P, cd* out) {
-  k_extract<<<grid2(P.cn, P.nb, 256, 2048), 256, 0, P.stream>>>(P.buf[0][0], P.delta, P.status, P.items, P.cn, out);
+  if (P.w == 7)
+    k_extract<7><<<grid2(P.cn, P.nb, 256, 2048), 256, 0, P.stream>>>(P.buf[0][0], P.delta, P.status, P.items, P.cn, out);
+  else
+    k_extract<5><<<grid2(P.cn, P.nb, 256, 2048), 256, 0, P.stream>>>(P.buf[0][0], P.delta, P.status, P.items, P.cn, out);
   return cudaGetLastError() == cudaSuccess ? 1 : TIKH_ECUDA;
 }
 
@@ -491,6 +600,49 @@ struct StoreMulTKeep {
   }
 };
 
+// general plans: X = DFT([x; 0]) (kept in gX) times L's spectrum, inverse, keep the window of L x
+struct LoadMulSpec {
+  const cd* X;
+  const cd* spec;
+  int64_t N;
+  __device__ cd operator()(int pb, int64_t j) const { return cmul(X[pb * N + j], spec[pb * N + j]); }
+};
+// keep the inverse-transform window [n + kl - 1, N) (L x) scaled at its own index, zero before
+struct StoreKeepFromL {
+  cd* out;
+  const ItemDev* items;
+  int64_t N;
+  double scale;
+  __device__ void operator()(int pb, int64_t j, cd v) const {
+    const int64_t off = items[pb].cn + items[pb].kl - 1;
+    out[pb * N + j] = j >= off ? cscale(v, scale) : mkc(0.0, 0.0);
+  }
+};
+// [w; 0] with w = in[n + kl - 1 .. n + kl - 1 + pl) (L x)
+struct LoadShiftL {
+  const cd* in;
+  const ItemDev* items;
+  int64_t N;
+  __device__ cd operator()(int pb, int64_t j) const {
+    const ItemDev& it = items[pb];
+    return j < it.pl ? in[pb * N + it.cn + it.kl - 1 + j] : mkc(0.0, 0.0);
+  }
+};
+// out += spectrum times lamLH_e = omega^{e(kl-1)} conj(lhat_e)  (L^H applied in the transform domain)
+struct StoreAddMulLamLH {
+  cd* out;
+  const cd* lhat;
+  const cd* wN;
+  const ItemDev* items;
+  int64_t N;
+  __device__ void operator()(int pb, int64_t e, cd v) const {
+    const int64_t kl = items[pb].kl;
+    const int64_t t = ((e * (kl - 1)) % N + N) % N;
+    const int64_t i = pb * N + e;
+    out[i] = cfma(v, cmul(tw_at(wN, t), cconj(lhat[i])), out[i]);
+  }
+};
+
 int launch_residual(Plan& P, const cd* y, const cd* x, cd* r) {
   cudaStream_t s = P.stream;
   const int64_t N = P.N;
@@ -499,7 +651,7 @@ int launch_residual(Plan& P, const cd* y, const cd* x, cd* r) {
   k_zero_norms<<<1, 256, 0, s>>>(P.norms, P.nb, 0);
   ++nl;
   // u = T_c x: rows cn+k-1.. of circ(c_T) [x; 0]
-  if (P.gram)
+  if (P.gram || P.general)
     q = fft_run(FN, P.nb, +1, LoadPadCn{x, P.items, P.cn}, StoreMulTKeep{P.work, P.gX, P.specT, N}, P.ftmpN, s);
   else
     q = fft_run(FN, P.nb, +1, LoadPadCn{x, P.items, P.cn}, StoreMulT{P.work, P.specT, N}, P.ftmpN, s);
@@ -518,6 +670,16 @@ int launch_residual(Plan& P, const cd* y, const cd* x, cd* r) {
                 P.ftmpN, s);
   if (q < 0) return TIKH_ECUDA;
   nl += q;
+  if (P.general) {  // + L^H L x: rows n+kl-1.. of circ(c_L) [x; 0], then L^H by lamLH, added to T^H T x
+    if ((q = fft_run(FN, P.nb, -1, LoadMulSpec{P.gX, P.specL, N}, StoreKeepFromL{P.work2, P.items, N, 1.0 / (double)N},
+                     P.ftmpN, s)) < 0)
+      return TIKH_ECUDA;
+    nl += q;
+    if ((q = fft_run(FN, P.nb, +1, LoadShiftL{P.work2, P.items, N}, StoreAddMulLamLH{P.work, P.specL, P.wN, P.items, N},
+                     P.ftmpN, s)) < 0)
+      return TIKH_ECUDA;
+    nl += q;
+  }
   StoreResidual sr{r, y, x, P.lam, P.items, P.cn, 1.0 / (double)N, P.norms};
   if ((q = fft_run(FN, P.nb, -1, LoadVec{P.work, N}, sr, P.ftmpN, s)) < 0) return TIKH_ECUDA;
   return nl + q;

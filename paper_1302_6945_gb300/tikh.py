@@ -29,7 +29,7 @@ class tikh_opts(ctypes.Structure):
 
 class tikh_stats(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int64), ("M", ctypes.c_int64), ("k", ctypes.c_int64), ("p", ctypes.c_int),
-                ("dual", ctypes.c_int), ("n_difficult", ctypes.c_int64), ("delta", ctypes.c_int * 5),
+                ("dual", ctypes.c_int), ("n_difficult", ctypes.c_int64), ("delta", ctypes.c_int * 7),
                 ("jstar", ctypes.c_int), ("retries", ctypes.c_int), ("kernel_launches", ctypes.c_int64),
                 ("workspace_bytes", ctypes.c_int64), ("refine_steps", ctypes.c_int), ("rel_residual", ctypes.c_double),
                 ("batch", ctypes.c_int), ("prof_leaf_ms", ctypes.c_double), ("prof_leaf_launches", ctypes.c_int64),
@@ -72,7 +72,9 @@ EXPORTED = ["tikh_plan_create", "tikh_solve", "tikh_solve_async", "tikh_solve_no
             "tikh_batch_plan_destroy", "tikh_test_fft32", "tikh_batch_set_profiling", "tikh_plan_create_gramian",
             "tikh_solve_gramian", "tikh_nufft_gramian", "tikh_test_rcp", "tikh_solve_grad_strided",
             "tikh_sync", "tikh_get_stats", "tikh_plan_destroy", "tikh_strerror", "tikh_test_fft", "tikh_test_leaf",
-            "tikh_fft_noalloc", "tikh_set_profiling", "tikh_solve_grad", "tikh_get_difficult", "tikh_test_peak"]
+            "tikh_fft_noalloc", "tikh_set_profiling", "tikh_solve_grad", "tikh_get_difficult", "tikh_test_peak",
+            "tikh_plan_create_general", "tikh_solve_general", "tikh_solve_general_normal",
+            "tikh_solve_general_strided"]
 
 
 def lib():
@@ -94,6 +96,10 @@ def lib():
         L.tikh_batch_get_stats.argtypes = [vp, ctypes.POINTER(tikh_batch_stats)]
         L.tikh_plan_create_gramian.argtypes = [ctypes.POINTER(vp), i64, i64, ci, ci, ctypes.POINTER(tikh_opts), vp]
         L.tikh_solve_gramian.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.tikh_plan_create_general.argtypes = [ctypes.POINTER(vp), i64, i64, i64, ci, ctypes.POINTER(tikh_opts), vp]
+        L.tikh_solve_general.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        L.tikh_solve_general_normal.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        L.tikh_solve_general_strided.argtypes = [vp, ci, vp, i64, vp, i64, vp, i64, vp, i64, vp, i64, vp, i64]
         L.tikh_nufft_gramian.argtypes = [i64, vp, vp, vp, i64, vp, vp, vp]
         L.tikh_batch_set_profiling.argtypes = [vp, ci]
         L.tikh_batch_plan_destroy.argtypes = [vp]
@@ -149,6 +155,29 @@ def tikh_plan_create_gramian(n, p, dtype=TIKH_R64, prec=TIKH_PREC_FP64, opts=Non
 
 def tikh_solve_gramian(plan, g, lcol, lrow, y, x):
     _check(lib().tikh_solve_gramian(plan, g, lcol, lrow, y, x), "tikh_solve_gramian")
+
+
+def tikh_plan_create_general(m, n, pl, dtype=TIKH_R64, opts=None, stream=0):
+    h = ctypes.c_void_p()
+    o = ctypes.byref(opts) if opts is not None else None
+    _check(lib().tikh_plan_create_general(ctypes.byref(h), int(m), int(n), int(pl), int(dtype), o,
+                                          ctypes.c_void_p(int(stream))), "tikh_plan_create_general")
+    return h
+
+
+def tikh_solve_general(plan, col, row, lcol, lrow, b, x):
+    _check(lib().tikh_solve_general(plan, col, row, lcol, lrow, b, x), "tikh_solve_general")
+
+
+def tikh_solve_general_normal(plan, col, row, lcol, lrow, y, x):
+    _check(lib().tikh_solve_general_normal(plan, col, row, lcol, lrow, y, x), "tikh_solve_general_normal")
+
+
+def tikh_solve_general_strided(plan, batch, col, col_stride, row, row_stride, lcol, lcol_stride, lrow, lrow_stride,
+                               b, b_stride, x, x_stride):
+    _check(lib().tikh_solve_general_strided(plan, int(batch), col, int(col_stride), row, int(row_stride), lcol,
+                                            int(lcol_stride), lrow, int(lrow_stride), b, int(b_stride), x,
+                                            int(x_stride)), "tikh_solve_general_strided")
 
 
 def tikh_nufft_gramian(K, f, w, X, n, g, y, stream=0):
@@ -462,7 +491,9 @@ class Plan:
         tikh_set_profiling(self.h, flags)
 
     def stats(self):
-        return tikh_get_stats(self.h)
+        d = tikh_get_stats(self.h)
+        d["delta"] = d["delta"][:getattr(self, "w", 5)]  # basis size: 5, or 7 for the general problem
+        return d
 
     def difficult(self):
         """(count, sorted ids 2e + f) of the conditions deferred in the last solve (problem 0)."""
@@ -512,6 +543,62 @@ class GramianPlan(Plan):
             x = torch.empty(self.n, dtype=y.dtype, device=y.device)
         p = lambda t: ctypes.c_void_p(t.data_ptr())
         tikh_solve_gramian(self.h, p(g), p(lcol), p(lrow), p(y), p(x))
+        return x
+
+
+class GeneralPlan(Plan):
+    """A plan for the general problem (Sec. 3.2): x = (T^H T + L^H L)^{-1} T^H b, T m x n, L pl x n Toeplitz."""
+
+    def __init__(self, m, n, pl, dtype="r64", n_lim=30, m_min=0, fill=0, eps_diff=1e-12, max_difficult=4096,
+                 refine_steps=0, batch=1, graph=False, prod_direct_max=0, eval_direct_max=0, wait_polls=0,
+                 refine_tol=0.0, fft_radix=0, fft_tile=0, stream=None):
+        import torch
+        self.m, self.n, self.pl = int(m), int(n), int(pl)
+        self.w = 7
+        self.dtype = TIKH_C128 if dtype in ("c128", TIKH_C128, torch.complex128) else TIKH_R64
+        self.batch = int(batch)
+        self.opts = tikh_opts(int(n_lim), int(m_min), int(fill), float(eps_diff), int(max_difficult),
+                              int(refine_steps), int(batch), 1 if graph else 0, int(prod_direct_max),
+                              int(eval_direct_max), int(wait_polls), float(refine_tol), int(fft_radix), int(fft_tile))
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        self.h = tikh_plan_create_general(self.m, self.n, self.pl, self.dtype, self.opts, handle)
+
+    def _check_args(self, pairs):
+        import torch
+        for t, ln in pairs:
+            if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
+                raise TypeError("expected contiguous CUDA tensors")
+            if _dtype_code(t) != self.dtype or t.shape[-1] != ln:
+                raise ValueError("tensor dtype/size does not match the plan")
+
+    def solve(self, col, row, lcol, lrow, b, x=None, normal=False):
+        """x = (T^H T + L^H L)^{-1} T^H b from contiguous CUDA tensors col (m), row (n), lcol (pl), lrow (n),
+        b (m); with normal=True the last argument is y (n) and x = (T^H T + L^H L)^{-1} y."""
+        import torch
+        self._check_args(((col, self.m), (row, self.n), (lcol, self.pl), (lrow, self.n),
+                          (b, self.n if normal else self.m)))
+        if x is None:
+            x = torch.empty(self.n, dtype=b.dtype, device=b.device)
+        p = lambda t: ctypes.c_void_p(t.data_ptr())
+        f = tikh_solve_general_normal if normal else tikh_solve_general
+        f(self.h, p(col), p(row), p(lcol), p(lrow), p(b), p(x))
+        return x
+
+    def solve_strided(self, col, row, lcol, lrow, b, x=None):
+        """A batch: col (B, m), row (B, n), lcol (B, pl), lrow (B, n), b (B, m) contiguous CUDA tensors (a 1-D
+        argument is shared by every problem, stride 0)."""
+        import torch
+        B = b.shape[0] if b.dim() == 2 else col.shape[0]
+        self._check_args(((col, self.m), (row, self.n), (lcol, self.pl), (lrow, self.n), (b, self.m)))
+        st = lambda t, ln: ln if t.dim() == 2 else 0
+        if x is None:
+            x = torch.empty((B, self.n), dtype=b.dtype, device=b.device)
+        p = lambda t: ctypes.c_void_p(t.data_ptr())
+        tikh_solve_general_strided(self.h, B, p(col), st(col, self.m), p(row), st(row, self.n), p(lcol),
+                                   st(lcol, self.pl), p(lrow), st(lrow, self.n), p(b), st(b, self.m), p(x), self.n)
         return x
 
 

@@ -139,7 +139,7 @@ def test_c5_batch_of_64_gradients_match_single_problem_adjoints():
 
 def test_autotune_picks_options_that_solve_correctly():
     opts, seen = tikh.autotune(700, 512, "r64", batch=2, reps=1)
-    assert len(seen) >= 3 and set(opts) == {"n_lim", "prod_direct_max", "eval_direct_max"}
+    assert len(seen) >= 3 and set(opts) == {"n_lim", "prod_direct_max", "eval_direct_max", "fft_radix", "fft_tile"}
     P = W.deconvolution_problem(700, 512, 3.0, 12, 1e-6, 1e-6, 1e-3, seed=9)
     plan = tikh.Plan(700, 512, "r64", **opts)
     x = plan.solve(t64(P["col"]), t64(P["row"]), t64(P["b"]), P["lam"]).cpu().numpy()
