@@ -7,9 +7,12 @@ every rank solves its own problem).  Inputs are resident in HBM when the timed r
 set (~1 GB) exceeds L2 and L2 is also flushed between steps.  e2e repeats the measurement through
 tikh_solve_host with host buffers (copies inside the timed region).  The default run also reports the
 metric's n sweep (n = 2^17 .. 2^20, m = 1.5 n, one FP64 refinement correction) under "sweep".
+The same run times one solve of the general problem (Sec. 3.2, T and L 65536 x 65536) under
+"general_problem".
 
 --config c3 runs the batching configuration instead: 512 real problems of uneven shape, each with a
 16-value regularisation path, as one ragged batch (tikh_solve_batched, one captured graph per call).
+--config general runs the general problem (Sec. 3.2) with square T and L as the main line.
 --precision selects FP64, FP32 stages, or FP32 stages with FP64 refinement.
 --impl reference times the CPU oracle (the paper's algorithm in plain C, FP64) on the host cores.
 """
@@ -277,7 +280,17 @@ def run_general(args, world, rank, local):
     col, row, lcol, lrow, b = t(P["col"]), t(P["row"]), t(P["lcol"]), t(P["lrow"]), t(P["b"])
     x = torch.empty(n, dtype=torch.float64, device=dev)
     stream = torch.cuda.Stream(device=dev)
-    plan = tikh.GeneralPlan(n, n, n, "r64", refine_steps=args.refine, graph=bool(args.graph), stream=stream)
+    plan = tikh.GeneralPlan(n, n, n, "r64", n_lim=args.n_lim, refine_steps=args.refine, graph=bool(args.graph),
+                            stream=stream)
+    if args.single:
+        with torch.cuda.stream(stream):
+            plan.solve(col, row, lcol, lrow, b, x)
+        torch.cuda.synchronize()
+        st = plan.stats()
+        print(json.dumps({"single_solve": True, "general": True, "N": st["N"], "p": st["p"], "M": st["M"],
+                          "kernel_launches": st["kernel_launches"]}))
+        plan.close()
+        return
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -343,7 +356,7 @@ def run_general(args, world, rank, local):
         y = toeplitz_mv_t(torch, col.cpu().to(torch.complex128), row.cpu().to(torch.complex128),
                           b.cpu().to(torch.complex128), True).numpy()
         t0 = time.perf_counter()
-        xo, _ = oracle.solve_general(P["col"], P["row"], P["lcol"], P["lrow"], y, nlim=30, is_complex=0)
+        xo, _ = oracle.solve_general(P["col"], P["row"], P["lcol"], P["lrow"], y, nlim=args.n_lim, is_complex=0)
         dt = time.perf_counter() - t0
         xg = x.cpu().numpy()
         cpu = {"value": 1.0 / dt, "unit": "solves/s", "cores": 1, "kind": "oracle",
@@ -355,7 +368,7 @@ def run_general(args, world, rank, local):
                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                "config": {"workload": "general problem (Sec. 3.2): min ||T x - b||^2 + ||L x||^2, T and L %d x %d "
                                       "real Toeplitz with standard-normal generators, b = T x_true" % (n, n),
-                          "m": n, "n": n, "pl": n, "N": st["N"], "p": st["p"], "M": st["M"],
+                          "m": n, "n": n, "pl": n, "N": st["N"], "p": st["p"], "M": st["M"], "n_lim": args.n_lim,
                           "refine_steps": args.refine, "cuda_graph": bool(st["graph"]),
                           "l2": "256 MB flush between steps"},
                "accuracy": {"rel_residual": rel_res, "n_difficult": st["n_difficult"]},
@@ -532,6 +545,34 @@ def sweep_point(tikh, torch, n, refine, args, stream, dev):
                              "correction at n = 2^20 against two)"}
 
 
+def general_point(tikh, torch, n, args, stream, dev):
+    """The general problem (Sec. 3.2) at T, L n x n: one warm-up (graph capture) and args.sweep_steps timed
+    solves, the normal-equation residual of the result."""
+    from paper_1302_6945_gb300 import workloads as W
+    P = W.general_problem(n, n, n, seed=20)
+    t = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)
+    col, row, lcol, lrow, b = t(P["col"]), t(P["row"]), t(P["lcol"]), t(P["lrow"]), t(P["b"])
+    x = torch.empty(n, dtype=torch.float64, device=dev)
+    plan = tikh.GeneralPlan(n, n, n, "r64", graph=True, stream=stream)
+    with torch.cuda.stream(stream):
+        plan.solve(col, row, lcol, lrow, b, x)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.sweep_steps):
+            plan.solve(col, row, lcol, lrow, b, x)
+        e1.record(stream)
+        e1.synchronize()
+    st = plan.stats()
+    ms = e0.elapsed_time(e1) / args.sweep_steps
+    res = general_residual_t(torch, col, row, lcol, lrow, b, x)
+    plan.close()
+    return {"problem": "general (Sec. 3.2): T and L %d x %d real Toeplitz, standard-normal generators" % (n, n),
+            "N": st["N"], "M": st["M"], "ms_per_solve": ms, "solves_per_s": 1e3 / ms,
+            "normal_eq_rel_residual": res, "n_difficult": st["n_difficult"],
+            "full_line": "bench.py --config general"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -542,7 +583,8 @@ def main():
                     help="c2 (default): the complex deconvolution solve; c3: the ragged batch of 512 problems x 16 "
                          "lambdas; general: the general problem (Sec. 3.2) with square T and L (--n, default 65536)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "fp32_refine"])
-    ap.add_argument("--n-lim", type=int, default=32)
+    ap.add_argument("--n-lim", type=int, default=None,
+                    help="leaf size limit N_lim (conditions per leaf): default 32, or 30 for --config general")
     ap.add_argument("--refine", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=None, help="sweep point: n unknowns, m = 1.5 n (default: c2)")
@@ -556,6 +598,8 @@ def main():
     ap.add_argument("--single", action="store_true",
                     help="build the plan, run one solve of the workload and exit (a short command for profiler captures)")
     args = ap.parse_args()
+    if args.n_lim is None:
+        args.n_lim = 30 if args.config == "general" else 32
     world, rank, local = dist_setup()
     if args.impl == "reference":
         return run_reference(args, world, rank)
@@ -723,6 +767,9 @@ def main():
         sweep = []
         for e in range(17, 21):
             sweep.append(sweep_point(tikh, torch, 1 << e, 1, args, stream, dev))
+    general = None
+    if rank == 0 and world == 1 and not args.no_sweep and args.n is None and B == 1 and args.precision == "fp64":
+        general = general_point(tikh, torch, 1 << 16, args, stream, dev)
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
@@ -755,6 +802,7 @@ def main():
                        / (t_max / 1e3) / 1e9 / pk.get("hbm_gbs", 6788.3)},
                "step_breakdown": breakdown,
                "sweep": sweep,
+               "general_problem": general,
                "cpu_baseline": cpu}
         print(json.dumps(out))
     plan.close()
