@@ -176,6 +176,38 @@ def c3_reference_sample(count=8, seed=11):
     return [(probs[i // len(lams)], float(lams[i % len(lams)])) for i in sorted(ids)], len(probs) * len(lams)
 
 
+def _oracle_item(item):
+    """One oracle solve of a batch item (a pool worker; the oracle is single-threaded); its time in s."""
+    import oracle
+    col, row, b, lam, n_lim = item
+    t0 = time.perf_counter()
+    oracle.solve(col, row, b, lam, nlim=n_lim, is_complex=0)
+    return time.perf_counter() - t0
+
+
+def c3_oracle_all_cores(n_lim, per_core=2, seed=11):
+    """The oracle on every host core, one item (problem, lambda) per process at a time: a bounded sample of
+    per_core x cores items of the batching configuration drawn uniformly; items / wall time (the slowest
+    items finish last, so this is below cores x the one-core rate)."""
+    import multiprocessing
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    sample, total = c3_reference_sample(count=min(per_core * cores, 8192), seed=seed)
+    items = [(P["col"], P["row"], P["b"], lam, n_lim) for P, lam in sample]
+    ctx = multiprocessing.get_context("spawn")  # safe after the process has used the GPU
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_item, [(P["col"][:64], P["row"][:64], P["b"][:64], lam, n_lim)
+                                for P, lam in sample[:cores]])  # workers up, oracle loaded
+        t0 = time.perf_counter()
+        per_item = pool.map(_oracle_item, sorted(items, key=lambda it: -len(it[0])), chunksize=1)
+        t = time.perf_counter() - t0
+    return {"value": len(items) / t, "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "cpu_seconds": sum(per_item), "wall_seconds": t,
+            "sample": "%d items (problem, lambda) drawn uniformly from the %d, one process per core, largest "
+                      "first" % (len(items), total)}
+
+
 def run_reference(args, world, rank):
     """The CPU oracle on the host cores, on this arm's workload and metric."""
     if rank != 0:
@@ -194,8 +226,10 @@ def run_reference(args, world, rank):
                 times.append(dt)
         t = sum(times) / len(times)
         v = len(sample) / t
+        allc = c3_oracle_all_cores(args.n_lim)
         cfg = {"workload": "c3: 512 real deconvolution problems, n log-uniform in [256, 65536], m = n + U[0, n/2], "
-                           "16-value lambda path 1e-6..1 (8192 solves)", "n_lim": args.n_lim}
+                           "16-value lambda path 1e-6..1 (8192 solves)", "n_lim": args.n_lim,
+               "all_cores": allc}
         out = {"metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference", "config": cfg,
@@ -471,6 +505,9 @@ def run_c3(args, world, rank, local):
     e2e_t = sum(e2e_times) / len(e2e_times)
     e2e_v = whole_job_rate(world, items, max_over_ranks(e2e_t, dev))
     p64, p32 = fma_peaks(tikh, stream.cuda_stream)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = c3_oracle_all_cores(args.n_lim)
     nref = args.refine if args.refine > 0 else (2 if args.precision == "fp32_refine" else 0)
     solves = 1 + nref
     pst_one = dict(pst)
@@ -506,7 +543,7 @@ def run_c3(args, world, rank, local):
                "e2e": {"value": e2e_v, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                "gpu_launches": int(st["kernel_launches"]) * args.steps, "clocks": clocks,
                "fma_peaks_gflops": {"fp64": p64, "fp32": p32}, "roofline": roof, "kinds": kr,
-               "cpu_baseline": None}
+               "cpu_baseline": cpu}
         print(json.dumps(out))
     bp.close()
     if world > 1:
