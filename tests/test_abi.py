@@ -46,3 +46,24 @@ def test_invalid_options_are_rejected_before_any_device_work(field, value):
     with pytest.raises(tikh.TikhError) as e:
         tikh.tikh_plan_create(64, 64, tikh.TIKH_R64, tikh.TIKH_PREC_FP64, o)
     assert "invalid" in str(e.value).lower() or str(tikh.TIKH_EINVAL) in str(e.value)
+
+
+@pytest.mark.parametrize("m,n,pl,dtype,n_lim", [(0, 8, 8, 0, 30), (8, 0, 8, 0, 30), (8, 8, 0, 0, 30),
+                                                (8, 8, 8, 7, 30), (40, 30, 20, 0, 64), (40, 30, 20, 0, 2)])
+def test_general_plan_arguments_are_checked_before_any_device_work(m, n, pl, dtype, n_lim):
+    # sizes, dtype and a leaf above 42 conditions (3 M > 42 for the 7 x 7 basis) are refused on the host
+    from paper_1302_6945_gb300 import tikh
+    o = tikh.tikh_opts(n_lim, 0, 0, 1e-12, 4096, 0, 1, 0, 0, 0, 0, 0.0)
+    with pytest.raises(tikh.TikhError) as e:
+        tikh.tikh_plan_create_general(m, n, pl, dtype, o)
+    assert e.value.status == tikh.TIKH_EINVAL
+
+
+def test_general_solves_refuse_a_missing_plan():
+    from paper_1302_6945_gb300 import tikh
+    for f in (tikh.tikh_solve_general, tikh.tikh_solve_general_normal):
+        with pytest.raises(tikh.TikhError) as e:
+            f(None, 1, 1, 1, 1, 1, 1)
+        assert e.value.status == tikh.TIKH_EINVAL
+    with pytest.raises(tikh.TikhError):
+        tikh.tikh_solve_general_strided(None, 1, 1, 0, 1, 0, 1, 0, 1, 0, 1, 0, 1, 0)
