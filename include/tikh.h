@@ -374,6 +374,14 @@ int tikh_test_fft32(int64_t n, void* data, int sign, void* stream);
  * within FP64 rounding of 1/d.  Synchronises the stream.  TIKH_EINVAL for n < 1 or a NULL pointer. */
 int tikh_test_rcp(int64_t n, const double* d, double* out, void* stream);
 
+/* The power-of-two column scaling of the basis (the bases of Sec. 4.3 carried with lazy column scales): for
+ * each i, v[i] times the scale of the column maximum bits[i] (the bit pattern of a non-negative double; the
+ * scale 2^k puts that maximum in [0.5, 1)), once by an add to the exponent field (out_exp, what the
+ * products' loaders use) and once by an FP64 multiply (out_mul).  The two agree bit for bit.  Device
+ * arrays; synchronises the stream.  TIKH_EINVAL for n < 1 or a NULL pointer. */
+int tikh_test_scale(int64_t n, const double* v, const unsigned long long* bits, double* out_exp, double* out_mul,
+                    void* stream);
+
 /* One leaf of Algorithm 1: the serial single-point construction of Eq. (spbasis) (Sec. 4.3) with
  * condition pivoting and difficult-point deferral (Sec. 5) over K <= 64 conditions.
  * Inputs (device): sigma (K complex128 nodes), r (K x 5 complex128 residual rows), delta_in (5 ints,

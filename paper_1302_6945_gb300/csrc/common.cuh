@@ -106,4 +106,32 @@ __device__ __forceinline__ double col_scale_from_bits(unsigned long long bits) {
   return ldexp(1.0, -e);
 }
 
+// The same scale as an exponent k (scale = 2^k) by integer operations on the bit pattern: a normal column
+// maximum with biased exponent E in [1, 2044] has frexp exponent E - 1022, so k = 1022 - E.  ok = false for
+// a zero, sub-normal or near-overflow maximum (then col_scale_from_bits applies).
+__device__ __forceinline__ int col_shift_from_bits(unsigned long long bits, bool& ok) {
+  const int E = (int)(bits >> 52);  // a non-negative double: no sign bit
+  ok = E >= 1 && E <= 2044;
+  return 1022 - E;
+}
+
+// v 2^k for k in [-1022, 1021], exactly as the FP64 multiply by 2^k rounds it: an add to the exponent field
+// (no FP64 instruction) when v and the result are normal; zeros unchanged; otherwise the multiply
+__device__ __forceinline__ double mul_pow2(double v, int k) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  if ((b << 1) == 0ULL) return v;
+  const int e = (int)((b >> 52) & 0x7ffULL);
+  if (e == 0 || e == 2047 || e + k <= 0 || e + k >= 2047)
+    return v * __longlong_as_double((long long)(1023 + k) << 52);
+  return __longlong_as_double((long long)(b + ((unsigned long long)(long long)k << 52)));
+}
+__device__ __forceinline__ cd cmul_pow2(cd v, int k) { return mkc(mul_pow2(v.x, k), mul_pow2(v.y, k)); }
+
+// v times the column scale of a column maximum's bit pattern (col_scale_from_bits), exact
+__device__ __forceinline__ cd col_scaled(cd v, unsigned long long bits) {
+  bool ok;
+  const int k = col_shift_from_bits(bits, ok);
+  return ok ? cmul_pow2(v, k) : cscale(v, col_scale_from_bits(bits));
+}
+
 }  // namespace tikh

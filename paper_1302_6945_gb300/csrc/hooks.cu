@@ -148,6 +148,26 @@ int tikh_test_rcp(int64_t n, const double* d, double* out, void* stream) {
   return cudaStreamSynchronize(s) == cudaSuccess ? TIKH_OK : TIKH_ECUDA;
 }
 
+__global__ void k_test_scale(int64_t n, const double* __restrict__ v, const unsigned long long* __restrict__ bits,
+                             double* out_exp, double* out_mul) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const cd a = mkc(v[i], -v[i]);
+    const cd e = col_scaled(a, bits[i]);
+    const cd m = cscale(a, col_scale_from_bits(bits[i]));
+    out_exp[i] = e.x;
+    out_mul[i] = m.x;
+  }
+}
+
+int tikh_test_scale(int64_t n, const double* v, const unsigned long long* bits, double* out_exp, double* out_mul,
+                    void* stream) {
+  if (n < 1 || !v || !bits || !out_exp || !out_mul) return TIKH_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  k_test_scale<<<(unsigned)std::min<int64_t>((n + 255) / 256, 1024), 256, 0, s>>>(n, v, bits, out_exp, out_mul);
+  if (cudaGetLastError() != cudaSuccess) return TIKH_ECUDA;
+  return cudaStreamSynchronize(s) == cudaSuccess ? TIKH_OK : TIKH_ECUDA;
+}
+
 int tikh_test_fft32(int64_t n, void* data, int sign, void* stream) {
   if (n < 1 || !data || (sign != 1 && sign != -1)) return TIKH_EINVAL;
   return launch_fft_test_t<cf>(n, (cf*)data, sign, (cudaStream_t)stream);

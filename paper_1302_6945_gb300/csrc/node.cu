@@ -237,7 +237,7 @@ struct LoadPad {  // transform t = 2 W^2 pb + b; b < W^2: B_L entry b; else B_R 
     const BasisBuf& B = b < WW ? BL : BR;
     int E = b < WW ? b : b - WW;
     if (q >= B.lp(pb)[E]) return czero<C>();
-    return cfrom<C>(cscale(B.cp(pb)[E * B.cap + q], col_scale_from_bits(B.mp(pb)[E % W])));
+    return cfrom<C>(col_scaled(B.cp(pb)[E * B.cap + q], B.mp(pb)[E % W]));
   }
 };
 template <class C, int W>
@@ -363,12 +363,12 @@ __global__ void __launch_bounds__(32 * PD_TC) k_prod_direct(BasisBuf BL, BasisBu
   for (int idx = tid; idx < W * capL; idx += blockDim.x) {
     const int u = idx / capL, q = idx - u * capL;
     if (q < min(ll[u], tmax))
-      As[idx] = cscale(BL.cp(pb)[(int64_t)(i * W + u) * capL + q], col_scale_from_bits(BL.mp(pb)[u]));
+      As[idx] = col_scaled(BL.cp(pb)[(int64_t)(i * W + u) * capL + q], BL.mp(pb)[u]);
   }
-  const double sr = col_scale_from_bits(BR.mp(pb)[j]);
+  const unsigned long long sr = BR.mp(pb)[j];
   for (int idx = tid; idx < W * capR; idx += blockDim.x) {
     const int u = idx / capR, q = idx - u * capR;
-    if (q < min(lr[u], tmax)) Bs[idx] = cscale(BR.cp(pb)[(int64_t)(u * W + j) * capR + q], sr);
+    if (q < min(lr[u], tmax)) Bs[idx] = col_scaled(BR.cp(pb)[(int64_t)(u * W + j) * capR + q], sr);
   }
   __syncthreads();
   double mx = 0.0;

@@ -74,7 +74,7 @@ EXPORTED = ["tikh_plan_create", "tikh_solve", "tikh_solve_async", "tikh_solve_no
             "tikh_sync", "tikh_get_stats", "tikh_plan_destroy", "tikh_strerror", "tikh_test_fft", "tikh_test_leaf",
             "tikh_fft_noalloc", "tikh_set_profiling", "tikh_solve_grad", "tikh_get_difficult", "tikh_test_peak",
             "tikh_plan_create_general", "tikh_solve_general", "tikh_solve_general_normal",
-            "tikh_solve_general_strided"]
+            "tikh_solve_general_strided", "tikh_test_scale"]
 
 
 def lib():
@@ -117,6 +117,7 @@ def lib():
         L.tikh_test_fft.argtypes = [i64, vp, ci, vp]
         L.tikh_test_fft32.argtypes = [i64, vp, ci, vp]
         L.tikh_test_rcp.argtypes = [i64, vp, vp, vp]
+        L.tikh_test_scale.argtypes = [i64, vp, vp, vp, vp, vp]
         L.tikh_fft_noalloc.argtypes = [i64, vp, ci, vp]
         L.tikh_test_peak.argtypes = [ci, ctypes.POINTER(dbl), vp]
         L.tikh_test_leaf.argtypes = [ci, vp, vp, vp, dbl, vp, vp, vp, vp, vp, vp, vp, vp]
@@ -310,6 +311,10 @@ def tikh_test_fft32(n, data, sign, stream=0):
 
 def tikh_test_rcp(n, d, out, stream=0):
     _check(lib().tikh_test_rcp(int(n), d, out, ctypes.c_void_p(int(stream))), "tikh_test_rcp")
+
+
+def tikh_test_scale(n, v, bits, out_exp, out_mul, stream=0):
+    _check(lib().tikh_test_scale(int(n), v, bits, out_exp, out_mul, ctypes.c_void_p(int(stream))), "tikh_test_scale")
 
 
 def tikh_test_peak(kind, stream=0):

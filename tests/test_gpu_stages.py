@@ -80,3 +80,26 @@ def test_leaf_series_reciprocal_is_within_fp64_rounding():
     ref = 1.0 / d
     ulp = np.abs(np.spacing(ref))
     assert (np.abs(got - ref) <= ulp).all(), np.max(np.abs(got - ref) / ulp)
+
+
+def test_column_scaling_by_exponent_arithmetic_matches_the_multiply():
+    # the products' loaders scale basis coefficients by the column's power of two through the exponent field;
+    # over normal, sub-normal, zero, huge, infinite and NaN values and column maxima from sub-normal to huge it
+    # must give exactly what the FP64 multiply by the same power of two gives
+    import ctypes
+    rng = np.random.default_rng(23)
+    n = 200000
+    with np.errstate(over="ignore"):
+        v = np.ldexp(rng.standard_normal(n), rng.integers(-1074, 1023, n))
+        mx = np.abs(np.ldexp(1.0 + rng.random(n), rng.integers(-1074, 1023, n)))
+    v[:8] = [0.0, -0.0, 5e-324, -1e-310, np.inf, -np.inf, 1.7e308, -2.2250738585072014e-308]
+    mx[:16] = [0.0, 5e-324, 1e-310, 2.2250738585072014e-308, 1.0, 0.75, 1.7e308, np.inf, 0.5, 1e-300, 1e300,
+               4.0, 3.9e-308, 8.9e307, 1.1e-308, 2.0]
+    vv = torch.tensor(np.append(v, np.nan), dtype=torch.float64, device=DEV)
+    bits = torch.tensor(np.append(mx, 1.0).view(np.int64), dtype=torch.int64, device=DEV)
+    oe, om = torch.empty_like(vv), torch.empty_like(vv)
+    p = lambda t: ctypes.c_void_p(t.data_ptr())
+    tikh.tikh_test_scale(vv.numel(), p(vv), p(bits), p(oe), p(om), torch.cuda.current_stream().cuda_stream)
+    a, b = oe.cpu().numpy(), om.cpu().numpy()
+    assert np.array_equal(a.view(np.int64)[:-1], b.view(np.int64)[:-1])
+    assert np.isnan(a[-1]) and np.isnan(b[-1])
