@@ -238,6 +238,18 @@ __device__ __forceinline__ void fft_smem(C* sm, const FftDesc& d, int tb, int si
 template <class LD>
 using ElemOf = typename std::decay<decltype(std::declval<LD>()(0, (int64_t)0))>::type;
 
+// A loader or storer may declare `bool active(int t)`: transform t is then computed only if both of them
+// call it active (a CTA whose transforms are all inactive returns at once and writes nothing).
+template <class T, class = void>
+struct HasActive : std::false_type {};
+template <class T>
+struct HasActive<T, std::void_t<decltype(std::declval<const T&>().active(0))>> : std::true_type {};
+template <class T>
+__device__ __forceinline__ bool active_of(const T& f, int t) {
+  if constexpr (HasActive<T>::value) return f.active(t);
+  else return true;
+}
+
 // generic tile kernel: transforms b0 .. b0 + tb - 1 of `batch`, loader ld(b, j), storer st(b, k, v)
 template <class LD, class ST>
 __global__ void __launch_bounds__(1024) fft_tile_kernel(FftDesc d, int tb, int batch, int sign, int load_jfast,
@@ -248,6 +260,11 @@ __global__ void __launch_bounds__(1024) fft_tile_kernel(FftDesc d, int tb, int b
   pdl_enter();
   const int b0 = blockIdx.x * tb;
   const int ntr = min(tb, batch - b0);
+  if constexpr (HasActive<LD>::value || HasActive<ST>::value) {
+    bool any = false;
+    for (int t = 0; t < ntr && !any; ++t) any = active_of(ld, b0 + t) && active_of(st, b0 + t);
+    if (!any) return;  // block-uniform
+  }
   const int L = d.L, n = tb * L;
   for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
     int t, j;
@@ -272,6 +289,8 @@ struct ColLoad {  // transform bb = b * L2 + j2, element j1 -> user element j1 *
     int64_t b = bb / L2, j2 = bb % L2;
     return ld((int)b, j1 * L2 + j2);
   }
+  template <class X = LD, class = std::enable_if_t<HasActive<X>::value>>
+  __device__ bool active(int bb) const { return ld.active((int)(bb / L2)); }
 };
 template <class C>
 struct ColStore {  // tmp[b * L + k1 * L2 + j2] = v * w_L^{sign j2 k1}
@@ -305,6 +324,8 @@ struct RowStore {  // output k = k1 + L1 * k2 of transform b
     int64_t b = bb / L1, k1 = bb % L1;
     st((int)b, k1 + L1 * k2, v);
   }
+  template <class X = ST, class = std::enable_if_t<HasActive<X>::value>>
+  __device__ bool active(int bb) const { return st.active((int)(bb / L1)); }
 };
 
 // host helpers ----------------------------------------------------------------------------------

@@ -211,6 +211,43 @@ __device__ __forceinline__ int prod_len_bound(const BasisBuf& BL, const BasisBuf
   return L;
 }
 
+// The extraction (Sec. 5) reads entries (0, j*) and (W-1, j*) of the root's basis only, j* its column of
+// tau-degree 0; when no condition of the problem was deferred the root's product B_L B_R is needed for those
+// two entries, i.e. rows 0 and W-1 of B_L and column j* of B_R.  RootNeed says which operand transforms and
+// which output entries the root's product computes (ndiff == nullptr: every one, as at the other nodes);
+// with deferred conditions, or without the final degree pattern, the whole product is computed.
+template <int W>
+struct RootNeed {
+  const int* ndiff;
+  const int* delta;
+  __device__ int jstar(int pb) const {
+    if (ndiff[4 * pb] != 0) return -1;
+    const int* d = delta + DSTR * pb;
+    int js = -1, nz = 0, no = 0;
+    for (int j = 0; j < W; ++j) {
+      if (d[j] == 0) { js = j; ++nz; } else if (d[j] == 1) ++no;
+    }
+    return nz == 1 && no == W - 1 ? js : -1;
+  }
+  // operand transform t = 2 W^2 pb + b (b < W^2: B_L entry b, else B_R entry b - W^2)
+  __device__ bool operand(int t) const {
+    if (!ndiff) return true;
+    const int pb = t / (2 * W * W), b = t % (2 * W * W);
+    const int js = jstar(pb);
+    if (js < 0) return true;
+    if (b < W * W) return b / W == 0 || b / W == W - 1;
+    return (b - W * W) % W == js;
+  }
+  // output entry t = W^2 pb + E
+  __device__ bool output(int t) const {
+    if (!ndiff) return true;
+    const int pb = t / (W * W), e = t % (W * W);
+    const int js = jstar(pb);
+    if (js < 0) return true;
+    return e % W == js && (e / W == 0 || e / W == W - 1);
+  }
+};
+
 template <class C, int W>
 struct LoadPad {  // transform t = 2 W^2 pb + b; b < W^2: B_L entry b; else B_R entry b - W^2; zero-padded to P
   BasisBuf BL, BR, OUT;
@@ -239,30 +276,38 @@ struct LoadPad {  // transform t = 2 W^2 pb + b; b < W^2: B_L entry b; else B_R 
     if (q >= B.lp(pb)[E]) return czero<C>();
     return cfrom<C>(col_scaled(B.cp(pb)[E * B.cap + q], B.mp(pb)[E % W]));
   }
+  RootNeed<W> need;
+  __device__ bool active(int t) const { return need.operand(t); }
 };
 template <class C, int W>
 struct StoreSpec {
   C* FA;
   C* FB;
   int64_t P;
+  RootNeed<W> need;
   __device__ void operator()(int t, int64_t k, C v) const {
     constexpr int WW = W * W;
     int pb = t / (2 * WW), b = t % (2 * WW);
     if (b < WW) FA[((int64_t)pb * WW + b) * P + k] = v;
     else FB[((int64_t)pb * WW + b - WW) * P + k] = v;
   }
+  __device__ bool active(int t) const { return need.operand(t); }
 };
-template <class C>
+template <class C, int W>
 struct StorePlain2 {
   C* out;
   int64_t P;
+  RootNeed<W> need;
   __device__ void operator()(int t, int64_t k, C v) const { out[(int64_t)t * P + k] = v; }
+  __device__ bool active(int t) const { return need.output(t); }
 };
 template <class C, int W>
 struct LoadProduct {  // transform t = W^2 pb + W i + j: sum_u FA[W i + u] FB[W u + j]
   const C* FA;
   const C* FB;
   int64_t P;
+  RootNeed<W> need;
+  __device__ bool active(int t) const { return need.output(t); }
   __device__ C operator()(int t, int64_t q) const {
     constexpr int WW = W * W;
     int pb = t / WW, e = t % WW, i = e / W, j = e % W;
@@ -286,11 +331,15 @@ __device__ __forceinline__ unsigned long long absmax_bits(cd v) {
 // trim to the degree bounds, scale by 1/P (in FP64), record column maxima and lengths
 template <class C, int W>
 __global__ void k_prod_finish(const C* __restrict__ FC, int64_t P, BasisBuf BL, BasisBuf BR, BasisBuf OUT,
-                              const int* dstack, int depth, const int* delta, int* status) {
+                              const int* dstack, int depth, const int* delta, int* status, RootNeed<W> need) {
   const int E = blockIdx.y, i = E / W, j = E % W, pb = blockIdx.z;
   __shared__ int want_s;
   __shared__ unsigned long long red[32];
   pdl_enter();
+  if (!need.output(pb * W * W + E)) {  // an entry of the root's basis that nothing reads
+    if (threadIdx.x == 0 && blockIdx.x == 0) OUT.lp(pb)[E] = 0;
+    return;
+  }
   if (threadIdx.x == 0) {
     int bnd = entry_bound_dev<W>(dstack + (pb * MAX_DEPTH + depth) * DSTR, delta + DSTR * pb, i, j);
     int64_t want = bnd < 0 ? 0 : (int64_t)bnd + 1;
@@ -334,13 +383,18 @@ __global__ void k_prod_finish(const C* __restrict__ FC, int64_t P, BasisBuf BL, 
 constexpr int PD_TC = 8;
 template <int W>
 __global__ void __launch_bounds__(32 * PD_TC) k_prod_direct(BasisBuf BL, BasisBuf BR, BasisBuf OUT, const int* dstack,
-                                                             int depth, const int* delta, int* status, int ntile) {
+                                                             int depth, const int* delta, int* status, int ntile,
+                                                             RootNeed<W> need) {
   extern __shared__ cd pd_sh[];  // A: W x BL.cap, then B: W x BR.cap
   const int E = blockIdx.x / ntile, tile = blockIdx.x % ntile;
   const int i = E / W, j = E % W, pb = blockIdx.y, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   __shared__ int want_s, ll[W], lr[W];
   __shared__ double red[PD_TC];
   pdl_enter();
+  if (!need.output(pb * W * W + E)) {  // an entry of the root's basis that nothing reads
+    if (tid == 0 && tile == 0) OUT.lp(pb)[E] = 0;
+    return;
+  }
   if (tid < W) {
     ll[tid] = BL.lp(pb)[i * W + tid];
     lr[tid] = BR.lp(pb)[tid * W + j];
@@ -420,15 +474,18 @@ static int launch_prod_fft(Plan& P, const Step& st, const BasisBuf& BL, const Ba
   C* FC = reinterpret_cast<C*>(P.FC);
   C* tmp = reinterpret_cast<C*>(P.ptmp);
   int nl = 0, r;
-  LoadPad<C, W> lp{BL, BR, OUT, P.dstack, P.delta, st.depth, P.status, st.P};
-  if ((r = fft_run(F, 2 * WW * P.nb, +1, lp, StoreSpec<C, W>{FA, FB, st.P}, tmp, P.stream)) < 0) return TIKH_ECUDA;
+  const RootNeed<W> need{st.depth == 0 ? P.ndiff : nullptr, P.delta};
+  LoadPad<C, W> lp{BL, BR, OUT, P.dstack, P.delta, st.depth, P.status, st.P, need};
+  if ((r = fft_run(F, 2 * WW * P.nb, +1, lp, StoreSpec<C, W>{FA, FB, st.P, need}, tmp, P.stream)) < 0)
+    return TIKH_ECUDA;
   nl += r;
-  if ((r = fft_run(F, WW * P.nb, -1, LoadProduct<C, W>{FA, FB, st.P}, StorePlain2<C>{FC, st.P}, tmp, P.stream)) < 0)
+  if ((r = fft_run(F, WW * P.nb, -1, LoadProduct<C, W>{FA, FB, st.P, need}, StorePlain2<C, W>{FC, st.P, need}, tmp,
+                   P.stream)) < 0)
     return TIKH_ECUDA;
   nl += r;
   int bx = (int)std::min<int64_t>((st.P + 255) / 256, 64);
   launch_k(pdl_enabled(), k_prod_finish<C, W>, dim3(bx, WW, P.nb), dim3(256), 0, P.stream, (const C*)FC, st.P, BL, BR,
-           OUT, (const int*)P.dstack, st.depth, (const int*)P.delta, P.status);
+           OUT, (const int*)P.dstack, st.depth, (const int*)P.delta, P.status, need);
   if (cudaGetLastError() != cudaSuccess) return TIKH_ECUDA;
   return nl + 1;
 }
@@ -441,8 +498,9 @@ static int launch_prod_t(Plan& P, const Step& st) {
   const size_t smem = sizeof(cd) * W * (size_t)(BL.cap + BR.cap);
   if (st.P <= P.prod_direct_max && smem <= 48 * 1024) {
     const int ntile = (int)((st.P + PD_TC - 1) / PD_TC);
+    const RootNeed<W> need{st.depth == 0 ? P.ndiff : nullptr, P.delta};
     launch_k(pdl_enabled(), k_prod_direct<W>, dim3(W * W * ntile, P.nb), dim3(32 * PD_TC), smem, P.stream, BL, BR,
-             OUT, (const int*)P.dstack, st.depth, (const int*)P.delta, P.status, ntile);
+             OUT, (const int*)P.dstack, st.depth, (const int*)P.delta, P.status, ntile, need);
     return cudaGetLastError() == cudaSuccess ? 1 : TIKH_ECUDA;
   }
   if constexpr (W == 5) {
