@@ -212,14 +212,19 @@ __device__ __forceinline__ int prod_len_bound(const BasisBuf& BL, const BasisBuf
 }
 
 // The extraction (Sec. 5) reads entries (0, j*) and (W-1, j*) of the root's basis only, j* its column of
-// tau-degree 0; when no condition of the problem was deferred the root's product B_L B_R is needed for those
-// two entries, i.e. rows 0 and W-1 of B_L and column j* of B_R.  RootNeed says which operand transforms and
-// which output entries the root's product computes (ndiff == nullptr: every one, as at the other nodes);
-// with deferred conditions, or without the final degree pattern, the whole product is computed.
+// tau-degree 0.  When no condition of the problem was deferred, the root's product B_L B_R is needed for
+// those two entries (rows 0 and W-1 of B_L, column j* of B_R), and the product of every other node on the
+// right spine (the root's right child, its right child, ...), whose basis only enters its parent's product
+// as B_R, is needed for its column j* (all of its B_L, column j* of its B_R).  These products come after the
+// last leaf, so the deferral count and the degree pattern are final when they run.  RootNeed says which
+// operand transforms and which output entries a product computes (mode 0, or ndiff == nullptr: every one;
+// 1: a right-spine node; 2: the root); with deferred conditions, or without the final degree pattern, the
+// whole product is computed.
 template <int W>
 struct RootNeed {
   const int* ndiff;
   const int* delta;
+  int mode;
   __device__ int jstar(int pb) const {
     if (ndiff[4 * pb] != 0) return -1;
     const int* d = delta + DSTR * pb;
@@ -231,20 +236,20 @@ struct RootNeed {
   }
   // operand transform t = 2 W^2 pb + b (b < W^2: B_L entry b, else B_R entry b - W^2)
   __device__ bool operand(int t) const {
-    if (!ndiff) return true;
+    if (!ndiff || mode == 0) return true;
     const int pb = t / (2 * W * W), b = t % (2 * W * W);
     const int js = jstar(pb);
     if (js < 0) return true;
-    if (b < W * W) return b / W == 0 || b / W == W - 1;
+    if (b < W * W) return mode == 1 || b / W == 0 || b / W == W - 1;
     return (b - W * W) % W == js;
   }
   // output entry t = W^2 pb + E
   __device__ bool output(int t) const {
-    if (!ndiff) return true;
+    if (!ndiff || mode == 0) return true;
     const int pb = t / (W * W), e = t % (W * W);
     const int js = jstar(pb);
     if (js < 0) return true;
-    return e % W == js && (e / W == 0 || e / W == W - 1);
+    return e % W == js && (mode == 1 || e / W == 0 || e / W == W - 1);
   }
 };
 
@@ -463,6 +468,13 @@ __global__ void __launch_bounds__(32 * PD_TC) k_prod_direct(BasisBuf BL, BasisBu
   }
 }
 
+// the root is (a, s) = (0, 2) and a right child is (a + s, 2 s): the right spine is a = s - 2
+template <int W>
+static RootNeed<W> need_of(const Plan& P, const Step& st) {
+  const int mode = st.depth == 0 ? 2 : (st.a == st.s - 2 ? 1 : 0);
+  return RootNeed<W>{mode ? P.ndiff : nullptr, P.delta, mode};
+}
+
 // step 4 by length-P transforms in precision C: the 2 W^2 operand spectra, W^2 pointwise products of W
 // terms, W^2 inverse transforms, then the FP64 trim / scale / column maxima
 template <class C, int W>
@@ -474,7 +486,7 @@ static int launch_prod_fft(Plan& P, const Step& st, const BasisBuf& BL, const Ba
   C* FC = reinterpret_cast<C*>(P.FC);
   C* tmp = reinterpret_cast<C*>(P.ptmp);
   int nl = 0, r;
-  const RootNeed<W> need{st.depth == 0 ? P.ndiff : nullptr, P.delta};
+  const RootNeed<W> need = need_of<W>(P, st);
   LoadPad<C, W> lp{BL, BR, OUT, P.dstack, P.delta, st.depth, P.status, st.P, need};
   if ((r = fft_run(F, 2 * WW * P.nb, +1, lp, StoreSpec<C, W>{FA, FB, st.P, need}, tmp, P.stream)) < 0)
     return TIKH_ECUDA;
@@ -498,7 +510,7 @@ static int launch_prod_t(Plan& P, const Step& st) {
   const size_t smem = sizeof(cd) * W * (size_t)(BL.cap + BR.cap);
   if (st.P <= P.prod_direct_max && smem <= 48 * 1024) {
     const int ntile = (int)((st.P + PD_TC - 1) / PD_TC);
-    const RootNeed<W> need{st.depth == 0 ? P.ndiff : nullptr, P.delta};
+    const RootNeed<W> need = need_of<W>(P, st);
     launch_k(pdl_enabled(), k_prod_direct<W>, dim3(W * W * ntile, P.nb), dim3(32 * PD_TC), smem, P.stream, BL, BR,
              OUT, (const int*)P.dstack, st.depth, (const int*)P.delta, P.status, ntile, need);
     return cudaGetLastError() == cudaSuccess ? 1 : TIKH_ECUDA;
