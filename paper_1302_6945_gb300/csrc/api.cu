@@ -140,7 +140,8 @@ void build_steps(Plan& P, std::vector<Step>& out, int depth, int64_t a, int64_t 
                  uint64_t& pending, int64_t slack) {
   const int W = P.w, NS = P.ns;
   if (depth == P.p) {
-    Step st{STEP_LEAF, depth, side, a, s, L, -1, 0, pending};
+    // the leaf saves its delta_in for its own depth too: the product of its parent reads the right leaf's
+    Step st{STEP_LEAF, depth, side, a, s, L, -1, 0, pending | (1ULL << depth)};
     pending = 0;
     waterfill(W, sd, 2 * NS * L);
     out.push_back(st);

@@ -41,6 +41,35 @@ __device__ __forceinline__ cd twiddle_of<cd>(const cd* wN, const cf*, int64_t i)
 template <>
 __device__ __forceinline__ cf twiddle_of<cf>(const cd*, const cf* wN32, int64_t i) { return tw_at(wN32, i); }
 
+// columns pivoted between two degree vectors (bit j: dout_j > din_j); a single-point factor of Eq. (spbasis)
+// changes only its pivot column and leaves every other row of the basis an identity row, so the rows of a
+// node's basis outside the columns pivoted in that node are exactly identity rows (scaled by the lazy
+// column scales)
+template <int W>
+__device__ __forceinline__ unsigned pivoted_cols(const int* din, const int* dout) {
+  unsigned m = 0u;
+#pragma unroll
+  for (int j = 0; j < W; ++j) m |= (dout[j] > din[j] ? 1u : 0u) << j;
+  return m;
+}
+
+// Step 2 at a node of depth `depth`: the rows of B_L outside the columns pivoted in the left child (from
+// delta_in of the node, dstack[depth], to the current delta) are identity rows, whose evaluation is the
+// constant diagonal; their transforms are skipped
+template <int W>
+struct EvalNeed {
+  const int* dstack;
+  const int* delta;
+  int depth;
+  __device__ unsigned sl(int pb) const {
+    return pivoted_cols<W>(dstack + (pb * MAX_DEPTH + depth) * DSTR, delta + DSTR * pb);
+  }
+  __device__ bool active(int t) const {  // transform t = 2 W^2 pb + 2E + c, E = W i + j
+    const int pb = t / (2 * W * W), i = ((t % (2 * W * W)) >> 1) / W;
+    return (sl(pb) >> i) & 1u;
+  }
+};
+
 template <class C, int W>
 struct LoadTwistFold {  // transform t = 2 W^2 pb + 2E + c
   BasisBuf B;
@@ -48,6 +77,8 @@ struct LoadTwistFold {  // transform t = 2 W^2 pb + 2E + c
   const cd* wN;
   const cf* wN32;
   int64_t N, Lr, beta0;
+  EvalNeed<W> need;
+  __device__ bool active(int t) const { return need.active(t); }
   __device__ C operator()(int t, int64_t u) const {
     int pb = t / (2 * W * W), b = t % (2 * W * W);
     if (b == 0 && u == 0)
@@ -68,26 +99,45 @@ struct LoadTwistFold {  // transform t = 2 W^2 pb + 2E + c
     return cscale(acc, (decltype(acc.x))col_scale_from_bits(B.mp(pb)[E % W]));
   }
 };
-template <class C>
+template <class C, int W>
 struct StoreEval {
   C* out;
   int64_t Lr;
+  EvalNeed<W> need;
+  __device__ bool active(int t) const { return need.active(t); }
   __device__ void operator()(int t, int64_t j, C v) const { out[(int64_t)t * Lr + j] = v; }
 };
 
 // phi <- phi B_L(sigma) for the NS conditions of every right-child node (in C's precision; the rows are
-// stored back in FP64)
+// stored back in FP64).  An identity row i of B_L (skipped by the transforms) evaluates to its constant
+// diagonal, computed here as the twist-fold transform computes it.  Also resets this node's column maxima
+// (the product accumulates them).
 template <class C, int W, int NS>
-__global__ void k_eval_update(cd* R, const C* __restrict__ vals, int64_t N, int64_t a0, int64_t s2, int64_t Lr) {
+__global__ void k_eval_update(cd* R, const C* __restrict__ vals, int64_t N, int64_t a0, int64_t s2, int64_t Lr,
+                              BasisBuf BL, BasisBuf OUT, EvalNeed<W> need) {
   pdl_enter();
   const int pb = blockIdx.y;
+  if (blockIdx.x == 0 && threadIdx.x < W) OUT.mp(pb)[threadIdx.x] = 0ULL;
+  const unsigned SL = need.sl(pb);
+  C D[W];  // the constant evaluation of each identity row's diagonal
+#pragma unroll
+  for (int i = 0; i < W; ++i) {
+    D[i] = czero<C>();
+    if (!((SL >> i) & 1u) && BL.lp(pb)[i * W + i] >= 1)
+      D[i] = cscale(cfrom<C>(BL.cp(pb)[(int64_t)(i * W + i) * BL.cap]),
+                    (decltype(D[i].x))col_scale_from_bits(BL.mp(pb)[i]));
+  }
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < 2 * Lr; g += (int64_t)gridDim.x * blockDim.x) {
     int c = (int)(g % 2);
     int64_t j = g / 2;
     int64_t e = a0 + c + s2 * j;
     C V[W * W];
 #pragma unroll
-    for (int E = 0; E < W * W; ++E) V[E] = vals[((int64_t)pb * (2 * W * W) + E * 2 + c) * Lr + j];
+    for (int E = 0; E < W * W; ++E) {
+      const int i = E / W;
+      V[E] = ((SL >> i) & 1u) ? vals[((int64_t)pb * (2 * W * W) + E * 2 + c) * Lr + j]
+                              : (E % W == i ? D[i] : czero<C>());
+    }
 #pragma unroll
     for (int f = 0; f < NS; ++f) {
       cd* r = R + ((int64_t)pb * N + e) * (NS * W) + f * W;
@@ -172,24 +222,25 @@ static int launch_eval_t(Plan& P, const Step& st) {
   }
   const FftPlan& F = P.ffts[st.fft];
   dim3 grid((unsigned)std::min<int64_t>((2 * Lr + 127) / 128, 4096), (unsigned)P.nb);
+  const EvalNeed<W> need{P.dstack, P.delta, st.depth};
   int r;
   if constexpr (W == 5) {
     if (P.stage32) {
       cf* ev = reinterpret_cast<cf*>(P.evalv);
-      r = fft_run(F, 2 * WW * P.nb, +1, LoadTwistFold<cf, W>{BL, OUT, P.wN, P.wN32, P.N, Lr, st.a + st.s},
-                  StoreEval<cf>{ev, Lr}, reinterpret_cast<cf*>(P.etmp), P.stream);
+      r = fft_run(F, 2 * WW * P.nb, +1, LoadTwistFold<cf, W>{BL, OUT, P.wN, P.wN32, P.N, Lr, st.a + st.s, need},
+                  StoreEval<cf, W>{ev, Lr, need}, reinterpret_cast<cf*>(P.etmp), P.stream);
       if (r < 0) return TIKH_ECUDA;
       launch_k(pdl_enabled(), k_eval_update<cf, W, NS>, grid, dim3(128), 0, P.stream, P.R, (const cf*)ev, P.N,
-               st.a + st.s, 2 * st.s, Lr);
+               st.a + st.s, 2 * st.s, Lr, BL, OUT, need);
       if (cudaGetLastError() != cudaSuccess) return TIKH_ECUDA;
       return r + 1;
     }
   }
-  r = fft_run(F, 2 * WW * P.nb, +1, LoadTwistFold<cd, W>{BL, OUT, P.wN, P.wN32, P.N, Lr, st.a + st.s},
-              StoreEval<cd>{P.evalv, Lr}, P.etmp, P.stream);
+  r = fft_run(F, 2 * WW * P.nb, +1, LoadTwistFold<cd, W>{BL, OUT, P.wN, P.wN32, P.N, Lr, st.a + st.s, need},
+              StoreEval<cd, W>{P.evalv, Lr, need}, P.etmp, P.stream);
   if (r < 0) return TIKH_ECUDA;
   launch_k(pdl_enabled(), k_eval_update<cd, W, NS>, grid, dim3(128), 0, P.stream, P.R, (const cd*)P.evalv, P.N,
-           st.a + st.s, 2 * st.s, Lr);
+           st.a + st.s, 2 * st.s, Lr, BL, OUT, need);
   if (cudaGetLastError() != cudaSuccess) return TIKH_ECUDA;
   return r + 1;
 }
@@ -211,22 +262,37 @@ __device__ __forceinline__ int prod_len_bound(const BasisBuf& BL, const BasisBuf
   return L;
 }
 
-// The extraction (Sec. 5) reads entries (0, j*) and (W-1, j*) of the root's basis only, j* its column of
-// tau-degree 0.  When no condition of the problem was deferred, the root's product B_L B_R is needed for
-// those two entries (rows 0 and W-1 of B_L, column j* of B_R), and the product of every other node on the
-// right spine (the root's right child, its right child, ...), whose basis only enters its parent's product
-// as B_R, is needed for its column j* (all of its B_L, column j* of its B_R).  These products come after the
-// last leaf, so the deferral count and the degree pattern are final when they run.  RootNeed says which
-// operand transforms and which output entries a product computes (mode 0, or ndiff == nullptr: every one;
-// 1: a right-spine node; 2: the root); with deferred conditions, or without the final degree pattern, the
-// whole product is computed.
+// entry (i, i) of an identity row i of basis B, as its evaluations and transforms see it (column scale
+// applied): the stored constant coefficient
 template <int W>
-struct RootNeed {
+__device__ __forceinline__ cd identity_diag(const BasisBuf& B, int pb, int i) {
+  const int E = i * W + i;
+  if (B.lp(pb)[E] < 1) return mkc(0.0, 0.0);
+  return col_scaled(B.cp(pb)[(int64_t)E * B.cap], B.mp(pb)[i]);
+}
+
+// What a product B = B_L B_R at recursion depth `depth` computes.
+// (1) Identity rows: rows of B_L outside the columns pivoted in the left child (S_L), and of B_R outside
+// S_R, are identity rows; their transforms are skipped and the products use their constant diagonal; the
+// output rows outside S_L u S_R are identity rows written directly.  S_L and S_R come from the degree
+// vectors: delta_in of the node (dstack[depth]), of its right child (dstack[depth + 1]) and delta_out.
+// (2) The extraction (Sec. 5) reads entries (0, j*) and (W-1, j*) of the root's basis only, j* its column
+// of tau-degree 0.  When no condition of the problem was deferred, the root's product is needed for those
+// two entries (rows 0 and W-1 of B_L, column j* of B_R), and the product of every other node on the right
+// spine (the root's right child, its right child, ...), whose basis only enters its parent's product as
+// B_R, for its column j* (all of its B_L, column j* of its B_R).  These products come after the last leaf,
+// so the deferral count and the degree pattern are final when they run (mode 1: a right-spine node, 2: the
+// root, 0: any other node; ndiff == nullptr: no such reduction).  With deferred conditions, or without
+// the final degree pattern, every entry is computed.
+template <int W>
+struct ProdNeed {
   const int* ndiff;
   const int* delta;
+  const int* dstack;
+  int depth;
   int mode;
   __device__ int jstar(int pb) const {
-    if (ndiff[4 * pb] != 0) return -1;
+    if (!ndiff || mode == 0 || ndiff[4 * pb] != 0) return -1;
     const int* d = delta + DSTR * pb;
     int js = -1, nz = 0, no = 0;
     for (int j = 0; j < W; ++j) {
@@ -234,54 +300,45 @@ struct RootNeed {
     }
     return nz == 1 && no == W - 1 ? js : -1;
   }
+  __device__ unsigned sl(int pb) const {
+    return pivoted_cols<W>(dstack + (pb * MAX_DEPTH + depth) * DSTR, dstack + (pb * MAX_DEPTH + depth + 1) * DSTR);
+  }
+  __device__ unsigned sr(int pb) const {
+    return pivoted_cols<W>(dstack + (pb * MAX_DEPTH + depth + 1) * DSTR, delta + DSTR * pb);
+  }
   // operand transform t = 2 W^2 pb + b (b < W^2: B_L entry b, else B_R entry b - W^2)
   __device__ bool operand(int t) const {
-    if (!ndiff || mode == 0) return true;
     const int pb = t / (2 * W * W), b = t % (2 * W * W);
     const int js = jstar(pb);
-    if (js < 0) return true;
-    if (b < W * W) return mode == 1 || b / W == 0 || b / W == W - 1;
-    return (b - W * W) % W == js;
+    if (b < W * W) {
+      const int i = b / W;
+      return ((sl(pb) >> i) & 1u) && (js < 0 || mode == 1 || i == 0 || i == W - 1);
+    }
+    const int u = (b - W * W) / W, j = (b - W * W) % W;
+    return ((sr(pb) >> u) & 1u) && (js < 0 || j == js);
   }
-  // output entry t = W^2 pb + E
-  __device__ bool output(int t) const {
-    if (!ndiff || mode == 0) return true;
-    const int pb = t / (W * W), e = t % (W * W);
+  // output entry t = W^2 pb + E: 0 nothing reads it, 1 an identity row (written directly), 2 computed
+  __device__ int output(int t) const {
+    const int pb = t / (W * W), e = t % (W * W), i = e / W, j = e % W;
     const int js = jstar(pb);
-    if (js < 0) return true;
-    return e % W == js && (mode == 1 || e / W == 0 || e / W == W - 1);
+    if (js >= 0 && !(j == js && (mode == 1 || i == 0 || i == W - 1))) return 0;
+    return (((sl(pb) | sr(pb)) >> i) & 1u) ? 2 : 1;
   }
 };
 
 template <class C, int W>
 struct LoadPad {  // transform t = 2 W^2 pb + b; b < W^2: B_L entry b; else B_R entry b - W^2; zero-padded to P
-  BasisBuf BL, BR, OUT;
-  const int* dstack;  // + (pb * MAX_DEPTH + depth) * DSTR: delta_in of the node
-  const int* delta;   // + DSTR pb: delta_out
-  int depth;
-  int* status;
+  BasisBuf BL, BR;
   int64_t P;
+  ProdNeed<W> need;
   __device__ C operator()(int t, int64_t q) const {
     constexpr int WW = W * W;
     int pb = t / (2 * WW), b = t % (2 * WW);
-    if (b == 0 && q == 0) {
-      // guard: the transform length must exceed every entry degree of the product (no wrap-around)
-      const int* din = dstack + (pb * MAX_DEPTH + depth) * DSTR;
-      const int* dout = delta + DSTR * pb;
-      int D = -1;
-      for (int i = 0; i < W; ++i)
-        for (int j = 0; j < W; ++j)
-          D = max(D, min(entry_bound_dev<W>(din, dout, i, j), prod_len_bound<W>(BL, BR, pb, i, j) - 1));
-      for (int E = 0; E < WW; ++E) D = max(D, max(BL.lp(pb)[E], BR.lp(pb)[E]) - 1);  // operands fit the transform
-      if (D >= P) set_status(status, ST_DEGREE);
-      for (int j = 0; j < W; ++j) OUT.mp(pb)[j] = 0ULL;
-    }
     const BasisBuf& B = b < WW ? BL : BR;
     int E = b < WW ? b : b - WW;
     if (q >= B.lp(pb)[E]) return czero<C>();
     return cfrom<C>(col_scaled(B.cp(pb)[E * B.cap + q], B.mp(pb)[E % W]));
   }
-  RootNeed<W> need;
   __device__ bool active(int t) const { return need.operand(t); }
 };
 template <class C, int W>
@@ -289,7 +346,7 @@ struct StoreSpec {
   C* FA;
   C* FB;
   int64_t P;
-  RootNeed<W> need;
+  ProdNeed<W> need;
   __device__ void operator()(int t, int64_t k, C v) const {
     constexpr int WW = W * W;
     int pb = t / (2 * WW), b = t % (2 * WW);
@@ -302,25 +359,35 @@ template <class C, int W>
 struct StorePlain2 {
   C* out;
   int64_t P;
-  RootNeed<W> need;
+  ProdNeed<W> need;
   __device__ void operator()(int t, int64_t k, C v) const { out[(int64_t)t * P + k] = v; }
-  __device__ bool active(int t) const { return need.output(t); }
+  __device__ bool active(int t) const { return need.output(t) == 2; }
 };
 template <class C, int W>
 struct LoadProduct {  // transform t = W^2 pb + W i + j: sum_u FA[W i + u] FB[W u + j]
   const C* FA;
   const C* FB;
   int64_t P;
-  RootNeed<W> need;
-  __device__ bool active(int t) const { return need.output(t); }
+  BasisBuf BL, BR;
+  ProdNeed<W> need;
+  __device__ bool active(int t) const { return need.output(t) == 2; }
   __device__ C operator()(int t, int64_t q) const {
     constexpr int WW = W * W;
     int pb = t / WW, e = t % WW, i = e / W, j = e % W;
     const C* a = FA + (int64_t)pb * WW * P;
     const C* b = FB + (int64_t)pb * WW * P;
+    // an identity row's transform is its constant diagonal at every bin (the transform of a constant)
+    const unsigned SL = need.sl(pb), SR = need.sr(pb);
+    const bool li = (SL >> i) & 1u;
+    const C dl = li ? czero<C>() : cfrom<C>(identity_diag<W>(BL, pb, i));
     C acc = czero<C>();
 #pragma unroll
-    for (int u = 0; u < W; ++u) acc = cfma(a[(int64_t)(W * i + u) * P + q], b[(int64_t)(W * u + j) * P + q], acc);
+    for (int u = 0; u < W; ++u) {
+      const C x = li ? a[(int64_t)(W * i + u) * P + q] : (u == i ? dl : czero<C>());
+      const C y = ((SR >> u) & 1u) ? b[(int64_t)(W * u + j) * P + q]
+                                  : (u == j ? cfrom<C>(identity_diag<W>(BR, pb, u)) : czero<C>());
+      acc = cfma(x, y, acc);
+    }
     return acc;
   }
 };
@@ -333,16 +400,38 @@ __device__ __forceinline__ unsigned long long absmax_bits(cd v) {
   return a > b ? a : b;
 }
 
-// trim to the degree bounds, scale by 1/P (in FP64), record column maxima and lengths
+// trim to the degree bounds, scale by 1/P (in FP64), record column maxima and lengths; identity rows
+// written directly; the guard that the transform length exceeds every entry degree of the product
 template <class C, int W>
 __global__ void k_prod_finish(const C* __restrict__ FC, int64_t P, BasisBuf BL, BasisBuf BR, BasisBuf OUT,
-                              const int* dstack, int depth, const int* delta, int* status, RootNeed<W> need) {
+                              const int* dstack, int depth, const int* delta, int* status, ProdNeed<W> need) {
   const int E = blockIdx.y, i = E / W, j = E % W, pb = blockIdx.z;
   __shared__ int want_s;
   __shared__ unsigned long long red[32];
   pdl_enter();
-  if (!need.output(pb * W * W + E)) {  // an entry of the root's basis that nothing reads
-    if (threadIdx.x == 0 && blockIdx.x == 0) OUT.lp(pb)[E] = 0;
+  if (blockIdx.x == 0 && E == 0 && threadIdx.x == 0) {  // no wrap-around (else a re-plan with more slack)
+    const int* din = dstack + (pb * MAX_DEPTH + depth) * DSTR;
+    const int* dout = delta + DSTR * pb;
+    int D = -1;
+    for (int a = 0; a < W; ++a)
+      for (int c = 0; c < W; ++c)
+        D = max(D, min(entry_bound_dev<W>(din, dout, a, c), prod_len_bound<W>(BL, BR, pb, a, c) - 1));
+    for (int e = 0; e < W * W; ++e) D = max(D, max(BL.lp(pb)[e], BR.lp(pb)[e]) - 1);  // operands fit
+    if (D >= P) set_status(status, ST_DEGREE);
+  }
+  const int code = need.output(pb * W * W + E);
+  if (code != 2) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+      if (code == 1 && i == j) {  // identity row: its diagonal is the product of the operands' diagonals
+        const cd v = cmul(identity_diag<W>(BL, pb, i), identity_diag<W>(BR, pb, i));
+        OUT.cp(pb)[(int64_t)E * OUT.cap] = v;
+        OUT.lp(pb)[E] = 1;
+        const unsigned long long m = absmax_bits(v);
+        if (m > 0ULL) atomicMax(OUT.mp(pb) + j, m);
+      } else {
+        OUT.lp(pb)[E] = 0;  // off the diagonal of an identity row, or an entry nothing reads
+      }
+    }
     return;
   }
   if (threadIdx.x == 0) {
@@ -389,14 +478,14 @@ constexpr int PD_TC = 8;
 template <int W>
 __global__ void __launch_bounds__(32 * PD_TC) k_prod_direct(BasisBuf BL, BasisBuf BR, BasisBuf OUT, const int* dstack,
                                                              int depth, const int* delta, int* status, int ntile,
-                                                             RootNeed<W> need) {
+                                                             ProdNeed<W> need) {
   extern __shared__ cd pd_sh[];  // A: W x BL.cap, then B: W x BR.cap
   const int E = blockIdx.x / ntile, tile = blockIdx.x % ntile;
   const int i = E / W, j = E % W, pb = blockIdx.y, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   __shared__ int want_s, ll[W], lr[W];
   __shared__ double red[PD_TC];
   pdl_enter();
-  if (!need.output(pb * W * W + E)) {  // an entry of the root's basis that nothing reads
+  if (need.output(pb * W * W + E) == 0) {  // an entry of the root's basis that nothing reads
     if (tid == 0 && tile == 0) OUT.lp(pb)[E] = 0;
     return;
   }
@@ -470,9 +559,9 @@ __global__ void __launch_bounds__(32 * PD_TC) k_prod_direct(BasisBuf BL, BasisBu
 
 // the root is (a, s) = (0, 2) and a right child is (a + s, 2 s): the right spine is a = s - 2
 template <int W>
-static RootNeed<W> need_of(const Plan& P, const Step& st) {
+static ProdNeed<W> need_of(const Plan& P, const Step& st) {
   const int mode = st.depth == 0 ? 2 : (st.a == st.s - 2 ? 1 : 0);
-  return RootNeed<W>{mode ? P.ndiff : nullptr, P.delta, mode};
+  return ProdNeed<W>{mode ? P.ndiff : nullptr, P.delta, P.dstack, st.depth, mode};
 }
 
 // step 4 by length-P transforms in precision C: the 2 W^2 operand spectra, W^2 pointwise products of W
@@ -486,13 +575,13 @@ static int launch_prod_fft(Plan& P, const Step& st, const BasisBuf& BL, const Ba
   C* FC = reinterpret_cast<C*>(P.FC);
   C* tmp = reinterpret_cast<C*>(P.ptmp);
   int nl = 0, r;
-  const RootNeed<W> need = need_of<W>(P, st);
-  LoadPad<C, W> lp{BL, BR, OUT, P.dstack, P.delta, st.depth, P.status, st.P, need};
+  const ProdNeed<W> need = need_of<W>(P, st);
+  LoadPad<C, W> lp{BL, BR, st.P, need};
   if ((r = fft_run(F, 2 * WW * P.nb, +1, lp, StoreSpec<C, W>{FA, FB, st.P, need}, tmp, P.stream)) < 0)
     return TIKH_ECUDA;
   nl += r;
-  if ((r = fft_run(F, WW * P.nb, -1, LoadProduct<C, W>{FA, FB, st.P, need}, StorePlain2<C, W>{FC, st.P, need}, tmp,
-                   P.stream)) < 0)
+  if ((r = fft_run(F, WW * P.nb, -1, LoadProduct<C, W>{FA, FB, st.P, BL, BR, need}, StorePlain2<C, W>{FC, st.P, need},
+                   tmp, P.stream)) < 0)
     return TIKH_ECUDA;
   nl += r;
   int bx = (int)std::min<int64_t>((st.P + 255) / 256, 64);
@@ -510,7 +599,7 @@ static int launch_prod_t(Plan& P, const Step& st) {
   const size_t smem = sizeof(cd) * W * (size_t)(BL.cap + BR.cap);
   if (st.P <= P.prod_direct_max && smem <= 48 * 1024) {
     const int ntile = (int)((st.P + PD_TC - 1) / PD_TC);
-    const RootNeed<W> need = need_of<W>(P, st);
+    const ProdNeed<W> need = need_of<W>(P, st);
     launch_k(pdl_enabled(), k_prod_direct<W>, dim3(W * W * ntile, P.nb), dim3(32 * PD_TC), smem, P.stream, BL, BR,
              OUT, (const int*)P.dstack, st.depth, (const int*)P.delta, P.status, ntile, need);
     return cudaGetLastError() == cudaSuccess ? 1 : TIKH_ECUDA;
