@@ -41,6 +41,19 @@ int64_t smooth_at_least(int64_t v) {
   return v;
 }
 
+// the automatic direct/FFT thresholds for `items` items per launch (a single item: the latency-bound forms)
+void auto_thresholds(int64_t items, int prec, int& prod, int& eval) {
+  if (items == 1 || prec != TIKH_PREC_FP64) { prod = 360; eval = 80; return; }
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    sms = 152;
+  }
+  const bool full = items >= sms;
+  prod = full ? FULL_BATCH_PROD_DIRECT_MAX : BATCH_PROD_DIRECT_MAX;
+  eval = full ? FULL_BATCH_EVAL_DIRECT_MAX : BATCH_EVAL_DIRECT_MAX;
+}
+
 void* dalloc(Plan& P, size_t bytes, int& err) {
   if (err) return nullptr;
   void* p = nullptr;
@@ -650,9 +663,10 @@ int plan_setup(Plan& P, const std::vector<Shape>& shapes, int64_t N, int64_t M, 
   // product; with FP32 stages the small nodes stay on the FP64 direct forms whatever the batch: the FP32 FFT
   // forms at the many small nodes dominate the error (measured: 1e-4 .. divergence in batches with the batch
   // thresholds, 3e-5 per solve with these)
-  const bool wide = o.batch == 1 || prec != TIKH_PREC_FP64;
-  P.prod_direct_max = o.prod_direct_max > 0 ? o.prod_direct_max : (wide ? 360 : BATCH_PROD_DIRECT_MAX);
-  P.eval_direct_max = o.eval_direct_max > 0 ? o.eval_direct_max : (wide ? 80 : BATCH_EVAL_DIRECT_MAX);
+  int auto_prod, auto_eval;
+  auto_thresholds(o.batch, prec, auto_prod, auto_eval);
+  P.prod_direct_max = o.prod_direct_max > 0 ? o.prod_direct_max : auto_prod;
+  P.eval_direct_max = o.eval_direct_max > 0 ? o.eval_direct_max : auto_eval;
   P.wait_polls = o.wait_polls > 0 ? o.wait_polls : (1 << 24);
   P.stream = stream;
   P.shapes = shapes;
@@ -1253,9 +1267,10 @@ int tikh_batch_plan_create(tikh_batch_plan* out, int nprob, const int64_t* m, co
     og.batch = G->W;
     // the direct/FFT thresholds follow the group's item count, not its wave size, so an item's arithmetic
     // does not depend on the workspace budget
-    const bool wide = cnt == 1 || prec != TIKH_PREC_FP64;
-    if (og.prod_direct_max == 0) og.prod_direct_max = wide ? 360 : BATCH_PROD_DIRECT_MAX;
-    if (og.eval_direct_max == 0) og.eval_direct_max = wide ? 80 : BATCH_EVAL_DIRECT_MAX;
+    int auto_prod, auto_eval;
+    auto_thresholds(cnt, prec, auto_prod, auto_eval);
+    if (og.prod_direct_max == 0) og.prod_direct_max = auto_prod;
+    if (og.eval_direct_max == 0) og.eval_direct_max = auto_eval;
     err = plan_setup(G->P, gshapes[g], keys[g].N, keys[g].M, keys[g].p, dtype, prec, og, gs, cnt);
     if (err) G->P.stream = gs;  // destroyed by batch_free
   }

@@ -37,8 +37,12 @@ struct BasisBuf {
 // DFS schedule of Algorithm 1: a node (a, s, L) at `depth` has nodes omega^{a + c + s j}, c in {0,1},
 // j < L (s L = N) and 2 NS L conditions (NS condition sets per node: 2, or 3 for the general problem).
 enum StepKind { STEP_LEAF = 0, STEP_EVAL = 1, STEP_PROD = 2 };
-constexpr int BATCH_PROD_DIRECT_MAX = 36;  // automatic thresholds for plans with batch > 1 (measured)
-constexpr int BATCH_EVAL_DIRECT_MAX = 10;
+// automatic direct/FFT thresholds of step 4 (product length P) and step 2 (nodes per coset) for plans with
+// more than one item per launch (measured on GB300): fewer items than SMs leave the GPU room for the
+// direct forms' many small blocks; at least one item per SM makes the FP64 arithmetic the bound, where the
+// O(P log P) transform forms win earlier
+constexpr int BATCH_PROD_DIRECT_MAX = 72, BATCH_EVAL_DIRECT_MAX = 20;            // items < SMs
+constexpr int FULL_BATCH_PROD_DIRECT_MAX = 36, FULL_BATCH_EVAL_DIRECT_MAX = 10;  // items >= SMs
 
 struct Step {
   int kind;
