@@ -103,3 +103,26 @@ def test_column_scaling_by_exponent_arithmetic_matches_the_multiply():
     a, b = oe.cpu().numpy(), om.cpu().numpy()
     assert np.array_equal(a.view(np.int64)[:-1], b.view(np.int64)[:-1])
     assert np.isnan(a[-1]) and np.isnan(b[-1])
+
+
+@pytest.mark.parametrize("K,delta_in,seed", [(8, [-10, -10, 0, 0, 0], 1), (12, [-30, -9, -9, -30, 0], 2),
+                                             (6, [-4, -20, -4, -4, -4], 3)])
+def test_leaf_rows_of_unpivoted_columns_are_exact_identity_rows(K, delta_in, seed):
+    # the evaluations and products skip the rows of a basis outside the columns pivoted in its node and use
+    # them as identity rows: the leaf kernel must produce them exactly (same pivots as the oracle's leaf)
+    rng = np.random.default_rng(seed)
+    sigma = np.exp(2j * np.pi * rng.permutation(4 * K)[:K] / (4 * K))
+    phi = rng.standard_normal((K, 5)) + 1j * rng.standard_normal((K, 5))
+    g = tikh.leaf(torch.tensor(sigma, device=DEV), torch.tensor(phi, device=DEV), delta_in, eps=1e-12)
+    o = oracle.leaf(sigma, phi.copy(), delta_in, eps=1e-12)
+    assert list(g["pivot"][:K]) == list(o["pivot"][:K])
+    unpivoted = [i for i in range(5) if i not in set(int(p) for p in g["pivot"][:K])]
+    assert unpivoted
+    B, ln = g["B"], g["len"]
+    for i in unpivoted:
+        for j in range(5):
+            e = B[5 * i + j, :ln[5 * i + j]]
+            if j == i:
+                assert ln[5 * i + j] >= 1 and e[0] == 1.0 and not np.any(e[1:])
+            else:
+                assert not np.any(e)

@@ -549,3 +549,26 @@ def test_general_difficult_points_processed_at_the_end_match_dense(m, n, p, eps)
     x, st = oracle.solve_general(P["col"], P["row"], P["lcol"], P["lrow"], y, nlim=24, eps_diff=eps)
     assert st["n_difficult"] > 0
     assert relerr(x, xd) <= 1e-10, (st, relerr(x, xd))
+
+
+@pytest.mark.parametrize("K,delta_in,seed", [(8, [-10, -10, 0, 0, 0], 1), (12, [-30, -9, -9, -30, 0], 2),
+                                             (6, [-4, -20, -4, -4, -4], 3)])
+def test_rows_of_unpivoted_columns_stay_identity_rows(K, delta_in, seed):
+    # Eq. (spbasis): a single-point factor changes only its pivot column and its rows other than the pivot's
+    # are identity rows, so in a basis built from several factors every row of a column that was never a
+    # pivot is exactly e_i (the GPU's evaluations and products rely on this to skip those rows)
+    rng = np.random.default_rng(seed)
+    sigma = np.exp(2j * np.pi * rng.permutation(4 * K)[:K] / (4 * K))
+    phi = rng.standard_normal((K, 5)) + 1j * rng.standard_normal((K, 5))
+    out = oracle.leaf(sigma, phi.copy(), delta_in, eps=1e-12)
+    pivoted = set(int(p) for p in out["pivot"][:K])
+    unpivoted = [i for i in range(5) if i not in pivoted]
+    assert unpivoted and all(out["delta"][i] == delta_in[i] for i in unpivoted)
+    B, ln = out["B"], out["len"]
+    for i in unpivoted:
+        for j in range(5):
+            e = B[5 * i + j, :ln[5 * i + j]]
+            if j == i:
+                assert ln[5 * i + j] >= 1 and e[0] == 1.0 and not np.any(e[1:])
+            else:
+                assert not np.any(e)
