@@ -148,16 +148,17 @@ __device__ __forceinline__ void named_sync(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
-// One CTA per problem (blockIdx.x), "component lanes": chain warp w holds residual rows 6w .. 6w+5,
-// lane 5 rr + j holding entry j of row 6w + rr (lanes 30, 31 idle), so the FP64 work of a step that is
-// per entry (magnitudes, the update) is one warp instruction spread over CWN warps on all four SM
-// sub-partitions.  Each step: magnitudes -> row scores (every lane of a row gathers its five
+// One CTA per problem (blockIdx.x), "component lanes": with RPW = 32 / W rows per warp, chain warp w holds
+// residual rows RPW w .. RPW w + RPW - 1, lane W rr + j holding entry j of row RPW w + rr (6 rows and lanes
+// 30, 31 idle for W = 5; 4 rows and lanes 28-31 idle for W = 7), so the FP64 work of a step that is per entry
+// (magnitudes, the update) is one warp instruction spread over CWN warps on all four SM sub-partitions.
+// Each step: magnitudes -> row scores (every lane of a row gathers its W
 // magnitudes) -> per-warp pick -> one named barrier among the chain warps -> the same global pick in
 // every chain warp -> multipliers mu_j (lane j's own column) -> update.  Chain warp 0 publishes the
 // records of step s and then the count s + 1; the four rebuild warps (one per sub-partition) apply
 // B <- B E_s as soon as step s is published, so the chain never waits for the rebuild.
 constexpr long long KEY_NONE = -0x7fffffffffffffffLL - 1;
-constexpr long long KEY_BAND = 16;  // units of 2^-23 in log2 scale; the key's error is below 6 units
+constexpr long long KEY_BAND = 16;  // units of 2^-23 in log2 scale; the key's error is below 8 units
 constexpr long long KEY_SPEC = 0x7fffffffffffffffLL;  // a warp holding a special row (FP64 path)
 
 // Approximate key of the row score |r_pi|^2 / ||r||^2 from the exact FP64 magnitudes' bit patterns,

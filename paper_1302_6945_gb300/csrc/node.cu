@@ -471,7 +471,7 @@ __global__ void k_prod_finish(const C* __restrict__ FC, int64_t P, BasisBuf BL, 
 // Small nodes: schoolbook product B = B_L B_R.  Block = (output entry E = (i, j), tile of PD_TC
 // coefficients, problem); warp w computes coefficient t = tile PD_TC + w, its lanes splitting the
 // terms (u, q) of sum_u sum_q a_iu[q] b_uj[t - q] and a shuffle reduction adding them, so each lane's
-// FP64 chain is short and the product spreads over 25 ceil(P / PD_TC) blocks.  Row i of B_L and
+// FP64 chain is short and the product spreads over W^2 ceil(P / PD_TC) blocks.  Row i of B_L and
 // column j of B_R are staged in shared memory with their column scales applied.  Output trimmed to
 // the degree bound; column maxima accumulated (reset by this node's evaluation step).
 constexpr int PD_TC = 8;
