@@ -164,9 +164,15 @@ void build_steps(Plan& P, std::vector<Step>& out, int depth, int64_t a, int64_t 
   memcpy(din, sd, sizeof(int) * W);
   pending |= (1ULL << depth);
   build_steps(P, out, depth + 1, a, 2 * s, L / 2, 0, sd, pending, slack);
+  int dmid[WMAX];
+  memcpy(dmid, sd, sizeof(int) * W);
+  unsigned sl = 0u, sr = 0u;
+  for (int j = 0; j < W; ++j) sl |= (dmid[j] > din[j] ? 1u : 0u) << j;
   Step ev{STEP_EVAL, depth, side, a, s, L, -1, 0, 0};
+  ev.sl = sl;
   out.push_back(ev);
   build_steps(P, out, depth + 1, a + s, 2 * s, L / 2, 1, sd, pending, slack);
+  for (int j = 0; j < W; ++j) sr |= (sd[j] > dmid[j] ? 1u : 0u) << j;
   int D = -1;
   for (int i = 0; i < W; ++i)
     for (int j = 0; j < W; ++j) D = std::max(D, entry_bound_host(W, din, sd, i, j));
@@ -176,6 +182,8 @@ void build_steps(Plan& P, std::vector<Step>& out, int depth, int64_t a, int64_t 
   int64_t Pn = smooth_at_least(
       std::max<int64_t>(NS * L + 1, std::min<int64_t>((int64_t)D + 1 + slack, 2 * NS * L + 1)));
   Step pr{STEP_PROD, depth, side, a, s, L, -1, Pn, 0};
+  pr.sl = sl;
+  pr.sr = sr;
   out.push_back(pr);
 }
 
@@ -186,11 +194,15 @@ void build_steps(Plan& P, std::vector<Step>& out, int depth, int64_t a, int64_t 
 //    remaining condition and 90 per step at W = 5, both proportional to the row length W) plus
 //    (W^2/25) 20 K^2 for the basis rebuild (W^2 entries); 50 K^2 + 90 K at W = 5;
 //  evaluation at Lr = L/2 nodes per coset: direct, 2 Lr nodes x W^2 entries x len Horner steps; FFT, the
-//    twist-fold (2 W^2 x len) and 2 W^2 transforms of Lr; both plus the update, 2 Lr nodes x NS rows x
+//    twist-fold (2 |S_L| W x len) and 2 |S_L| W transforms of Lr (the identity rows of B_L, outside the
+//    columns S_L the left child pivots, are not transformed); both plus the update, 2 Lr nodes x NS rows x
 //    W^2 CMACs; len = NS L / W + 1 is the mean entry length of the left child (its NS L conditions raise
 //    each of the W columns by NS L / W);
-//  product of length P: direct, W^2 outputs x W convolutions of len x len; FFT, 3 W^2 transforms of P
-//    and W^2 x W pointwise CMACs per bin;
+//  product of length P: direct, W^2 outputs x W convolutions of len x len; FFT, one transform of P per
+//    operand entry outside the identity rows ((|S_L| + |S_R|) W) and per output entry in the rows S_L u S_R,
+//    and W pointwise CMACs per output entry and bin; on the right spine (no deferred condition assumed)
+//    only column j*: |S_L| W + |S_R| operand and |S| output transforms, and at the root only rows 0 and
+//    W - 1 of B_L and those two rows of the output;  S_L, S_R from the water-filling prediction;
 //  other: the length-N transforms of the extension (one more for L or G), right-hand side and conditions.
 void model_flops(Plan& P) {
   auto fft = [](double L) { return L > 1 ? 5.0 * L * std::log2(L) : 0.0; };
@@ -203,10 +215,11 @@ void model_flops(Plan& P) {
       P.last.model_flops[0] += (W / 5) * (30 * K * K + 90 * K) + (WW / 25) * 20 * K * K;
     } else if (st.kind == STEP_EVAL) {
       const double upd = 2 * Lr * NS * WW * 8;
+      const double nsl = __builtin_popcount(st.sl);
       if (st.L / 2 <= P.eval_direct_max) {
         P.last.model_flops[1] += 2 * Lr * WW * len * 8 + upd;
       } else {
-        const double f = 2 * WW * len * 8 + 2 * WW * fft(Lr) + upd;
+        const double f = 2 * nsl * W * len * 8 + 2 * nsl * W * fft(Lr) + upd;
         P.last.model_flops[1] += f;
         if (P.stage32) P.last.model_flops_fp32[1] += f;
       }
@@ -215,7 +228,16 @@ void model_flops(Plan& P) {
       if (st.P <= P.prod_direct_max) {
         P.last.model_flops[2] += WW * W * len * len * 8;
       } else {
-        const double f = 3 * WW * fft(Pl) + WW * W * Pl * 8;
+        const int mode = st.depth == 0 ? 2 : (st.a == st.s - 2 ? 1 : 0);  // the root, the right spine, other
+        const unsigned su = st.sl | st.sr;
+        const double nsl = __builtin_popcount(st.sl), nsr = __builtin_popcount(st.sr), nsu = __builtin_popcount(su);
+        const double ends = (double)((su & 1u) != 0) + (double)(((su >> (P.w - 1)) & 1u) != 0);  // rows 0, W - 1
+        const double endsl = (double)((st.sl & 1u) != 0) + (double)(((st.sl >> (P.w - 1)) & 1u) != 0);
+        double operands, outputs;
+        if (mode == 0) { operands = (nsl + nsr) * W; outputs = nsu * W; }
+        else if (mode == 1) { operands = nsl * W + nsr; outputs = nsu; }
+        else { operands = endsl * W + nsr; outputs = ends; }
+        const double f = (operands + outputs) * fft(Pl) + outputs * W * Pl * 8;
         P.last.model_flops[2] += f;
         if (P.stage32) P.last.model_flops_fp32[2] += f;
       }

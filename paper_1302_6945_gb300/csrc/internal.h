@@ -52,6 +52,9 @@ struct Step {
   int fft;          // FFT plan index: eval length L/2 (STEP_EVAL) or product length P (STEP_PROD)
   int64_t P;        // product transform length (STEP_PROD)
   uint64_t save_mask;  // STEP_LEAF: depths whose delta_in is this leaf's delta_in
+  // STEP_EVAL / STEP_PROD: the columns the water-filling prediction pivots in the left child (sl) and the
+  // right child (sr), i.e. the rows of their bases that are not identity rows (the cost model's count)
+  unsigned sl = 0u, sr = 0u;
 };
 
 // Shape of one problem: user m x n, the core (tall) problem cm x cn (cm >= cn; T^H for m < n) and the
