@@ -413,7 +413,7 @@ int tikh_test_peak(int kind, double* gflops, void* stream);
  * tikh_test_fft).  data: n complex128 values on the device, transformed in place; the call
  * synchronises the stream.
  * The first call on each device looks up the scratch array's device address (cudaGetSymbolAddress)
- * with that device current; make that first call before any stream capture.  Every call rewrites the
+ * with that device current.  Every call rewrites the
  * parts of the scratch it reads, so nothing needs clearing, but all calls share the one array: calls
  * that overlap on the GPU (other streams, other host threads) race and must be serialised by the
  * caller. */
