@@ -59,6 +59,28 @@ def test_batch_of_problems_matches_single_solves(m, n, cplx):
         assert relerr(xa[i], xs_auto) <= max(1e-10, 5 * relerr(xo, xd)), (i, relerr(xa[i], xs_auto))
 
 
+@pytest.mark.parametrize("m,n,cplx", [(900, 640, False), (400, 600, True)])
+def test_several_right_hand_sides_of_one_matrix(m, n, cplx):
+    # one T (col and row shared, stride 0) and R right-hand sides: b enters every pivot decision (Sec. 4.3),
+    # so each is its own item of one strided batch; each matches its single solve and the dense solution
+    R = 5
+    P = W.deconvolution_problem(m, n, 4.0, 16, 1e-6, 1e-6, 1e-3, seed=77, complex_data=cplx, signal="smooth")
+    rng = np.random.default_rng(78)
+    bs = rng.standard_normal((R, m)) + (1j * rng.standard_normal((R, m)) if cplx else 0.0)
+    dt = torch.complex128 if cplx else torch.float64
+    t = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=dt, device=DEV)
+    same = dict(prod_direct_max=36, eval_direct_max=10)
+    plan = tikh.Plan(m, n, "c128" if cplx else "r64", batch=R, **same)
+    x = plan.solve_strided(t(P["col"]), t(P["row"]), t(bs), [P["lam"]] * R).cpu().numpy()
+    plan.close()
+    for i in range(R):
+        q = dict(P, b=bs[i])
+        xs = _single(q, cplx, **same)
+        assert relerr(x[i], xs) <= 1e-14, (i, relerr(x[i], xs))
+        xd = oracle.dense_solve(P["col"], P["row"], bs[i], P["lam"])
+        assert relerr(x[i], xd if cplx else xd.real) <= 1e-9, (i, relerr(x[i], xd))
+
+
 def test_regularisation_path_shares_generator_and_data():
     # one T and b, 16 lambdas log-spaced 1e-6 .. 1 (the batching workload's path), stride 0 inputs
     P = W.deconvolution_problem(1024, 1024, 4.0, 16, 1e-6, 1e-6, 1.0, seed=5)
