@@ -1135,9 +1135,9 @@ static int grad_run(Plan& P, const std::vector<ItemDev>& items, const double* la
   if (P.dual || P.gram || P.general) return TIKH_EINVAL;  // the adjoint is implemented for the l2 problem, m >= n
   const int nb = (int)items.size();
   int err = 0;
-  if (!P.gbuf) {  // adjoint workspace, allocated by the first gradient call
-    P.gbuf = (cd*)dalloc(P, sizeof(cd) * (size_t)(4 * P.N + 2 * P.cm) * (size_t)P.batch_max, err);
-    P.gdl = (double*)dalloc(P, sizeof(double) * (size_t)P.batch_max, err);
+  if (!P.gbuf || !P.gdl) {  // adjoint workspace, allocated by the first gradient call (again after a failure)
+    if (!P.gbuf) P.gbuf = (cd*)dalloc(P, sizeof(cd) * (size_t)(4 * P.N + 2 * P.cm) * (size_t)P.batch_max, err);
+    if (!P.gdl) P.gdl = (double*)dalloc(P, sizeof(double) * (size_t)P.batch_max, err);
     if (err) return err;
   }
   P.items = P.items_base;
