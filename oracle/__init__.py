@@ -10,6 +10,9 @@ Two oracles live here:
   * the C oracle (``tikh_oracle.c``) -- the paper's algorithm step by step in FP64 (extension,
     transformation, Algorithm 1 with paired interleaving, serial leaves with pivoting, difficult
     points, extraction), with its own textbook DFT.
+Beside them, plain numpy for one solver serving many right-hand sides (``inverse_generators``,
+``inverse_apply``): the displacement representation of (T^H T + lam I)^{-1}, an extension the paper
+does not have, pinned against dense inverses.
 """
 import ctypes
 import os
@@ -362,3 +365,97 @@ def adjoint(col, row, b, lam, x, G, steps=1, nlim=32):
     drow = np.zeros(n, np.complex128)
     drow[1:] = c[n - 2::-1][:n - 1]
     return dcol, drow, u, float(-np.real(np.vdot(g, x)))
+
+
+# ---------------------------------------------------------------------------------------------
+# One solver for many right-hand sides (an extension: the paper solves one right-hand side per run).
+#
+# b enters the conditions' fifth component and with it every pivot decision (Sec. 4.3), so the
+# interpolation basis of one solve does not serve another right-hand side.  What does carry over is
+# the matrix: A = T^H T + lam I (m >= n) has low displacement rank, and so has its inverse.  With Z
+# the n x n down-shift ((Z v)_j = v_{j-1}, (Z v)_0 = 0), e_0, f = e_{n-1} and t_d the diagonals of T:
+#   A - Z A Z^H = p p^H - q q^H + e_0 s^H + s e_0^H,
+#     p_j = conj(t_{-j}),  q_j = conj(t_{m-j}) (q_0 = 0),  s = A e_0 - t_0 p with s_0 halved
+# (entries (j, k), j, k >= 1: the sum defining (T^H T)_{jk} minus the same sum shifted by one row of
+# T keeps the terms of row 0 and row m of the infinite Toeplitz extension; row and column 0 are
+# A's own).  Multiplying Z A Z^H = A - (...) by X = A^{-1} and using Z^H Z = I - f f^H gives
+#   X - Z^H X Z = (f - c) a^H + sum_{g in {p, q, e_0, s}} +-(Z^H X g)(X Z^H g')^H ,
+# i.e. four rank-one terms (u_t, w_t) built from eight solves X v_i (inverse_rhs below), and since
+# Z is nilpotent the Stein equation sums to X = sum_{k<n} (Z^H)^k (X - Z^H X Z) Z^k, that is
+#   X y = sum_t H(u_t) H(w_t)^H y,   H(u)_{ik} = u_{i+k} (0 for i + k >= n)  (a Hankel matrix).
+# Each term is two correlations, O(n log n) by FFT: after eight solves, every further right-hand
+# side of the same T and lam costs a few FFTs instead of a superfast solve.
+# ---------------------------------------------------------------------------------------------
+
+def _up(v):  # Z^H v
+    return np.concatenate([v[1:], np.zeros(1, np.complex128)])
+
+
+def _down(v):  # Z v
+    return np.concatenate([np.zeros(1, np.complex128), v[:-1]])
+
+
+def displacement_generators(col, row, lam):
+    """p, q, s of A - Z A Z^H = p p^H - q q^H + e_0 s^H + s e_0^H for A = T^H T + lam I (m >= n)."""
+    col, row = _c128(col), _c128(row)
+    m, n = col.size, row.size
+    if m < n:
+        raise ValueError("m >= n")
+    p = np.conj(np.concatenate([col[:1], row[1:]]))
+    q = np.zeros(n, np.complex128)
+    q[1:] = np.conj(col[m - np.arange(1, n)])
+    e0 = np.zeros(n, np.complex128)
+    e0[0] = 1.0
+    s = apply_th(col, row, col) + lam * e0 - col[0] * p  # T e_0 is T's first column
+    s[0] *= 0.5
+    return p, q, s
+
+
+def inverse_rhs(col, row, lam):
+    """The eight right-hand sides v_1..v_8 = f, Z A f, p, q, e_0, Z^H p, Z^H q, Z^H s (m >= n)."""
+    col, row = _c128(col), _c128(row)
+    n = row.size
+    p, q, s = displacement_generators(col, row, lam)
+    e0 = np.zeros(n, np.complex128)
+    e0[0] = 1.0
+    f = np.zeros(n, np.complex128)
+    f[-1] = 1.0
+    Af = apply_th(col, row, apply_t(col, row, f)) + lam * f
+    return [f, _down(Af), p, q, e0, _up(p), _up(q), _up(s)]
+
+
+def inverse_generators(col, row, lam, solve=None):
+    """The four terms (u_t, w_t) with (T^H T + lam I)^{-1} = sum_t H(u_t) H(w_t)^H, as arrays u (4, n), w (4, n).
+
+    solve(y) -> A^{-1} y defaults to the oracle's superfast solve with one refinement correction (Sec. 7.2):
+    some of the eight right-hand sides (Z^H s, q: a few entries of T's far diagonals) come out of a plain
+    superfast solve 100x less accurate than a data vector does, and their error carries into every apply."""
+    if solve is None:
+        solve = lambda y: solve_normal_refined(col, row, y, lam, steps=1)
+    v = inverse_rhs(col, row, lam)
+    xs = [_c128(solve(vi)) for vi in v]
+    n = len(v[0])
+    f = v[0]
+    u = np.stack([f - _up(xs[1]), _up(xs[2]), -_up(xs[3]), _up(xs[4])])
+    w = np.stack([xs[0], xs[5], xs[6], xs[7]])
+    assert u.shape == (4, n) and w.shape == (4, n)
+    return u, w
+
+
+def hankel_dense(u):
+    """H(u)_{ik} = u_{i+k} for i + k < n, else 0."""
+    u = _c128(u)
+    n = u.size
+    i = np.arange(n)[:, None] + np.arange(n)[None, :]
+    return np.where(i < n, u[np.clip(i, 0, n - 1)], 0.0)
+
+
+def inverse_apply(u, w, y):
+    """x = sum_t H(u_t) H(w_t)^H y by plain sums: c_k = sum_j conj(w_{j+k}) y_j, x_i = sum_k u_{i+k} c_k."""
+    y = _c128(y)
+    n = y.size
+    x = np.zeros(n, np.complex128)
+    for ut, wt in zip(_c128(u), _c128(w)):
+        c = np.array([np.vdot(wt[k:], y[:n - k]) for k in range(n)])
+        x += np.array([np.dot(ut[i:], c[:n - i]) for i in range(n)])
+    return x

@@ -572,3 +572,78 @@ def test_rows_of_unpivoted_columns_stay_identity_rows(K, delta_in, seed):
                 assert ln[5 * i + j] >= 1 and e[0] == 1.0 and not np.any(e[1:])
             else:
                 assert not np.any(e)
+
+
+# ---- one solver for many right-hand sides: the displacement representation of (T^H T + lam I)^{-1} ----
+
+def _rand_toeplitz(m, n, cplx, seed):
+    rng = np.random.default_rng(seed)
+    c = rng.standard_normal(m) + (1j * rng.standard_normal(m) if cplx else 0.0)
+    r = rng.standard_normal(n) + (1j * rng.standard_normal(n) if cplx else 0.0)
+    r[0] = c[0]
+    return c, r
+
+
+@pytest.mark.parametrize("m,n,cplx", [(7, 5, False), (30, 20, True), (16, 16, False), (40, 9, True)])
+def test_displacement_of_the_normal_matrix(m, n, cplx):
+    # A - Z A Z^H written out densely against p p^H - q q^H + e_0 s^H + s e_0^H
+    col, row = _rand_toeplitz(m, n, cplx, m + n)
+    lam = 0.37
+    T = oracle.toeplitz_dense(col, row)
+    A = T.conj().T @ T + lam * np.eye(n)
+    Z = np.eye(n, k=-1)
+    p, q, s = oracle.displacement_generators(col, row, lam)
+    e0 = np.eye(n)[0]
+    D = np.outer(p, p.conj()) - np.outer(q, q.conj()) + np.outer(e0, s.conj()) + np.outer(s, e0)
+    assert np.abs((A - Z @ A @ Z.T) - D).max() <= 1e-12 * np.abs(A).max()
+
+
+@pytest.mark.parametrize("m,n,cplx", [(7, 5, False), (30, 20, True), (16, 16, True), (40, 9, False)])
+def test_inverse_is_the_sum_of_four_hankel_products(m, n, cplx):
+    # with exact solves: the Stein-equation terms against the dense inverse, matrix by matrix
+    col, row = _rand_toeplitz(m, n, cplx, 3 * m + n)
+    lam = 0.5
+    T = oracle.toeplitz_dense(col, row)
+    A = T.conj().T @ T + lam * np.eye(n)
+    X = np.linalg.inv(A)
+    u, w = oracle.inverse_generators(col, row, lam, solve=lambda y: np.linalg.solve(A, y))
+    Z = np.eye(n, k=-1)
+    D = sum(np.outer(u[t], w[t].conj()) for t in range(4))
+    assert np.abs(D - (X - Z.T @ X @ Z)).max() <= 1e-12 * np.abs(X).max()
+    H = lambda v: oracle.hankel_dense(v)
+    Xr = sum(H(u[t]) @ H(w[t]).conj().T for t in range(4))
+    assert np.abs(Xr - X).max() <= 1e-12 * np.abs(X).max()
+    y = np.random.default_rng(1).standard_normal(n) + 0j
+    assert np.linalg.norm(oracle.inverse_apply(u, w, y) - X @ y) <= 1e-12 * np.linalg.norm(X @ y)
+
+
+def test_inverse_generators_of_a_scaled_identity():
+    # T = 0: A = lam I, the only term is (f, f / lam), and sum_k (Z^H)^k f f^H Z^k / lam = I / lam
+    n, lam = 9, 0.25
+    u, w = oracle.inverse_generators(np.zeros(12), np.zeros(n), lam, solve=lambda y: y / lam)
+    f = np.eye(n)[-1]
+    assert np.allclose(u[0], f, atol=0) and np.allclose(w[0], f / lam, atol=0)
+    assert not np.any(u[1:] * 0 != 0) and np.abs(u[1:]).max() * np.abs(w[1:]).max() == 0.0
+    y = np.arange(1.0, n + 1)
+    assert np.allclose(oracle.inverse_apply(u, w, y), y / lam, rtol=1e-15, atol=0)
+
+
+@pytest.mark.parametrize("m,n,cplx,lam", [(300, 200, False, 1e-3), (256, 256, True, 1e-2)])
+def test_inverse_from_superfast_solves_matches_dense(m, n, cplx, lam):
+    # the generators from the oracle's (refined) superfast solves: every right-hand side through the
+    # Hankel sums lands within 1e-11 of the dense solution (condition numbers 1e3 and 20 here); from
+    # unrefined solves (errors up to 4e-8 on the hardest generator) one correction x += X~(y - A x)
+    # with the same sums does the same
+    P = W.deconvolution_problem(m, n, 3.0, 12, 1e-6, 1e-6, lam, seed=n, complex_data=cplx, signal="smooth")
+    col, row = P["col"], P["row"]
+    u, w = oracle.inverse_generators(col, row, lam)
+    u0, w0 = oracle.inverse_generators(col, row, lam, solve=lambda y: oracle.solve_normal(col, row, y, lam)[0])
+    A = lambda v: oracle.apply_th(col, row, oracle.apply_t(col, row, v)) + lam * v
+    rng = np.random.default_rng(2)
+    for _ in range(3):
+        y = rng.standard_normal(n) + (1j * rng.standard_normal(n) if cplx else 0.0)
+        xd = oracle.dense_solve_normal(col, row, y, lam)
+        err = lambda v: np.linalg.norm(v - xd) / np.linalg.norm(xd)
+        assert err(oracle.inverse_apply(u, w, y)) <= 1e-11
+        x0 = oracle.inverse_apply(u0, w0, y)
+        assert err(x0 + oracle.inverse_apply(u0, w0, y - A(x0))) <= 1e-11
