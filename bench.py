@@ -8,7 +8,8 @@ set (~1 GB) exceeds L2 and L2 is also flushed between steps.  e2e repeats the me
 tikh_solve_host with host buffers (copies inside the timed region).  The default run also reports the
 metric's n sweep (n = 2^17 .. 2^20, m = 1.5 n, one FP64 refinement correction) under "sweep".
 The same run times one solve of the general problem (Sec. 3.2, T and L 65536 x 65536) under
-"general_problem".
+"general_problem", and under "many_rhs" the benchmarked T and lambda with 16 right-hand sides per call
+through the displacement representation of the inverse (tikh_inverse_*, an extension of the paper).
 
 --config c3 runs the batching configuration instead: 512 real problems of uneven shape, each with a
 16-value regularisation path, as one ragged batch (tikh_solve_batched, one captured graph per call).
@@ -582,6 +583,56 @@ def sweep_point(tikh, torch, n, refine, args, stream, dev):
                              "correction at n = 2^20 against two)"}
 
 
+def many_rhs_point(tikh, torch, P, col, row, x_ref, superfast_ms, p64, args, stream, dev, R=16):
+    """Many right-hand sides of the benchmarked T and lambda (tikh_inverse_*, an extension of the paper): the
+    displacement representation of (T^H T + lam I)^{-1} from eight superfast solves (one batch of 8, one FP64
+    correction each), then R right-hand sides per apply (T^H b, ten transforms, one correction of fourteen).
+    Right-hand side 0 is the benchmarked b, whose solution is compared with the refined superfast solve."""
+    import numpy as np
+    m, n, lam = P["m"], P["n"], P["lam"]
+    rng = np.random.default_rng(31)
+    bs = np.stack([P["b"]] + [P["b"] + 0.05 * np.abs(P["b"]).max() * (rng.standard_normal(m) + 1j * rng.standard_normal(m))
+                              for _ in range(R - 1)])
+    bt = torch.tensor(bs, dtype=torch.complex128, device=dev)
+    xs = torch.empty((R, n), dtype=torch.complex128, device=dev)
+    plan = tikh.Plan(m, n, "c128", n_lim=args.n_lim, refine_steps=1, batch=8, graph=True, stream=stream)
+    with torch.cuda.stream(stream):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        inv = tikh.Inverse(plan, col, row, lam, max_rhs=R)
+        create_ms = (time.perf_counter() - t0) * 1e3
+        create_launches = inv.info()["kernel_launches"]
+        inv.apply(bt, refine_steps=1, x=xs)  # warm-up
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        steps = max(3, args.sweep_steps)
+        e0.record(stream)
+        for _ in range(steps):
+            inv.apply(bt, refine_steps=1, x=xs)
+        e1.record(stream)
+        e1.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    info = inv.info()
+    N = plan.stats()["N"]
+    err = float(torch.linalg.norm(xs[0] - x_ref) / torch.linalg.norm(x_ref))
+    inv.close()
+    plan.close()
+    transforms = R * (12 + 14)  # from b: T^H b and the apply; one correction
+    flops = transforms * 5.0 * N * math.log2(N)
+    per_rhs = ms / R
+    return {"what": "many right-hand sides of one T and lambda: displacement representation of (T^H T + lam I)^-1 "
+                    "(eight superfast solves), then FFT applies (tikh_inverse_create / tikh_inverse_apply)",
+            "rhs_per_apply": R, "ms_per_apply": ms, "rhs_per_s": R * 1e3 / ms, "ms_per_rhs": per_rhs,
+            "create_ms": create_ms, "create_kernel_launches": create_launches,
+            "apply_kernel_launches": info["kernel_launches"], "workspace_bytes": info["workspace_bytes"],
+            "superfast_ms_per_solve": superfast_ms,
+            "speedup_per_extra_rhs": superfast_ms / per_rhs,
+            "break_even_rhs": create_ms / max(superfast_ms - per_rhs, 1e-9),
+            "rel_err_vs_refined_superfast": err, "refine_steps": 1,
+            "fft_fp64": {"model_flops_per_apply": flops, "model": "5 N log2 N per length-N transform, %d transforms"
+                         % transforms, "achieved_gflops": flops / (ms * 1e-3) / 1e9,
+                         "frac_of_fp64_peak": flops / (ms * 1e-3) / 1e9 / p64}}
+
+
 def general_point(tikh, torch, n, args, stream, dev):
     """The general problem (Sec. 3.2) at T, L n x n: one warm-up (graph capture) and args.sweep_steps timed
     solves, the normal-equation residual of the result."""
@@ -807,6 +858,9 @@ def main():
     general = None
     if rank == 0 and world == 1 and not args.no_sweep and args.n is None and B == 1 and args.precision == "fp64":
         general = general_point(tikh, torch, 1 << 16, args, stream, dev)
+    many = None
+    if rank == 0 and world == 1 and not args.no_sweep and args.n is None and B == 1 and args.precision == "fp64":
+        many = many_rhs_point(tikh, torch, P, col[0], row[0], x_ref, t_step, p64, args, stream, dev)
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
@@ -840,6 +894,7 @@ def main():
                "step_breakdown": breakdown,
                "sweep": sweep,
                "general_problem": general,
+               "many_rhs": many,
                "cpu_baseline": cpu}
         print(json.dumps(out))
     plan.close()

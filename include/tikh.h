@@ -399,6 +399,43 @@ int tikh_test_leaf(int K, const void* sigma, const void* r, const int* delta_in,
  * TIKH_EINVAL for a NULL gflops or another kind. */
 int tikh_test_peak(int kind, double* gflops, void* stream);
 
+/* ---- one solver for many right-hand sides ---- */
+
+/* The paper's solver builds one interpolation basis per right-hand side: b enters the conditions' fifth
+ * component and every pivot decision (Sec. 4.3).  For many right-hand sides of one T and lambda this
+ * extension (the paper has none) reuses the matrix instead: A = T^H T + lambda I has displacement rank 4
+ * (A - Z A Z^H, Z the down-shift), and so has X = A^{-1}.  Eight superfast solves X v_i (right-hand sides
+ * built from T's first row, first column, last column and A e_0) give four pairs (u_t, w_t) with
+ *   X = sum_t H(u_t) H(w_t)^H,   H(u)_{ik} = u_{i+k} (0 for i + k >= n)  (Hankel),
+ * and every further right-hand side costs ten length-N transforms (twelve from b), plus fourteen per
+ * refinement correction x += X~(y - A x) (the residual by the FFT matvec of Sec. 7.3, as in Sec. 7.2).
+ * The handle keeps the spectra of the four pairs and of T's generator (9 N complex128) and the workspace
+ * of one pass over up to max_rhs right-hand sides (about 13 max_rhs N complex128). */
+typedef struct tikh_inverse_s* tikh_inverse;
+
+/* Build the representation for the l2 plan `plan` (m >= n; not a Toeplitz-Gramian or general plan) with
+ * T given by col, row (device arrays of the plan's dtype) and weight lambda > 0.  The eight solves run on
+ * the plan (its options apply: batch size, refinement, graph) in batches of opts.batch; the plan must
+ * outlive the handle and must not run other calls concurrently with it (same stream).  max_rhs in
+ * 1..4096.  Synchronises; returns the first failing solve's status, TIKH_ENOMEM, or TIKH_EINVAL. */
+int tikh_inverse_create(tikh_inverse* out, tikh_plan plan, const void* col, const void* row, double lambda,
+                        int max_rhs);
+
+/* x_r = (T^H T + lambda I)^{-1} T^H b_r (normal = 0; b_r has m entries) or (T^H T + lambda I)^{-1} y_r
+ * (normal = 1; n entries), r < nrhs, then refine_steps (0..16) corrections each.  Right-hand side r at
+ * b + r * b_stride, its solution at x + r * x_stride (device arrays, plan dtype; strides in elements,
+ * >= the vector lengths when nrhs > 1).  Passes of max_rhs right-hand sides.  Synchronises. */
+int tikh_inverse_apply(tikh_inverse inv, int nrhs, const void* b, int64_t b_stride, void* x, int64_t x_stride,
+                       int normal, int refine_steps);
+
+/* Copy u_0..u_3, w_0..w_3 (8 n complex128, n apart) to the device array out.  Synchronises. */
+int tikh_inverse_generators(tikh_inverse inv, void* out);
+
+/* Kernels launched by the last create or apply, and the handle's device bytes. */
+int tikh_inverse_info(tikh_inverse inv, int64_t* kernel_launches, int64_t* workspace_bytes);
+
+void tikh_inverse_destroy(tikh_inverse inv);
+
 /* ---- allocation-free variant ---- */
 
 /* The DFT of tikh_test_fft (same transform, same kernels, same result) for callers that must not

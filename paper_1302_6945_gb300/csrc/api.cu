@@ -1463,6 +1463,155 @@ void tikh_plan_destroy(tikh_plan h) {
   delete h;
 }
 
+// ---- one solver for many right-hand sides (csrc/inverse.cu) ----
+
+struct tikh_inverse_s {
+  Plan* P = nullptr;  // the plan it was built with (not owned): FFT tables, stream
+  InvWork w;
+  std::vector<void*> allocs;
+  int64_t bytes = 0;
+  int64_t launches = 0;  // kernels of the last create or apply
+};
+
+static void inverse_free(tikh_inverse v) {
+  for (void* p : v->allocs) cudaFree(p);
+  delete v;
+}
+
+int tikh_inverse_create(tikh_inverse* out, tikh_plan h, const void* col, const void* row, double lambda,
+                        int max_rhs) {
+  if (!out) return TIKH_EINVAL;
+  *out = nullptr;
+  if (!h || !col || !row || !valid_lambda(lambda) || max_rhs < 1 || max_rhs > 4096) return TIKH_EINVAL;
+  Plan& P = h->P;
+  if (P.gram || P.general || P.dual || P.shapes.size() != 1) return TIKH_EINVAL;
+  // the batched four-step passes index batch x L2 transforms with int
+  const FftPlan& F0 = P.ffts[P.fft_of_len.at(P.N)];
+  if (F0.four && (int64_t)std::max(4 * max_rhs, 8) * std::max(F0.L1, F0.L2) >= (int64_t)1 << 30) return TIKH_EINVAL;
+  tikh_inverse v = new (std::nothrow) tikh_inverse_s;
+  if (!v) return TIKH_ENOMEM;
+  v->P = &P;
+  InvWork& w = v->w;
+  w.m = P.m;
+  w.n = P.n;
+  w.N = P.N;
+  w.dtype = P.dtype;
+  w.lam = lambda;
+  w.R = max_rhs;
+  int err = 0;
+  auto al = [&](size_t bytes) -> void* {
+    if (err) return nullptr;
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      err = TIKH_ENOMEM;
+      return nullptr;
+    }
+    v->allocs.push_back(p);
+    v->bytes += (int64_t)bytes;
+    return p;
+  };
+  const size_t N = (size_t)P.N, n = (size_t)P.n, m = (size_t)P.m, R = (size_t)max_rhs, c = sizeof(cd);
+  const size_t es = P.dtype == TIKH_C128 ? 16 : 8;
+  w.spec = (cd*)al(c * 9 * N);
+  w.gen = (cd*)al(c * 8 * n);
+  w.Ae = (cd*)al(c * 2 * n);
+  w.rhs8 = al(es * 8 * n);
+  w.sol8 = al(es * 8 * n);
+  w.Y = (cd*)al(c * std::max<size_t>(R, 2) * N);
+  w.C = (cd*)al(c * 4 * R * N);
+  w.G = (cd*)al(c * 4 * R * N);
+  w.tmp = (cd*)al(c * std::max<size_t>(4 * R, 8) * N);
+  w.y = (cd*)al(c * R * n);
+  w.x = (cd*)al(c * R * n);
+  w.r = (cd*)al(c * R * n);
+  w.u = (cd*)al(c * R * m);
+  if (err) {
+    inverse_free(v);
+    return err;
+  }
+  int rc = launch_inv_prepare(F0, w, col, row, P.stream);
+  if (rc < 0) {
+    inverse_free(v);
+    return rc;
+  }
+  int64_t nl = rc;
+  // the eight solves X v_i (normal form), as batches of the plan's size
+  for (int i0 = 0; i0 < 8; i0 += P.batch_max) {
+    const int cnt = std::min(8 - i0, P.batch_max);
+    std::vector<ItemDev> items;
+    for (int i = i0; i < i0 + cnt; ++i)
+      items.push_back(make_item(P.shapes[0], col, row, (const char*)w.rhs8 + es * n * (size_t)i,
+                                (char*)w.sol8 + es * n * (size_t)i));
+    const std::vector<double> lams((size_t)cnt, lambda);
+    if ((rc = solve_with_retry(P, items, lams.data(), 1, nullptr, nullptr, 0))) {
+      inverse_free(v);
+      return rc;
+    }
+    nl += P.last.kernel_launches;
+  }
+  // a re-plan inside the solves may have grown P.ffts: look the length-N transform up again
+  if ((rc = launch_inv_terms(P.ffts[P.fft_of_len.at(P.N)], w, P.stream)) < 0) {
+    inverse_free(v);
+    return rc;
+  }
+  v->launches = nl + rc;
+  if (cudaStreamSynchronize(P.stream) != cudaSuccess) {
+    cudaGetLastError();
+    inverse_free(v);
+    return TIKH_ECUDA;
+  }
+  *out = v;
+  return TIKH_OK;
+}
+
+int tikh_inverse_apply(tikh_inverse v, int nrhs, const void* b, int64_t b_stride, void* x, int64_t x_stride,
+                       int normal, int refine_steps) {
+  if (!v || !b || !x || nrhs < 1 || refine_steps < 0 || refine_steps > 16 || (normal != 0 && normal != 1))
+    return TIKH_EINVAL;
+  InvWork& w = v->w;
+  if (nrhs > 1 && (b_stride < (normal ? w.n : w.m) || x_stride < w.n)) return TIKH_EINVAL;
+  Plan& P = *v->P;
+  const FftPlan& F = P.ffts[P.fft_of_len.at(w.N)];
+  const size_t es = w.dtype == TIKH_C128 ? 16 : 8;
+  int64_t nl = 0;
+  for (int c0 = 0; c0 < nrhs; c0 += w.R) {
+    const int nb = std::min(w.R, nrhs - c0);
+    const int rc = launch_inv_apply(F, w, nb, (const char*)b + es * (size_t)c0 * (size_t)b_stride, b_stride, normal,
+                                    refine_steps, (char*)x + es * (size_t)c0 * (size_t)x_stride, x_stride, P.stream);
+    if (rc < 0) return rc;
+    nl += rc;
+  }
+  v->launches = nl;
+  if (cudaStreamSynchronize(P.stream) != cudaSuccess) {
+    cudaGetLastError();
+    return TIKH_ECUDA;
+  }
+  return TIKH_OK;
+}
+
+int tikh_inverse_generators(tikh_inverse v, void* out) {
+  if (!v || !out) return TIKH_EINVAL;
+  if (cudaMemcpyAsync(out, v->w.gen, sizeof(cd) * 8 * (size_t)v->w.n, cudaMemcpyDeviceToDevice, v->P->stream) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(v->P->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return TIKH_ECUDA;
+  }
+  return TIKH_OK;
+}
+
+int tikh_inverse_info(tikh_inverse v, int64_t* kernel_launches, int64_t* workspace_bytes) {
+  if (!v || !kernel_launches || !workspace_bytes) return TIKH_EINVAL;
+  *kernel_launches = v->launches;
+  *workspace_bytes = v->bytes;
+  return TIKH_OK;
+}
+
+void tikh_inverse_destroy(tikh_inverse v) {
+  if (v) inverse_free(v);
+}
+
 const char* tikh_strerror(int s) {
   switch (s) {
     case TIKH_OK: return "ok";

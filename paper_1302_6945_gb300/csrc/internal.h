@@ -177,6 +177,30 @@ struct Plan {
   tikh_stats last{};
 };
 
+// Device state of one displacement representation of (T^H T + lam I)^{-1} (tikh_inverse_*): the spectra
+// it is applied with and the workspace of one pass over up to R right-hand sides.
+struct InvWork {
+  int64_t m = 0, n = 0, N = 0;
+  int dtype = 0;
+  double lam = 0.0;
+  int R = 1;              // right-hand sides per pass
+  cd* spec = nullptr;     // [9][N]: F a, U_0..U_3, W_0..W_3 (sign +1 DFTs)
+  cd* gen = nullptr;      // [8][n]: u_0..u_3, w_0..w_3
+  cd* Ae = nullptr;       // [2][n]: A e_0, A f
+  void* rhs8 = nullptr;   // [8][n] the eight right-hand sides (plan dtype)
+  void* sol8 = nullptr;   // [8][n] their solutions (plan dtype)
+  cd* Y = nullptr;        // [max(R, 2)][N]
+  cd* C = nullptr;        // [4R][N]
+  cd* G = nullptr;        // [4R][N]
+  cd* tmp = nullptr;      // [max(4R, 8)][N] four-step temporary
+  cd *y = nullptr, *x = nullptr, *r = nullptr;  // [R][n]
+  cd* u = nullptr;        // [R][m]
+};
+int launch_inv_prepare(const FftPlan& F, InvWork& w, const void* col, const void* row, cudaStream_t s);
+int launch_inv_terms(const FftPlan& F, InvWork& w, cudaStream_t s);
+int launch_inv_apply(const FftPlan& F, InvWork& w, int nb, const void* b, int64_t b_stride, int normal, int refine,
+                     void* x, int64_t x_stride, cudaStream_t s);
+
 // launchers (return the number of kernels enqueued, or a negative TIKH_E* code)
 int launch_twiddle(cd* tab, int64_t L, cudaStream_t s);
 int launch_to_cf(const cd* in, cf* out, int64_t n, cudaStream_t s);

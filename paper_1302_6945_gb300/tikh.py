@@ -74,7 +74,8 @@ EXPORTED = ["tikh_plan_create", "tikh_solve", "tikh_solve_async", "tikh_solve_no
             "tikh_sync", "tikh_get_stats", "tikh_plan_destroy", "tikh_strerror", "tikh_test_fft", "tikh_test_leaf",
             "tikh_fft_noalloc", "tikh_set_profiling", "tikh_solve_grad", "tikh_get_difficult", "tikh_test_peak",
             "tikh_plan_create_general", "tikh_solve_general", "tikh_solve_general_normal",
-            "tikh_solve_general_strided", "tikh_test_scale"]
+            "tikh_solve_general_strided", "tikh_test_scale", "tikh_inverse_create", "tikh_inverse_apply",
+            "tikh_inverse_generators", "tikh_inverse_info", "tikh_inverse_destroy"]
 
 
 def lib():
@@ -121,6 +122,12 @@ def lib():
         L.tikh_fft_noalloc.argtypes = [i64, vp, ci, vp]
         L.tikh_test_peak.argtypes = [ci, ctypes.POINTER(dbl), vp]
         L.tikh_test_leaf.argtypes = [ci, vp, vp, vp, dbl, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.tikh_inverse_create.argtypes = [ctypes.POINTER(vp), vp, vp, vp, dbl, ci]
+        L.tikh_inverse_apply.argtypes = [vp, ci, vp, i64, vp, i64, ci, ci]
+        L.tikh_inverse_generators.argtypes = [vp, vp]
+        L.tikh_inverse_info.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+        L.tikh_inverse_destroy.argtypes = [vp]
+        L.tikh_inverse_destroy.restype = None
         _lib = L
     return _lib
 
@@ -295,6 +302,31 @@ def tikh_get_difficult(plan, cap=1 << 16):
 
 def tikh_plan_destroy(plan):
     lib().tikh_plan_destroy(plan)
+
+
+def tikh_inverse_create(plan, col, row, lam, max_rhs):
+    h = ctypes.c_void_p()
+    _check(lib().tikh_inverse_create(ctypes.byref(h), plan, col, row, float(lam), int(max_rhs)), "tikh_inverse_create")
+    return h
+
+
+def tikh_inverse_apply(inv, nrhs, b, b_stride, x, x_stride, normal, refine_steps):
+    _check(lib().tikh_inverse_apply(inv, int(nrhs), b, int(b_stride), x, int(x_stride), int(normal),
+                                    int(refine_steps)), "tikh_inverse_apply")
+
+
+def tikh_inverse_generators(inv, out):
+    _check(lib().tikh_inverse_generators(inv, out), "tikh_inverse_generators")
+
+
+def tikh_inverse_info(inv):
+    nl, nb = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().tikh_inverse_info(inv, ctypes.byref(nl), ctypes.byref(nb)), "tikh_inverse_info")
+    return {"kernel_launches": nl.value, "workspace_bytes": nb.value}
+
+
+def tikh_inverse_destroy(inv):
+    lib().tikh_inverse_destroy(inv)
 
 
 def tikh_set_profiling(plan, flags):
@@ -605,6 +637,52 @@ class GeneralPlan(Plan):
         tikh_solve_general_strided(self.h, B, p(col), st(col, self.m), p(row), st(row, self.n), p(lcol),
                                    st(lcol, self.pl), p(lrow), st(lrow, self.n), p(b), st(b, self.m), p(x), self.n)
         return x
+
+
+class Inverse:
+    """(T^H T + lam I)^{-1} of one T and lam as four Hankel-product pairs, from eight superfast solves on `plan`
+    (an l2 Plan with m >= n, which must stay open): every further right-hand side costs FFTs only."""
+
+    def __init__(self, plan, col, row, lam, max_rhs=8):
+        c, r, _ = plan._args(col, row, row, plan.n)
+        self.plan, self.m, self.n, self.dtype, self.max_rhs = plan, plan.m, plan.n, plan.dtype, int(max_rhs)
+        self.h = tikh_inverse_create(plan.h, c, r, lam, self.max_rhs)
+
+    def apply(self, b, normal=False, refine_steps=1, x=None):
+        """x for b of shape (R, m) or (m,) (normal: y of shape (R, n) or (n,)); R right-hand sides."""
+        import torch
+        ln = self.n if normal else self.m
+        if not (isinstance(b, torch.Tensor) and b.is_cuda and b.is_contiguous()):
+            raise TypeError("expected a contiguous CUDA tensor")
+        if _dtype_code(b) != self.dtype or b.shape[-1] != ln or b.dim() > 2:
+            raise ValueError("tensor dtype/shape does not match the plan")
+        R = b.shape[0] if b.dim() == 2 else 1
+        if x is None:
+            x = torch.empty(b.shape[:-1] + (self.n,), dtype=b.dtype, device=b.device)
+        tikh_inverse_apply(self.h, R, ctypes.c_void_p(b.data_ptr()), ln, ctypes.c_void_p(x.data_ptr()), self.n,
+                           1 if normal else 0, refine_steps)
+        return x
+
+    def generators(self):
+        """u_0..u_3, w_0..w_3 as an (8, n) complex128 tensor."""
+        import torch
+        out = torch.empty((8, self.n), dtype=torch.complex128, device="cuda")
+        tikh_inverse_generators(self.h, ctypes.c_void_p(out.data_ptr()))
+        return out
+
+    def info(self):
+        return tikh_inverse_info(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            tikh_inverse_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class BatchPlan:

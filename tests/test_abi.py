@@ -67,3 +67,19 @@ def test_general_solves_refuse_a_missing_plan():
         assert e.value.status == tikh.TIKH_EINVAL
     with pytest.raises(tikh.TikhError):
         tikh.tikh_solve_general_strided(None, 1, 1, 0, 1, 0, 1, 0, 1, 0, 1, 0, 1, 0)
+
+
+def test_inverse_entry_points_refuse_a_missing_handle():
+    # host checks before any device work: a null plan or handle is TIKH_EINVAL, destroy(NULL) is a no-op
+    from paper_1302_6945_gb300 import tikh
+    with pytest.raises(tikh.TikhError) as e:
+        tikh.tikh_inverse_create(None, 1, 1, 1.0, 4)
+    assert e.value.status == tikh.TIKH_EINVAL
+    with pytest.raises(tikh.TikhError) as e:
+        tikh.tikh_inverse_apply(None, 1, 1, 0, 1, 0, 0, 0)
+    assert e.value.status == tikh.TIKH_EINVAL
+    with pytest.raises(tikh.TikhError):
+        tikh.tikh_inverse_generators(None, 1)
+    with pytest.raises(tikh.TikhError):
+        tikh.tikh_inverse_info(None)
+    tikh.tikh_inverse_destroy(None)
